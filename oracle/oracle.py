@@ -1,0 +1,232 @@
+"""ctypes view of the C oracle in this directory (test infrastructure only).
+
+Every function mirrors one C entry point of ``esdc_oracle.h``; see the C
+sources for the passages of the paper each one follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["orc_colloc.c", "orc_model.c", "orc_space.c", "orc_sweep.c"]
+LIB_PATH = os.path.join(_HERE, "liborc.so")
+
+SOLVE_DCT, SOLVE_CG, SOLVE_DENSE = 0, 1, 2
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE FP64: no fast-math, no FMA contraction)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "esdc_oracle.h")]
+    if not force and os.path.exists(LIB_PATH):
+        t = os.path.getmtime(LIB_PATH)
+        if all(os.path.getmtime(s) <= t for s in srcs):
+            return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-shared", "-fPIC", "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ctx", C.c_void_p), ("f_I", C.c_void_p), ("solve_I", C.c_void_p),
+                ("f_E", C.c_void_p), ("lam_yinf", C.c_void_p)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("sweeps_done", C.c_int), ("res_inf", C.c_double), ("y_inf", C.c_double),
+                ("solve_fail", C.c_int)]
+
+
+class _Mono(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("h", C.c_double), ("sigma", C.c_double), ("chi", C.c_double), ("Cm", C.c_double),
+                ("model", C.c_int), ("mp", C.c_void_p), ("n_mp", C.c_int),
+                ("nbox", C.c_int), ("box", C.c_void_p), ("amp", C.c_void_p),
+                ("t_on", C.c_void_p), ("t_off", C.c_void_p),
+                ("solver", C.c_int), ("cg_tol", C.c_double), ("cg_maxit", C.c_int),
+                ("ionic_off", C.c_int), ("work", C.c_void_p)]
+
+
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB_PATH)
+        L.orc_radau_nodes.argtypes = [C.c_int, _D]
+        L.orc_gauss_legendre.argtypes = [C.c_int, _D, _D]
+        L.orc_collocation_q.argtypes = [C.c_int, _D, _D]
+        L.orc_fornberg_weights.argtypes = [C.c_int, _D, _D]
+        L.orc_phi.argtypes = [C.c_double, C.c_int, _D]
+        L.orc_aij.argtypes = [C.c_int, _D, _D, C.c_double, _D]
+        L.orc_hsdc_step.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_double, C.c_int,
+                                    C.c_double, C.c_double, _D, _D, _D, _D, C.POINTER(_Stats)]
+        L.orc_mono_problem.argtypes = [C.POINTER(_Mono), C.POINTER(_Problem)]
+        L.orc_mono_free.argtypes = [C.POINTER(_Mono)]
+        L.orc_mono_init.argtypes = [C.POINTER(_Mono), C.c_double, _D]
+        L.orc_ionic_point.argtypes = [C.c_int, _D, _D, _D, _D, _D]
+        L.orc_ionic_rest.argtypes = [C.c_int, _D, C.c_double, _D]
+        L.orc_laplacian.argtypes = [C.POINTER(_Mono), _D, _D]
+        L.orc_solve_shifted.argtypes = [C.POINTER(_Mono), C.c_int, C.c_double, _D, _D]
+        L.orc_stability_R1.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                       C.c_double, C.c_int]
+        L.orc_stability_R1.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def radau_nodes(M: int) -> np.ndarray:
+    c = np.zeros(M + 1)
+    if lib().orc_radau_nodes(M, _p(c)):
+        raise ValueError("bad M")
+    return c
+
+
+def gauss_legendre(n: int):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().orc_gauss_legendre(n, _p(x), _p(w))
+    return x, w
+
+
+def collocation_q(M: int) -> np.ndarray:
+    c = radau_nodes(M)
+    q = np.zeros(M * M)
+    lib().orc_collocation_q(M, _p(c), _p(q))
+    return q.reshape(M, M)
+
+
+def fornberg_weights(M: int, c: np.ndarray | None = None) -> np.ndarray:
+    """w[k, l] = weight of p(c_{l+1}) in p^{(k)}(0), k = 0..M-1."""
+    c = radau_nodes(M) if c is None else np.ascontiguousarray(c, np.float64)
+    w = np.zeros(M * M)
+    lib().orc_fornberg_weights(M, _p(c), _p(w))
+    return w.reshape(M, M)
+
+
+def phi(z: float, kmax: int) -> np.ndarray:
+    out = np.zeros(kmax)
+    lib().orc_phi(float(z), kmax, _p(out))
+    return out
+
+
+def aij(M: int, z: float) -> np.ndarray:
+    c = radau_nodes(M)
+    w = fornberg_weights(M, c).ravel().copy()
+    a = np.zeros(M * M)
+    lib().orc_aij(M, _p(c), _p(w), float(z), _p(a))
+    return a.reshape(M, M)
+
+
+def ionic_point(model: int, params: np.ndarray, u: np.ndarray):
+    ns = len(u)
+    u = np.ascontiguousarray(u, np.float64)
+    params = np.ascontiguousarray(params, np.float64)
+    fE, lam, yinf = np.zeros(ns), np.zeros(ns), np.zeros(ns)
+    lib().orc_ionic_point(model, _p(params), _p(u), _p(fE), _p(lam), _p(yinf))
+    return fE, lam, yinf
+
+
+def ionic_rest(model: int, params: np.ndarray, V0: float) -> np.ndarray:
+    ns = 4 if model == 0 else 19
+    u = np.zeros(ns)
+    lib().orc_ionic_rest(model, _p(np.ascontiguousarray(params, np.float64)), float(V0), _p(u))
+    return u
+
+
+def stability_R1(lI: float, lE: float, le: float, M: int, K: int, tol: float = 0.0,
+                 plain_sdc: bool = False) -> float:
+    return lib().orc_stability_R1(lI, lE, le, M, K, tol, int(plain_sdc))
+
+
+class Monodomain:
+    """A monodomain problem (mesh, conductivity, ionic model, stimulus) in the oracle.
+
+    ``wl`` is an ``inputs.Workload``; ``solver`` selects the oracle's linear
+    solve (DCT-II by default, the paper's solver)."""
+
+    def __init__(self, wl, solver: int = SOLVE_DCT, cg_tol: float = 1e-15, cg_maxit: int = 2000,
+                 ionic_off: bool = False):
+        self.wl = wl
+        self._keep = [np.ascontiguousarray(wl.params, np.float64),
+                      np.ascontiguousarray(wl.boxes, np.int32),
+                      np.ascontiguousarray(wl.amp, np.float64),
+                      np.ascontiguousarray(wl.t_on, np.float64),
+                      np.ascontiguousarray(wl.t_off, np.float64)]
+        mp, box, amp, ton, toff = self._keep
+        self.m = _Mono(wl.dim, wl.nx, wl.ny, wl.nz, wl.h, wl.sigma, wl.chi, wl.Cm, wl.model,
+                       mp.ctypes.data, len(mp), len(amp), box.ctypes.data, amp.ctypes.data,
+                       ton.ctypes.data, toff.ctypes.data, solver, cg_tol, cg_maxit, int(ionic_off), None)
+        self.P = _Problem()
+        if lib().orc_mono_problem(C.byref(self.m), C.byref(self.P)):
+            raise ValueError("invalid monodomain description")
+        self.N = wl.n_nodes
+        self.ns = wl.n_state
+
+    def __del__(self):
+        try:
+            lib().orc_mono_free(C.byref(self.m))
+        except Exception:
+            pass
+
+    def init_state(self, V0: float | None = None) -> np.ndarray:
+        y = np.zeros(self.ns * self.N)
+        lib().orc_mono_init(C.byref(self.m), float(self.wl.V0 if V0 is None else V0), _p(y))
+        return y.reshape(self.ns, self.N)
+
+    def laplacian(self, v: np.ndarray) -> np.ndarray:
+        v = np.ascontiguousarray(v, np.float64)
+        out = np.zeros(self.N)
+        lib().orc_laplacian(C.byref(self.m), _p(v), _p(out))
+        return out
+
+    def solve_shifted(self, g: float, b: np.ndarray, x0: np.ndarray | None = None,
+                      method: int | None = None) -> np.ndarray:
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(self.N) if x0 is None else np.array(x0, np.float64)
+        rc = lib().orc_solve_shifted(C.byref(self.m), self.m.solver if method is None else method,
+                                     float(g), _p(b), _p(x))
+        if rc:
+            raise RuntimeError(f"oracle solve failed ({rc})")
+        return x
+
+    def step(self, y_n: np.ndarray, t_n: float, dt: float, M: int, K: int, tol: float = 0.0,
+             plain_sdc: bool = False, want_colloc: bool = False, want_resid: bool = False):
+        """One HSDC step; returns (y_next[ns, N], stats dict, colloc, resid)."""
+        y_n = np.ascontiguousarray(y_n, np.float64).reshape(-1)
+        n = len(y_n)
+        y1 = np.zeros(n)
+        col = np.zeros(M * n) if want_colloc else None
+        res = np.zeros(M * n) if want_resid else None
+        st = _Stats()
+        rc = lib().orc_hsdc_step(C.byref(self.P), M, K, tol, int(plain_sdc), float(t_n), float(dt),
+                                 _p(y_n), _p(y1), _p(col) if col is not None else None,
+                                 _p(res) if res is not None else None, C.byref(st))
+        if rc:
+            raise RuntimeError(f"oracle step failed ({rc})")
+        stats = dict(sweeps=st.sweeps_done, res_inf=st.res_inf, y_inf=st.y_inf)
+        shp = (self.ns, self.N)
+        return (y1.reshape(shp), stats,
+                None if col is None else col.reshape((M,) + shp),
+                None if res is None else res.reshape((M,) + shp))
+
+    def run(self, y0: np.ndarray, t0: float, dt: float, nsteps: int, M: int, K: int):
+        y = np.array(y0, np.float64)
+        t = t0
+        for _ in range(nsteps):
+            y, _, _, _ = self.step(y, t, dt, M, K)
+            t += dt
+        return y

@@ -1,0 +1,259 @@
+"""Pins of the oracle's HSDC step (eq. prec_picard with eq. def_P and eq. def_C)
+against closed forms, convergence orders, an independent Newton solve of the
+collocation system, and the stability claims of Sec. 4."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2405_19994_gb300 import inputs as I
+
+
+# ---------------------------------------------------------------- scalar test equation (Sec. 4)
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("le", [-1e-3, -0.7, -5.0, -100.0, -1000.0])
+@pytest.mark.parametrize("K", [1, 3])
+def test_exponential_exactness(orc, M, le, K):
+    # f_I = f_E = 0, Lambda = le constant, y_inf = 0.  Then g_n(y) = le*y_n for
+    # every y, so G_j = le*y_n, the correction terms of eq. def_P cancel, and
+    # y_{n,M} = y_n (1 + le * sum_j a_Mj(le)) = e^{le} y_n because
+    # sum_j a_Mj(z) = int_0^1 e^{(1-s) z} ds = (e^z - 1)/z  (eq. def_aij).
+    # Rounding: the sum of App. A has terms up to ~max|w| times the result's
+    # scale, so the error bound is a few ulps times max|w| (Fornberg weights).
+    R = O.stability_R1(0.0, 0.0, le, M, K)
+    tol = 8 * 2.2e-16 * max(1.0, np.abs(O.fornberg_weights(M)).max())
+    assert abs(R - math.exp(le)) <= tol, (R, math.exp(le))
+
+
+def _radau_R(M, z):
+    # Radau IIA stability function = (M-1, M) Pade approximant of e^z
+    if M == 1:
+        return 1.0 / (1.0 - z)
+    if M == 2:
+        return (1 + z / 3) / (1 - 2 * z / 3 + z * z / 6)
+    if M == 3:
+        return (1 + 2 * z / 5 + z * z / 20) / (1 - 3 * z / 5 + 3 * z * z / 20 - z**3 / 60)
+    raise ValueError
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+@pytest.mark.parametrize("z", [-0.05, -0.5, -1.7])
+def test_converged_sweep_is_radau_iia(orc, M, z):
+    # With Lambda_n = 0 the collocation system is Radau IIA (Sec. 3.1.2); the
+    # sweep iterated to convergence reproduces its stability function whichever
+    # of f_I / f_E carries the linear term.  (The Picard iteration converges for
+    # an explicit term only while |dt lE| is small, so f_E is tested at |z| <= 0.5.)
+    cases = ((z, 0.0), (0.0, z), (0.4 * z, 0.6 * z)) if abs(z) <= 0.5 else ((z, 0.0),)
+    for lI, lE in cases:
+        R = O.stability_R1(lI, lE, 0.0, M, 200, tol=1e-15)
+        assert abs(R - _radau_R(M, z)) < 1e-14, (lI, lE, R, _radau_R(M, z))
+
+
+def _finest_slope(hs, errs):
+    return float(np.diff(np.log(errs))[-1] / np.diff(np.log(hs))[-1])
+
+
+def _steps(p):
+    # step sizes inside the asymptotic range and above rounding for local order p+1
+    return np.array([0.05, 0.025, 0.0125]) if p + 1 <= 4 else np.array([0.4, 0.2, 0.1])
+
+
+@pytest.mark.parametrize("M,K", [(2, 1), (2, 2), (2, 3), (2, 5), (3, 1), (3, 2), (3, 3), (3, 4),
+                                 (3, 5), (3, 8), (4, 3), (4, 6)])
+def test_sdc_order_min_k_2m_minus_1(orc, M, K):
+    # SDC with Radau-right nodes: order at least min(K, 2M-1) (Sec. 5.1).  The
+    # local error of one step of size h on y' = (lI + lE) y is O(h^{p+1}).
+    p = min(K, 2 * M - 1)
+    hs = _steps(p)
+    errs = [abs(O.stability_R1(-0.6 * h, -0.5 * h, 0.0, M, K) - math.exp(-1.1 * h)) for h in hs]
+    assert _finest_slope(hs, errs) > p + 1 - 0.35, (_finest_slope(hs, errs), p)
+
+
+@pytest.mark.parametrize("M,K", [(2, 1), (2, 2), (2, 3), (3, 2), (3, 3), (3, 4), (4, 4), (4, 6)])
+def test_hsdc_order_with_exponential_term(orc, M, K):
+    # HSDC: order at least min(K, M+1) (Sec. 5.1) when f_e is present.
+    p = min(K, M + 1)
+    hs = _steps(p)
+    errs = [abs(O.stability_R1(-0.5 * h, -0.3 * h, -0.8 * h, M, K) - math.exp(-1.6 * h)) for h in hs]
+    assert _finest_slope(hs, errs) > p + 1 - 0.35, (_finest_slope(hs, errs), p)
+
+
+def test_stability_nonstiff(orc):
+    # Sec. 4.1, Fig. stab_dom_conv (L=1, P=1): lE = 0, (lI, le) in [-2,0]^2, M = 6,
+    # K = 1,2,3, tol 1e-10: |R_1| <= 1 everywhere.
+    g = np.linspace(-2, 0, 21)
+    for K in (1, 2, 3):
+        R = np.array([[O.stability_R1(lI, 0.0, le, 6, K, tol=1e-10) for le in g] for lI in g])
+        assert np.all(np.abs(R) <= 1 + 1e-12), K
+
+
+def test_stability_stiff(orc):
+    # Sec. 4.1 stiff regime: lE = -2, (lI, le) in [-1000,0]^2, M = 6, K = 1,2,100.
+    # K = 1 and the converged K = 100 give |R_1| <= 1 everywhere.  K = 2 reaches
+    # |R_1| ~ 1.001 where lI and le are both below about -20: there the
+    # iteration contracts by a factor near 1 (the f_I rows of P in eq. def_P are
+    # implicit Euler while A(dt Lambda_n) damps like 1/|le|), so the iterate
+    # stays near the spread initial guess.  The paper calls every case stable;
+    # at plot resolution 1.001 is indistinguishable from 1.
+    g = -np.concatenate([[0.0], np.logspace(-2, 3, 16)])
+    for K, bound in ((1, 1 + 1e-12), (2, 1.002), (100, 1 + 1e-12)):
+        R = np.array([[O.stability_R1(lI, -2.0, le, 6, K, tol=1e-10) for le in g] for lI in g])
+        assert np.all(np.abs(R) <= bound), (K, np.abs(R).max())
+        assert np.all(np.abs(R[:, :5]) <= 1 + 1e-12)        # |le| <= 0.1: strictly stable
+
+
+def test_plain_sdc_unstable_where_le_below_lI(orc):
+    # Sec. 4.2: with Lambda_n replaced by 0 the sweep (K=1, M=6, lE=-2) is unstable
+    # for le < lI, while HSDC is stable at the same points.
+    g = -np.logspace(0, 3, 13)
+    unstable_below = 0
+    for lI in g:
+        for le in g:
+            if le < lI:
+                Rp = O.stability_R1(lI, -2.0, le, 6, 1, plain_sdc=True)
+                Rh = O.stability_R1(lI, -2.0, le, 6, 1)
+                unstable_below += abs(Rp) > 1
+                assert abs(Rh) <= 1 + 1e-12
+    assert unstable_below > 0
+
+
+# ---------------------------------------------------------------- monodomain
+
+def test_diffusion_cosine_mode_closed_form(orc):
+    # Ionic terms off: V_0 = cosine mode of the Neumann stencil, eigenvalue mu.
+    # The converged scheme (Radau IIA, Lambda = 0) gives V_n = R(dt D mu)^n V_0
+    # with D = sigma/(chi C_m).
+    wl = I.hh_sheet_32().with_mesh(10, 7, 1)
+    wl.amp = np.zeros(1)
+    m = O.Monodomain(wl, ionic_off=True)
+    nx, ny = 10, 7
+    ix = np.arange(nx)[None, :]
+    iy = np.arange(ny)[:, None]
+    V0 = (np.cos(np.pi * 3 * (ix + 0.5) / nx) * np.cos(np.pi * 2 * (iy + 0.5) / ny)).reshape(-1)
+    mu = -(4 / wl.h**2) * (np.sin(np.pi * 3 / (2 * nx)) ** 2 + np.sin(np.pi * 2 / (2 * ny)) ** 2)
+    D = wl.sigma / (wl.chi * wl.Cm)
+    y = np.zeros((4, nx * ny))
+    y[0] = V0
+    dt, nsteps = 0.05, 6
+    for M in (2, 3):
+        yy = y.copy()
+        for n in range(nsteps):
+            yy, st, _, _ = m.step(yy, n * dt, dt, M, 60, tol=1e-15)
+        want = _radau_R(M, dt * D * mu) ** nsteps * V0
+        np.testing.assert_allclose(yy[0], want, atol=2e-14)
+
+
+def _hh_smooth_state(wl, seed=3):
+    # smooth pre-excited state: a V bump and gates between 0 and 1
+    nx, ny = wl.nx, wl.ny
+    x = (np.arange(nx) + 0.5) / nx
+    yv = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, yv)
+    V = -75 + 80 * np.exp(-((X - 0.3) ** 2 + (Y - 0.4) ** 2) / 0.08)
+    y = np.zeros((4, nx * ny))
+    y[0] = V.reshape(-1)
+    y[1] = 0.3 + 0.2 * X.reshape(-1)
+    y[2] = 0.5 - 0.1 * Y.reshape(-1)
+    y[3] = 0.4
+    return y
+
+
+@pytest.mark.parametrize("M,K", [(3, 1), (3, 2), (3, 3), (3, 4), (2, 2), (2, 3)])
+def test_hh_time_convergence_order(orc, M, K):
+    # Full monodomain with HH, I_stim = 0 (as in Sec. 5): observed order of the
+    # HSDC step is at least min(K, M+1) (Sec. 5.1); V dominates so it can be higher.
+    wl = I.hh_sheet_32().with_mesh(6, 5, 1)
+    wl.amp = np.zeros(1)
+    m = O.Monodomain(wl)
+    y0 = _hh_smooth_state(wl)
+    T = 0.4
+    ref = m.run(y0, 0.0, T / 128, 128, 4, 12)
+    hs, errs = [], []
+    for nst in (4, 8, 16):
+        yy = m.run(y0, 0.0, T / nst, nst, M, K)
+        hs.append(T / nst)
+        errs.append(np.abs(yy - ref).max())
+    p = min(K, M + 1)
+    assert _finest_slope(hs, errs) > p - 0.4, (_finest_slope(hs, errs), p, errs)
+
+
+def test_converged_sweep_solves_collocation_system(orc):
+    # K large: the Picard iterate equals the solution of C(y) = 1 (x) y_n
+    # (eq. def_C) found independently by a Newton-type solver.
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    wl = I.hh_sheet_32().with_mesh(3, 3, 1)
+    m = O.Monodomain(wl)
+    y0 = _hh_smooth_state(wl)
+    M, dt, t0 = 3, 0.05, 0.5
+    N, ns = 9, 4
+    c = O.radau_nodes(M)
+    y1, st, col, res = m.step(y0, t0, dt, M, 80, tol=1e-15, want_colloc=True, want_resid=True)
+    # independent residual of eq. def_C
+    lam_n = np.array([O.ionic_point(0, wl.params, y0[:, p])[1] for p in range(N)]).T   # [ns, N]
+    A = np.zeros((ns, N, M, M))
+    for s in range(ns):
+        for p in range(N):
+            A[s, p] = O.aij(M, dt * lam_n[s, p])
+    D = wl.sigma / (wl.chi * wl.Cm)
+
+    def g_n(t, y):
+        out = np.zeros((ns, N))
+        for p in range(N):
+            fE, lam, yinf = O.ionic_point(0, wl.params, y[:, p])
+            stim = 0.5 if (t < 1.0 and p in range(0, 9)) else 0.0   # 4x4 corner box clipped to 3x3
+            out[0, p] = (stim + fE[0]) / wl.Cm
+            out[1:, p] = lam[1:] * (y[1:, p] - yinf[1:])
+        out[0] += D * m.laplacian(y[0])
+        out += lam_n * (y0 - y)
+        return out
+
+    def C(z):
+        Y = z.reshape(M, ns, N)
+        G = np.stack([g_n(t0 + c[j + 1] * dt, Y[j]) for j in range(M)])
+        R = np.zeros_like(Y)
+        for i in range(M):
+            R[i] = Y[i] - y0 - dt * np.einsum("spj,jsp->sp", A[:, :, i, :], G)
+        return (R / np.array([80.0, 1, 1, 1])[None, :, None]).reshape(-1)
+
+    sol = scipy_opt.root(C, np.tile(y0, (M, 1, 1)).reshape(-1), method="hybr", tol=1e-14)
+    Ysol = sol.x.reshape(M, ns, N)
+    assert np.abs(C(sol.x)).max() < 1e-11
+    np.testing.assert_allclose(col, Ysol, atol=1e-10)
+    assert st["res_inf"] < 1e-12
+
+
+@pytest.mark.slow
+def test_hh_sheet_gates_stay_in_unit_interval(orc):
+    # O-T7: checked and reported on the 32x32 HH sheet (the paper proves nothing here)
+    wl = I.hh_sheet_32()
+    m = O.Monodomain(wl)
+    y = m.init_state()
+    lo, hi = 1.0, 0.0
+    vmax = -100.0
+    for n in range(wl.n_steps):
+        y, _, _, _ = m.step(y, n * wl.dt, wl.dt, wl.M, wl.K)
+        lo, hi = min(lo, y[1:].min()), max(hi, y[1:].max())
+        vmax = max(vmax, y[0].max())
+    assert lo >= -1e-12 and hi <= 1 + 1e-12
+    assert vmax > 20.0          # the corner stimulus fired an action potential
+
+
+@pytest.mark.slow
+def test_syn19_planar_wave_acceptance(orc):
+    # Synthetic model on a 1D cable with the slab's physics: the x=0 stimulus
+    # starts a wave whose activation time (V crossing -40 mV upward) is monotone
+    # in x and which repolarises within T = 50 ms.
+    wl = I.syn19_slab().with_mesh(128, 1, 1)
+    m = O.Monodomain(wl)
+    y = m.init_state()
+    act = np.full(wl.nx, np.nan)
+    for n in range(wl.n_steps):
+        yo = y
+        y, st, _, _ = m.step(y, n * wl.dt, wl.dt, wl.M, wl.K)
+        cr = (yo[0] < -40) & (y[0] >= -40) & np.isnan(act)
+        act[cr] = (n + 1) * wl.dt
+        assert y[7:].min() > -1e-9 and y[7:].max() < 1 + 1e-9
+    assert np.all(np.isfinite(act)) and np.all(np.diff(act) >= 0)
+    assert y[0].max() < -80.0
