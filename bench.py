@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""ES-SDC (HSDC) benchmark on one GB300.
+
+Workload (the headline configuration): 128x128x32 slab (524,288 nodes),
+h = 0.2 mm, seeded 19-state synthetic stiff ionic model, planar stimulus at
+x = 0 for t < 1 ms, M = 4 Radau IIA nodes, K = 6 sweeps, dt = 0.05 ms, FP64.
+A bench "step" is one HSDC time step: set-up, K sweeps over the M nodes (fused
+ionic/quadrature kernel + CG diffusion solve each) and the collocation residual.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is node-updates/s (one mesh node advanced by
+one dt), device-timed with CUDA events over K steps after W warm-up steps from
+rest (t = 0 is the stimulus onset, so the timed window follows the stimulus).
+``--impl reference`` times the FP64 CPU oracle on this host instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ES-SDC node-updates/s and s per simulated ms at stated V-error; % roofline"
+UNIT = "node-updates/s"
+
+# Algorithmic work per unit, used for the roofline of the dominant kernel.
+#  node kernel (one collocation node of one sweep, per mesh node), SYN19, M = 4:
+#    reads y_{i-1} (19), G^k_{1..M} (76), FI (2), Lambda_n (12), y_n gates (12),
+#    S row (48), phi_1 row (12); writes G_{i-1} (19), FI (1), y_i (18), rhs (1)
+#    -> 220 doubles = 1760 B.
+#  cg (per mesh node and iteration): p, q (A p); r, q, x, p -> x, r, z; z, p -> p
+#    -> 11 doubles = 88 B, plus one set-up pass of 7 doubles = 56 B per solve.
+NODE_BYTES_PER_NODE = {4: 1760}
+CG_BYTES_PER_NODE_ITER = 88
+CG_BYTES_PER_NODE_SETUP = 56
+
+
+def _peaks():
+    p = {"hbm_gbs": None, "source": None}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        p["hbm_gbs"] = d.get("hbm_gbs")
+        p["source"] = "measured"
+    if not p["hbm_gbs"]:
+        p["hbm_gbs"], p["source"] = 6800.0, "fallback"
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region (200 ms period)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on this host's cores.  Each step is a
+    bounded sample of the workload: one HSDC step of the 128x128x2 sub-slab
+    (32,768 nodes, the same per-node work)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.syn19_slab()
+    sub = wl.with_mesh(wl.nx, wl.ny, 2)
+    m = oracle.Monodomain(sub)
+    y = m.init_state()
+    t = 0.0
+    for n in range(args.warmup):
+        y, _, _, _ = m.step(y, t, wl.dt, wl.M, wl.K)
+        t += wl.dt
+    t0 = time.perf_counter()
+    for n in range(args.steps):
+        y, _, _, _ = m.step(y, t, wl.dt, wl.M, wl.K)
+        t += wl.dt
+    el = time.perf_counter() - t0
+    value = sub.n_nodes * args.steps / el
+    cores = oracle.oracle.threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "sample": "128x128x2 sub-slab (32768 nodes)", "M": wl.M,
+                   "K": wl.K, "dt_ms": wl.dt, "model": "syn19 (seed 20240530)"},
+        "s_per_sim_ms": (el / args.steps) / wl.dt * (wl.n_nodes / sub.n_nodes),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "HSDC steps of the 128x128x2 sub-slab of the workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    wl = I.syn19_slab()
+    if args.nz != wl.nz:                     # smaller slab for profiler captures
+        wl = wl.with_mesh(wl.nx, wl.ny, args.nz)
+    M, K, dt = wl.M, wl.K, wl.dt
+    N = wl.n_nodes
+    solver = P.Solver.from_workload(wl, M_max=M)
+    y = solver.new_state()
+    solver.init_state(y, wl.V0)
+    stream = torch.cuda.current_stream()
+    t = 0.0
+    for _ in range(args.warmup):
+        solver.sweep(y, t, dt, M, K)
+        t += dt
+    rc = solver.residual()[0]
+    if rc != 0:
+        raise RuntimeError(f"warm-up step failed with code {rc}")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    solver.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.sweep(y, t, dt, M, K)
+        t += dt
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = solver.profile_read()
+    solver.profile(False)
+    clk = clocks.stop()
+    rc, res_inf, y_inf, _ = solver.residual()
+    cg_iters = solver.stats(K * M).tolist()
+    if rc != 0:
+        raise RuntimeError(f"timed step failed with code {rc}")
+    if pg:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = N * args.steps * ws / (ms * 1e-3)
+    ms_step = ms / args.steps
+
+    # ---- end to end: the same steps through the host-buffer entry point (H2D + step + D2H)
+    ns, ld = solver.n_state, solver.ld
+    y_host = torch.empty((ns, ld), dtype=torch.float64, pin_memory=True)
+    y_host.copy_(y)
+    torch.cuda.synchronize()
+    n_e2e = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        solver.sweep_host(y_host, t, dt, M, K)
+        t += dt
+    e2e_s = time.perf_counter() - t0
+    e2e_value = N * n_e2e * ws / e2e_s
+    y.copy_(y_host.cuda())
+
+    # ---- roofline of the dominant kernel class
+    peaks = _peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
+    roof = {"kernel": dom, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+            "peak_source": peaks["source"], "traffic": None}
+    if dom == "node":
+        bytes_launch = NODE_BYTES_PER_NODE.get(M, 1760) * N
+    elif dom == "cg":
+        it_mean = sum(cg_iters) / max(len(cg_iters), 1)
+        bytes_launch = (CG_BYTES_PER_NODE_ITER * it_mean + CG_BYTES_PER_NODE_SETUP) * N
+    else:
+        bytes_launch = None
+    if bytes_launch and per_launch_ms[dom]:
+        ach = bytes_launch / (per_launch_ms[dom] * 1e-3) / 1e9
+        roof.update({"achieved": ach, "frac": ach / roof["peak"]})
+    else:
+        roof.update({"achieved": None, "frac": None})
+
+    # ---- CPU oracle baseline on one full-size step from the live state (rank 0, N = 1)
+    cpu = None
+    verr = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        yh = y[:, :N].cpu().numpy().copy()
+        ycopy = y.clone()
+        solver.sweep(ycopy, t, dt, M, K)
+        g1 = ycopy[:, :N].cpu().numpy()
+        m = oracle.Monodomain(wl)
+        c0 = time.perf_counter()
+        want, _, _, _ = m.step(yh, t, dt, M, K)
+        cel = time.perf_counter() - c0
+        cpu = {"value": N / cel, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
+               "sample": f"one HSDC step of the full {wl.nx}x{wl.ny}x{wl.nz} slab at t={t:.2f} ms"}
+        verr = {"V_max_rel_vs_oracle_one_step": float(np.abs(g1[0] - want[0]).max() / np.abs(want[0]).max()),
+                "state_max_abs_vs_oracle_one_step": float(np.abs(g1 - want).max())}
+
+    launches = int(sum(v[1] for v in prof.values()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": N, "n_state": wl.n_state, "M": M, "K": K, "dt_ms": dt,
+                   "model": "syn19 (seed 20240530)", "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (state + workspace ~2 GB per GPU)",
+                   "window_ms": [args.warmup * dt, (args.warmup + args.steps) * dt]},
+        "s_per_sim_ms": ms_step * 1e-3 / dt,
+        "v_error": verr,
+        "residual": {"res_inf": res_inf, "y_inf": y_inf},
+        "cg_iters_last_step": cg_iters,
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "kernel_launches": {k: v[1] for k, v in prof.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "steps": n_e2e,
+                "h2d_bytes_per_step": ns * N * 8, "d2h_bytes_per_step": ns * N * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nz", type=int, default=32, help="slab depth (32 = the benchmark workload)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * esdc.h -- C ABI of the GB300 (sm_103a) HSDC / ES-SDC library for the
+ * semi-discrete monodomain equation
+ *
+ *     y' = f_I(t,y) + f_E(t,y) + f_e(t,y),   f_e = Lambda(y) (y - y_inf(y))
+ *
+ * (arXiv 2405.19994, Sec. 1 eq. (1) and Sec. 2.2 eqs. (sd_sys), (def_f_IE),
+ * (def_Lambda)).  One call of esdc_sweep advances one time step with the
+ * hybrid SDC method: K sweeps of the preconditioned Picard iteration
+ * P(y^{k+1}) = (P - C)(y^k) + 1 (x) y_n (Sec. 3.1.3, eq. (prec_picard)) with
+ * the IMEX Rush-Larsen preconditioner P of eq. (def_P) and the exponential
+ * collocation operator C of eq. (def_C), on M Radau IIA nodes.
+ *
+ * Conventions for every entry point:
+ *   - Return value: ESDC_OK (0) on success, a negative ESDC_ERR_* code on
+ *     failure.  No C++ exception crosses the ABI.  After a failure,
+ *     esdc_last_error() returns a one-line description owned by the handle.
+ *   - "device" pointers are CUDA device pointers on the device that was current
+ *     when esdc_create was called; "host" pointers are ordinary CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it in order; calls that return data
+ *     to host memory synchronise that stream before returning.
+ *   - The caller owns every buffer it passes.  The handle owns its workspace,
+ *     allocated once in esdc_create (sized for M <= options.M_max) and freed in
+ *     esdc_destroy.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - State layout ("SoA"): y[s * ld + p] holds state s (0 = V_m [mV], then the
+ *     m_1 auxiliary variables, then the m_2 gating variables) at mesh node
+ *     p = ix + nx*(iy + ny*iz).  ld >= n_nodes is the row pitch returned by
+ *     esdc_state_size (a multiple of 32 doubles); columns p >= n_nodes are
+ *     ignored and left unchanged.
+ *   - Units: mm, ms, mV, mS/mm (sigma), 1/mm (chi), uF/mm^2 (C_m), uA/mm^2.
+ */
+#ifndef ESDC_H
+#define ESDC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESDC_OK                     0
+#define ESDC_ERR_INVALID_ARG       -1   /* a null pointer, size or value out of range */
+#define ESDC_ERR_CUDA              -2   /* a CUDA runtime call failed                  */
+#define ESDC_ERR_CG_NOT_CONVERGED  -3   /* a diffusion solve hit cg_maxit              */
+#define ESDC_ERR_NONFINITE         -4   /* NaN/Inf in the residual or the state        */
+#define ESDC_ERR_DEVICE_TIMEOUT    -5   /* a bounded device-side wait gave up          */
+#define ESDC_ERR_UNSUPPORTED       -6   /* valid but not implemented combination       */
+#define ESDC_ERR_NO_MEMORY         -7   /* device allocation failed                    */
+
+/* Ionic models (Sec. 5).  Parameters are passed explicitly to esdc_create:
+ *  ESDC_MODEL_HH1952: Hodgkin-Huxley 1952, states (V, m, h, n) (m_1 = 0,
+ *    m_2 = 3), 7 parameters [gNa, gK, gL, ENa, EK, EL, Vrest] (mS/mm^2, mV).
+ *  ESDC_MODEL_SYN19: 19-state synthetic stiff model with the shape of ten
+ *    Tusscher-Panfilov 2006 (m_1 = 6, m_2 = 12), 88 parameters: 12 gates x
+ *    (Vh, k, r, ln rho, Vr, sr), then [G_f, E_f, G_s, E_s, G_K, E_K, G_K1,
+ *    G_b, E_b, c_K6], then tau_1..tau_6. */
+#define ESDC_MODEL_HH1952 0
+#define ESDC_MODEL_SYN19  1
+
+typedef struct esdc_handle esdc_handle;
+
+/* Uniform cell-centred mesh of the rectangle/box Omega (Sec. 2.2, Sec. 5):
+ * dim in {1,2,3}; extents nx, ny, nz >= 1 (ny = nz = 1 in 1D, nz = 1 in 2D);
+ * h > 0 the mesh size.  A = sigma * L with L the 3/5/7-point Laplacian with
+ * mirrored ghost nodes (zero normal flux, the boundary condition of
+ * eq. (monodomain)). */
+typedef struct {
+    int    dim;
+    int    nx, ny, nz;
+    double h;
+} esdc_mesh;
+
+typedef struct {
+    int    M_max;      /* largest M that esdc_sweep will be called with, 1..8      */
+    double tol_cg;     /* relative 2-norm stop ||r|| <= tol_cg ||b|| of each solve */
+    int    cg_maxit;   /* iteration cap of each solve (>= 1)                       */
+    int    precond;    /* 1 = Jacobi-preconditioned CG, 0 = plain CG               */
+} esdc_options;
+
+/* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1. */
+void esdc_default_options(esdc_options* opt);
+
+/*
+ * Creates a solver for the semi-discrete monodomain equation eq. (sd_sys) on
+ * `mesh` with conductivity `sigma`, surface-to-volume ratio `chi` and membrane
+ * capacitance `Cm` (eq. (monodomain)), and the ionic model `model` with
+ * `n_params` host doubles `params` (copied).  `opt` may be NULL for defaults.
+ * Allocates all device workspace on the current device.
+ * Errors: INVALID_ARG (bad sizes/values/model/param count), NO_MEMORY, CUDA.
+ * On failure *out is set to NULL.
+ */
+int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm,
+                int model, const double* params, int n_params,
+                const esdc_options* opt, esdc_handle** out);
+
+/* Frees the handle and its device workspace (NULL is a no-op). */
+void esdc_destroy(esdc_handle* h);
+
+/* One-line description of the last error on this handle ("" if none). */
+const char* esdc_last_error(const esdc_handle* h);
+
+/*
+ * Stimulus I_stim(t, x) of eq. (monodomain): a sum of boxes.  Box b adds
+ * amp[b] uA/mm^2 at nodes ix in [box[6b], box[6b+1]), iy in [box[6b+2],
+ * box[6b+3]), iz in [box[6b+4], box[6b+5]) while t_on[b] <= t < t_off[b].
+ * All arrays are host memory, copied.  nbox = 0 removes the stimulus.
+ * At most 16 boxes.  Errors: INVALID_ARG.
+ */
+int esdc_set_stimulus(esdc_handle* h, int nbox, const int* box, const double* amp,
+                      const double* t_on, const double* t_off);
+
+/* Reports the number of states per node (1 + m_1 + m_2), the number of mesh
+ * nodes and the row pitch ld (in doubles) of a state buffer. */
+int esdc_state_size(const esdc_handle* h, int* n_state, int64_t* n_nodes, int64_t* ld);
+
+/*
+ * Writes a resting state into the device buffer y [n_state][ld]: V = V0,
+ * gates at w_inf(V0) (eq. monodomain_g_lambda), auxiliaries at the model's
+ * V0 steady state.  Enqueued on `stream`.
+ */
+int esdc_init_state(esdc_handle* h, double* y, double V0, void* stream);
+
+/*
+ * One HSDC time step [t, t + dt] (Sec. 3.1): y (device [n_state][ld]) holds
+ * y_n on entry and y_{n+1} = y_{n,M}^K on return (eq. (sys_erk_aij), c_M = 1).
+ *   Lambda_n = Lambda(y_n) is frozen for the step (eq. (def_ode_esdc));
+ *   the gate coefficients a_ij(dt Lambda_n) follow App. A eq.
+ *   (def_aij_computable); y^0 = 1 (x) y_n; each sweep visits the nodes
+ *   i = 1..M in order and solves (I - dt d_i (chi C_m)^{-1} A) V_i = rhs with
+ *   preconditioned CG (the implicit f_I row of P); K >= 0 sweeps are taken.
+ * After the sweeps the residual r_i = y_n + dt sum_j a_ij G_j - y_i of
+ * eq. (def_C) is formed on the device (see esdc_residual).
+ * 1 <= M <= M_max, dt > 0.  Work is enqueued on `stream`; the call does not
+ * synchronise.  Errors: INVALID_ARG, CUDA.  Convergence failures of the
+ * solves are recorded on the device and reported by esdc_residual/esdc_stats.
+ */
+int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, void* stream);
+
+/*
+ * Same step with y in HOST memory (pitch ld_host >= n_nodes, layout as
+ * above): copies y to the device, steps, and copies y_{n+1} back, all on
+ * `stream`, then synchronises it.  For callers that keep the state on the host.
+ */
+int esdc_sweep_host(esdc_handle* h, double* y_host, int64_t ld_host, double t, double dt,
+                    int M, int K, void* stream);
+
+/*
+ * Residual of the most recent esdc_sweep (Algorithm 1 stop test, Sec. 3.2):
+ * res_inf = max_{i,s,p} |r_i|, y_inf = max over y_n and y_1..y_M of |y|
+ * (the paper leaves the norm unnamed; this library uses the max norm).
+ * res_state (host, optional, length n_state) receives the per-state maxima.
+ * Synchronises the stream of that sweep.  Returns ESDC_ERR_NONFINITE if the
+ * residual or the state is not finite, ESDC_ERR_CG_NOT_CONVERGED if a solve of
+ * that step hit cg_maxit (the values are still written).
+ */
+int esdc_residual(esdc_handle* h, double* res_inf, double* y_inf, double* res_state);
+
+/*
+ * Iteration counts of the diffusion solves of the most recent esdc_sweep:
+ * cg_iters (host, length >= K*M) receives the count of solve (k, i) at
+ * index k*M + (i-1).  n = length of cg_iters.  Synchronises that stream.
+ */
+int esdc_stats(esdc_handle* h, int* cg_iters, int n);
+
+/*
+ * Copies the collocation iterate y_{n,1..M}^K of the most recent esdc_sweep
+ * (device [M][n_state][ld]) and, if r_out != NULL, the residual vectors
+ * r_1..r_M of eq. (def_C) (device [M][n_state][ld]; requires
+ * esdc_keep_residual(h, 1) before that sweep) into caller buffers.
+ */
+int esdc_collocation(esdc_handle* h, double* y_out, double* r_out, void* stream);
+
+/*
+ * Kernel timing.  enable != 0 makes every later esdc_sweep record a CUDA event
+ * pair on its stream around each launch of the four kernel classes of the step:
+ * 0 = step set-up (Lambda_n, a_ij(dt Lambda_n), spread), 1 = sweep node kernel
+ * (ionic model + quadrature), 2 = diffusion solve (CG), 3 = residual.
+ * esdc_profile_read returns, per class, the summed milliseconds ms[4] and the
+ * number of launches launches[4] since the last read, then resets them; it
+ * synchronises the recorded events.  Not part of the method; no effect on results.
+ */
+int esdc_profile(esdc_handle* h, int enable);
+int esdc_profile_read(esdc_handle* h, double* ms, long long* launches);
+
+/*
+ * keep != 0 makes every later esdc_sweep also store the residual vectors
+ * r_1..r_M (allocates M_max*n_state*ld doubles); keep = 0 frees them.
+ */
+int esdc_keep_residual(esdc_handle* h, int keep);
+
+/*
+ * Exponential collocation coefficients (App. A eq. (def_aij_computable)):
+ * for n values z (device), writes a[(i*M + j)*n + e] = a_{i+1,j+1}(z[e])
+ * (device [M*M][n]) for the M Radau IIA nodes.  Enqueued on `stream`.
+ */
+int esdc_coefficients(esdc_handle* h, const double* z, int64_t n, int M, double* a, void* stream);
+
+/*
+ * Diffusion solve (I - g L) x = b on the handle's mesh (the implicit step of
+ * eq. (def_P) with g = dt d_i sigma/(chi C_m)): b, x device [n_nodes]; x holds
+ * the initial guess on entry and the solution on return.  iters (host,
+ * optional) receives the iteration count; synchronises `stream`.  Returns
+ * ESDC_ERR_CG_NOT_CONVERGED if cg_maxit was reached.
+ */
+int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, int* iters,
+                         void* stream);
+
+/*
+ * Pointwise ionic model at every node of y (device [n_state][ld]): writes
+ * fE = (-I_ion, h_a, 0), lam = (0, 0, Lambda_g(V)), yinf = (0, 0, w_g,inf(V))
+ * (eq. monodomain_g_lambda; device [n_state][ld] each).
+ */
+int esdc_ionic(esdc_handle* h, const double* y, double* fE, double* lam, double* yinf,
+               void* stream);
+
+/*
+ * Diagnostic: the library's FP64 exponential and reciprocal, used by the
+ * synthetic ionic model (table-driven exp after Tang 1989; Newton reciprocal
+ * from the FP32 one), elementwise on device arrays of length n:
+ * ex[e] = e^{x[e]}, rc[e] = 1/x[e].  Not part of the method.
+ */
+int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

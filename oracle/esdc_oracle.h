@@ -138,4 +138,7 @@ int  orc_solve_shifted(const orc_mono* m, int method, double g, const double* b,
 double orc_stability_R1(double lI, double lE, double le, int M, int K, double tol,
                         int plain_sdc);
 
+/* Threads used by the oracle's parallel loops. */
+int orc_threads(void);
+
 #endif

@@ -80,6 +80,7 @@ def lib():
         L.orc_stability_R1.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
                                        C.c_double, C.c_int]
         L.orc_stability_R1.restype = C.c_double
+        L.orc_threads.restype = C.c_int
         _lib = L
     return _lib
 
@@ -145,6 +146,11 @@ def ionic_rest(model: int, params: np.ndarray, V0: float) -> np.ndarray:
     u = np.zeros(ns)
     lib().orc_ionic_rest(model, _p(np.ascontiguousarray(params, np.float64)), float(V0), _p(u))
     return u
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops run on."""
+    return int(lib().orc_threads())
 
 
 def stability_R1(lI: float, lE: float, le: float, M: int, K: int, tol: float = 0.0,

@@ -1,0 +1,5 @@
+"""GB300 (sm_103a) implementation of the hybrid exponential / semi-implicit
+spectral deferred correction (HSDC, "ES-SDC") step for the monodomain equation
+of arXiv 2405.19994, behind the C ABI of include/esdc.h."""
+from . import inputs  # noqa: F401
+from .esdc import Solver, EsdcError, lib  # noqa: F401

@@ -1,0 +1,304 @@
+// Matrix-free Jacobi-preconditioned conjugate gradients for the implicit
+// diffusion rows of the HSDC preconditioner (eq. def_P: the f_I(y_{n,i}) term
+// is taken implicitly, so each node solves (I - g L) V_i = rhs with
+// g = dt d_i sigma/(chi C_m)).  The paper solves these systems with DCT-II
+// (Sec. 5); this library uses CG on the 3/5/7-point Neumann stencil.
+//
+// One cooperative launch runs the whole solve: the blocks stay resident and
+// meet at a grid barrier (bounded spin; on timeout a flag is raised and every
+// block returns).  Dot products are reduced deterministically: each block
+// writes one partial per quantity, and after the barrier every block sums the
+// partials in block order, so all blocks take identical control decisions.
+// Each phase writes its own partial slots, so a slot is never rewritten before
+// every block has passed a later barrier (and so finished reading it).
+#include <cooperative_groups.h>
+
+#include "esdc_internal.h"
+
+namespace {
+
+constexpr unsigned long long kSpinLimit = 1ull << 24;   // ~1-2 s with nanosleep
+
+struct CgArgs {
+    MeshDev m;
+    double g;
+    double dinv[7];          // inverse diagonal of I - g L by neighbour count
+    const double* b;
+    double* x;
+    double *r, *p, *q, *z;
+    double* part;            // [6][nblocks]: setup r.z, r.r, b.b | p.q | r.z, r.r
+    unsigned* bar;           // count, generation
+    int* status;             // [0] iterations, [1] flags
+    int* iter_log;
+    int* flags;
+    double tol2;
+    int maxit;
+    int precond;
+};
+
+// Grid barrier with bounded spin.  Returns false (and raises TIMEOUT) if the
+// wait gave up; the caller must then return from the kernel.
+__device__ bool grid_barrier(unsigned* bar, int* flags)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        int ok = 1;
+        if (arrived == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > kSpinLimit) { ok = 0; atomicOr(flags, ESDC_FLAG_TIMEOUT); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Block sum of up to three values, fixed order (warp shuffle, then warps in order).
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* out)
+{
+    __shared__ double sh[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            out[k] = s;
+        }
+    __syncthreads();
+}
+
+// Every block sums the partials of all blocks.  Thread t adds partials t,
+// t + blockDim, ... in order, then the block reduces those sums in a fixed tree,
+// so every block obtains the same bits.  The partials were written by other
+// blocks before the last barrier; __ldcg reads them from L2, past this SM's L1.
+template <int NV>
+__device__ void grid_total(const double* part, int off0, double (&tot)[NV])
+{
+    __shared__ double sh[NV][32];
+    __shared__ double res[NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double* pk = part + (size_t)(off0 + k) * gridDim.x;
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(pk + b);
+        v[k] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double w = (lane < nw) ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+            if (lane == 0) res[k] = w;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = res[k];
+    __syncthreads();
+}
+
+struct NodeIdx { int ix, iy, iz; };
+
+__device__ __forceinline__ NodeIdx node_idx(const MeshDev& m, int p)
+{
+    NodeIdx n;
+    int r = p / m.nx;
+    n.ix = p - r * m.nx;
+    n.iz = r / m.ny;
+    n.iy = r - n.iz * m.ny;
+    return n;
+}
+
+// (I - g L) v at node p (L: mirrored-ghost 3/5/7-point Laplacian) and the
+// number of in-domain neighbours.  The vectors are rewritten by other blocks
+// between phases, so neighbour values are read with __ldcg (L2, coherent).
+__device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, int p,
+                                           NodeIdx n, double gih2, int* nnb)
+{
+    const double vp = __ldcg(v + p);
+    const int sxy = m.nx * m.ny;
+    double s = 0.0;
+    int c = 0;
+    if (n.ix > 0)        { s += __ldcg(v + p - 1); ++c; }
+    if (n.ix < m.nx - 1) { s += __ldcg(v + p + 1); ++c; }
+    if (n.iy > 0)        { s += __ldcg(v + p - m.nx); ++c; }
+    if (n.iy < m.ny - 1) { s += __ldcg(v + p + m.nx); ++c; }
+    if (n.iz > 0)        { s += __ldcg(v + p - sxy); ++c; }
+    if (n.iz < m.nz - 1) { s += __ldcg(v + p + sxy); ++c; }
+    *nnb = c;
+    // v_p - g/h^2 * (sum_q v_q - c v_p)
+    return fma(gih2, fma((double)c, vp, -s), vp);
+}
+
+__global__ void __launch_bounds__(512) k_cg(CgArgs a)
+{
+    const MeshDev& m = a.m;
+    const int N = m.N;
+    const int stride = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double* part = a.part;
+    const double gih2 = a.g * m.ih2;
+    __shared__ double bs[3];
+
+    // r = b - A x, z = D^{-1} r, partials r.z, r.r, b.b
+    {
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int p = tid; p < N; p += stride) {
+            NodeIdx n = node_idx(m, p);
+            int c;
+            double ax = apply_op(m, a.x, p, n, gih2, &c);
+            double bp = a.b[p];
+            double rp = bp - ax;
+            double zp = a.precond ? a.dinv[c] * rp : rp;
+            a.r[p] = rp;
+            a.z[p] = zp;
+            a.p[p] = zp;
+            v[0] += rp * zp;
+            v[1] += rp * rp;
+            v[2] += bp * bp;
+        }
+        block_sum<3>(v, bs);
+        if (threadIdx.x == 0) for (int k = 0; k < 3; ++k) part[k * gridDim.x + blockIdx.x] = bs[k];
+    }
+    if (!grid_barrier(a.bar, a.flags)) return;
+    double tot[3];
+    grid_total<3>(part, 0, tot);
+    double rz = tot[0], rr = tot[1];
+    const double stop = a.tol2 * tot[2];
+    int it = 0;
+    bool done = rr <= stop;
+    bool bad = !isfinite(rr) || !isfinite(stop);
+    while (!done && !bad && it < a.maxit) {
+        // q = A p, partial p.q
+        {
+            double v[1] = {0.0};
+            for (int p = tid; p < N; p += stride) {
+                NodeIdx n = node_idx(m, p);
+                int c;
+                double pp;
+                double qp = apply_op(m, a.p, p, n, gih2, &c);
+                pp = __ldcg(a.p + p);
+                a.q[p] = qp;
+                v[0] += pp * qp;
+            }
+            block_sum<1>(v, bs);
+            if (threadIdx.x == 0) part[3 * gridDim.x + blockIdx.x] = bs[0];
+        }
+        if (!grid_barrier(a.bar, a.flags)) return;
+        double pq[1];
+        grid_total<1>(part, 3, pq);
+        const double alpha = rz / pq[0];
+        // x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z, r.r
+        {
+            double v[2] = {0.0, 0.0};
+            for (int p = tid; p < N; p += stride) {
+                double rp = a.r[p] - alpha * a.q[p];
+                a.x[p] += alpha * __ldcg(a.p + p);
+                a.r[p] = rp;
+                double zp = rp;
+                if (a.precond) {
+                    NodeIdx n = node_idx(m, p);
+                    int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
+                            (n.iz > 0) + (n.iz < m.nz - 1);
+                    zp = a.dinv[c] * rp;
+                }
+                a.z[p] = zp;
+                v[0] += rp * zp;
+                v[1] += rp * rp;
+            }
+            block_sum<2>(v, bs);
+            if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[(4 + k) * gridDim.x + blockIdx.x] = bs[k];
+        }
+        if (!grid_barrier(a.bar, a.flags)) return;
+        double t2[2];
+        grid_total<2>(part, 4, t2);
+        const double beta = t2[0] / rz;
+        rz = t2[0];
+        rr = t2[1];
+        ++it;
+        if (!isfinite(rr)) { bad = true; break; }
+        if (rr <= stop) { done = true; break; }
+        // p = z + beta p  (own nodes; neighbours are read only after the barrier)
+        for (int p = tid; p < N; p += stride) a.p[p] = fma(beta, __ldcg(a.p + p), a.z[p]);
+        if (!grid_barrier(a.bar, a.flags)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = it;
+        if (a.iter_log) *a.iter_log = it;
+        if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+        else if (!done) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+    }
+}
+
+}  // namespace
+
+int esdc_cg_blocks(const MeshDev& mesh, int threads)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg, threads, 0) != cudaSuccess) return 0;
+    long long want = ((long long)mesh.N + (long long)threads * 2 - 1) / ((long long)threads * 2);
+    long long cap = (long long)sms * (per_sm < 2 ? per_sm : 2);
+    if (want < 1) want = 1;
+    return (int)(want < cap ? want : cap);
+}
+
+cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
+                           double* x, double tol, int maxit, int precond, int* iter_log,
+                           int* flags, cudaStream_t s)
+{
+    CgArgs a;
+    a.m = mesh;
+    a.g = g;
+    for (int c = 0; c < 7; ++c) a.dinv[c] = 1.0 / (1.0 + g * mesh.ih2 * c);
+    a.b = b;
+    a.x = x;
+    a.r = w.r; a.p = w.p; a.q = w.q; a.z = w.z;
+    a.part = w.part;
+    a.bar = w.bar;
+    a.status = w.status;
+    a.iter_log = iter_log;
+    a.flags = flags;
+    a.tol2 = tol * tol;
+    a.maxit = maxit;
+    a.precond = precond;
+    int nb = w.max_blocks;
+    void* args[] = {&a};
+    // The arrival counter is reset before every solve (a previous launch that
+    // timed out may have left it non-zero).
+    cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void*)k_cg, dim3(nb), dim3(w.threads), args, 0, s);
+}

@@ -1,0 +1,69 @@
+// Internal declarations of the HSDC library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/esdc.h"
+
+#define ESDC_MMAX 8        // collocation nodes
+#define ESDC_NSMAX 19      // states per mesh node
+#define ESDC_NGMAX 12      // gating variables per mesh node
+#define ESDC_NPMAX 128     // ionic-model parameters (+ derived reciprocals)
+#define ESDC_MAXBOX 16     // stimulus boxes
+#define ESDC_NSER 48       // reciprocal table length for the phi_k series
+#define ESDC_PROF_CLASSES 4  // esdc_profile kernel classes
+
+// Collocation data of one M (Sec. 3.1.2, App. A), computed on the host once.
+struct ColloData {
+    double c[ESDC_MMAX + 1];                       // c_0 = 0 < c_1 < ... < c_M = 1 (Radau IIA)
+    double d[ESDC_MMAX + 1];                       // d_i = c_i - c_{i-1}
+    // B[i-1][j-1][k-1] = c_i^k w_j^{k-1}: a_ij(z) = sum_k B_ijk phi_k(c_i z)   (App. A)
+    double B[ESDC_MMAX][ESDC_MMAX][ESDC_MMAX];
+    double A0[ESDC_MMAX][ESDC_MMAX];               // a_ij(0) (collocation matrix)
+    double S0[ESDC_MMAX][ESDC_MMAX];               // a_ij(0) - a_{i-1,j}(0), a_0j = 0
+    double X1;                                     // series / recurrence switch for phi_k
+    int nser;                                      // terms of the phi_M series
+};
+
+// Fills ColloData for 1 <= M <= 8.  Returns 0 on success.
+int esdc_colloc_build(int M, ColloData* out);
+
+// Uniform cell-centred mesh as seen by the kernels.
+struct MeshDev {
+    int nx, ny, nz;
+    int N;            // nx*ny*nz
+    int64_t ld;       // row pitch of state arrays (doubles)
+    double ih2;       // 1/h^2
+};
+
+struct StimDev {
+    int nbox;
+    int box[ESDC_MAXBOX][6];
+    double amp[ESDC_MAXBOX], t_on[ESDC_MAXBOX], t_off[ESDC_MAXBOX];
+};
+
+struct ModelDev {
+    double p[ESDC_NPMAX];
+};
+
+// CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
+struct CgWork {
+    double *r, *p, *q, *z;          // [ld] each
+    double* part;                   // [6 * max_blocks] block partial sums
+    unsigned* bar;                  // [2] grid barrier: arrival count, generation
+    int* status;                    // [2]: iterations of the last solve, flag bits
+    int max_blocks;
+    int threads;
+};
+
+#define ESDC_FLAG_CG_MAXIT   1
+#define ESDC_FLAG_TIMEOUT    2
+#define ESDC_FLAG_NONFINITE  4
+
+// Enqueue one CG solve; iter_log (device, optional) receives the iteration count.
+// flags (device) accumulates ESDC_FLAG_* bits.  Returns a cudaError_t.
+cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
+                           double* x, double tol, int maxit, int precond, int* iter_log,
+                           int* flags, cudaStream_t s);
+// Blocks to use for a cooperative CG launch on this device.
+int esdc_cg_blocks(const MeshDev& mesh, int threads);

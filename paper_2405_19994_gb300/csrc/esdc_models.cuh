@@ -1,0 +1,118 @@
+// Pointwise ionic models on the device (eq. monodomain; gates in the form of
+// eq. monodomain_g_lambda).  Each model evaluates, for one mesh node u:
+//   mI   = -I_ion(u)                               [uA/mm^2]
+//   ha   = h_a(u)   (NA auxiliary derivatives)
+//   lam  = Lambda_g(V) = -(alpha + beta)           (NG gates)
+//   yinf = w_g,inf(V) = alpha/(alpha + beta)       (NG gates)
+// State order in u: V, the NA auxiliaries, the NG gates.
+#pragma once
+#include "esdc_fmath.cuh"
+
+namespace esdc {
+
+// x/(e^x - 1) with the removable singularity at x = 0 (second-order Taylor
+// polynomial for |x| < 1e-6, where its error is below 1e-19).
+__device__ __forceinline__ double x_over_expm1(double x)
+{
+    if (fabs(x) < 1e-6) return 1.0 - x * (0.5 - x * (1.0 / 12.0));
+    return x / expm1(x);
+}
+
+// Hodgkin & Huxley 1952, V = Vrest + v.  params: gNa, gK, gL, ENa, EK, EL, Vrest.
+struct HH1952 {
+    static constexpr int NS = 4, NA = 0, NG = 3;
+    static constexpr int NPARAM = 7, NDERIVED = 0;
+    __device__ static void eval(const double* __restrict__ mp, const double* u, double& mI,
+                                double* ha, double* lam, double* yinf)
+    {
+        (void)ha;
+        const double V = u[0], m = u[1], h = u[2], n = u[3];
+        const double v = V - mp[6];
+        const double am = x_over_expm1((25.0 - v) * 0.1);
+        const double bm = 4.0 * exp(v * (-1.0 / 18.0));
+        const double ah = 0.07 * exp(v * (-0.05));
+        const double bh = 1.0 / (exp((30.0 - v) * 0.1) + 1.0);
+        const double an = 0.1 * x_over_expm1((10.0 - v) * 0.1);
+        const double bn = 0.125 * exp(v * (-0.0125));
+        const double m3h = m * m * m * h, n2 = n * n;
+        mI = -(mp[0] * m3h * (V - mp[3]) + mp[1] * n2 * n2 * (V - mp[4]) + mp[2] * (V - mp[5]));
+        double sm = am + bm, sh = ah + bh, sn = an + bn;
+        lam[0] = -sm; yinf[0] = am / sm;
+        lam[1] = -sh; yinf[1] = ah / sh;
+        lam[2] = -sn; yinf[2] = an / sn;
+    }
+    // Resting state at V0: gates at w_inf(V0).
+    __device__ static void rest(const double* mp, double V0, double* u)
+    {
+        double mI, lam[NG], yinf[NG];
+        u[0] = V0; u[1] = u[2] = u[3] = 0.0;
+        eval(mp, u, mI, nullptr, lam, yinf);
+        for (int g = 0; g < NG; ++g) u[1 + g] = yinf[g];
+    }
+};
+
+// 19-state synthetic stiff model (shape of ten Tusscher-Panfilov 2006),
+// evaluated with esdc_exp / esdc_rcp and host-side reciprocals of the constant
+// divisors (each differs from the IEEE quotient by about one ulp):
+// V, auxiliaries a1..a6, gates g1..g12.  params (88): 12 x (Vh, k, r, ln rho,
+// Vr, sr), [G_f, E_f, G_s, E_s, G_K, E_K, G_K1, G_b, E_b, c_K6], tau_1..tau_6.
+//   w_inf = 1/(1 + e^{-(V-Vh)/k}),  rate = r exp(ln rho / (1 + e^{-(V-Vr)/sr}))
+//   I_ion = G_f g1 g2 g3 a1 (V-E_f) + G_s g4 g5 a3 (V-E_s)
+//         + G_K a2 (1 + c_K6 a6)(V-E_K) + G_K1 g7 g8 (V-E_K)
+//         + G_b (g9+g10+g11+g12)/4 (V-E_b)
+//   a1' = (1-g6-a1)/tau1, a2' = (g6-a2)/tau2, a3' = (1-g6-a3)/tau3,
+//   a4' = (g4 g5 - a4)/tau4, a5' = (a4-a5)/tau5, a6' = (a5-a6)/tau6
+struct SYN19 {
+    static constexpr int NS = 19, NA = 6, NG = 12;
+    // mp[88 + q] = 1/k_q, mp[100 + q] = 1/sr_q, mp[112 + l] = 1/tau_l (set on the host)
+    static constexpr int NPARAM = 88, NDERIVED = 30;
+    __device__ static void eval(const double* __restrict__ mp, const double* u, double& mI,
+                                double* ha, double* lam, double* yinf)
+    {
+        const double V = u[0];
+        const double* a = u + 1;
+        const double* g = u + 7;
+        const double* inv = mp + 88;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const double* p = mp + 6 * q;
+            const double w = esdc_rcp(1.0 + esdc_exp((p[0] - V) * inv[q]));
+            const double s = esdc_rcp(1.0 + esdc_exp((p[4] - V) * inv[12 + q]));
+            lam[q] = -p[2] * esdc_exp(p[3] * s);
+            yinf[q] = w;
+        }
+        const double* c = mp + 72;
+        const double If = c[0] * g[0] * g[1] * g[2] * a[0] * (V - c[1]);
+        const double Is = c[2] * g[3] * g[4] * a[2] * (V - c[3]);
+        const double IK = c[4] * a[1] * (1.0 + c[9] * a[5]) * (V - c[5]);
+        const double IK1 = c[6] * g[6] * g[7] * (V - c[5]);
+        const double Ib = c[7] * 0.25 * (g[8] + g[9] + g[10] + g[11]) * (V - c[8]);
+        mI = -(If + Is + IK + IK1 + Ib);
+        if (ha) {
+            const double* itau = inv + 24;
+            ha[0] = ((1.0 - g[5]) - a[0]) * itau[0];
+            ha[1] = (g[5] - a[1]) * itau[1];
+            ha[2] = ((1.0 - g[5]) - a[2]) * itau[2];
+            ha[3] = (g[3] * g[4] - a[3]) * itau[3];
+            ha[4] = (a[3] - a[4]) * itau[4];
+            ha[5] = (a[4] - a[5]) * itau[5];
+        }
+    }
+    __device__ static void rest(const double* mp, double V0, double* u)
+    {
+        double mI, lam[NG], yinf[NG];
+        for (int s = 0; s < NS; ++s) u[s] = 0.0;
+        u[0] = V0;
+        eval(mp, u, mI, nullptr, lam, yinf);
+        for (int q = 0; q < NG; ++q) u[7 + q] = yinf[q];
+        const double g6 = yinf[5];
+        u[1] = 1.0 - g6;
+        u[2] = g6;
+        u[3] = 1.0 - g6;
+        u[4] = yinf[3] * yinf[4];
+        u[5] = u[4];
+        u[6] = u[4];
+    }
+};
+
+}  // namespace esdc

@@ -1,0 +1,234 @@
+"""Python binding of the HSDC C library (include/esdc.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``libesdc.so``.  Torch supplies device memory and streams; tensors are passed to
+the library as raw pointers (``data_ptr()``) together with the current CUDA
+stream.  The binding fails loudly when the library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libesdc.so")
+
+ESDC_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "CG_NOT_CONVERGED", -4: "NONFINITE",
+          -5: "DEVICE_TIMEOUT", -6: "UNSUPPORTED", -7: "NO_MEMORY"}
+MODEL_HH1952, MODEL_SYN19 = 0, 1
+
+
+class EsdcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"esdc error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class esdc_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double)]
+
+
+class esdc_options(C.Structure):
+    _fields_ = [("M_max", C.c_int), ("tol_cg", C.c_double), ("cg_maxit", C.c_int), ("precond", C.c_int)]
+
+
+_lib = None
+_VP, _D, _I64 = C.c_void_p, C.c_double, C.c_int64
+
+
+def lib() -> C.CDLL:
+    """Load libesdc.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "esdc_default_options": (None, [C.POINTER(esdc_options)]),
+            "esdc_create": (C.c_int, [C.POINTER(esdc_mesh), _D, _D, _D, C.c_int, C.POINTER(_D), C.c_int,
+                                      C.POINTER(esdc_options), C.POINTER(_VP)]),
+            "esdc_destroy": (None, [_VP]),
+            "esdc_last_error": (C.c_char_p, [_VP]),
+            "esdc_set_stimulus": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(_D), C.POINTER(_D),
+                                            C.POINTER(_D)]),
+            "esdc_state_size": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(_I64), C.POINTER(_I64)]),
+            "esdc_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
+            "esdc_sweep": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
+            "esdc_sweep_host": (C.c_int, [_VP, _VP, _I64, _D, _D, C.c_int, C.c_int, _VP]),
+            "esdc_residual": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)]),
+            "esdc_stats": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
+            "esdc_keep_residual": (C.c_int, [_VP, C.c_int]),
+            "esdc_profile": (C.c_int, [_VP, C.c_int]),
+            "esdc_profile_read": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(C.c_longlong)]),
+            "esdc_collocation": (C.c_int, [_VP, _VP, _VP, _VP]),
+            "esdc_coefficients": (C.c_int, [_VP, _VP, _I64, C.c_int, _VP, _VP]),
+            "esdc_diffusion_solve": (C.c_int, [_VP, _D, _VP, _VP, C.POINTER(C.c_int), _VP]),
+            "esdc_ionic": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+            "esdc_math_check": (C.c_int, [_VP, _I64, _VP, _VP, _VP]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _ptr(t) -> int:
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return t.data_ptr()
+
+
+def math_check(x, stream=None):
+    """The library's FP64 exp and reciprocal of a float64 CUDA tensor x."""
+    import torch
+    ex, rc = torch.empty_like(x), torch.empty_like(x)
+    rc_ = lib().esdc_math_check(_ptr(x), x.numel(), _ptr(ex), _ptr(rc), _stream(stream))
+    if rc_ != ESDC_OK:
+        raise EsdcError(rc_, "esdc_math_check failed")
+    return ex, rc
+
+
+class Solver:
+    """One HSDC solver handle: a mesh, conductivity and ionic model on the current GPU.
+
+    Every method maps onto one C entry point of the same name without the
+    ``esdc_`` prefix."""
+
+    def __init__(self, dim: int, nx: int, ny: int, nz: int, h: float, sigma: float, chi: float,
+                 Cm: float, model: int, params, M_max: int = 8, tol_cg: float = 1e-14,
+                 cg_maxit: int = 200, precond: bool = True):
+        self._h = None
+        L = lib()
+        mesh = esdc_mesh(dim, nx, ny, nz, h)
+        opt = esdc_options()
+        L.esdc_default_options(C.byref(opt))
+        opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond = M_max, tol_cg, cg_maxit, int(precond)
+        p = np.ascontiguousarray(params, np.float64)
+        out = _VP()
+        rc = L.esdc_create(C.byref(mesh), sigma, chi, Cm, model, p.ctypes.data_as(C.POINTER(_D)), len(p),
+                           C.byref(opt), C.byref(out))
+        if rc != ESDC_OK:
+            raise EsdcError(rc, "esdc_create failed")
+        self._h = out.value
+        ns, nn, ld = C.c_int(), _I64(), _I64()
+        self._check(L.esdc_state_size(self._h, C.byref(ns), C.byref(nn), C.byref(ld)))
+        self.n_state, self.n_nodes, self.ld = ns.value, nn.value, ld.value
+        self.M_max = M_max
+
+    @classmethod
+    def from_workload(cls, wl, **kw) -> "Solver":
+        s = cls(wl.dim, wl.nx, wl.ny, wl.nz, wl.h, wl.sigma, wl.chi, wl.Cm, wl.model, wl.params, **kw)
+        s.set_stimulus(wl.boxes, wl.amp, wl.t_on, wl.t_off)
+        return s
+
+    def _check(self, rc: int):
+        if rc != ESDC_OK:
+            msg = lib().esdc_last_error(self._h).decode() if self._h else ""
+            raise EsdcError(rc, msg)
+
+    def close(self):
+        if self._h:
+            lib().esdc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- ABI calls
+    def set_stimulus(self, boxes, amp, t_on, t_off):
+        b = np.ascontiguousarray(boxes, np.int32).reshape(-1)
+        a, on, off = (np.ascontiguousarray(x, np.float64) for x in (amp, t_on, t_off))
+        n = len(a)
+        self._check(lib().esdc_set_stimulus(self._h, n, b.ctypes.data_as(C.POINTER(C.c_int)),
+                                            a.ctypes.data_as(C.POINTER(_D)), on.ctypes.data_as(C.POINTER(_D)),
+                                            off.ctypes.data_as(C.POINTER(_D))))
+
+    def new_state(self, device=None):
+        import torch
+        return torch.zeros((self.n_state, self.ld), dtype=torch.float64, device=device or "cuda")
+
+    def init_state(self, y, V0: float, stream=None):
+        self._check(lib().esdc_init_state(self._h, _ptr(y), V0, _stream(stream)))
+        return y
+
+    def sweep(self, y, t: float, dt: float, M: int, K: int, stream=None):
+        self._check(lib().esdc_sweep(self._h, _ptr(y), t, dt, M, K, _stream(stream)))
+        return y
+
+    def sweep_host(self, y_host: np.ndarray, t: float, dt: float, M: int, K: int, stream=None):
+        """y_host: host float64 array [n_state, ld_host] (C-contiguous, e.g. pinned)."""
+        if isinstance(y_host, np.ndarray):
+            assert y_host.dtype == np.float64 and y_host.flags.c_contiguous
+            ptr, ld = y_host.ctypes.data, y_host.shape[1]
+        else:   # a CPU torch tensor (pinned memory for asynchronous copies)
+            assert y_host.dtype.is_floating_point and y_host.is_contiguous() and not y_host.is_cuda
+            ptr, ld = y_host.data_ptr(), y_host.shape[1]
+        self._check(lib().esdc_sweep_host(self._h, ptr, ld, t, dt, M, K, _stream(stream)))
+        return y_host
+
+    def residual(self):
+        r, yv = _D(), _D()
+        rs = np.zeros(self.n_state)
+        rc = lib().esdc_residual(self._h, C.byref(r), C.byref(yv), rs.ctypes.data_as(C.POINTER(_D)))
+        return rc, r.value, yv.value, rs
+
+    def stats(self, n: int) -> np.ndarray:
+        out = np.zeros(n, np.int32)
+        self._check(lib().esdc_stats(self._h, out.ctypes.data_as(C.POINTER(C.c_int)), n))
+        return out
+
+    def profile(self, enable: bool = True):
+        self._check(lib().esdc_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """Per kernel class (setup, node, cg, residual): (milliseconds, launches)."""
+        ms = (_D * 4)()
+        n = (C.c_longlong * 4)()
+        self._check(lib().esdc_profile_read(self._h, ms, n))
+        names = ("setup", "node", "cg", "residual")
+        return {names[c]: (ms[c], n[c]) for c in range(4)}
+
+    def keep_residual(self, keep: bool = True):
+        self._check(lib().esdc_keep_residual(self._h, int(keep)))
+
+    def collocation(self, M: int, with_residual: bool = False, stream=None):
+        import torch
+        y = torch.empty((M, self.n_state, self.ld), dtype=torch.float64, device="cuda")
+        r = torch.empty_like(y) if with_residual else None
+        self._check(lib().esdc_collocation(self._h, _ptr(y), _ptr(r) if r is not None else None,
+                                           _stream(stream)))
+        return y, r
+
+    def coefficients(self, z, M: int, stream=None):
+        import torch
+        n = z.numel()
+        a = torch.empty((M, M, n), dtype=torch.float64, device="cuda")
+        self._check(lib().esdc_coefficients(self._h, _ptr(z), n, M, _ptr(a), _stream(stream)))
+        return a
+
+    def diffusion_solve(self, g: float, b, x, stream=None) -> int:
+        it = C.c_int()
+        self._check(lib().esdc_diffusion_solve(self._h, g, _ptr(b), _ptr(x), C.byref(it), _stream(stream)))
+        return it.value
+
+    def ionic(self, y, stream=None):
+        import torch
+        fE, lam, yinf = (torch.empty_like(y) for _ in range(3))
+        self._check(lib().esdc_ionic(self._h, _ptr(y), _ptr(fE), _ptr(lam), _ptr(yinf), _stream(stream)))
+        return fE, lam, yinf

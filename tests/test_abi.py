@@ -1,0 +1,86 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/esdc.h declares, and rejects invalid arguments before touching CUDA."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2405_19994_gb300 import build as B
+    B.build()
+    from paper_2405_19994_gb300 import esdc
+    return esdc.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "esdc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(esdc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("esdc_create", "esdc_sweep", "esdc_residual", "esdc_destroy", "esdc_set_stimulus",
+                 "esdc_state_size", "esdc_init_state", "esdc_stats", "esdc_last_error", "esdc_sweep_host"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_invalid_arguments_rejected_without_gpu(L):
+    from paper_2405_19994_gb300 import esdc as E
+    from paper_2405_19994_gb300 import inputs as I
+    p = I.hh1952_params()
+    pp = p.ctypes.data_as(C.POINTER(C.c_double))
+    out = C.c_void_p(1)
+
+    def create(mesh, sigma=0.17, chi=140.0, Cm=0.01, model=0, params=pp, n=7, optp=None):
+        return L.esdc_create(C.byref(mesh), sigma, chi, Cm, model, params, n, optp, C.byref(out))
+
+    ok = E.esdc_mesh(2, 8, 8, 1, 0.25)
+    assert create(E.esdc_mesh(0, 8, 8, 1, 0.25)) == -1 and out.value is None
+    assert create(E.esdc_mesh(2, 0, 8, 1, 0.25)) == -1
+    assert create(E.esdc_mesh(2, 8, 8, 3, 0.25)) == -1          # 2D with nz != 1
+    assert create(E.esdc_mesh(1, 8, 2, 1, 0.25)) == -1          # 1D with ny != 1
+    assert create(E.esdc_mesh(2, 8, 8, 1, 0.0)) == -1
+    assert create(E.esdc_mesh(2, 8, 8, 1, float("nan"))) == -1
+    assert create(E.esdc_mesh(3, 70000, 70000, 1, 0.1)) == -1   # more than 2^31 nodes
+    assert create(ok, chi=0.0) == -1
+    assert create(ok, Cm=-1.0) == -1
+    assert create(ok, model=7) == -1
+    assert create(ok, n=6) == -1                                # HH needs 7 parameters
+    assert create(ok, params=None) == -1
+    bad = p.copy(); bad[2] = np.inf
+    assert create(ok, params=bad.ctypes.data_as(C.POINTER(C.c_double))) == -1
+    opt = E.esdc_options(); L.esdc_default_options(C.byref(opt))
+    assert (opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond) == (8, 1e-14, 200, 1)
+    opt.M_max = 9
+    assert create(ok, optp=C.byref(opt)) == -1
+    opt.M_max = 4; opt.cg_maxit = 0
+    assert create(ok, optp=C.byref(opt)) == -1
+    # null handles
+    assert L.esdc_sweep(None, None, 0.0, 0.1, 3, 4, None) == -1
+    assert L.esdc_residual(None, None, None, None) == -1
+    assert L.esdc_state_size(None, None, None, None) == -1
+    L.esdc_destroy(None)
+    assert L.esdc_last_error(None) == b"null handle"
+
+
+def test_no_product_import_of_the_oracle():
+    # The product path (package + C sources) must never reach the oracle.
+    pkg = os.path.join(ROOT, "paper_2405_19994_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "esdc_oracle" not in txt and "liborc" not in txt, f

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element
+by element on seeded inputs.  Tolerances: the hot path is FP64 end to end, so
+single kernels agree to a few ulps times the conditioning of the step (stated
+per test); multi-step runs are held to the 1e-10 relative max-norm bound on V.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+import paper_2405_19994_gb300 as P  # noqa: E402
+from paper_2405_19994_gb300 import inputs as I  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    P.lib()
+
+
+def to_dev(solver, y):
+    t = solver.new_state()
+    t[:, : y.shape[1]] = torch.from_numpy(np.ascontiguousarray(y))
+    return t
+
+
+def from_dev(solver, t):
+    torch.cuda.synchronize()
+    return t[:, : solver.n_nodes].cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------- coefficient kernel (App. A)
+
+@pytest.mark.parametrize("M", range(1, 9))
+def test_coefficients_match_oracle(M):
+    wl = I.hh_sheet_32().with_mesh(4, 4, 1)
+    s = P.Solver.from_workload(wl)
+    zs = -np.concatenate([[0.0, 1e-14, 1e-9, 1e-5], np.linspace(1e-3, 12, 97), np.logspace(1, 3.5, 40)])
+    a_gpu = s.coefficients(torch.from_numpy(zs).cuda(), M).cpu().numpy()
+    w = np.abs(O.fornberg_weights(M)).max()
+    for e, z in enumerate(zs):
+        a_orc = O.aij(M, z)
+        # rounding of sum_k c_i^k w_j^{k-1} phi_k grows with max|w| (both sides use the sum)
+        np.testing.assert_allclose(a_gpu[:, :, e], a_orc, rtol=0, atol=16 * 2.2e-16 * max(1.0, w),
+                                   err_msg=f"z={z}")
+
+
+# ---------------------------------------------------------------- FP64 exp / reciprocal
+
+def test_library_exp_and_reciprocal_error_bounds():
+    from paper_2405_19994_gb300 import esdc as E
+    rng = np.random.default_rng(0)
+    x = np.concatenate([np.linspace(-706.9, 709.7, 200001), rng.uniform(-50, 50, 200000),
+                        rng.uniform(-1e-3, 1e-3, 10000), [0.0, -0.0, 1e-300, -1e-300]])
+    xd = torch.from_numpy(x).cuda()
+    ex, _ = E.math_check(xd)
+    ref = torch.exp(xd)                    # CUDA's exp
+    ulp = torch.abs(ex - ref) / torch.abs(torch.nextafter(ref, torch.full_like(ref, np.inf)) - ref)
+    assert float(ulp.max()) <= 2.0, float(ulp.max())
+    # special values
+    sp = torch.tensor([-800.0, 710.0, float("nan"), float("inf"), -float("inf")], dtype=torch.float64).cuda()
+    e2, _ = E.math_check(sp)
+    e2 = e2.cpu().numpy()
+    assert e2[0] == 0.0 and np.isinf(e2[1]) and np.isnan(e2[2]) and np.isinf(e2[3]) and e2[4] == 0.0
+    d = np.concatenate([np.geomspace(1e-30, 1e290, 100001), -np.geomspace(1e-30, 1e290, 1001),
+                        1 + rng.uniform(0, 1e12, 100000)])
+    dd = torch.from_numpy(d).cuda()
+    _, rc = E.math_check(dd)
+    ref = 1.0 / dd
+    ulp = torch.abs(rc - ref) / torch.abs(torch.nextafter(ref, torch.full_like(ref, np.inf)) - ref)
+    assert float(ulp.max()) <= 2.0, float(ulp.max())
+
+
+# ---------------------------------------------------------------- ionic models
+
+@pytest.mark.parametrize("model", [I.MODEL_HH1952, I.MODEL_SYN19])
+def test_ionic_pointwise(model):
+    wl = I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()
+    wl = wl.with_mesh(37, 5, 1)
+    s = P.Solver.from_workload(wl)
+    y = I.random_state(wl, seed=11)
+    y[0] = np.linspace(-110, 70, wl.n_nodes)
+    y[0, 3] = wl.params[6] + 25.0 if model == I.MODEL_HH1952 else y[0, 3]    # alpha_m's 0/0 point
+    y[0, 4] = wl.params[6] + 10.0 if model == I.MODEL_HH1952 else y[0, 4]    # alpha_n's 0/0 point
+    fE, lam, yinf = (from_dev(s, t) for t in s.ionic(to_dev(s, y)))
+    for p in range(wl.n_nodes):
+        f0, l0, i0 = O.ionic_point(model, wl.params, y[:, p])
+        np.testing.assert_allclose(fE[:, p], f0, rtol=4e-14, atol=1e-15)
+        np.testing.assert_allclose(lam[:, p], l0, rtol=4e-14, atol=0)
+        np.testing.assert_allclose(yinf[:, p], i0, rtol=4e-14, atol=1e-300)
+
+
+@pytest.mark.parametrize("model", [I.MODEL_HH1952, I.MODEL_SYN19])
+def test_init_state(model):
+    wl = (I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()).with_mesh(7, 3, 2)
+    s = P.Solver.from_workload(wl)
+    y = s.new_state()
+    s.init_state(y, wl.V0)
+    got = from_dev(s, y)
+    want = O.Monodomain(wl).init_state()
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-300)
+
+
+# ---------------------------------------------------------------- diffusion solve (CG) vs DCT-II
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5)])
+@pytest.mark.parametrize("g", [1e-3, 0.05, 2.0])
+def test_diffusion_solve_matches_dct(shape, g):
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    s = P.Solver.from_workload(wl, cg_maxit=2000)
+    m = O.Monodomain(wl)
+    rng = np.random.default_rng(5)
+    b = rng.normal(size=wl.n_nodes)
+    x0 = rng.normal(size=wl.n_nodes)
+    want = m.solve_shifted(g, b, method=O.SOLVE_DCT)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.from_numpy(x0).cuda()
+    it = s.diffusion_solve(g, bd, xd)
+    got = xd.cpu().numpy()
+    # ||x - x*|| <= kappa * tol * ||x*|| with kappa = 1 + 4 d g / h^2
+    kappa = 1 + 4 * 3 * g / wl.h**2
+    assert rel(got, want) < 50 * kappa * 1e-14, (rel(got, want), it)
+    assert it <= 2000
+
+
+# ---------------------------------------------------------------- one HSDC step
+
+CASES = [
+    # (model, mesh, M, K, t0)
+    (I.MODEL_HH1952, (12, 10, 1), 3, 4, 0.5),
+    (I.MODEL_HH1952, (9, 7, 3), 2, 3, 0.2),
+    (I.MODEL_HH1952, (33, 1, 1), 1, 2, 0.0),
+    (I.MODEL_HH1952, (6, 5, 1), 8, 3, 1.7),
+    (I.MODEL_HH1952, (1, 1, 1), 3, 4, 0.0),
+    (I.MODEL_HH1952, (10, 9, 1), 3, 0, 0.5),
+    (I.MODEL_SYN19, (11, 6, 4), 4, 6, 0.5),
+    (I.MODEL_SYN19, (40, 3, 1), 3, 2, 0.9),
+    (I.MODEL_SYN19, (7, 7, 2), 6, 5, 0.0),
+]
+
+
+@pytest.mark.parametrize("model,mesh,M,K,t0", CASES)
+def test_one_step_matches_oracle(model, mesh, M, K, t0):
+    base = I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()
+    wl = base.with_mesh(*mesh)
+    wl.boxes = np.array([[0, 2, 0, 3, 0, 2]], np.int32)       # stimulus on a corner box, on for t < 1
+    dt = wl.dt
+    s = P.Solver.from_workload(wl, M_max=M)
+    s.keep_residual(True)
+    y0 = I.random_state(wl, seed=hash((model, mesh, M, K)) % 1000)
+    yd = to_dev(s, y0)
+    s.sweep(yd, t0, dt, M, K)
+    rc, res_inf, y_inf, res_state = s.residual()
+    col, res = s.collocation(M, with_residual=True)
+    got = from_dev(s, yd)
+    col = col[:, :, : wl.n_nodes].cpu().numpy()
+    res = res[:, :, : wl.n_nodes].cpu().numpy()
+    m = O.Monodomain(wl, solver=O.SOLVE_DCT)
+    want, st, wcol, wres = m.step(y0, t0, dt, M, K, want_colloc=True, want_resid=True)
+    assert rc == 0
+    # per state: relative to that state's scale
+    for srow in range(wl.n_state):
+        scale = max(np.abs(want[srow]).max(), 1e-3)
+        assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (srow, np.abs(got[srow] - want[srow]).max())
+        for i in range(M):
+            assert np.abs(col[i, srow] - wcol[i, srow]).max() / scale < 1e-12
+    # residual vectors: absolute, scaled by dt*|G| (the residual is a difference of O(1) terms)
+    rscale = max(np.abs(wres).max(), 1e-12 * y_inf)
+    assert np.abs(res - wres).max() <= 1e-12 * max(y_inf, 1.0) + 1e-9 * rscale
+    assert math.isclose(res_inf, np.abs(res).max(), rel_tol=0, abs_tol=0)
+    assert y_inf == max(np.abs(y0).max(), np.abs(col).max())
+
+
+def test_sweep_host_matches_device():
+    wl = I.hh_sheet_32().with_mesh(20, 9, 1)
+    s = P.Solver.from_workload(wl)
+    y0 = I.random_state(wl, seed=3)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.3, wl.dt, wl.M, wl.K)
+    dev = from_dev(s, yd)
+    yh = np.ascontiguousarray(y0.copy())
+    s.sweep_host(yh, 0.3, wl.dt, wl.M, wl.K)
+    np.testing.assert_array_equal(yh, dev)
+
+
+def test_errors_reported():
+    wl = I.hh_sheet_32().with_mesh(16, 16, 1)
+    s = P.Solver.from_workload(wl, M_max=3, cg_maxit=1, tol_cg=1e-15)
+    y = to_dev(s, I.random_state(wl, seed=1))
+    with pytest.raises(P.EsdcError) as e:
+        s.sweep(y, 0.0, wl.dt, 4, 2)                          # M > M_max
+    assert e.value.code == -1
+    s.sweep(y, 0.0, wl.dt, 3, 2)
+    rc, *_ = s.residual()
+    assert rc == -3                                           # CG_NOT_CONVERGED
+    s2 = P.Solver.from_workload(wl, M_max=3)
+    y2 = I.random_state(wl, seed=2)
+    y2[0, 17] = np.nan
+    yd = to_dev(s2, y2)
+    s2.sweep(yd, 0.0, wl.dt, 3, 2)
+    rc, *_ = s2.residual()
+    assert rc == -4                                           # NONFINITE
+    s3 = P.Solver.from_workload(wl, M_max=3)
+    yd = to_dev(s3, I.random_state(wl, seed=2))
+    s3.sweep(yd, 0.0, wl.dt, 3, 2)
+    assert s3.residual()[0] == 0                              # a fresh handle is clean
+    it = s3.stats(6)
+    assert np.all(it >= 1) and np.all(it < 200)
+
+
+# ---------------------------------------------------------------- full workloads
+
+def test_hh_sheet_full_run_matches_oracle():
+    """32x32 HH sheet, corner stimulus, M=3, K=4, dt=0.025, T=4 ms (160 steps)."""
+    wl = I.hh_sheet_32()
+    s = P.Solver.from_workload(wl)
+    y = s.new_state()
+    s.init_state(y, wl.V0)
+    m = O.Monodomain(wl)
+    ref = m.init_state()
+    np.testing.assert_allclose(from_dev(s, y), ref, rtol=1e-14)
+    for n in range(wl.n_steps):
+        s.sweep(y, n * wl.dt, wl.dt, wl.M, wl.K)
+        ref, _, _, _ = m.step(ref, n * wl.dt, wl.dt, wl.M, wl.K)
+        if n % 40 == 39:
+            assert s.residual()[0] == 0
+    got = from_dev(s, y)
+    err = rel(got[0], ref[0])
+    assert ref[0].max() > -60.0            # the wave is present in the sheet at T
+    assert err < 1e-10, err
+    assert got[1:].min() >= -1e-12 and got[1:].max() <= 1 + 1e-12
+
+
+@pytest.mark.slow
+def test_syn19_slab_full_size_one_step():
+    """128x128x32 synthetic slab (524,288 nodes), M=4, K=6, dt=0.05: one step from a
+    seeded mid-wave state, every output element against the oracle."""
+    wl = I.syn19_slab()
+    s = P.Solver.from_workload(wl, M_max=wl.M)
+    y0 = I.random_state(wl, seed=2024)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.5, wl.dt, wl.M, wl.K)
+    rc, res_inf, y_inf, _ = s.residual()
+    got = from_dev(s, yd)
+    m = O.Monodomain(wl)
+    want, st, _, _ = m.step(y0, 0.5, wl.dt, wl.M, wl.K)
+    assert rc == 0
+    for srow in range(wl.n_state):
+        scale = max(np.abs(want[srow]).max(), 1e-3)
+        assert np.abs(got[srow] - want[srow]).max() / scale < 1e-11, srow
+    assert abs(res_inf - st["res_inf"]) <= 1e-9 * max(st["res_inf"], 1e-6)
