@@ -9,8 +9,9 @@
 // block returns).  Dot products are reduced deterministically: each block
 // writes one partial per quantity, and after the barrier every block sums the
 // partials in block order, so all blocks take identical control decisions.
-// Each phase writes its own partial slots, so a slot is never rewritten before
-// every block has passed a later barrier (and so finished reading it).
+// Each phase writes its own partial slots (set-up 0-2, [A] 3, [B] 4-5), so a
+// slot is rewritten only after every block has passed a later barrier and so
+// finished reading it.
 #include <cooperative_groups.h>
 
 #include "esdc_internal.h"
@@ -66,60 +67,48 @@ __device__ bool grid_barrier(unsigned* bar, int* flags)
     return ok_s != 0;
 }
 
-// Block sum of up to three values, fixed order (warp shuffle, then warps in order).
+// Block sum of up to three values in a fixed order: every thread stores its
+// value, lane l of warp 0 adds the values of lane l of all warps (in warp
+// order), then warp 0 reduces its 32 sums with a shuffle tree.  Few FP64 adds
+// per thread: the FP64 pipe is the scarce unit.
 template <int NV>
 __device__ void block_sum(double (&v)[NV], double* out)
 {
-    __shared__ double sh[NV][32];
+    __shared__ double sh[NV][32][17];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    for (int k = 0; k < NV; ++k) sh[k][lane][wid] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += sh[k][w];
-            out[k] = s;
+            double s = sh[k][lane][0];
+            for (int w = 1; w < nw; ++w) s += sh[k][lane][w];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) out[k] = s;
         }
+    }
     __syncthreads();
 }
 
-// Every block sums the partials of all blocks.  Thread t adds partials t,
-// t + blockDim, ... in order, then the block reduces those sums in a fixed tree,
-// so every block obtains the same bits.  The partials were written by other
-// blocks before the last barrier; __ldcg reads them from L2, past this SM's L1.
+// Every block sums the partials of all blocks: lane l of warp 0 adds partials
+// l, l+32, ... in order, then a shuffle tree; the result is broadcast through
+// shared memory, so every block obtains the same bits.  The partials were
+// written by other blocks before the last barrier; __ldcg reads them from L2,
+// past this SM's L1.
 template <int NV>
 __device__ void grid_total(const double* part, int off0, double (&tot)[NV])
 {
-    __shared__ double sh[NV][32];
     __shared__ double res[NV];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    double v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const double* pk = part + (size_t)(off0 + k) * gridDim.x;
-        double s = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(pk + b);
-        v[k] = s;
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
-    __syncthreads();
     if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double w = (lane < nw) ? sh[k][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-            if (lane == 0) res[k] = w;
+            const double* pk = part + (size_t)(off0 + k) * gridDim.x;
+            double s = 0.0;
+            for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(pk + b);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) res[k] = s;
         }
     }
     __syncthreads();
@@ -161,6 +150,12 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
     return fma(gih2, fma((double)c, vp, -s), vp);
 }
 
+// Jacobi-PCG with two grid barriers per iteration.  The search direction
+// p = z + beta p and its image q = A p are both updated by recurrences,
+// q = A z + beta q, so the stencil acts on z, which is complete at the barrier
+// that also completes the reduction for beta:
+//   [A] p = z + beta p; q = A z + beta q; partial p.q        | barrier -> alpha
+//   [B] x += alpha p; r -= alpha q; z = D^{-1} r; r.z, r.r   | barrier -> beta, stop test
 __global__ void __launch_bounds__(512) k_cg(CgArgs a)
 {
     const MeshDev& m = a.m;
@@ -171,7 +166,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
     const double gih2 = a.g * m.ih2;
     __shared__ double bs[3];
 
-    // r = b - A x, z = D^{-1} r, partials r.z, r.r, b.b
+    // r = b - A x, z = D^{-1} r, p = q = 0; partials r.z, r.r, b.b
     {
         double v[3] = {0.0, 0.0, 0.0};
         for (int p = tid; p < N; p += stride) {
@@ -183,7 +178,8 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
             double zp = a.precond ? a.dinv[c] * rp : rp;
             a.r[p] = rp;
             a.z[p] = zp;
-            a.p[p] = zp;
+            a.p[p] = 0.0;
+            a.q[p] = 0.0;
             v[0] += rp * zp;
             v[1] += rp * rp;
             v[2] += bp * bp;
@@ -196,21 +192,23 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
     grid_total<3>(part, 0, tot);
     double rz = tot[0], rr = tot[1];
     const double stop = a.tol2 * tot[2];
+    double beta = 0.0;
     int it = 0;
     bool done = rr <= stop;
     bool bad = !isfinite(rr) || !isfinite(stop);
     while (!done && !bad && it < a.maxit) {
-        // q = A p, partial p.q
+        // [A] p = z + beta p, q = A z + beta q, partial p.q (slot 3)
         {
             double v[1] = {0.0};
             for (int p = tid; p < N; p += stride) {
                 NodeIdx n = node_idx(m, p);
                 int c;
-                double pp;
-                double qp = apply_op(m, a.p, p, n, gih2, &c);
-                pp = __ldcg(a.p + p);
+                const double az = apply_op(m, a.z, p, n, gih2, &c);
+                const double pp = fma(beta, a.p[p], __ldcg(a.z + p));
+                const double qp = fma(beta, a.q[p], az);
+                a.p[p] = pp;
                 a.q[p] = qp;
-                v[0] += pp * qp;
+                v[0] = fma(pp, qp, v[0]);
             }
             block_sum<1>(v, bs);
             if (threadIdx.x == 0) part[3 * gridDim.x + blockIdx.x] = bs[0];
@@ -219,12 +217,12 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
         double pq[1];
         grid_total<1>(part, 3, pq);
         const double alpha = rz / pq[0];
-        // x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z, r.r
+        // [B] x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z, r.r (slots 4, 5)
         {
             double v[2] = {0.0, 0.0};
             for (int p = tid; p < N; p += stride) {
-                double rp = a.r[p] - alpha * a.q[p];
-                a.x[p] += alpha * __ldcg(a.p + p);
+                const double rp = fma(-alpha, a.q[p], a.r[p]);
+                a.x[p] = fma(alpha, a.p[p], a.x[p]);
                 a.r[p] = rp;
                 double zp = rp;
                 if (a.precond) {
@@ -234,8 +232,8 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
                     zp = a.dinv[c] * rp;
                 }
                 a.z[p] = zp;
-                v[0] += rp * zp;
-                v[1] += rp * rp;
+                v[0] = fma(rp, zp, v[0]);
+                v[1] = fma(rp, rp, v[1]);
             }
             block_sum<2>(v, bs);
             if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[(4 + k) * gridDim.x + blockIdx.x] = bs[k];
@@ -243,15 +241,12 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
         if (!grid_barrier(a.bar, a.flags)) return;
         double t2[2];
         grid_total<2>(part, 4, t2);
-        const double beta = t2[0] / rz;
+        beta = t2[0] / rz;
         rz = t2[0];
         rr = t2[1];
         ++it;
         if (!isfinite(rr)) { bad = true; break; }
         if (rr <= stop) { done = true; break; }
-        // p = z + beta p  (own nodes; neighbours are read only after the barrier)
-        for (int p = tid; p < N; p += stride) a.p[p] = fma(beta, __ldcg(a.p + p), a.z[p]);
-        if (!grid_barrier(a.bar, a.flags)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.status[0] = it;

@@ -132,6 +132,28 @@ int esdc_colloc_build(int M, ColloData* out)
         while (t > 2e-17 || n < 4) { ++n; t *= out->X1 / n; }
         out->nser = n;
         if (out->nser + M >= ESDC_NSER) return -1;
+        // ser[m] = 1/((M-1)! m! (m+M))
+        double fm1 = 1.0;
+        for (int k = 2; k < M; ++k) fm1 *= k;
+        double mf = 1.0;
+        for (int m = 0; m <= n; ++m) {
+            if (m > 0) mf *= m;
+            out->ser[m] = 1.0 / (fm1 * mf * (m + M));
+        }
+        // Truncating after term n leaves a relative tail below
+        // X^{n+1} M / ((n+1)! (n+1+M)) (the sum is at least its first term).
+        for (int l = 0; l < 5; ++l) {
+            const double X = out->X1 / (double)(1 << (4 - l));
+            int k = 0;
+            double tail = X * M / (1.0 + M);       // n = 0
+            while (tail > 1e-17 && k < out->nser) {
+                ++k;
+                tail *= X / (k + 1.0) * (k + M) / (k + 1.0 + M);
+            }
+            out->xb[l] = X;
+            out->nb[l] = k;
+        }
+        out->nb[4] = out->nser;
     }
     return 0;
 }

@@ -11,13 +11,16 @@
 // comes from the round-to-nearest "add 1.5*2^52" trick; ln2/64 is split into a
 // 29-bit head and a tail so k * head is exact (|k| < 2^17).  2^m is applied by adding m to
 // the exponent field (an integer operation).  Error: about 1 ulp.
-// Arguments below -707 return 0 (results < 1e-307), above 709.78 return +inf,
-// NaN returns NaN.  Cost: 10 FP64 operations, 1 table load.
+// |x| < 512 takes the fast path (the range test is an integer test on the
+// high word); elsewhere arguments below -707 return 0 (results < 1e-307),
+// above 709.78 return +inf, NaN returns NaN.  Cost: 10 FP64 operations, 1 table
+// load.
 //
-// esdc_rcp: 1/d for finite d with 1e-37 < |d| < 1e300 by two Newton steps
-// r <- r + r (1 - d r) from the FP32 reciprocal (relative error 2^-22 -> 2^-44
-// -> rounding), about 1 ulp.  d >= 1e300 returns 0.  Cost: 4 FP64 operations
-// and two conversions.
+// esdc_rcp: 1/d by two Newton steps r <- r + r (1 - d r) from the FP32
+// reciprocal (relative error 2^-22 -> 2^-44 -> rounding), about 1 ulp, for
+// 2^-99 <= |d| < 2^100 (an integer test on the exponent field); other values
+// (0, tiny, huge, inf, NaN) use the IEEE division.  Cost: 4 FP64 operations and
+// two conversions.
 #pragma once
 #include <cstdint>
 
@@ -43,10 +46,16 @@ static __device__ const double g_exp2_table[64] = {
     0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
 };
 
-__device__ __forceinline__ double esdc_exp(double x)
+static __device__ __noinline__ double esdc_exp_wide(double x)
 {
     if (!(x >= -707.0)) return (x != x) ? x : 0.0;
     if (x > 709.78) return __longlong_as_double(0x7ff0000000000000LL);
+    return exp(x);
+}
+
+__device__ __forceinline__ double esdc_exp(double x)
+{
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x40800000) return esdc_exp_wide(x);   // |x| >= 512 or NaN
     const double kInvL = 0x1.71547652b82fep+6;           // 64 / ln 2
     const double kMagic = 0x1.8p+52;                      // 1.5 * 2^52
     const double kL1 = 0x1.62e42ff000000p-7;              // ln2/64, leading 29 bits
@@ -70,7 +79,8 @@ __device__ __forceinline__ double esdc_exp(double x)
 
 __device__ __forceinline__ double esdc_rcp(double d)
 {
-    if (d >= 1e300) return 0.0;
+    const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+    if (ex - 924u > 198u) return 1.0 / d;
     double r = (double)__frcp_rn((float)d);
     double e = fma(-d, r, 1.0);
     r = fma(r, e, r);

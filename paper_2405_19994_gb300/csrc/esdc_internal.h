@@ -23,6 +23,11 @@ struct ColloData {
     double S0[ESDC_MMAX][ESDC_MMAX];               // a_ij(0) - a_{i-1,j}(0), a_0j = 0
     double X1;                                     // series / recurrence switch for phi_k
     int nser;                                      // terms of the phi_M series
+    // ser[m] = 1/((M-1)! m! (m+M)): phi_M(x) = e^x sum_m ser[m] (-x)^m
+    double ser[ESDC_NSER];
+    // shorter series for smaller |x|: |x| <= xb[l] needs nb[l] terms (l = 0..4)
+    double xb[5];
+    int nb[5];
 };
 
 // Fills ColloData for 1 <= M <= 8.  Returns 0 on success.

@@ -45,6 +45,9 @@ struct StepArgs {
     ModelDev mp;
     int i;                 // collocation node 1..M (k_node), M+1: evaluate G at node M only
     double dt, t_n, D, inv_Cm;
+    double dS0[ESDC_MMAX][ESDC_MMAX];   // dt * (a_ij(0) - a_{i-1,j}(0))
+    double dtd[ESDC_MMAX + 1];          // dt * d_i
+    unsigned stim_on[ESDC_MMAX + 1];    // boxes active at t_{n,j}, j = 0..M (bit b = box b)
     const double* yn;
     double* yout;          // residual kernel: destination of y_{n+1}
     double* Y;
@@ -84,11 +87,13 @@ __device__ __forceinline__ double lap(const MeshDev& m, const double* __restrict
     return s * m.ih2;
 }
 
-__device__ __forceinline__ double stim_at(const StimDev& st, double t, int ix, int iy, int iz)
+// I_stim at a node for the boxes whose time window contains the node's time
+// (the window test t_on <= t < t_off is made once on the host: bit b of `on`).
+__device__ __forceinline__ double stim_at(const StimDev& st, unsigned on, int ix, int iy, int iz)
 {
     double s = 0.0;
     for (int b = 0; b < st.nbox; ++b) {
-        if (t >= st.t_on[b] && t < st.t_off[b] && ix >= st.box[b][0] && ix < st.box[b][1] &&
+        if (((on >> b) & 1u) && ix >= st.box[b][0] && ix < st.box[b][1] &&
             iy >= st.box[b][2] && iy < st.box[b][3] && iz >= st.box[b][4] && iz < st.box[b][5])
             s += st.amp[b];
     }
@@ -96,37 +101,46 @@ __device__ __forceinline__ double stim_at(const StimDev& st, double t, int ix, i
 }
 
 // phi_1..phi_M at x <= 0 (App. A eq. def_phik).  Two regimes:
-//  |x| >  X1: phi_1 = expm1(x)/x, then phi_{k+1} = (phi_k - 1/k!)/x;
-//  |x| <= X1: phi_M = e^x/(M-1)! sum_m (-x)^m/(m! (m+M)) (all terms >= 0),
-//             then phi_k = x phi_{k+1} + 1/k!.
+//  |x| >  X1: phi_1 = (e^x - 1)/x (no cancellation there: X1 > 1.4 for M >= 2),
+//             then phi_{k+1} = (phi_k - 1/k!)/x;
+//  |x| <= X1: phi_M = e^x/(M-1)! sum_m (-x)^m/(m! (m+M)) (all terms >= 0,
+//             Horner form with host coefficients; the number of terms steps
+//             down with |x|), then phi_k = x phi_{k+1} + 1/k!.
 // X1 balances the rounding growth of the two recurrences (set on the host).
+// M = 1: phi_1 = expm1(x)/x.
 template <int M>
 __device__ __forceinline__ void phi_all(double x, double (&ph)[M])
 {
     const ColloData& C = c_col[M - 1];
-    if (M == 1 || -x > C.X1) {
+    if (M == 1) {
         ph[0] = (x == 0.0) ? 1.0 : expm1(x) / x;
-        if (M > 1) {
-            const double rx = 1.0 / x;
+    } else if (-x > C.X1) {
+        const double rx = esdc::esdc_rcp(x);
+        ph[0] = (esdc::esdc_exp(x) - 1.0) * rx;
 #pragma unroll
-            for (int k = 1; k < M; ++k) ph[k] = (ph[k - 1] - c_invfact[k]) * rx;
-        }
+        for (int k = 1; k < M; ++k) ph[k] = (ph[k - 1] - c_invfact[k]) * rx;
     } else {
-        double t = 1.0, acc = 0.0;
-        const int n = C.nser;
-        for (int m = 0; m <= n; ++m) {
-            acc = fma(t, c_inv[m + M], acc);
-            t *= -x * c_inv[m + 1];
-        }
-        ph[M - 1] = exp(x) * acc * c_invfact[M - 1];
+        const double nx = -x;
+        const int n = nx <= C.xb[0] ? C.nb[0] : nx <= C.xb[1] ? C.nb[1] : nx <= C.xb[2] ? C.nb[2]
+                    : nx <= C.xb[3] ? C.nb[3] : C.nb[4];
+        double acc = C.ser[n];
+        for (int m = n - 1; m >= 0; --m) acc = fma(acc, nx, C.ser[m]);
+        ph[M - 1] = esdc::esdc_exp(x) * acc;
 #pragma unroll
         for (int k = M - 1; k >= 1; --k) ph[k - 1] = fma(x, ph[k], c_invfact[k]);
     }
 }
 
+// phi_1(y) = (e^y - 1)/y for y <= 0.
+__device__ __forceinline__ double phi1(double y)
+{
+    if (y < -1.0) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);
+    return (y == 0.0) ? 1.0 : expm1(y) / y;
+}
+
 // ------------------------------------------------------------------ set-up
-// Lambda_n, S_ij(dt Lambda_n), phi_1(d_i dt Lambda_n); y^0 = 1 (x) y_n;
-// G_j^0 = g_n(t_{n,j}, y_n); FI_j^0 = f_I(y_n).
+// Lambda_n, dt S_ij(dt Lambda_n), dt d_i phi_1(d_i dt Lambda_n) (tables carry the
+// step size); y^0 = 1 (x) y_n; G_j^0 = g_n(t_{n,j}, y_n); FI_j^0 = f_I(y_n).
 template <class Model, int M>
 __global__ void __launch_bounds__(128) k_setup(StepArgs a)
 {
@@ -147,8 +161,7 @@ __global__ void __launch_bounds__(128) k_setup(StepArgs a)
         for (int j = 0; j < M; ++j) {
             double* Yj = a.Y + (int64_t)j * NS * ld;
             double* Gj = a.Gnew + (int64_t)j * NS * ld;
-            const double tj = a.t_n + C.c[j + 1] * a.dt;
-            Gj[p] = fi + (stim_at(a.st, tj, ix, iy, iz) + mI) * a.inv_Cm;
+            Gj[p] = fi + (stim_at(a.st, a.stim_on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
             Yj[p] = u[0];
 #pragma unroll
             for (int s = 1; s <= NA; ++s) { Gj[s * ld + p] = ha[s - 1]; Yj[s * ld + p] = u[s]; }
@@ -171,19 +184,14 @@ __global__ void __launch_bounds__(128) k_setup(StepArgs a)
             for (int i = 0; i < M; ++i) {
                 double ph[M];
                 phi_all<M>(C.c[i + 1] * z, ph);
-                double p1;
-                if (i == 0) p1 = ph[0];
-                else {
-                    double t1[1];
-                    phi_all<1>(C.d[i + 1] * z, t1);
-                    p1 = t1[0];
-                }
-                a.PHI[((int64_t)i * NG + g) * ld + p] = p1;
+                const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
+                a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
 #pragma unroll
                 for (int j = 0; j < M; ++j) {
                     double aij = 0.0;
 #pragma unroll
                     for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
+                    aij *= a.dt;                                                 // dt a_ij
                     a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
                     aprev[j] = aij;
                 }
@@ -218,8 +226,7 @@ __global__ void __launch_bounds__(128) k_node(StepArgs a)
             const double fi = a.D * lap(m, Yp, p, ix, iy, iz);
             double mI, ha[NA > 0 ? NA : 1], lam[NG], yinf[NG];
             Model::eval(a.mp.p, u, mI, NA > 0 ? ha : nullptr, lam, yinf);
-            const double tprev = a.t_n + C.c[i - 1] * a.dt;
-            const double fE = (stim_at(a.st, tprev, ix, iy, iz) + mI) * a.inv_Cm;
+            const double fE = (stim_at(a.st, a.stim_on[i - 1], ix, iy, iz) + mI) * a.inv_Cm;
             const double fi_old = a.FI[(int64_t)jm * ld + p];
             a.FI[(int64_t)jm * ld + p] = fi;
             Gq[p] = fi + fE;
@@ -243,37 +250,37 @@ __global__ void __launch_bounds__(128) k_node(StepArgs a)
         }
         if (i > M) continue;
         const int ii = i - 1;                                    // 0-based node index
-        const double dtd = a.dt * C.d[i];
+        const double dtd = a.dtd[i];
         double* Yi = a.Y + (int64_t)ii * NS * ld;
         // V row: right-hand side of (I - dt d_i D L) V_i = rhs
         {
-            double q = 0.0;
+            double q = u[0];
 #pragma unroll
-            for (int j = 0; j < M; ++j) q = fma(C.S0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
-            a.rhs[p] = u[0] + a.dt * q + dtd * (dlt[0] - a.FI[(int64_t)ii * ld + p]);
+            for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
+            a.rhs[p] = fma(dtd, dlt[0] - a.FI[(int64_t)ii * ld + p], q);
         }
 #pragma unroll
         for (int s = 1; s <= NA; ++s) {
-            double q = 0.0;
+            double q = u[s];
 #pragma unroll
-            for (int j = 0; j < M; ++j) q = fma(C.S0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], q);
-            Yi[s * ld + p] = u[s] + a.dt * q + dtd * dlt[s];
+            for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], q);
+            Yi[s * ld + p] = fma(dtd, dlt[s], q);
         }
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             const int s = 1 + NA + g;
-            double q = 0.0;
+            double q = u[s];
 #pragma unroll
             for (int j = 0; j < M; ++j)
                 q = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
                         a.Gold[((int64_t)j * NS + s) * ld + p], q);
-            Yi[s * ld + p] = u[s] + a.dt * q + dtd * a.PHI[((int64_t)ii * NG + g) * ld + p] * dlt[s];
+            Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dlt[s], q);
         }
     }
 }
 
 // ------------------------------------------------------------------ residual + output
-// r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C) with a_ij = sum_{l<=i} S_lj;
+// r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C) with dt a_ij = sum_{l<=i} dt S_lj;
 // per-state max |r| and max |y|; y_{n+1} = y_M.
 template <class Model, int M>
 __global__ void __launch_bounds__(128) k_residual(StepArgs a)
@@ -300,11 +307,11 @@ __global__ void __launch_bounds__(128) k_residual(StepArgs a)
                 double q = 0.0;
 #pragma unroll
                 for (int j = 0; j < M; ++j) {
-                    acoef[j] += (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : C.S0[i][j];
+                    acoef[j] += (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
                     q = fma(acoef[j], a.Gold[((int64_t)j * NS + s) * ld + p], q);
                 }
                 const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
-                const double r = yns + a.dt * q - yi;
+                const double r = (yns + q) - yi;
                 if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
                 bad |= !isfinite(r) || !isfinite(yi);
                 rmax = fmax(rmax, fabs(r));
@@ -495,18 +502,55 @@ int grid_for(const esdc_handle* h, int threads)
     return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
 }
 
+// Grid of a per-node kernel: the resident capacity of the device (blocks per SM
+// from the occupancy calculator x SMs), so that the grid-stride loop spreads the
+// nodes evenly over all SMs in one wave; smaller meshes use one block per 128 nodes.
+template <class F>
+int blocks_per_sm(F kernel, int threads)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm;
+}
+
+int resident_grid(const esdc_handle* h, int per_sm, int threads)
+{
+    long long cap = (long long)h->sms * per_sm;
+    long long need = ((long long)h->mesh.N + threads - 1) / threads;
+    return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
+}
+
 template <class Model, int M>
 cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, cudaStream_t s)
 {
     const int T = 128;
-    const int nb = grid_for(h, T);
+    static int occ_setup = 0, occ_node = 0, occ_res = 0;    // blocks/SM per (model, M) instantiation
+    if (!occ_setup) {
+        occ_node = blocks_per_sm(k_node<Model, M>, T);
+        occ_res = blocks_per_sm(k_residual<Model, M>, T);
+        occ_setup = blocks_per_sm(k_setup<Model, M>, T);
+    }
+    const int nb_setup = resident_grid(h, occ_setup, T);
+    const int nb_node = resident_grid(h, occ_node, T);
+    const int nb_res = resident_grid(h, occ_res, T);
     const double g0 = h->D;   // operator scale: (I - dt d_i D L)
     const ColloData* C = &h->col[M - 1];
 
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) a.dS0[i][j] = a.dt * C->S0[i][j];
+    for (int i = 0; i <= M; ++i) {
+        a.dtd[i] = a.dt * C->d[i];
+        const double tj = a.t_n + C->c[i] * a.dt;
+        unsigned on = 0;
+        for (int b = 0; b < h->stim.nbox; ++b)
+            if (tj >= h->stim.t_on[b] && tj < h->stim.t_off[b]) on |= 1u << b;
+        a.stim_on[i] = on;
+    }
     a.Gnew = h->G0;
     a.Gold = h->G0;
     prof_begin(h, 0, s);
-    k_setup<Model, M><<<nb, T, 0, s>>>(a);
+    k_setup<Model, M><<<nb_setup, T, 0, s>>>(a);
     prof_end(h, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -518,7 +562,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
         for (int i = 1; i <= M + 1; ++i) {
             a.i = i;
             prof_begin(h, 1, s);
-            k_node<Model, M><<<nb, T, 0, s>>>(a);
+            k_node<Model, M><<<nb_node, T, 0, s>>>(a);
             prof_end(h, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (i <= M) {
@@ -537,7 +581,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     a.Gold = Gold;
     a.yout = y;
     prof_begin(h, 3, s);
-    k_residual<Model, M><<<nb, T, 0, s>>>(a);
+    k_residual<Model, M><<<nb_res, T, 0, s>>>(a);
     prof_end(h, s);
     h->last_Gfinal = Gold;
     return cudaGetLastError();
