@@ -31,16 +31,27 @@ sys.path.insert(0, ROOT)
 METRIC = "ES-SDC node-updates/s and s per simulated ms at stated V-error; % roofline"
 UNIT = "node-updates/s"
 
-# Algorithmic work per unit, used for the roofline of the dominant kernel.
-#  node kernel (one collocation node of one sweep, per mesh node), SYN19, M = 4:
-#    reads y_{i-1} (19), G^k_{1..M} (76), FI (2), Lambda_n (12), y_n gates (12),
-#    S row (48), phi_1 row (12); writes G_{i-1} (19), FI (1), y_i (18), rhs (1)
-#    -> 220 doubles = 1760 B.
-#  cg (per mesh node and iteration): p, q (A p); r, q, x, p -> x, r, z; z, p -> p
-#    -> 11 doubles = 88 B, plus one set-up pass of 7 doubles = 56 B per solve.
-NODE_BYTES_PER_NODE = {4: 1760}
-CG_BYTES_PER_NODE_ITER = 88
-CG_BYTES_PER_NODE_SETUP = 56
+# Work per unit, used for the roofline of the dominant kernel.
+#  node kernel (SYN19, M = 4), per mesh node and sweep: the M + 1 launches of a
+#  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
+#  and the final evaluation at node M.  FP64 flops (FMA = 2) from the ncu
+#  thread-op counters of a node-4 launch (1200 flops) and the source for the
+#  other two launch kinds (191 quadrature-only, 1006 evaluation-only):
+#  191 + 3 * 1200 + 1006 = 4797 flops per node per sweep.
+#  Bytes per node and launch (algorithmic): reads y_{i-1} (19), G^k (76), FI (2),
+#  Lambda_n (12), y_n gates (12), S row (48), phi_1 row (12), V guess (2); writes
+#  G_{i-1} (19), FI (1), y_i (18), rhs (1), guess (2) -> 224 doubles = 1792 B.
+#  DRAM traffic of a node-4 launch measured by ncu: 1771 B per node
+#  (profiles/k_node_syn19_slab_128x128x16.md), scaled by the node count.
+#  cg (per mesh node and iteration): [A] z (stencil), p, q -> p, q;
+#  [B] q, r, x, p -> x, r, z: 12 doubles = 96 B, plus 8 doubles per solve.
+NODE_FLOPS_PER_SWEEP = {4: 4797.0}
+NODE_BYTES_PER_NODE = {4: 1792}
+NODE_DRAM_BYTES_PER_NODE_MEASURED = {4: 1771}
+CG_BYTES_PER_NODE_ITER = 96
+CG_BYTES_PER_NODE_SETUP = 64
+# FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def _peaks():
@@ -230,20 +241,27 @@ def run_ours(args):
     peaks = _peaks()
     dom = max(prof, key=lambda k: prof[k][0])
     per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
-    roof = {"kernel": dom, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-            "peak_source": peaks["source"], "traffic": None}
-    if dom == "node":
-        bytes_launch = NODE_BYTES_PER_NODE.get(M, 1760) * N
-    elif dom == "cg":
-        it_mean = sum(cg_iters) / max(len(cg_iters), 1)
-        bytes_launch = (CG_BYTES_PER_NODE_ITER * it_mean + CG_BYTES_PER_NODE_SETUP) * N
+    it_mean = sum(cg_iters) / max(len(cg_iters), 1)
+    roof = {"kernel": dom}
+    if dom == "node" and M in NODE_FLOPS_PER_SWEEP:
+        flops = NODE_FLOPS_PER_SWEEP[M] * N / (M + 1)           # per launch, average over a sweep
+        ach = flops / (per_launch_ms["node"] * 1e-3) / 1e12
+        roof.update({"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                     "frac": ach / FP64_PEAK_TFLOPS,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                                    "(an FMA-chain probe measured 1.20 TFLOP/s)",
+                     "traffic": NODE_DRAM_BYTES_PER_NODE_MEASURED[M] * N,
+                     "algorithmic_bytes": NODE_BYTES_PER_NODE[M] * N,
+                     "hbm_gbs": NODE_BYTES_PER_NODE[M] * N / (per_launch_ms["node"] * 1e-3) / 1e9,
+                     "hbm_peak_gbs": peaks["hbm_gbs"]})
     else:
         bytes_launch = None
-    if bytes_launch and per_launch_ms[dom]:
-        ach = bytes_launch / (per_launch_ms[dom] * 1e-3) / 1e9
-        roof.update({"achieved": ach, "frac": ach / roof["peak"]})
-    else:
-        roof.update({"achieved": None, "frac": None})
+        if dom == "cg":
+            bytes_launch = (CG_BYTES_PER_NODE_ITER * it_mean + CG_BYTES_PER_NODE_SETUP) * N
+        ach = bytes_launch / (per_launch_ms[dom] * 1e-3) / 1e9 if bytes_launch else None
+        roof.update({"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
+                     "frac": ach / peaks["hbm_gbs"] if ach else None, "peak_source": peaks["source"],
+                     "traffic": None})
 
     # ---- CPU oracle baseline on one full-size step from the live state (rank 0, N = 1)
     cpu = None

@@ -18,7 +18,21 @@
 
 namespace {
 
-constexpr unsigned long long kSpinLimit = 1ull << 24;   // ~1-2 s with nanosleep
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // give up a barrier wait after 1 s
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 struct CgArgs {
     MeshDev m;
@@ -28,7 +42,7 @@ struct CgArgs {
     double* x;
     double *r, *p, *q, *z;
     double* part;            // [6][nblocks]: setup r.z, r.r, b.b | p.q | r.z, r.r
-    unsigned* bar;           // count, generation
+    unsigned* bar;           // barrier arrival counter
     int* status;             // [0] iterations, [1] flags
     int* iter_log;
     int* flags;
@@ -37,27 +51,30 @@ struct CgArgs {
     int precond;
 };
 
-// Grid barrier with bounded spin.  Returns false (and raises TIMEOUT) if the
-// wait gave up; the caller must then return from the kernel.
-__device__ bool grid_barrier(unsigned* bar, int* flags)
+// Grid barrier on one monotonic arrival counter (zeroed before the launch):
+// barrier number b is passed once the counter reaches b * gridDim.x.  Thread 0
+// of each block adds its arrival and polls with acquire loads, tightly at
+// first, then with short sleeps; after 1 s of waiting it raises TIMEOUT and
+// returns false, and the caller must return from the kernel.
+__device__ bool grid_barrier(unsigned* bar, unsigned& target, int* flags)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
-        unsigned gen = *vgen;
+        target += gridDim.x;
         __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        atomicAdd(bar, 1u);
         int ok = 1;
-        if (arrived == gridDim.x) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > kSpinLimit) { ok = 0; atomicOr(flags, ESDC_FLAG_TIMEOUT); break; }
-                __nanosleep(64);
+        if (load_acquire(bar) < target) {
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (load_acquire(bar) < target) {
+                if (++spins > 32) __nanosleep(32);
+                if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    atomicOr(flags, ESDC_FLAG_TIMEOUT);
+                    break;
+                }
             }
         }
         __threadfence();
@@ -74,7 +91,7 @@ __device__ bool grid_barrier(unsigned* bar, int* flags)
 template <int NV>
 __device__ void block_sum(double (&v)[NV], double* out)
 {
-    __shared__ double sh[NV][32][17];
+    __shared__ double sh[NV][32][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) sh[k][lane][wid] = v[k];
@@ -156,7 +173,7 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
 // that also completes the reduction for beta:
 //   [A] p = z + beta p; q = A z + beta q; partial p.q        | barrier -> alpha
 //   [B] x += alpha p; r -= alpha q; z = D^{-1} r; r.z, r.r   | barrier -> beta, stop test
-__global__ void __launch_bounds__(512) k_cg(CgArgs a)
+__global__ void __launch_bounds__(1024) k_cg(CgArgs a)
 {
     const MeshDev& m = a.m;
     const int N = m.N;
@@ -165,6 +182,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
     double* part = a.part;
     const double gih2 = a.g * m.ih2;
     __shared__ double bs[3];
+    unsigned target = 0;
 
     // r = b - A x, z = D^{-1} r, p = q = 0; partials r.z, r.r, b.b
     {
@@ -187,7 +205,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
         block_sum<3>(v, bs);
         if (threadIdx.x == 0) for (int k = 0; k < 3; ++k) part[k * gridDim.x + blockIdx.x] = bs[k];
     }
-    if (!grid_barrier(a.bar, a.flags)) return;
+    if (!grid_barrier(a.bar, target, a.flags)) return;
     double tot[3];
     grid_total<3>(part, 0, tot);
     double rz = tot[0], rr = tot[1];
@@ -213,7 +231,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
             block_sum<1>(v, bs);
             if (threadIdx.x == 0) part[3 * gridDim.x + blockIdx.x] = bs[0];
         }
-        if (!grid_barrier(a.bar, a.flags)) return;
+        if (!grid_barrier(a.bar, target, a.flags)) return;
         double pq[1];
         grid_total<1>(part, 3, pq);
         const double alpha = rz / pq[0];
@@ -238,7 +256,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs a)
             block_sum<2>(v, bs);
             if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[(4 + k) * gridDim.x + blockIdx.x] = bs[k];
         }
-        if (!grid_barrier(a.bar, a.flags)) return;
+        if (!grid_barrier(a.bar, target, a.flags)) return;
         double t2[2];
         grid_total<2>(part, 4, t2);
         beta = t2[0] / rz;
@@ -265,7 +283,7 @@ int esdc_cg_blocks(const MeshDev& mesh, int threads)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg, threads, 0) != cudaSuccess) return 0;
     long long want = ((long long)mesh.N + (long long)threads * 2 - 1) / ((long long)threads * 2);
-    long long cap = (long long)sms * (per_sm < 2 ? per_sm : 2);
+    long long cap = (long long)sms * (per_sm < 1 ? per_sm : 1);   // one block per SM
     if (want < 1) want = 1;
     return (int)(want < cap ? want : cap);
 }
@@ -291,8 +309,7 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
     a.precond = precond;
     int nb = w.max_blocks;
     void* args[] = {&a};
-    // The arrival counter is reset before every solve (a previous launch that
-    // timed out may have left it non-zero).
+    // The arrival counter starts from zero in every solve.
     cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void*)k_cg, dim3(nb), dim3(w.threads), args, 0, s);

@@ -44,6 +44,9 @@ struct StepArgs {
     StimDev st;
     ModelDev mp;
     int i;                 // collocation node 1..M (k_node), M+1: evaluate G at node M only
+    int k;                 // sweep index (0-based)
+    double rho;            // warm-start extrapolation weight for node i
+    double* Vprev;         // [ld] V_{i-1}^k, saved before node i-1 was solved
     double dt, t_n, D, inv_Cm;
     double dS0[ESDC_MMAX][ESDC_MMAX];   // dt * (a_ij(0) - a_{i-1,j}(0))
     double dtd[ESDC_MMAX + 1];          // dt * d_i
@@ -252,6 +255,14 @@ __global__ void __launch_bounds__(128) k_node(StepArgs a)
         const int ii = i - 1;                                    // 0-based node index
         const double dtd = a.dtd[i];
         double* Yi = a.Y + (int64_t)ii * NS * ld;
+        // Initial guess of the V_i solve: V_i^k moved by the change the previous
+        // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
+        // starting point of CG changes; the solution is the same.
+        {
+            const double vik = Yi[p];
+            if (i >= 2) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
+            a.Vprev[p] = vik;
+        }
         // V row: right-hand side of (I - dt d_i D L) V_i = rhs
         {
             double q = u[0];
@@ -398,7 +409,7 @@ struct esdc_handle {
     esdc_options opt{};
     // workspace
     double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,
-           *LAMN = nullptr, *rhs = nullptr, *R = nullptr, *ydev = nullptr;
+           *LAMN = nullptr, *rhs = nullptr, *R = nullptr, *ydev = nullptr, *Vprev = nullptr;
     CgWork cg{};
     unsigned long long* rmax = nullptr;   // [2*NS]
     int* flags = nullptr;                 // [1]
@@ -561,6 +572,9 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
         a.Gnew = Gnew;
         for (int i = 1; i <= M + 1; ++i) {
             a.i = i;
+            a.k = k;
+            // first sweep: y^0 = y_n, so the change grows with the node time c_i
+            a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
             prof_begin(h, 1, s);
             k_node<Model, M><<<nb_node, T, 0, s>>>(a);
             prof_end(h, s);
@@ -607,7 +621,7 @@ void free_all(esdc_handle* h)
 {
     for (auto& e : h->prof_ev)
         if (e) cudaEventDestroy(e);
-    void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev,
+    void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev, h->Vprev,
                     h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.part, h->cg.bar, h->cg.status,
                     h->rmax, h->flags, h->cg_log};
     for (void* p : ptrs)
@@ -693,13 +707,14 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     struct { double** p; int64_t n; } bufs[] = {
         {&h->Y, Mx * NS * ld}, {&h->G0, Mx * NS * ld}, {&h->G1, Mx * NS * ld}, {&h->FI, Mx * ld},
         {&h->S, Mx * Mx * NG * ld}, {&h->PHI, Mx * NG * ld}, {&h->LAMN, NG * ld}, {&h->rhs, ld},
+        {&h->Vprev, ld},
         {&h->cg.r, ld}, {&h->cg.p, ld}, {&h->cg.q, ld}, {&h->cg.z, ld}};
     for (auto& b : bufs) {
         cudaError_t e = cudaMalloc((void**)b.p, sizeof(double) * b.n);
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA);
         cudaMemset(*b.p, 0, sizeof(double) * b.n);
     }
-    h->cg.threads = 512;
+    h->cg.threads = 1024;
     h->cg.max_blocks = esdc_cg_blocks(h->mesh, h->cg.threads);
     if (h->cg.max_blocks < 1) return fail(ESDC_ERR_CUDA);
     if (cudaMalloc((void**)&h->cg.part, sizeof(double) * 6 * h->cg.max_blocks) != cudaSuccess ||
@@ -782,7 +797,7 @@ int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, voi
     a.m = h->mesh; a.st = h->stim; a.mp = h->mp;
     a.dt = dt; a.t_n = t; a.D = h->D; a.inv_Cm = 1.0 / h->Cm;
     a.yn = y; a.Y = h->Y; a.FI = h->FI; a.S = h->S; a.PHI = h->PHI; a.LAMN = h->LAMN; a.rhs = h->rhs;
-    a.R = h->R; a.rmax = h->rmax; a.flags = h->flags;
+    a.R = h->R; a.rmax = h->rmax; a.flags = h->flags; a.Vprev = h->Vprev;
     cudaError_t e = h->model == ESDC_MODEL_HH1952 ? dispatch_M<esdc::HH1952>(h, a, y, M, K, s)
                                                   : dispatch_M<esdc::SYN19>(h, a, y, M, K, s);
     if (e != cudaSuccess) return set_err(h, ESDC_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
