@@ -48,6 +48,7 @@ extern "C" {
 #define ESDC_ERR_DEVICE_TIMEOUT    -5   /* a bounded device-side wait gave up          */
 #define ESDC_ERR_UNSUPPORTED       -6   /* valid but not implemented combination       */
 #define ESDC_ERR_NO_MEMORY         -7   /* device allocation failed                    */
+#define ESDC_ERR_TOO_LARGE         -8   /* mesh exceeds esdc_diffusion_solve_static's fixed scratch */
 
 /* Ionic models (Sec. 5).  Parameters are passed explicitly to esdc_create:
  *  ESDC_MODEL_HH1952: Hodgkin-Huxley 1952, states (V, m, h, n) (m_1 = 0,
@@ -222,6 +223,36 @@ int esdc_ionic(esdc_handle* h, const double* y, double* fE, double* lam, double*
  * ex[e] = e^{x[e]}, rc[e] = 1/x[e].  Not part of the method.
  */
 int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* stream);
+
+/*
+ * Allocation-free diffusion solve (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory, e.g. code that
+ * runs inside a memory-pool or allocator callback, in a process whose device
+ * memory another framework has reserved up front, or in a loop that must not
+ * enter the allocator after start-up; such callers cannot call esdc_create).
+ *
+ * Solves (I - g L) x = b on `mesh` like esdc_diffusion_solve (same kernel,
+ * Jacobi-preconditioned when precond != 0, stop at ||r|| <= tol ||b||, at most
+ * maxit iterations; x holds the initial guess on entry), but needs no handle and
+ * allocates nothing: its scratch (CG vectors, block partial sums, barrier
+ * counter) lives in one fixed array compiled into the library, of
+ * ESDC_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library holds
+ * until the process exits.  b and x are caller-owned device arrays of
+ * nx*ny*nz doubles.  iters (host, optional) receives the iteration count; the
+ * call synchronises `stream`.
+ * Limits and rules:
+ *   - meshes with more than ESDC_STATIC_MAX_NODES nodes return ESDC_ERR_TOO_LARGE;
+ *   - all calls share the scratch array: calls whose GPU work overlaps (other
+ *     streams, other host threads) race on it and must be serialised;
+ *   - the first call on each device looks up the array's device address with
+ *     cudaGetSymbolAddress, so make it before any stream capture begins.
+ * Returns ESDC_OK, ESDC_ERR_INVALID_ARG, ESDC_ERR_TOO_LARGE, ESDC_ERR_CUDA,
+ * ESDC_ERR_CG_NOT_CONVERGED, ESDC_ERR_NONFINITE or ESDC_ERR_DEVICE_TIMEOUT.
+ */
+#define ESDC_STATIC_MAX_NODES 262144
+#define ESDC_STATIC_SCRATCH_BYTES ((4LL * ESDC_STATIC_MAX_NODES + 6 * 1024 + 32) * 8)
+int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, const double* b, double* x,
+                                double tol, int maxit, int precond, int* iters, void* stream);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libesdc.so")
 
 ESDC_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "CG_NOT_CONVERGED", -4: "NONFINITE",
-          -5: "DEVICE_TIMEOUT", -6: "UNSUPPORTED", -7: "NO_MEMORY"}
+          -5: "DEVICE_TIMEOUT", -6: "UNSUPPORTED", -7: "NO_MEMORY", -8: "TOO_LARGE"}
 MODEL_HH1952, MODEL_SYN19 = 0, 1
 
 
@@ -70,6 +70,8 @@ def lib() -> C.CDLL:
             "esdc_diffusion_solve": (C.c_int, [_VP, _D, _VP, _VP, C.POINTER(C.c_int), _VP]),
             "esdc_ionic": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
             "esdc_math_check": (C.c_int, [_VP, _I64, _VP, _VP, _VP]),
+            "esdc_diffusion_solve_static": (C.c_int, [C.POINTER(esdc_mesh), _D, _VP, _VP, _D, C.c_int, C.c_int,
+                                                      C.POINTER(C.c_int), _VP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
