@@ -34,20 +34,18 @@ UNIT = "node-updates/s"
 # Work per unit, used for the roofline of the dominant kernel.
 #  node kernel (SYN19, M = 4), per mesh node and sweep: the M + 1 launches of a
 #  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
-#  and the final evaluation at node M.  FP64 flops (FMA = 2) from the ncu
-#  thread-op counters of a node-4 launch (1200 flops) and the source for the
-#  other two launch kinds (191 quadrature-only, 1006 evaluation-only):
-#  191 + 3 * 1200 + 1006 = 4797 flops per node per sweep.
-#  Bytes per node and launch (algorithmic): reads y_{i-1} (19), G^k (76), FI (2),
-#  Lambda_n (12), y_n gates (12), S row (48), phi_1 row (12), V guess (2); writes
-#  G_{i-1} (19), FI (1), y_i (18), rhs (1), guess (2) -> 224 doubles = 1792 B.
-#  DRAM traffic of a node-4 launch measured by ncu: 1771 B per node
-#  (profiles/k_node_syn19_slab_128x128x16.md), scaled by the node count.
+#  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu
+#  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep:
+#  191.0 + 3 x 1200.7 + 988.7 = 4781.8 flops per node per sweep
+#  (profiles/k_node_syn19_slab_128x128x16.md).
+#  Algorithmic bytes per node: node 1 reads 158 / writes 20 doubles, nodes 2..M
+#  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep, 1493 B per launch
+#  on average; DRAM traffic measured by ncu: 7045 B per sweep (1409 B per launch).
 #  cg (per mesh node and iteration): [A] z (stencil), p, q -> p, q;
 #  [B] q, r, x, p -> x, r, z: 12 doubles = 96 B, plus 8 doubles per solve.
-NODE_FLOPS_PER_SWEEP = {4: 4797.0}
-NODE_BYTES_PER_NODE = {4: 1792}
-NODE_DRAM_BYTES_PER_NODE_MEASURED = {4: 1771}
+NODE_FLOPS_PER_SWEEP = {4: 4781.8}
+NODE_BYTES_PER_LAUNCH = {4: 1493}
+NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {4: 1409}
 CG_BYTES_PER_NODE_ITER = 96
 CG_BYTES_PER_NODE_SETUP = 64
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.
@@ -250,9 +248,9 @@ def run_ours(args):
                      "frac": ach / FP64_PEAK_TFLOPS,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                     "(an FMA-chain probe measured 1.20 TFLOP/s)",
-                     "traffic": NODE_DRAM_BYTES_PER_NODE_MEASURED[M] * N,
-                     "algorithmic_bytes": NODE_BYTES_PER_NODE[M] * N,
-                     "hbm_gbs": NODE_BYTES_PER_NODE[M] * N / (per_launch_ms["node"] * 1e-3) / 1e9,
+                     "traffic": NODE_DRAM_BYTES_PER_LAUNCH_MEASURED[M] * N,
+                     "algorithmic_bytes": NODE_BYTES_PER_LAUNCH[M] * N,
+                     "hbm_gbs": NODE_BYTES_PER_LAUNCH[M] * N / (per_launch_ms["node"] * 1e-3) / 1e9,
                      "hbm_peak_gbs": peaks["hbm_gbs"]})
     else:
         bytes_launch = None

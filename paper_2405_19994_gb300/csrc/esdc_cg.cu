@@ -173,8 +173,14 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
 // that also completes the reduction for beta:
 //   [A] p = z + beta p; q = A z + beta q; partial p.q        | barrier -> alpha
 //   [B] x += alpha p; r -= alpha q; z = D^{-1} r; r.z, r.r   | barrier -> beta, stop test
-__global__ void __launch_bounds__(1024) k_cg(CgArgs a)
+// Each thread handles ESDC_CG_UNROLL nodes per pass of its grid-stride loop and
+// issues all their loads before the arithmetic, so their L2 latencies overlap.
+#ifndef ESDC_CG_UNROLL
+#define ESDC_CG_UNROLL 2        // best of 1/2/4/8 on GB300 (with 512-thread blocks)
+#endif
+__global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
 {
+    constexpr int U = ESDC_CG_UNROLL;
     const MeshDev& m = a.m;
     const int N = m.N;
     const int stride = gridDim.x * blockDim.x;
@@ -218,15 +224,31 @@ __global__ void __launch_bounds__(1024) k_cg(CgArgs a)
         // [A] p = z + beta p, q = A z + beta q, partial p.q (slot 3)
         {
             double v[1] = {0.0};
-            for (int p = tid; p < N; p += stride) {
-                NodeIdx n = node_idx(m, p);
-                int c;
-                const double az = apply_op(m, a.z, p, n, gih2, &c);
-                const double pp = fma(beta, a.p[p], __ldcg(a.z + p));
-                const double qp = fma(beta, a.q[p], az);
-                a.p[p] = pp;
-                a.q[p] = qp;
-                v[0] = fma(pp, qp, v[0]);
+            for (int p0 = tid; p0 < N; p0 += U * stride) {
+                double az[U], zp[U], po[U], qo[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * stride;
+                    if (p < N) {
+                        NodeIdx n = node_idx(m, p);
+                        int c;
+                        az[u] = apply_op(m, a.z, p, n, gih2, &c);
+                        zp[u] = __ldcg(a.z + p);
+                        po[u] = a.p[p];
+                        qo[u] = a.q[p];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * stride;
+                    if (p < N) {
+                        const double pp = fma(beta, po[u], zp[u]);
+                        const double qp = fma(beta, qo[u], az[u]);
+                        a.p[p] = pp;
+                        a.q[p] = qp;
+                        v[0] = fma(pp, qp, v[0]);
+                    }
+                }
             }
             block_sum<1>(v, bs);
             if (threadIdx.x == 0) part[3 * gridDim.x + blockIdx.x] = bs[0];
@@ -238,20 +260,32 @@ __global__ void __launch_bounds__(1024) k_cg(CgArgs a)
         // [B] x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z, r.r (slots 4, 5)
         {
             double v[2] = {0.0, 0.0};
-            for (int p = tid; p < N; p += stride) {
-                const double rp = fma(-alpha, a.q[p], a.r[p]);
-                a.x[p] = fma(alpha, a.p[p], a.x[p]);
-                a.r[p] = rp;
-                double zp = rp;
-                if (a.precond) {
-                    NodeIdx n = node_idx(m, p);
-                    int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
-                            (n.iz > 0) + (n.iz < m.nz - 1);
-                    zp = a.dinv[c] * rp;
+            for (int p0 = tid; p0 < N; p0 += U * stride) {
+                double qv[U], rv[U], xv[U], pv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * stride;
+                    if (p < N) { qv[u] = a.q[p]; rv[u] = a.r[p]; xv[u] = a.x[p]; pv[u] = a.p[p]; }
                 }
-                a.z[p] = zp;
-                v[0] = fma(rp, zp, v[0]);
-                v[1] = fma(rp, rp, v[1]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * stride;
+                    if (p < N) {
+                        const double rp = fma(-alpha, qv[u], rv[u]);
+                        a.x[p] = fma(alpha, pv[u], xv[u]);
+                        a.r[p] = rp;
+                        double zq = rp;
+                        if (a.precond) {
+                            NodeIdx n = node_idx(m, p);
+                            int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
+                                    (n.iz > 0) + (n.iz < m.nz - 1);
+                            zq = a.dinv[c] * rp;
+                        }
+                        a.z[p] = zq;
+                        v[0] = fma(rp, zq, v[0]);
+                        v[1] = fma(rp, rp, v[1]);
+                    }
+                }
             }
             block_sum<2>(v, bs);
             if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[(4 + k) * gridDim.x + blockIdx.x] = bs[k];

@@ -12,6 +12,9 @@
 #define ESDC_MAXBOX 16     // stimulus boxes
 #define ESDC_NSER 48       // reciprocal table length for the phi_k series
 #define ESDC_PROF_CLASSES 4  // esdc_profile kernel classes
+#ifndef ESDC_CG_THREADS
+#define ESDC_CG_THREADS 512    // threads per CG block (one block per SM)
+#endif
 
 // Collocation data of one M (Sec. 3.1.2, App. A), computed on the host once.
 struct ColloData {

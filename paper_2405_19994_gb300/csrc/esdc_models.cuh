@@ -1,5 +1,7 @@
 // Pointwise ionic models on the device (eq. monodomain; gates in the form of
-// eq. monodomain_g_lambda).  Each model evaluates, for one mesh node u:
+// eq. monodomain_g_lambda).  eval() returns everything at once; currents() and
+// gate() return the same numbers piecewise, so that a kernel can use each gate's
+// rate as soon as it is computed.  For one mesh node u:
 //   mI   = -I_ion(u)                               [uA/mm^2]
 //   ha   = h_a(u)   (NA auxiliary derivatives)
 //   lam  = Lambda_g(V) = -(alpha + beta)           (NG gates)
@@ -40,6 +42,26 @@ struct HH1952 {
         lam[0] = -sm; yinf[0] = am / sm;
         lam[1] = -sh; yinf[1] = ah / sh;
         lam[2] = -sn; yinf[2] = an / sn;
+    }
+    // -I_ion only (the currents need the gate values, not their rates).
+    __device__ static void currents(const double* __restrict__ mp, const double* u, double& mI, double* ha)
+    {
+        (void)ha;
+        const double V = u[0], m = u[1], h = u[2], n = u[3];
+        const double m3h = m * m * m * h, n2 = n * n;
+        mI = -(mp[0] * m3h * (V - mp[3]) + mp[1] * n2 * n2 * (V - mp[4]) + mp[2] * (V - mp[5]));
+    }
+    // Lambda_g and w_g,inf of gate q (0 = m, 1 = h, 2 = n) at potential V.
+    __device__ static void gate(const double* __restrict__ mp, int q, double V, double& lam, double& yinf)
+    {
+        const double v = V - mp[6];
+        double al, be;
+        if (q == 0) { al = x_over_expm1((25.0 - v) * 0.1); be = 4.0 * exp(v * (-1.0 / 18.0)); }
+        else if (q == 1) { al = 0.07 * exp(v * (-0.05)); be = 1.0 / (exp((30.0 - v) * 0.1) + 1.0); }
+        else { al = 0.1 * x_over_expm1((10.0 - v) * 0.1); be = 0.125 * exp(v * (-0.0125)); }
+        const double sum = al + be;
+        lam = -sum;
+        yinf = al / sum;
     }
     // Resting state at V0: gates at w_inf(V0).
     __device__ static void rest(const double* mp, double V0, double* u)
@@ -97,6 +119,34 @@ struct SYN19 {
             ha[4] = (a[3] - a[4]) * itau[4];
             ha[5] = (a[4] - a[5]) * itau[5];
         }
+    }
+    __device__ static void currents(const double* __restrict__ mp, const double* u, double& mI, double* ha)
+    {
+        const double V = u[0];
+        const double* a = u + 1;
+        const double* g = u + 7;
+        const double* c = mp + 72;
+        const double If = c[0] * g[0] * g[1] * g[2] * a[0] * (V - c[1]);
+        const double Is = c[2] * g[3] * g[4] * a[2] * (V - c[3]);
+        const double IK = c[4] * a[1] * (1.0 + c[9] * a[5]) * (V - c[5]);
+        const double IK1 = c[6] * g[6] * g[7] * (V - c[5]);
+        const double Ib = c[7] * 0.25 * (g[8] + g[9] + g[10] + g[11]) * (V - c[8]);
+        mI = -(If + Is + IK + IK1 + Ib);
+        const double* itau = mp + 112;
+        ha[0] = ((1.0 - g[5]) - a[0]) * itau[0];
+        ha[1] = (g[5] - a[1]) * itau[1];
+        ha[2] = ((1.0 - g[5]) - a[2]) * itau[2];
+        ha[3] = (g[3] * g[4] - a[3]) * itau[3];
+        ha[4] = (a[3] - a[4]) * itau[4];
+        ha[5] = (a[4] - a[5]) * itau[5];
+    }
+    __device__ static void gate(const double* __restrict__ mp, int q, double V, double& lam, double& yinf)
+    {
+        const double* p = mp + 6 * q;
+        const double* inv = mp + 88;
+        yinf = esdc_rcp(1.0 + esdc_exp((p[0] - V) * inv[q]));
+        const double s = esdc_rcp(1.0 + esdc_exp((p[4] - V) * inv[12 + q]));
+        lam = -p[2] * esdc_exp(p[3] * s);
     }
     __device__ static void rest(const double* mp, double V0, double* u)
     {

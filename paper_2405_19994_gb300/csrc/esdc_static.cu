@@ -92,7 +92,7 @@ extern "C" int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, cons
     w.bar = reinterpret_cast<unsigned*>(ctl);              // barrier counter (zeroed per solve by the launch)
     w.status = reinterpret_cast<int*>(ctl + 1);            // [0] iterations, [1] spare
     int* flags = reinterpret_cast<int*>(ctl + 2);          // error flags, cleared below
-    w.threads = 1024;
+    w.threads = ESDC_CG_THREADS;
     w.max_blocks = esdc_cg_blocks(m, w.threads);
     if (w.max_blocks < 1) return ESDC_ERR_CUDA;
     if (w.max_blocks > kMaxBlocks) w.max_blocks = kMaxBlocks;

@@ -206,92 +206,95 @@ __global__ void __launch_bounds__(128) k_setup(StepArgs a)
 // ------------------------------------------------------------------ sweep node i
 // i in 1..M: ionic evaluation at y_{i-1}^{k+1} (i >= 2), G_{i-1}^{k+1}, FI_{i-1}^{k+1},
 // explicit rows (auxiliaries, gates) of y_i^{k+1} and the right-hand side of the
-// V row.  i == M+1: only the evaluation at y_M^{k+1}.
+// V row.  i == M+1: only the evaluation at y_M^{k+1}.  Each gate's rate is used
+// as soon as it is computed (its G, Delta and update), which keeps few values live.
+#ifndef ESDC_NODE_MINBLOCKS
+#define ESDC_NODE_MINBLOCKS 5      // 5 x 128 threads per SM: at most 102 registers
+#endif
 template <class Model, int M>
-__global__ void __launch_bounds__(128) k_node(StepArgs a)
+__global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
     const MeshDev& m = a.m;
-    const ColloData& C = c_col[M - 1];
     const int64_t ld = m.ld;
     const int i = a.i;
+    const bool eval = i >= 2;                 // G at y_{i-1}^{k+1}
+    const bool quad = i <= M;                 // explicit rows of y_i^{k+1}
+    const int jm = i - 2;                     // 0-based index of node i-1
+    const int ii = i - 1;                     // 0-based index of node i
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
         int ix, iy, iz;
         node_xyz(m, p, ix, iy, iz);
-        double u[NS], dlt[NS];
-        if (i >= 2) {
-            const int jm = i - 2;                                // 0-based index of node i-1
-            const double* Yp = a.Y + (int64_t)jm * NS * ld;
-            const double* Gp = a.Gold + (int64_t)jm * NS * ld;
-            double* Gq = a.Gnew + (int64_t)jm * NS * ld;
+        const double* src = eval ? a.Y + (int64_t)jm * NS * ld : a.yn;   // y_{i-1}^{k+1}
+        double u[NS];
 #pragma unroll
-            for (int s = 0; s < NS; ++s) u[s] = Yp[s * ld + p];
-            const double fi = a.D * lap(m, Yp, p, ix, iy, iz);
-            double mI, ha[NA > 0 ? NA : 1], lam[NG], yinf[NG];
-            Model::eval(a.mp.p, u, mI, NA > 0 ? ha : nullptr, lam, yinf);
+        for (int s = 0; s < NS; ++s) u[s] = src[s * ld + p];
+        const double* Gp = a.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
+        double* Gq = a.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
+        double* Yi = a.Y + (int64_t)ii * NS * ld;
+        const double dtd = quad ? a.dtd[i] : 0.0;
+
+        // ---- V row and auxiliaries
+        double dlt0 = 0.0, ha[NA > 0 ? NA : 1];
+        if (eval) {
+            const double fi = a.D * lap(m, src, p, ix, iy, iz);
+            double mI;
+            Model::currents(a.mp.p, u, mI, ha);
             const double fE = (stim_at(a.st, a.stim_on[i - 1], ix, iy, iz) + mI) * a.inv_Cm;
             const double fi_old = a.FI[(int64_t)jm * ld + p];
             a.FI[(int64_t)jm * ld + p] = fi;
             Gq[p] = fi + fE;
-            dlt[0] = fE - (Gp[p] - fi_old);
+            dlt0 = fE - (Gp[p] - fi_old);
 #pragma unroll
-            for (int s = 1; s <= NA; ++s) {
-                Gq[s * ld + p] = ha[s - 1];
-                dlt[s] = ha[s - 1] - Gp[s * ld + p];
-            }
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                const int s = 1 + NA + g;
-                const double gn = lam[g] * (u[s] - yinf[g]) +
-                                  a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
-                Gq[s * ld + p] = gn;
-                dlt[s] = gn - Gp[s * ld + p];
-            }
-        } else {
-#pragma unroll
-            for (int s = 0; s < NS; ++s) { u[s] = a.yn[s * ld + p]; dlt[s] = 0.0; }
+            for (int s = 1; s <= NA; ++s) Gq[s * ld + p] = ha[s - 1];
         }
-        if (i > M) continue;
-        const int ii = i - 1;                                    // 0-based node index
-        const double dtd = a.dtd[i];
-        double* Yi = a.Y + (int64_t)ii * NS * ld;
-        // Initial guess of the V_i solve: V_i^k moved by the change the previous
-        // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
-        // starting point of CG changes; the solution is the same.
-        {
+        if (quad) {
+            // Initial guess of the V_i solve: V_i^k moved by the change the previous
+            // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
+            // starting point of CG changes; the solution is the same.
             const double vik = Yi[p];
-            if (i >= 2) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
+            if (eval) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
             a.Vprev[p] = vik;
-        }
-        // V row: right-hand side of (I - dt d_i D L) V_i = rhs
-        {
             double q = u[0];
 #pragma unroll
             for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
-            a.rhs[p] = fma(dtd, dlt[0] - a.FI[(int64_t)ii * ld + p], q);
-        }
+            a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
 #pragma unroll
-        for (int s = 1; s <= NA; ++s) {
-            double q = u[s];
+            for (int s = 1; s <= NA; ++s) {
+                const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
+                double qa = u[s];
 #pragma unroll
-            for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], q);
-            Yi[s * ld + p] = fma(dtd, dlt[s], q);
+                for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
+                Yi[s * ld + p] = fma(dtd, dl, qa);
+            }
         }
+        // ---- gates, one at a time
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             const int s = 1 + NA + g;
-            double q = u[s];
+            double dl = 0.0;
+            if (eval) {
+                double lam, yinf;
+                Model::gate(a.mp.p, g, u[0], lam, yinf);
+                const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
+                Gq[s * ld + p] = gn;
+                dl = gn - Gp[s * ld + p];
+            }
+            if (quad) {
+                double qg = u[s];
 #pragma unroll
-            for (int j = 0; j < M; ++j)
-                q = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
-                        a.Gold[((int64_t)j * NS + s) * ld + p], q);
-            Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dlt[s], q);
+                for (int j = 0; j < M; ++j)
+                    qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
+                             a.Gold[((int64_t)j * NS + s) * ld + p], qg);
+                Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
+            }
         }
     }
 }
 
 // ------------------------------------------------------------------ residual + output
-// r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C) with dt a_ij = sum_{l<=i} dt S_lj;
+// r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C), accumulated over i from the row
+// differences dt S_ij = dt (a_ij - a_{i-1,j});
 // per-state max |r| and max |y|; y_{n+1} = y_M.
 template <class Model, int M>
 __global__ void __launch_bounds__(128) k_residual(StepArgs a)
@@ -310,19 +313,19 @@ __global__ void __launch_bounds__(128) k_residual(StepArgs a)
             const int g = s - 1 - NA;
             const double yns = a.yn[s * ld + p];
             double ymax = fabs(yns), rmax = 0.0;
-            double acoef[M];
-#pragma unroll
-            for (int j = 0; j < M; ++j) acoef[j] = 0.0;
+            // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
+            double r = 0.0, yprev = yns;
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 double q = 0.0;
 #pragma unroll
                 for (int j = 0; j < M; ++j) {
-                    acoef[j] += (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
-                    q = fma(acoef[j], a.Gold[((int64_t)j * NS + s) * ld + p], q);
+                    const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
+                    q = fma(sij, a.Gold[((int64_t)j * NS + s) * ld + p], q);
                 }
                 const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
-                const double r = (yns + q) - yi;
+                r += q - (yi - yprev);
+                yprev = yi;
                 if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
                 bad |= !isfinite(r) || !isfinite(yi);
                 rmax = fmax(rmax, fabs(r));
@@ -714,7 +717,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA);
         cudaMemset(*b.p, 0, sizeof(double) * b.n);
     }
-    h->cg.threads = 1024;
+    h->cg.threads = ESDC_CG_THREADS;
     h->cg.max_blocks = esdc_cg_blocks(h->mesh, h->cg.threads);
     if (h->cg.max_blocks < 1) return fail(ESDC_ERR_CUDA);
     if (cudaMalloc((void**)&h->cg.part, sizeof(double) * 6 * h->cg.max_blocks) != cudaSuccess ||
