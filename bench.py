@@ -178,7 +178,7 @@ def run_ours(args):
         wl = wl.with_mesh(wl.nx, wl.ny, args.nz)
     M, K, dt = wl.M, wl.K, wl.dt
     N = wl.n_nodes
-    solver = P.Solver.from_workload(wl, M_max=M)
+    solver = P.Solver.from_workload(wl, M_max=M, precision=args.precision)
     y = solver.new_state()
     solver.init_state(y, wl.V0)
     stream = torch.cuda.current_stream()
@@ -241,7 +241,7 @@ def run_ours(args):
     per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
     it_mean = sum(cg_iters) / max(len(cg_iters), 1)
     roof = {"kernel": dom}
-    if dom == "node" and M in NODE_FLOPS_PER_SWEEP:
+    if dom == "node" and M in NODE_FLOPS_PER_SWEEP and args.precision == "fp64":
         flops = NODE_FLOPS_PER_SWEEP[M] * N / (M + 1)           # per launch, average over a sweep
         ach = flops / (per_launch_ms["node"] * 1e-3) / 1e12
         roof.update({"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
@@ -256,6 +256,8 @@ def run_ours(args):
         bytes_launch = None
         if dom == "cg":
             bytes_launch = (CG_BYTES_PER_NODE_ITER * it_mean + CG_BYTES_PER_NODE_SETUP) * N
+        elif dom == "node":
+            bytes_launch = NODE_BYTES_PER_LAUNCH.get(M, 1493) * N
         ach = bytes_launch / (per_launch_ms[dom] * 1e-3) / 1e9 if bytes_launch else None
         roof.update({"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
                      "frac": ach / peaks["hbm_gbs"] if ach else None, "peak_source": peaks["source"],
@@ -278,13 +280,23 @@ def run_ours(args):
                "sample": f"one HSDC step of the full {wl.nx}x{wl.ny}x{wl.nz} slab at t={t:.2f} ms"}
         verr = {"V_max_rel_vs_oracle_one_step": float(np.abs(g1[0] - want[0]).max() / np.abs(want[0]).max()),
                 "state_max_abs_vs_oracle_one_step": float(np.abs(g1 - want).max())}
+        if args.precision != "fp64":
+            ref64 = P.Solver.from_workload(wl, M_max=M)
+            y64 = y.clone()
+            y64[:, :N] = torch.from_numpy(yh).cuda()
+            ref64.sweep(y64, t, dt, M, K)
+            g64 = y64[:, :N].cpu().numpy()
+            verr["V_max_rel_vs_fp64_gpu_one_step"] = float(np.abs(g1[0] - g64[0]).max() / np.abs(g64[0]).max())
+            ref64.close()
 
     launches = int(sum(v[1] for v in prof.values()))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
         "config": {"workload": wl.name, "nodes": N, "n_state": wl.n_state, "M": M, "K": K, "dt_ms": dt,
+                   "precision": args.precision,
                    "model": "syn19 (seed 20240530)", "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (state + workspace ~2 GB per GPU)",
                    "window_ms": [args.warmup * dt, (args.warmup + args.steps) * dt]},
@@ -315,6 +327,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=32, help="slab depth (32 = the benchmark workload)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -78,9 +78,14 @@ typedef struct {
     double tol_cg;     /* relative 2-norm stop ||r|| <= tol_cg ||b|| of each solve */
     int    cg_maxit;   /* iteration cap of each solve (>= 1)                       */
     int    precond;    /* 1 = Jacobi-preconditioned CG, 0 = plain CG               */
+    int    precision;  /* 0 = FP64 throughout; 1 = precision form: the ionic model
+                          (f_E, Lambda, y_inf) evaluated in FP32, everything else
+                          (state, coefficient tables, quadrature, solves, residual)
+                          in FP64                                                  */
 } esdc_options;
 
-/* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1. */
+/* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1,
+ * precision 0. */
 void esdc_default_options(esdc_options* opt);
 
 /*

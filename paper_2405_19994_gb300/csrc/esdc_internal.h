@@ -54,6 +54,10 @@ struct ModelDev {
     double p[ESDC_NPMAX];
 };
 
+struct ModelDevF {            // FP32 copy of the parameters (precision form)
+    float p[ESDC_NPMAX];
+};
+
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
 struct CgWork {
     double *r, *p, *q, *z;          // [ld] each

@@ -1,0 +1,462 @@
+// Device side of the HSDC step, shared by the translation units that
+// instantiate it (esdc_step.cu: FP64; esdc_step_mixed.cu: precision form).
+#pragma once
+#include <cmath>
+
+#include "esdc_handle.h"
+#include "esdc_models.cuh"
+
+namespace {
+
+// Each translation unit that includes this header owns a copy of these
+// constants and uploads it with upload_constants_local().
+static __constant__ ColloData c_col[ESDC_MMAX];     // index M-1
+static __constant__ double c_inv[ESDC_NSER];        // c_inv[m] = 1/m (c_inv[0] unused)
+static __constant__ double c_invfact[ESDC_MMAX + 2];
+
+
+
+__device__ __forceinline__ void node_xyz(const MeshDev& m, int p, int& ix, int& iy, int& iz)
+{
+    int r = p / m.nx;
+    ix = p - r * m.nx;
+    iz = r / m.ny;
+    iy = r - iz * m.ny;
+}
+
+// L v at node p: (1/h^2) sum over in-domain neighbours of (v_q - v_p).
+__device__ __forceinline__ double lap(const MeshDev& m, const double* __restrict__ v, int p,
+                                      int ix, int iy, int iz)
+{
+    const double vp = v[p];
+    const int sxy = m.nx * m.ny;
+    double s = 0.0;
+    if (ix > 0)        s += v[p - 1] - vp;
+    if (ix < m.nx - 1) s += v[p + 1] - vp;
+    if (iy > 0)        s += v[p - m.nx] - vp;
+    if (iy < m.ny - 1) s += v[p + m.nx] - vp;
+    if (iz > 0)        s += v[p - sxy] - vp;
+    if (iz < m.nz - 1) s += v[p + sxy] - vp;
+    return s * m.ih2;
+}
+
+// I_stim at a node for the boxes whose time window contains the node's time
+// (the window test t_on <= t < t_off is made once on the host: bit b of `on`).
+__device__ __forceinline__ double stim_at(const StimDev& st, unsigned on, int ix, int iy, int iz)
+{
+    double s = 0.0;
+    for (int b = 0; b < st.nbox; ++b) {
+        if (((on >> b) & 1u) && ix >= st.box[b][0] && ix < st.box[b][1] &&
+            iy >= st.box[b][2] && iy < st.box[b][3] && iz >= st.box[b][4] && iz < st.box[b][5])
+            s += st.amp[b];
+    }
+    return s;
+}
+
+// phi_1..phi_M at x <= 0 (App. A eq. def_phik).  Two regimes:
+//  |x| >  X1: phi_1 = (e^x - 1)/x (no cancellation there: X1 > 1.4 for M >= 2),
+//             then phi_{k+1} = (phi_k - 1/k!)/x;
+//  |x| <= X1: phi_M = e^x/(M-1)! sum_m (-x)^m/(m! (m+M)) (all terms >= 0,
+//             Horner form with host coefficients; the number of terms steps
+//             down with |x|), then phi_k = x phi_{k+1} + 1/k!.
+// X1 balances the rounding growth of the two recurrences (set on the host).
+// M = 1: phi_1 = expm1(x)/x.
+template <int M>
+__device__ __forceinline__ void phi_all(double x, double (&ph)[M])
+{
+    const ColloData& C = c_col[M - 1];
+    if (M == 1) {
+        ph[0] = (x == 0.0) ? 1.0 : expm1(x) / x;
+    } else if (-x > C.X1) {
+        const double rx = esdc::esdc_rcp(x);
+        ph[0] = (esdc::esdc_exp(x) - 1.0) * rx;
+#pragma unroll
+        for (int k = 1; k < M; ++k) ph[k] = (ph[k - 1] - c_invfact[k]) * rx;
+    } else {
+        const double nx = -x;
+        const int n = nx <= C.xb[0] ? C.nb[0] : nx <= C.xb[1] ? C.nb[1] : nx <= C.xb[2] ? C.nb[2]
+                    : nx <= C.xb[3] ? C.nb[3] : C.nb[4];
+        double acc = C.ser[n];
+        for (int m = n - 1; m >= 0; --m) acc = fma(acc, nx, C.ser[m]);
+        ph[M - 1] = esdc::esdc_exp(x) * acc;
+#pragma unroll
+        for (int k = M - 1; k >= 1; --k) ph[k - 1] = fma(x, ph[k], c_invfact[k]);
+    }
+}
+
+// phi_1(y) = (e^y - 1)/y for y <= 0.
+__device__ __forceinline__ double phi1(double y)
+{
+    if (y < -1.0) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);
+    return (y == 0.0) ? 1.0 : expm1(y) / y;
+}
+
+// ------------------------------------------------------------------ set-up
+// Lambda_n, dt S_ij(dt Lambda_n), dt d_i phi_1(d_i dt Lambda_n) (tables carry the
+// step size); y^0 = 1 (x) y_n; G_j^0 = g_n(t_{n,j}, y_n); FI_j^0 = f_I(y_n).
+template <class Model, int M, bool MIXED>
+__global__ void __launch_bounds__(128) k_setup(StepArgs a)
+{
+    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
+    const MeshDev& m = a.m;
+    const ColloData& C = c_col[M - 1];
+    const int64_t ld = m.ld;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        node_xyz(m, p, ix, iy, iz);
+        double u[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) u[s] = a.yn[s * ld + p];
+        const double fi = a.D * lap(m, a.yn, p, ix, iy, iz);
+        double mI, ha[NA > 0 ? NA : 1];
+        float uf[NS];
+        if (MIXED) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) uf[s] = (float)u[s];
+            float mIf, haf[NA > 0 ? NA : 1];
+            Model::currents_f(a.mpf.p, uf, mIf, haf);
+            mI = mIf;
+#pragma unroll
+            for (int s = 0; s < NA; ++s) ha[s] = haf[s];
+        } else {
+            Model::currents(a.mp.p, u, mI, ha);
+        }
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            double* Yj = a.Y + (int64_t)j * NS * ld;
+            double* Gj = a.Gnew + (int64_t)j * NS * ld;
+            Gj[p] = fi + (stim_at(a.st, a.stim_on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
+            Yj[p] = u[0];
+#pragma unroll
+            for (int s = 1; s <= NA; ++s) { Gj[s * ld + p] = ha[s - 1]; Yj[s * ld + p] = u[s]; }
+            a.FI[(int64_t)j * ld + p] = fi;
+        }
+#pragma unroll 1
+        for (int g = 0; g < NG; ++g) {
+            const int s = 1 + NA + g;
+            double lam, yinf;
+            if (MIXED) {
+                float lf, yf;
+                Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
+                lam = lf; yinf = yf;
+            } else {
+                Model::gate(a.mp.p, g, u[0], lam, yinf);
+            }
+            const double us = a.yn[s * ld + p];
+            const double g0 = lam * (us - yinf);
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                a.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
+                a.Y[((int64_t)j * NS + s) * ld + p] = us;
+            }
+            const double z = a.dt * lam;
+            a.LAMN[(int64_t)g * ld + p] = lam;
+            double aprev[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) aprev[j] = 0.0;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                double ph[M];
+                phi_all<M>(C.c[i + 1] * z, ph);
+                const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
+                a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    double aij = 0.0;
+#pragma unroll
+                    for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
+                    aij *= a.dt;                                                 // dt a_ij
+                    a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
+                    aprev[j] = aij;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ sweep node i
+// i in 1..M: ionic evaluation at y_{i-1}^{k+1} (i >= 2), G_{i-1}^{k+1}, FI_{i-1}^{k+1},
+// explicit rows (auxiliaries, gates) of y_i^{k+1} and the right-hand side of the
+// V row.  i == M+1: only the evaluation at y_M^{k+1}.  Each gate's rate is used
+// as soon as it is computed (its G, Delta and update), which keeps few values live.
+#ifndef ESDC_NODE_MINBLOCKS
+#define ESDC_NODE_MINBLOCKS 5      // 5 x 128 threads per SM: at most 102 registers
+#endif
+template <class Model, int M, bool MIXED>
+__global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
+{
+    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
+    const MeshDev& m = a.m;
+    const int64_t ld = m.ld;
+    const int i = a.i;
+    const bool eval = i >= 2;                 // G at y_{i-1}^{k+1}
+    const bool quad = i <= M;                 // explicit rows of y_i^{k+1}
+    const int jm = i - 2;                     // 0-based index of node i-1
+    const int ii = i - 1;                     // 0-based index of node i
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        node_xyz(m, p, ix, iy, iz);
+        const double* src = eval ? a.Y + (int64_t)jm * NS * ld : a.yn;   // y_{i-1}^{k+1}
+        double u[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) u[s] = src[s * ld + p];
+        const double* Gp = a.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
+        double* Gq = a.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
+        double* Yi = a.Y + (int64_t)ii * NS * ld;
+        const double dtd = quad ? a.dtd[i] : 0.0;
+
+        // ---- V row and auxiliaries
+        double dlt0 = 0.0, ha[NA > 0 ? NA : 1];
+        float uf[NS];
+        if (eval) {
+            const double fi = a.D * lap(m, src, p, ix, iy, iz);
+            double mI;
+            if (MIXED) {                      // precision form: the ionic model in FP32
+#pragma unroll
+                for (int s = 0; s < NS; ++s) uf[s] = (float)u[s];
+                float mIf, haf[NA > 0 ? NA : 1];
+                Model::currents_f(a.mpf.p, uf, mIf, haf);
+                mI = mIf;
+#pragma unroll
+                for (int s = 0; s < NA; ++s) ha[s] = haf[s];
+            } else {
+                Model::currents(a.mp.p, u, mI, ha);
+            }
+            const double fE = (stim_at(a.st, a.stim_on[i - 1], ix, iy, iz) + mI) * a.inv_Cm;
+            const double fi_old = a.FI[(int64_t)jm * ld + p];
+            a.FI[(int64_t)jm * ld + p] = fi;
+            Gq[p] = fi + fE;
+            dlt0 = fE - (Gp[p] - fi_old);
+#pragma unroll
+            for (int s = 1; s <= NA; ++s) Gq[s * ld + p] = ha[s - 1];
+        }
+        if (quad) {
+            // Initial guess of the V_i solve: V_i^k moved by the change the previous
+            // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
+            // starting point of CG changes; the solution is the same.
+            const double vik = Yi[p];
+            if (eval) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
+            a.Vprev[p] = vik;
+            double q = u[0];
+#pragma unroll
+            for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
+            a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
+#pragma unroll
+            for (int s = 1; s <= NA; ++s) {
+                const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
+                double qa = u[s];
+#pragma unroll
+                for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
+                Yi[s * ld + p] = fma(dtd, dl, qa);
+            }
+        }
+        // ---- gates, one at a time
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const int s = 1 + NA + g;
+            double dl = 0.0;
+            if (eval) {
+                double lam, yinf;
+                if (MIXED) {
+                    float lf, yf;
+                    Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
+                    lam = lf; yinf = yf;
+                } else {
+                    Model::gate(a.mp.p, g, u[0], lam, yinf);
+                }
+                const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
+                Gq[s * ld + p] = gn;
+                dl = gn - Gp[s * ld + p];
+            }
+            if (quad) {
+                double qg = u[s];
+#pragma unroll
+                for (int j = 0; j < M; ++j)
+                    qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
+                             a.Gold[((int64_t)j * NS + s) * ld + p], qg);
+                Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ residual + output
+// r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C), accumulated over i from the row
+// differences dt S_ij = dt (a_ij - a_{i-1,j});
+// per-state max |r| and max |y|; y_{n+1} = y_M.
+template <class Model, int M>
+__global__ void __launch_bounds__(128) k_residual(StepArgs a)
+{
+    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
+    const MeshDev& m = a.m;
+    const ColloData& C = c_col[M - 1];
+    const int64_t ld = m.ld;
+    __shared__ double smax[2 * ESDC_NSMAX];
+    for (int s = threadIdx.x; s < 2 * NS; s += blockDim.x) smax[s] = 0.0;
+    __syncthreads();
+    bool bad = false;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
+#pragma unroll 1
+        for (int s = 0; s < NS; ++s) {
+            const int g = s - 1 - NA;
+            const double yns = a.yn[s * ld + p];
+            double ymax = fabs(yns), rmax = 0.0;
+            // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
+            double r = 0.0, yprev = yns;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                double q = 0.0;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
+                    q = fma(sij, a.Gold[((int64_t)j * NS + s) * ld + p], q);
+                }
+                const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
+                r += q - (yi - yprev);
+                yprev = yi;
+                if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
+                bad |= !isfinite(r) || !isfinite(yi);
+                rmax = fmax(rmax, fabs(r));
+                ymax = fmax(ymax, fabs(yi));
+            }
+            // y_{n+1} = y_{n,M} (c_M = 1); y_n was read above by this thread only.
+            a.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
+            // shared-memory max of non-negative doubles through their bit patterns
+            atomicMax((unsigned long long*)&smax[s], (unsigned long long)__double_as_longlong(rmax));
+            atomicMax((unsigned long long*)&smax[NS + s], (unsigned long long)__double_as_longlong(ymax));
+        }
+    }
+    if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+    __syncthreads();
+    for (int s = threadIdx.x; s < 2 * NS; s += blockDim.x)
+        atomicMax(a.rmax + s, (unsigned long long)__double_as_longlong(smax[s]));
+}
+
+
+
+// Uploads this translation unit's copy of the collocation constants to the
+// current device (once per device).
+inline cudaError_t upload_constants_local(bool* done, int dev)
+{
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    ColloData col[ESDC_MMAX];
+    for (int M = 1; M <= ESDC_MMAX; ++M)
+        if (esdc_colloc_build(M, &col[M - 1])) return cudaErrorInvalidValue;
+    double inv[ESDC_NSER], invf[ESDC_MMAX + 2];
+    inv[0] = 0.0;
+    for (int k = 1; k < ESDC_NSER; ++k) inv[k] = 1.0 / k;
+    invf[0] = 1.0;
+    for (int k = 1; k < ESDC_MMAX + 2; ++k) invf[k] = invf[k - 1] / k;
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(c_col, col, sizeof col)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_inv, inv, sizeof inv)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_invfact, invf, sizeof invf)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
+}
+
+// Grid of a per-node kernel: the resident capacity of the device (blocks per SM
+// from the occupancy calculator x SMs), so that the grid-stride loop spreads the
+// nodes evenly over all SMs in one wave; smaller meshes use one block per 128 nodes.
+template <class F>
+inline int blocks_per_sm(F kernel, int threads)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm;
+}
+
+inline int resident_grid(const esdc_handle* h, int per_sm, int threads)
+{
+    long long cap = (long long)h->sms * per_sm;
+    long long need = ((long long)h->mesh.N + threads - 1) / threads;
+    return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
+}
+
+template <class Model, int M, bool MIXED>
+cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, cudaStream_t s)
+{
+    const int T = 128;
+    static int occ_setup = 0, occ_node = 0, occ_res = 0;    // blocks/SM per (model, M) instantiation
+    if (!occ_setup) {
+        occ_node = blocks_per_sm(k_node<Model, M, MIXED>, T);
+        occ_res = blocks_per_sm(k_residual<Model, M>, T);
+        occ_setup = blocks_per_sm(k_setup<Model, M, MIXED>, T);
+    }
+    const int nb_setup = resident_grid(h, occ_setup, T);
+    const int nb_node = resident_grid(h, occ_node, T);
+    const int nb_res = resident_grid(h, occ_res, T);
+    const double g0 = h->D;   // operator scale: (I - dt d_i D L)
+    const ColloData* C = &h->col[M - 1];
+
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) a.dS0[i][j] = a.dt * C->S0[i][j];
+    for (int i = 0; i <= M; ++i) {
+        a.dtd[i] = a.dt * C->d[i];
+        const double tj = a.t_n + C->c[i] * a.dt;
+        unsigned on = 0;
+        for (int b = 0; b < h->stim.nbox; ++b)
+            if (tj >= h->stim.t_on[b] && tj < h->stim.t_off[b]) on |= 1u << b;
+        a.stim_on[i] = on;
+    }
+    a.Gnew = h->G0;
+    a.Gold = h->G0;
+    prof_begin(h, 0, s);
+    k_setup<Model, M, MIXED><<<nb_setup, T, 0, s>>>(a);
+    prof_end(h, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double* Gold = h->G0;
+    double* Gnew = h->G1;
+    for (int k = 0; k < K; ++k) {
+        a.Gold = Gold;
+        a.Gnew = Gnew;
+        for (int i = 1; i <= M + 1; ++i) {
+            a.i = i;
+            a.k = k;
+            // first sweep: y^0 = y_n, so the change grows with the node time c_i
+            a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
+            prof_begin(h, 1, s);
+            k_node<Model, M, MIXED><<<nb_node, T, 0, s>>>(a);
+            prof_end(h, s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (i <= M) {
+                double* Vi = h->Y + (int64_t)(i - 1) * h->NS * h->mesh.ld;
+                const double g = a.dt * C->d[i] * g0;
+                int* log = (k * M + (i - 1) < h->cg_log_len) ? h->cg_log + k * M + (i - 1) : nullptr;
+                prof_begin(h, 2, s);
+                e = esdc_cg_launch(h->mesh, h->cg, g, h->rhs, Vi, h->opt.tol_cg, h->opt.cg_maxit,
+                                   h->opt.precond, log, h->flags, s);
+                prof_end(h, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        double* t = Gold; Gold = Gnew; Gnew = t;
+    }
+    a.Gold = Gold;
+    a.yout = y;
+    prof_begin(h, 3, s);
+    k_residual<Model, M><<<nb_res, T, 0, s>>>(a);
+    prof_end(h, s);
+    h->last_Gfinal = Gold;
+    return cudaGetLastError();
+}
+
+template <class Model, bool MIXED>
+cudaError_t dispatch_M(esdc_handle* h, StepArgs& a, double* y, int M, int K, cudaStream_t s)
+{
+    switch (M) {
+        case 1: return launch_step_kernels<Model, 1, MIXED>(h, a, y, K, s);
+        case 2: return launch_step_kernels<Model, 2, MIXED>(h, a, y, K, s);
+        case 3: return launch_step_kernels<Model, 3, MIXED>(h, a, y, K, s);
+        case 4: return launch_step_kernels<Model, 4, MIXED>(h, a, y, K, s);
+        case 5: return launch_step_kernels<Model, 5, MIXED>(h, a, y, K, s);
+        case 6: return launch_step_kernels<Model, 6, MIXED>(h, a, y, K, s);
+        case 7: return launch_step_kernels<Model, 7, MIXED>(h, a, y, K, s);
+        case 8: return launch_step_kernels<Model, 8, MIXED>(h, a, y, K, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace

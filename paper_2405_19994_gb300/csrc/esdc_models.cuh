@@ -1,7 +1,8 @@
 // Pointwise ionic models on the device (eq. monodomain; gates in the form of
 // eq. monodomain_g_lambda).  eval() returns everything at once; currents() and
 // gate() return the same numbers piecewise, so that a kernel can use each gate's
-// rate as soon as it is computed.  For one mesh node u:
+// rate as soon as it is computed; currents_f() and gate_f() are the FP32
+// counterparts used by the precision form.  For one mesh node u:
 //   mI   = -I_ion(u)                               [uA/mm^2]
 //   ha   = h_a(u)   (NA auxiliary derivatives)
 //   lam  = Lambda_g(V) = -(alpha + beta)           (NG gates)
@@ -18,6 +19,13 @@ __device__ __forceinline__ double x_over_expm1(double x)
 {
     if (fabs(x) < 1e-6) return 1.0 - x * (0.5 - x * (1.0 / 12.0));
     return x / expm1(x);
+}
+
+// FP32 versions (the precision form): x/(e^x - 1) with a Taylor branch.
+__device__ __forceinline__ float x_over_expm1f(float x)
+{
+    if (fabsf(x) < 1e-3f) return 1.0f - x * (0.5f - x * (1.0f / 12.0f));
+    return x / expm1f(x);
 }
 
 // Hodgkin & Huxley 1952, V = Vrest + v.  params: gNa, gK, gL, ENa, EK, EL, Vrest.
@@ -60,6 +68,25 @@ struct HH1952 {
         else if (q == 1) { al = 0.07 * exp(v * (-0.05)); be = 1.0 / (exp((30.0 - v) * 0.1) + 1.0); }
         else { al = 0.1 * x_over_expm1((10.0 - v) * 0.1); be = 0.125 * exp(v * (-0.0125)); }
         const double sum = al + be;
+        lam = -sum;
+        yinf = al / sum;
+    }
+    // FP32 counterparts of currents() and gate() (parameters as floats).
+    __device__ static void currents_f(const float* __restrict__ mp, const float* u, float& mI, float* ha)
+    {
+        (void)ha;
+        const float V = u[0], m = u[1], h = u[2], n = u[3];
+        const float m3h = m * m * m * h, n2 = n * n;
+        mI = -(mp[0] * m3h * (V - mp[3]) + mp[1] * n2 * n2 * (V - mp[4]) + mp[2] * (V - mp[5]));
+    }
+    __device__ static void gate_f(const float* __restrict__ mp, int q, float V, float& lam, float& yinf)
+    {
+        const float v = V - mp[6];
+        float al, be;
+        if (q == 0) { al = x_over_expm1f((25.0f - v) * 0.1f); be = 4.0f * expf(v * (-1.0f / 18.0f)); }
+        else if (q == 1) { al = 0.07f * expf(v * (-0.05f)); be = 1.0f / (expf((30.0f - v) * 0.1f) + 1.0f); }
+        else { al = 0.1f * x_over_expm1f((10.0f - v) * 0.1f); be = 0.125f * expf(v * (-0.0125f)); }
+        const float sum = al + be;
         lam = -sum;
         yinf = al / sum;
     }
@@ -147,6 +174,34 @@ struct SYN19 {
         yinf = esdc_rcp(1.0 + esdc_exp((p[0] - V) * inv[q]));
         const double s = esdc_rcp(1.0 + esdc_exp((p[4] - V) * inv[12 + q]));
         lam = -p[2] * esdc_exp(p[3] * s);
+    }
+    __device__ static void currents_f(const float* __restrict__ mp, const float* u, float& mI, float* ha)
+    {
+        const float V = u[0];
+        const float* a = u + 1;
+        const float* g = u + 7;
+        const float* c = mp + 72;
+        const float If = c[0] * g[0] * g[1] * g[2] * a[0] * (V - c[1]);
+        const float Is = c[2] * g[3] * g[4] * a[2] * (V - c[3]);
+        const float IK = c[4] * a[1] * (1.0f + c[9] * a[5]) * (V - c[5]);
+        const float IK1 = c[6] * g[6] * g[7] * (V - c[5]);
+        const float Ib = c[7] * 0.25f * (g[8] + g[9] + g[10] + g[11]) * (V - c[8]);
+        mI = -(If + Is + IK + IK1 + Ib);
+        const float* itau = mp + 112;
+        ha[0] = ((1.0f - g[5]) - a[0]) * itau[0];
+        ha[1] = (g[5] - a[1]) * itau[1];
+        ha[2] = ((1.0f - g[5]) - a[2]) * itau[2];
+        ha[3] = (g[3] * g[4] - a[3]) * itau[3];
+        ha[4] = (a[3] - a[4]) * itau[4];
+        ha[5] = (a[4] - a[5]) * itau[5];
+    }
+    __device__ static void gate_f(const float* __restrict__ mp, int q, float V, float& lam, float& yinf)
+    {
+        const float* p = mp + 6 * q;
+        const float* inv = mp + 88;
+        yinf = 1.0f / (1.0f + expf((p[0] - V) * inv[q]));
+        const float s = 1.0f / (1.0f + expf((p[4] - V) * inv[12 + q]));
+        lam = -p[2] * expf(p[3] * s);
     }
     __device__ static void rest(const double* mp, double V0, double* u)
     {

@@ -31,318 +31,12 @@
 #include <new>
 
 #include "esdc_internal.h"
-#include "esdc_models.cuh"
+#include "esdc_kernels.cuh"
 
 namespace {
 
-__constant__ ColloData c_col[ESDC_MMAX];     // index M-1
-__constant__ double c_inv[ESDC_NSER];        // c_inv[m] = 1/m (c_inv[0] unused)
-__constant__ double c_invfact[ESDC_MMAX + 2];
-
-struct StepArgs {
-    MeshDev m;
-    StimDev st;
-    ModelDev mp;
-    int i;                 // collocation node 1..M (k_node), M+1: evaluate G at node M only
-    int k;                 // sweep index (0-based)
-    double rho;            // warm-start extrapolation weight for node i
-    double* Vprev;         // [ld] V_{i-1}^k, saved before node i-1 was solved
-    double dt, t_n, D, inv_Cm;
-    double dS0[ESDC_MMAX][ESDC_MMAX];   // dt * (a_ij(0) - a_{i-1,j}(0))
-    double dtd[ESDC_MMAX + 1];          // dt * d_i
-    unsigned stim_on[ESDC_MMAX + 1];    // boxes active at t_{n,j}, j = 0..M (bit b = box b)
-    const double* yn;
-    double* yout;          // residual kernel: destination of y_{n+1}
-    double* Y;
-    const double* Gold;
-    double* Gnew;
-    double* FI;
-    double* S;
-    double* PHI;
-    double* LAMN;
-    double* rhs;
-    double* R;             // residual vectors (optional)
-    unsigned long long* rmax;   // [NS] per-state max |r| (as ordered bits), [NS] max |y|
-    int* flags;
-};
-
-__device__ __forceinline__ void node_xyz(const MeshDev& m, int p, int& ix, int& iy, int& iz)
-{
-    int r = p / m.nx;
-    ix = p - r * m.nx;
-    iz = r / m.ny;
-    iy = r - iz * m.ny;
-}
-
-// L v at node p: (1/h^2) sum over in-domain neighbours of (v_q - v_p).
-__device__ __forceinline__ double lap(const MeshDev& m, const double* __restrict__ v, int p,
-                                      int ix, int iy, int iz)
-{
-    const double vp = v[p];
-    const int sxy = m.nx * m.ny;
-    double s = 0.0;
-    if (ix > 0)        s += v[p - 1] - vp;
-    if (ix < m.nx - 1) s += v[p + 1] - vp;
-    if (iy > 0)        s += v[p - m.nx] - vp;
-    if (iy < m.ny - 1) s += v[p + m.nx] - vp;
-    if (iz > 0)        s += v[p - sxy] - vp;
-    if (iz < m.nz - 1) s += v[p + sxy] - vp;
-    return s * m.ih2;
-}
-
-// I_stim at a node for the boxes whose time window contains the node's time
-// (the window test t_on <= t < t_off is made once on the host: bit b of `on`).
-__device__ __forceinline__ double stim_at(const StimDev& st, unsigned on, int ix, int iy, int iz)
-{
-    double s = 0.0;
-    for (int b = 0; b < st.nbox; ++b) {
-        if (((on >> b) & 1u) && ix >= st.box[b][0] && ix < st.box[b][1] &&
-            iy >= st.box[b][2] && iy < st.box[b][3] && iz >= st.box[b][4] && iz < st.box[b][5])
-            s += st.amp[b];
-    }
-    return s;
-}
-
-// phi_1..phi_M at x <= 0 (App. A eq. def_phik).  Two regimes:
-//  |x| >  X1: phi_1 = (e^x - 1)/x (no cancellation there: X1 > 1.4 for M >= 2),
-//             then phi_{k+1} = (phi_k - 1/k!)/x;
-//  |x| <= X1: phi_M = e^x/(M-1)! sum_m (-x)^m/(m! (m+M)) (all terms >= 0,
-//             Horner form with host coefficients; the number of terms steps
-//             down with |x|), then phi_k = x phi_{k+1} + 1/k!.
-// X1 balances the rounding growth of the two recurrences (set on the host).
-// M = 1: phi_1 = expm1(x)/x.
-template <int M>
-__device__ __forceinline__ void phi_all(double x, double (&ph)[M])
-{
-    const ColloData& C = c_col[M - 1];
-    if (M == 1) {
-        ph[0] = (x == 0.0) ? 1.0 : expm1(x) / x;
-    } else if (-x > C.X1) {
-        const double rx = esdc::esdc_rcp(x);
-        ph[0] = (esdc::esdc_exp(x) - 1.0) * rx;
-#pragma unroll
-        for (int k = 1; k < M; ++k) ph[k] = (ph[k - 1] - c_invfact[k]) * rx;
-    } else {
-        const double nx = -x;
-        const int n = nx <= C.xb[0] ? C.nb[0] : nx <= C.xb[1] ? C.nb[1] : nx <= C.xb[2] ? C.nb[2]
-                    : nx <= C.xb[3] ? C.nb[3] : C.nb[4];
-        double acc = C.ser[n];
-        for (int m = n - 1; m >= 0; --m) acc = fma(acc, nx, C.ser[m]);
-        ph[M - 1] = esdc::esdc_exp(x) * acc;
-#pragma unroll
-        for (int k = M - 1; k >= 1; --k) ph[k - 1] = fma(x, ph[k], c_invfact[k]);
-    }
-}
-
-// phi_1(y) = (e^y - 1)/y for y <= 0.
-__device__ __forceinline__ double phi1(double y)
-{
-    if (y < -1.0) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);
-    return (y == 0.0) ? 1.0 : expm1(y) / y;
-}
-
-// ------------------------------------------------------------------ set-up
-// Lambda_n, dt S_ij(dt Lambda_n), dt d_i phi_1(d_i dt Lambda_n) (tables carry the
-// step size); y^0 = 1 (x) y_n; G_j^0 = g_n(t_{n,j}, y_n); FI_j^0 = f_I(y_n).
-template <class Model, int M>
-__global__ void __launch_bounds__(128) k_setup(StepArgs a)
-{
-    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const MeshDev& m = a.m;
-    const ColloData& C = c_col[M - 1];
-    const int64_t ld = m.ld;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        node_xyz(m, p, ix, iy, iz);
-        double u[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) u[s] = a.yn[s * ld + p];
-        const double fi = a.D * lap(m, a.yn, p, ix, iy, iz);
-        double mI, ha[NA > 0 ? NA : 1], lam[NG], yinf[NG];
-        Model::eval(a.mp.p, u, mI, NA > 0 ? ha : nullptr, lam, yinf);
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-            double* Yj = a.Y + (int64_t)j * NS * ld;
-            double* Gj = a.Gnew + (int64_t)j * NS * ld;
-            Gj[p] = fi + (stim_at(a.st, a.stim_on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
-            Yj[p] = u[0];
-#pragma unroll
-            for (int s = 1; s <= NA; ++s) { Gj[s * ld + p] = ha[s - 1]; Yj[s * ld + p] = u[s]; }
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                const int s = 1 + NA + g;
-                Gj[s * ld + p] = lam[g] * (u[s] - yinf[g]);
-                Yj[s * ld + p] = u[s];
-            }
-            a.FI[(int64_t)j * ld + p] = fi;
-        }
-#pragma unroll 1
-        for (int g = 0; g < NG; ++g) {
-            const double z = a.dt * lam[g];
-            a.LAMN[(int64_t)g * ld + p] = lam[g];
-            double aprev[M];
-#pragma unroll
-            for (int j = 0; j < M; ++j) aprev[j] = 0.0;
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                double ph[M];
-                phi_all<M>(C.c[i + 1] * z, ph);
-                const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
-                a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    double aij = 0.0;
-#pragma unroll
-                    for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
-                    aij *= a.dt;                                                 // dt a_ij
-                    a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
-                    aprev[j] = aij;
-                }
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ sweep node i
-// i in 1..M: ionic evaluation at y_{i-1}^{k+1} (i >= 2), G_{i-1}^{k+1}, FI_{i-1}^{k+1},
-// explicit rows (auxiliaries, gates) of y_i^{k+1} and the right-hand side of the
-// V row.  i == M+1: only the evaluation at y_M^{k+1}.  Each gate's rate is used
-// as soon as it is computed (its G, Delta and update), which keeps few values live.
-#ifndef ESDC_NODE_MINBLOCKS
-#define ESDC_NODE_MINBLOCKS 5      // 5 x 128 threads per SM: at most 102 registers
-#endif
-template <class Model, int M>
-__global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
-{
-    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const MeshDev& m = a.m;
-    const int64_t ld = m.ld;
-    const int i = a.i;
-    const bool eval = i >= 2;                 // G at y_{i-1}^{k+1}
-    const bool quad = i <= M;                 // explicit rows of y_i^{k+1}
-    const int jm = i - 2;                     // 0-based index of node i-1
-    const int ii = i - 1;                     // 0-based index of node i
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        node_xyz(m, p, ix, iy, iz);
-        const double* src = eval ? a.Y + (int64_t)jm * NS * ld : a.yn;   // y_{i-1}^{k+1}
-        double u[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) u[s] = src[s * ld + p];
-        const double* Gp = a.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
-        double* Gq = a.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
-        double* Yi = a.Y + (int64_t)ii * NS * ld;
-        const double dtd = quad ? a.dtd[i] : 0.0;
-
-        // ---- V row and auxiliaries
-        double dlt0 = 0.0, ha[NA > 0 ? NA : 1];
-        if (eval) {
-            const double fi = a.D * lap(m, src, p, ix, iy, iz);
-            double mI;
-            Model::currents(a.mp.p, u, mI, ha);
-            const double fE = (stim_at(a.st, a.stim_on[i - 1], ix, iy, iz) + mI) * a.inv_Cm;
-            const double fi_old = a.FI[(int64_t)jm * ld + p];
-            a.FI[(int64_t)jm * ld + p] = fi;
-            Gq[p] = fi + fE;
-            dlt0 = fE - (Gp[p] - fi_old);
-#pragma unroll
-            for (int s = 1; s <= NA; ++s) Gq[s * ld + p] = ha[s - 1];
-        }
-        if (quad) {
-            // Initial guess of the V_i solve: V_i^k moved by the change the previous
-            // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
-            // starting point of CG changes; the solution is the same.
-            const double vik = Yi[p];
-            if (eval) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
-            a.Vprev[p] = vik;
-            double q = u[0];
-#pragma unroll
-            for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
-            a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
-#pragma unroll
-            for (int s = 1; s <= NA; ++s) {
-                const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
-                double qa = u[s];
-#pragma unroll
-                for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
-                Yi[s * ld + p] = fma(dtd, dl, qa);
-            }
-        }
-        // ---- gates, one at a time
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            const int s = 1 + NA + g;
-            double dl = 0.0;
-            if (eval) {
-                double lam, yinf;
-                Model::gate(a.mp.p, g, u[0], lam, yinf);
-                const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
-                Gq[s * ld + p] = gn;
-                dl = gn - Gp[s * ld + p];
-            }
-            if (quad) {
-                double qg = u[s];
-#pragma unroll
-                for (int j = 0; j < M; ++j)
-                    qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
-                             a.Gold[((int64_t)j * NS + s) * ld + p], qg);
-                Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ residual + output
-// r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C), accumulated over i from the row
-// differences dt S_ij = dt (a_ij - a_{i-1,j});
-// per-state max |r| and max |y|; y_{n+1} = y_M.
-template <class Model, int M>
-__global__ void __launch_bounds__(128) k_residual(StepArgs a)
-{
-    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const MeshDev& m = a.m;
-    const ColloData& C = c_col[M - 1];
-    const int64_t ld = m.ld;
-    __shared__ double smax[2 * ESDC_NSMAX];
-    for (int s = threadIdx.x; s < 2 * NS; s += blockDim.x) smax[s] = 0.0;
-    __syncthreads();
-    bool bad = false;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
-#pragma unroll 1
-        for (int s = 0; s < NS; ++s) {
-            const int g = s - 1 - NA;
-            const double yns = a.yn[s * ld + p];
-            double ymax = fabs(yns), rmax = 0.0;
-            // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
-            double r = 0.0, yprev = yns;
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                double q = 0.0;
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
-                    q = fma(sij, a.Gold[((int64_t)j * NS + s) * ld + p], q);
-                }
-                const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
-                r += q - (yi - yprev);
-                yprev = yi;
-                if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
-                bad |= !isfinite(r) || !isfinite(yi);
-                rmax = fmax(rmax, fabs(r));
-                ymax = fmax(ymax, fabs(yi));
-            }
-            // y_{n+1} = y_{n,M} (c_M = 1); y_n was read above by this thread only.
-            a.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
-            // shared-memory max of non-negative doubles through their bit patterns
-            atomicMax((unsigned long long*)&smax[s], (unsigned long long)__double_as_longlong(rmax));
-            atomicMax((unsigned long long*)&smax[NS + s], (unsigned long long)__double_as_longlong(ymax));
-        }
-    }
-    if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
-    __syncthreads();
-    for (int s = threadIdx.x; s < 2 * NS; s += blockDim.x)
-        atomicMax(a.rmax + s, (unsigned long long)__double_as_longlong(smax[s]));
-}
+std::mutex g_const_mu;
+bool g_const_done[64] = {false};
 
 template <class Model>
 __global__ void k_init(MeshDev m, ModelDev mp, double V0, double* y)
@@ -399,75 +93,7 @@ __global__ void k_coef(const double* z, int64_t n, double* out)
 
 }  // namespace
 
-// ====================================================================== host side
-
-struct esdc_handle {
-    int device = 0, sms = 152;
-    int model = 0, NS = 0, NA = 0, NG = 0;
-    ColloData col[ESDC_MMAX];
-    MeshDev mesh{};
-    StimDev stim{};
-    ModelDev mp{};
-    double sigma = 0, chi = 0, Cm = 0, D = 0;
-    esdc_options opt{};
-    // workspace
-    double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,
-           *LAMN = nullptr, *rhs = nullptr, *R = nullptr, *ydev = nullptr, *Vprev = nullptr;
-    CgWork cg{};
-    unsigned long long* rmax = nullptr;   // [2*NS]
-    int* flags = nullptr;                 // [1]
-    int* cg_log = nullptr;                // [K_log] iteration counts of the last step
-    int cg_log_len = 0;
-    // state of the most recent sweep
-    int last_M = 0, last_K = 0;
-    double last_dt = 0.0;
-    const double* last_Gfinal = nullptr;
-    cudaStream_t last_stream = nullptr;
-    // kernel-class timing (esdc_profile): event pairs around each launch
-    bool prof_on = false;
-    cudaEvent_t prof_ev[2 * 512] = {};
-    int prof_cls[512] = {};
-    int prof_used = 0;
-    double prof_ms[ESDC_PROF_CLASSES] = {};
-    long long prof_cnt[ESDC_PROF_CLASSES] = {};
-    char err[256] = {0};
-};
-
 namespace {
-
-// Folds the recorded event pairs into the per-class totals (synchronises them).
-cudaError_t prof_flush(esdc_handle* h)
-{
-    for (int k = 0; k < h->prof_used; ++k) {
-        cudaError_t e = cudaEventSynchronize(h->prof_ev[2 * k + 1]);
-        if (e != cudaSuccess) return e;
-        float ms = 0.f;
-        e = cudaEventElapsedTime(&ms, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]);
-        if (e != cudaSuccess) return e;
-        h->prof_ms[h->prof_cls[k]] += ms;
-        h->prof_cnt[h->prof_cls[k]] += 1;
-    }
-    h->prof_used = 0;
-    return cudaSuccess;
-}
-
-inline void prof_begin(esdc_handle* h, int cls, cudaStream_t s)
-{
-    if (!h->prof_on) return;
-    if (h->prof_used == 512) prof_flush(h);
-    h->prof_cls[h->prof_used] = cls;
-    cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
-}
-
-inline void prof_end(esdc_handle* h, cudaStream_t s)
-{
-    if (!h->prof_on) return;
-    cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
-    h->prof_used++;
-}
-
-std::mutex g_const_mu;
-bool g_const_done[64] = {false};
 
 int set_err(esdc_handle* h, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
 int set_err(esdc_handle* h, int code, const char* fmt, ...)
@@ -489,135 +115,11 @@ int set_err(esdc_handle* h, int code, const char* fmt, ...)
                            "%s: %s", #call, cudaGetErrorString(e_));                           \
     } while (0)
 
-int upload_constants(esdc_handle* h, int dev)
-{
-    std::lock_guard<std::mutex> lk(g_const_mu);
-    if (dev >= 0 && dev < 64 && g_const_done[dev]) return ESDC_OK;
-    ColloData col[ESDC_MMAX];
-    for (int M = 1; M <= ESDC_MMAX; ++M)
-        if (esdc_colloc_build(M, &col[M - 1]))
-            return set_err(h, ESDC_ERR_CUDA, "collocation data for M=%d failed", M);
-    double inv[ESDC_NSER], invf[ESDC_MMAX + 2];
-    inv[0] = 0.0;
-    for (int k = 1; k < ESDC_NSER; ++k) inv[k] = 1.0 / k;
-    invf[0] = 1.0;
-    for (int k = 1; k < ESDC_MMAX + 2; ++k) invf[k] = invf[k - 1] / k;
-    CUDA_TRY(h, cudaMemcpyToSymbol(c_col, col, sizeof col));
-    CUDA_TRY(h, cudaMemcpyToSymbol(c_inv, inv, sizeof inv));
-    CUDA_TRY(h, cudaMemcpyToSymbol(c_invfact, invf, sizeof invf));
-    if (dev >= 0 && dev < 64) g_const_done[dev] = true;
-    return ESDC_OK;
-}
-
 int grid_for(const esdc_handle* h, int threads)
 {
     long long need = ((long long)h->mesh.N + threads - 1) / threads;
     long long cap = (long long)h->sms * 16;
     return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
-}
-
-// Grid of a per-node kernel: the resident capacity of the device (blocks per SM
-// from the occupancy calculator x SMs), so that the grid-stride loop spreads the
-// nodes evenly over all SMs in one wave; smaller meshes use one block per 128 nodes.
-template <class F>
-int blocks_per_sm(F kernel, int threads)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    return per_sm;
-}
-
-int resident_grid(const esdc_handle* h, int per_sm, int threads)
-{
-    long long cap = (long long)h->sms * per_sm;
-    long long need = ((long long)h->mesh.N + threads - 1) / threads;
-    return (int)(need < cap ? (need < 1 ? 1 : need) : cap);
-}
-
-template <class Model, int M>
-cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, cudaStream_t s)
-{
-    const int T = 128;
-    static int occ_setup = 0, occ_node = 0, occ_res = 0;    // blocks/SM per (model, M) instantiation
-    if (!occ_setup) {
-        occ_node = blocks_per_sm(k_node<Model, M>, T);
-        occ_res = blocks_per_sm(k_residual<Model, M>, T);
-        occ_setup = blocks_per_sm(k_setup<Model, M>, T);
-    }
-    const int nb_setup = resident_grid(h, occ_setup, T);
-    const int nb_node = resident_grid(h, occ_node, T);
-    const int nb_res = resident_grid(h, occ_res, T);
-    const double g0 = h->D;   // operator scale: (I - dt d_i D L)
-    const ColloData* C = &h->col[M - 1];
-
-    for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j) a.dS0[i][j] = a.dt * C->S0[i][j];
-    for (int i = 0; i <= M; ++i) {
-        a.dtd[i] = a.dt * C->d[i];
-        const double tj = a.t_n + C->c[i] * a.dt;
-        unsigned on = 0;
-        for (int b = 0; b < h->stim.nbox; ++b)
-            if (tj >= h->stim.t_on[b] && tj < h->stim.t_off[b]) on |= 1u << b;
-        a.stim_on[i] = on;
-    }
-    a.Gnew = h->G0;
-    a.Gold = h->G0;
-    prof_begin(h, 0, s);
-    k_setup<Model, M><<<nb_setup, T, 0, s>>>(a);
-    prof_end(h, s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    double* Gold = h->G0;
-    double* Gnew = h->G1;
-    for (int k = 0; k < K; ++k) {
-        a.Gold = Gold;
-        a.Gnew = Gnew;
-        for (int i = 1; i <= M + 1; ++i) {
-            a.i = i;
-            a.k = k;
-            // first sweep: y^0 = y_n, so the change grows with the node time c_i
-            a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
-            prof_begin(h, 1, s);
-            k_node<Model, M><<<nb_node, T, 0, s>>>(a);
-            prof_end(h, s);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if (i <= M) {
-                double* Vi = h->Y + (int64_t)(i - 1) * h->NS * h->mesh.ld;
-                const double g = a.dt * C->d[i] * g0;
-                int* log = (k * M + (i - 1) < h->cg_log_len) ? h->cg_log + k * M + (i - 1) : nullptr;
-                prof_begin(h, 2, s);
-                e = esdc_cg_launch(h->mesh, h->cg, g, h->rhs, Vi, h->opt.tol_cg, h->opt.cg_maxit,
-                                   h->opt.precond, log, h->flags, s);
-                prof_end(h, s);
-                if (e != cudaSuccess) return e;
-            }
-        }
-        double* t = Gold; Gold = Gnew; Gnew = t;
-    }
-    a.Gold = Gold;
-    a.yout = y;
-    prof_begin(h, 3, s);
-    k_residual<Model, M><<<nb_res, T, 0, s>>>(a);
-    prof_end(h, s);
-    h->last_Gfinal = Gold;
-    return cudaGetLastError();
-}
-
-template <class Model>
-cudaError_t dispatch_M(esdc_handle* h, StepArgs& a, double* y, int M, int K, cudaStream_t s)
-{
-    switch (M) {
-        case 1: return launch_step_kernels<Model, 1>(h, a, y, K, s);
-        case 2: return launch_step_kernels<Model, 2>(h, a, y, K, s);
-        case 3: return launch_step_kernels<Model, 3>(h, a, y, K, s);
-        case 4: return launch_step_kernels<Model, 4>(h, a, y, K, s);
-        case 5: return launch_step_kernels<Model, 5>(h, a, y, K, s);
-        case 6: return launch_step_kernels<Model, 6>(h, a, y, K, s);
-        case 7: return launch_step_kernels<Model, 7>(h, a, y, K, s);
-        case 8: return launch_step_kernels<Model, 8>(h, a, y, K, s);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 void free_all(esdc_handle* h)
@@ -642,6 +144,7 @@ void esdc_default_options(esdc_options* opt)
     opt->tol_cg = 1e-14;
     opt->cg_maxit = 200;
     opt->precond = 1;
+    opt->precision = 0;
 }
 
 int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int model,
@@ -674,6 +177,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     esdc_default_options(&o);
     if (opt) o = *opt;
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
+    if (o.precision != 0 && o.precision != 1) return ESDC_ERR_INVALID_ARG;
 
     esdc_handle* h = new (std::nothrow) esdc_handle();
     if (!h) return ESDC_ERR_NO_MEMORY;
@@ -696,15 +200,18 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
         }
         for (int l = 0; l < 6; ++l) h->mp.p[112 + l] = 1.0 / params[82 + l];
     }
+    for (int k = 0; k < ESDC_NPMAX; ++k) h->mpf.p[k] = (float)h->mp.p[k];
 
-    int rc = ESDC_OK;
     auto fail = [&](int code) { free_all(h); delete h; return code; };
     for (int M = 1; M <= ESDC_MMAX; ++M)
         if (esdc_colloc_build(M, &h->col[M - 1])) return fail(ESDC_ERR_CUDA);
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(ESDC_ERR_CUDA);
     if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
         return fail(ESDC_ERR_CUDA);
-    if ((rc = upload_constants(h, h->device)) != ESDC_OK) return fail(rc);
+    {
+        std::lock_guard<std::mutex> lk(g_const_mu);
+        if (upload_constants_local(g_const_done, h->device) != cudaSuccess) return fail(ESDC_ERR_CUDA);
+    }
 
     const int64_t ld = h->mesh.ld, NS = h->NS, NG = h->NG, Mx = o.M_max;
     struct { double** p; int64_t n; } bufs[] = {
@@ -797,12 +304,16 @@ int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, voi
     CUDA_TRY(h, cudaMemsetAsync(h->cg_log, 0, sizeof(int) * h->cg_log_len, s));
     StepArgs a;
     std::memset(&a, 0, sizeof a);
-    a.m = h->mesh; a.st = h->stim; a.mp = h->mp;
+    a.m = h->mesh; a.st = h->stim; a.mp = h->mp; a.mpf = h->mpf;
     a.dt = dt; a.t_n = t; a.D = h->D; a.inv_Cm = 1.0 / h->Cm;
     a.yn = y; a.Y = h->Y; a.FI = h->FI; a.S = h->S; a.PHI = h->PHI; a.LAMN = h->LAMN; a.rhs = h->rhs;
     a.R = h->R; a.rmax = h->rmax; a.flags = h->flags; a.Vprev = h->Vprev;
-    cudaError_t e = h->model == ESDC_MODEL_HH1952 ? dispatch_M<esdc::HH1952>(h, a, y, M, K, s)
-                                                  : dispatch_M<esdc::SYN19>(h, a, y, M, K, s);
+    cudaError_t e;
+    if (h->opt.precision == 1)
+        e = esdc_dispatch_mixed(h, a, y, M, K, s);
+    else
+        e = h->model == ESDC_MODEL_HH1952 ? dispatch_M<esdc::HH1952, false>(h, a, y, M, K, s)
+                                          : dispatch_M<esdc::SYN19, false>(h, a, y, M, K, s);
     if (e != cudaSuccess) return set_err(h, ESDC_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     h->last_M = M; h->last_K = K; h->last_dt = dt; h->last_stream = s;
     return ESDC_OK;

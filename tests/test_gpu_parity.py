@@ -220,6 +220,46 @@ def test_errors_reported():
     assert np.all(it >= 1) and np.all(it < 200)
 
 
+# ---------------------------------------------------------------- precision form (FP32 ionic model)
+
+@pytest.mark.parametrize("model,mesh,M,K", [(I.MODEL_HH1952, (12, 10, 1), 3, 4), (I.MODEL_SYN19, (11, 6, 4), 4, 6)])
+def test_precision_form_one_step(model, mesh, M, K):
+    """The precision form evaluates f_E, Lambda and y_inf in FP32; everything else
+    is FP64.  One step from a seeded state: per state, the difference from the FP64
+    oracle is bounded by the FP32 rounding of the ionic terms (relative 2^-23 ~ 1.2e-7)
+    times the step's sensitivity: 1e-5 of the state's scale for V, 1e-5 absolute for
+    the auxiliaries and gates."""
+    base = I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()
+    wl = base.with_mesh(*mesh)
+    s = P.Solver.from_workload(wl, M_max=M, precision="mixed")
+    y0 = I.random_state(wl, seed=77)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.4, wl.dt, M, K)
+    assert s.residual()[0] == 0
+    got = from_dev(s, yd)
+    want, _, _, _ = O.Monodomain(wl).step(y0, 0.4, wl.dt, M, K)
+    assert np.abs(got[0] - want[0]).max() <= 1e-5 * np.abs(want[0]).max()
+    assert np.abs(got[1:] - want[1:]).max() <= 1e-5
+    assert np.abs(got - want).max() > 0.0        # it really is a different (FP32) evaluation
+
+
+def test_precision_form_hh_sheet_run():
+    """32x32 HH sheet for 4 ms (160 steps) in the precision form against the oracle:
+    the V error stays at the FP32 level (< 1e-4 relative in the max norm)."""
+    wl = I.hh_sheet_32()
+    s = P.Solver.from_workload(wl, precision="mixed")
+    y = s.new_state()
+    s.init_state(y, wl.V0)
+    m = O.Monodomain(wl)
+    ref = m.init_state()
+    for n in range(wl.n_steps):
+        s.sweep(y, n * wl.dt, wl.dt, wl.M, wl.K)
+        ref, _, _, _ = m.step(ref, n * wl.dt, wl.dt, wl.M, wl.K)
+    got = from_dev(s, y)
+    err = rel(got[0], ref[0])
+    assert err < 1e-4, err
+
+
 # ---------------------------------------------------------------- full workloads
 
 def test_hh_sheet_full_run_matches_oracle():
