@@ -79,9 +79,11 @@ typedef struct {
     int    cg_maxit;   /* iteration cap of each solve (>= 1)                       */
     int    precond;    /* 1 = Jacobi-preconditioned CG, 0 = plain CG               */
     int    precision;  /* 0 = FP64 throughout; 1 = precision form: the ionic model
-                          (f_E, Lambda, y_inf) evaluated in FP32, everything else
-                          (state, coefficient tables, quadrature, solves, residual)
-                          in FP64                                                  */
+                          (f_E, Lambda, y_inf) evaluated in FP32, and each diffusion
+                          solve done by iterative refinement (FP64 residuals
+                          r = b - A x, FP32 inner PCG on A e = r, x += e) to the
+                          same tol_cg; state, coefficient tables, quadrature and
+                          residual stay FP64                                       */
 } esdc_options;
 
 /* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1,
@@ -208,7 +210,9 @@ int esdc_coefficients(esdc_handle* h, const double* z, int64_t n, int M, double*
  * eq. (def_P) with g = dt d_i sigma/(chi C_m)): b, x device [n_nodes]; x holds
  * the initial guess on entry and the solution on return.  iters (host,
  * optional) receives the iteration count; synchronises `stream`.  Returns
- * ESDC_ERR_CG_NOT_CONVERGED if cg_maxit was reached.
+ * ESDC_ERR_CG_NOT_CONVERGED if cg_maxit was reached.  With precision = 1 the
+ * solve is the refinement of the precision form and iters counts the inner
+ * (FP32) iterations.
  */
 int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, int* iters,
                          void* stream);

@@ -178,6 +178,23 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
 #ifndef ESDC_CG_UNROLL
 #define ESDC_CG_UNROLL 2        // best of 1/2/4/8 on GB300 (with 512-thread blocks)
 #endif
+// FP32 (I - g L) v for the inner solves of the precision form.
+__device__ __forceinline__ float apply_op_f(const MeshDev& m, const float* v, int p, NodeIdx n, float gih2, int* nnb)
+{
+    const float vp = __ldcg(v + p);
+    const int sxy = m.nx * m.ny;
+    float s = 0.0f;
+    int c = 0;
+    if (n.ix > 0)        { s += __ldcg(v + p - 1); ++c; }
+    if (n.ix < m.nx - 1) { s += __ldcg(v + p + 1); ++c; }
+    if (n.iy > 0)        { s += __ldcg(v + p - m.nx); ++c; }
+    if (n.iy < m.ny - 1) { s += __ldcg(v + p + m.nx); ++c; }
+    if (n.iz > 0)        { s += __ldcg(v + p - sxy); ++c; }
+    if (n.iz < m.nz - 1) { s += __ldcg(v + p + sxy); ++c; }
+    *nnb = c;
+    return fmaf(gih2, fmaf((float)c, vp, -s), vp);
+}
+
 __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
 {
     constexpr int U = ESDC_CG_UNROLL;
@@ -308,6 +325,202 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
     }
 }
 
+
+// Precision form of the solve: iterative refinement with FP64 residuals and
+// FP32 inner Jacobi-PCG (the matrix-vector products of the inner solve are FP32):
+//   r = b - A x (FP64); until ||r|| <= tol ||b||:
+//     solve A e = r in FP32 to ||r - A e|| <= eta ||r|| (at most maxin iterations);
+//     x += e (FP64); r = b - A x (FP64).
+// Same barrier, reduction order and slot discipline as k_cg; partial slots:
+// 0-1 initial r.r, b.b | 2-3 inner start | 4 p.q | 5-6 r.z, r.r | 7 outer r.r.
+struct CgMixArgs {
+    float *r, *p, *q, *z, *e;   // FP32 inner vectors [ld]
+    float dinv[7];
+    float eta2;
+    int maxin, maxout;
+};
+
+__global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArgs f)
+{
+    const MeshDev& m = a.m;
+    const int N = m.N;
+    const int stride = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double* part = a.part;
+    const double gih2 = a.g * m.ih2;
+    const float gih2f = (float)gih2;
+    __shared__ double bs[3];
+    unsigned target = 0;
+
+    // r = b - A x (FP64); partials r.r, b.b
+    {
+        double v[2] = {0.0, 0.0};
+        for (int p = tid; p < N; p += stride) {
+            NodeIdx n = node_idx(m, p);
+            int c;
+            const double bp = a.b[p];
+            const double rp = bp - apply_op(m, a.x, p, n, gih2, &c);
+            a.r[p] = rp;
+            v[0] = fma(rp, rp, v[0]);
+            v[1] = fma(bp, bp, v[1]);
+        }
+        block_sum<2>(v, bs);
+        if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[k * gridDim.x + blockIdx.x] = bs[k];
+    }
+    if (!grid_barrier(a.bar, target, a.flags)) return;
+    double t0[2];
+    grid_total<2>(part, 0, t0);
+    double rr = t0[0];
+    const double stop = a.tol2 * t0[1];
+    bool done = rr <= stop;
+    bool bad = !isfinite(rr) || !isfinite(stop);
+    int outer = 0, inner_total = 0;
+    while (!done && !bad && outer < f.maxout) {
+        // inner start: r32 = r, e = 0, z = D^{-1} r32, p = q = 0; partials r.z, r.r
+        {
+            double v[2] = {0.0, 0.0};
+            for (int p = tid; p < N; p += stride) {
+                const float rp = (float)a.r[p];
+                float zp = rp;
+                if (a.precond) {
+                    NodeIdx n = node_idx(m, p);
+                    int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
+                            (n.iz > 0) + (n.iz < m.nz - 1);
+                    zp = f.dinv[c] * rp;
+                }
+                f.r[p] = rp; f.z[p] = zp; f.p[p] = 0.0f; f.q[p] = 0.0f; f.e[p] = 0.0f;
+                v[0] += (double)(rp * zp);
+                v[1] += (double)(rp * rp);
+            }
+            block_sum<2>(v, bs);
+            if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[(2 + k) * gridDim.x + blockIdx.x] = bs[k];
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        double ti[2];
+        grid_total<2>(part, 2, ti);
+        double rz = ti[0], rri = ti[1];
+        const double stop_in = f.eta2 * rri;
+        double beta = 0.0;
+        int inner = 0;
+        while (rri > stop_in && inner < f.maxin) {
+            // [A] p = z + beta p, q = A z + beta q (FP32); partial p.q
+            {
+                constexpr int U = ESDC_CG_UNROLL;
+                float acc = 0.0f;
+                const float bf = (float)beta;
+                for (int p0 = tid; p0 < N; p0 += U * stride) {
+                    float az[U], zp[U], po[U], qo[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int p = p0 + u * stride;
+                        if (p < N) {
+                            NodeIdx n = node_idx(m, p);
+                            int c;
+                            az[u] = apply_op_f(m, f.z, p, n, gih2f, &c);
+                            zp[u] = __ldcg(f.z + p);
+                            po[u] = f.p[p];
+                            qo[u] = f.q[p];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int p = p0 + u * stride;
+                        if (p < N) {
+                            const float pp = fmaf(bf, po[u], zp[u]);
+                            const float qp = fmaf(bf, qo[u], az[u]);
+                            f.p[p] = pp;
+                            f.q[p] = qp;
+                            acc = fmaf(pp, qp, acc);
+                        }
+                    }
+                }
+                double v[1] = {(double)acc};
+                block_sum<1>(v, bs);
+                if (threadIdx.x == 0) part[4 * gridDim.x + blockIdx.x] = bs[0];
+            }
+            if (!grid_barrier(a.bar, target, a.flags)) return;
+            double pq[1];
+            grid_total<1>(part, 4, pq);
+            const float alpha = (float)(rz / pq[0]);
+            // [B] e += alpha p, r -= alpha q, z = D^{-1} r; partials r.z, r.r
+            {
+                constexpr int U = ESDC_CG_UNROLL;
+                float acc0 = 0.0f, acc1 = 0.0f;
+                for (int p0 = tid; p0 < N; p0 += U * stride) {
+                    float qv[U], rv[U], ev[U], pv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int p = p0 + u * stride;
+                        if (p < N) { qv[u] = f.q[p]; rv[u] = f.r[p]; ev[u] = f.e[p]; pv[u] = f.p[p]; }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int p = p0 + u * stride;
+                        if (p < N) {
+                            const float rp = fmaf(-alpha, qv[u], rv[u]);
+                            f.e[p] = fmaf(alpha, pv[u], ev[u]);
+                            f.r[p] = rp;
+                            float zp = rp;
+                            if (a.precond) {
+                                NodeIdx n = node_idx(m, p);
+                                int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
+                                        (n.iz > 0) + (n.iz < m.nz - 1);
+                                zp = f.dinv[c] * rp;
+                            }
+                            f.z[p] = zp;
+                            acc0 = fmaf(rp, zp, acc0);
+                            acc1 = fmaf(rp, rp, acc1);
+                        }
+                    }
+                }
+                double v[2] = {(double)acc0, (double)acc1};
+                block_sum<2>(v, bs);
+                if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[(5 + k) * gridDim.x + blockIdx.x] = bs[k];
+            }
+            if (!grid_barrier(a.bar, target, a.flags)) return;
+            double t2[2];
+            grid_total<2>(part, 5, t2);
+            beta = t2[0] / rz;
+            rz = t2[0];
+            rri = t2[1];
+            ++inner;
+            if (!isfinite(rri)) { bad = true; break; }
+        }
+        inner_total += inner;
+        if (bad) break;
+        // x += e (FP64)
+        for (int p = tid; p < N; p += stride) a.x[p] += (double)f.e[p];
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        // r = b - A x (FP64); partial r.r
+        {
+            double v[1] = {0.0};
+            for (int p = tid; p < N; p += stride) {
+                NodeIdx n = node_idx(m, p);
+                int c;
+                const double rp = a.b[p] - apply_op(m, a.x, p, n, gih2, &c);
+                a.r[p] = rp;
+                v[0] = fma(rp, rp, v[0]);
+            }
+            block_sum<1>(v, bs);
+            if (threadIdx.x == 0) part[7 * gridDim.x + blockIdx.x] = bs[0];
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        double t3[1];
+        grid_total<1>(part, 7, t3);
+        rr = t3[0];
+        ++outer;
+        if (!isfinite(rr)) { bad = true; break; }
+        done = rr <= stop;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = inner_total;
+        a.status[1] = outer;
+        if (a.iter_log) *a.iter_log = inner_total;
+        if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+        else if (!done) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+    }
+}
+
 }  // namespace
 
 int esdc_cg_blocks(const MeshDev& mesh, int threads)
@@ -347,4 +560,35 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
     cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void*)k_cg, dim3(nb), dim3(w.threads), args, 0, s);
+}
+
+cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b, double* x,
+                                 double tol, int maxit, int precond, int* iter_log, int* flags, cudaStream_t s)
+{
+    CgArgs a;
+    a.m = mesh;
+    a.g = g;
+    for (int c = 0; c < 7; ++c) a.dinv[c] = 1.0 / (1.0 + g * mesh.ih2 * c);
+    a.b = b;
+    a.x = x;
+    a.r = w.r; a.p = w.p; a.q = w.q; a.z = w.z;
+    a.part = w.part;
+    a.bar = w.bar;
+    a.status = w.status;
+    a.iter_log = iter_log;
+    a.flags = flags;
+    a.tol2 = tol * tol;
+    a.maxit = maxit;
+    a.precond = precond;
+    CgMixArgs f;
+    f.r = w.r32; f.p = w.p32; f.q = w.q32; f.z = w.z32; f.e = w.e32;
+    for (int c = 0; c < 7; ++c) f.dinv[c] = (float)a.dinv[c];
+    f.eta2 = 1e-10f;            // inner solves reduce the residual by 1e-5
+    f.maxin = maxit < 60 ? maxit : 60;
+    f.maxout = 8;
+    int nb = w.max_blocks;
+    void* args[] = {&a, &f};
+    cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void*)k_cg_mixed, dim3(nb), dim3(w.threads), args, 0, s);
 }

@@ -61,7 +61,8 @@ struct ModelDevF {            // FP32 copy of the parameters (precision form)
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
 struct CgWork {
     double *r, *p, *q, *z;          // [ld] each
-    double* part;                   // [6 * max_blocks] block partial sums
+    float *r32, *p32, *q32, *z32, *e32;   // [ld] each, precision form only (else null)
+    double* part;                   // [8 * max_blocks] block partial sums
     unsigned* bar;                  // [2] grid barrier: arrival count, generation
     int* status;                    // [2]: iterations of the last solve, flag bits
     int max_blocks;
@@ -77,5 +78,10 @@ struct CgWork {
 cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
                            double* x, double tol, int maxit, int precond, int* iter_log,
                            int* flags, cudaStream_t s);
+// Precision form: FP32 inner PCG with FP64 iterative refinement (same contract;
+// iter_log receives the number of inner iterations).
+cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
+                                 double* x, double tol, int maxit, int precond, int* iter_log,
+                                 int* flags, cudaStream_t s);
 // Blocks to use for a cooperative CG launch on this device.
 int esdc_cg_blocks(const MeshDev& mesh, int threads);

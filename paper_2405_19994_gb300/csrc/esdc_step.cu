@@ -127,7 +127,8 @@ void free_all(esdc_handle* h)
     for (auto& e : h->prof_ev)
         if (e) cudaEventDestroy(e);
     void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev, h->Vprev,
-                    h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.part, h->cg.bar, h->cg.status,
+                    h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.r32, h->cg.p32, h->cg.q32, h->cg.z32,
+                    h->cg.e32, h->cg.part, h->cg.bar, h->cg.status,
                     h->rmax, h->flags, h->cg_log};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -227,7 +228,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     h->cg.threads = ESDC_CG_THREADS;
     h->cg.max_blocks = esdc_cg_blocks(h->mesh, h->cg.threads);
     if (h->cg.max_blocks < 1) return fail(ESDC_ERR_CUDA);
-    if (cudaMalloc((void**)&h->cg.part, sizeof(double) * 6 * h->cg.max_blocks) != cudaSuccess ||
+    if (cudaMalloc((void**)&h->cg.part, sizeof(double) * 8 * h->cg.max_blocks) != cudaSuccess ||
         cudaMalloc((void**)&h->cg.bar, sizeof(unsigned) * 2) != cudaSuccess ||
         cudaMalloc((void**)&h->cg.status, sizeof(int) * 2) != cudaSuccess ||
         cudaMalloc((void**)&h->rmax, sizeof(unsigned long long) * 2 * ESDC_NSMAX) != cudaSuccess ||
@@ -235,6 +236,13 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
         cudaMalloc((void**)&h->cg_log, sizeof(int) * 64 * ESDC_MMAX) != cudaSuccess)
         return fail(ESDC_ERR_NO_MEMORY);
     h->cg_log_len = 64 * ESDC_MMAX;
+    if (o.precision == 1) {                       // FP32 vectors of the inner solves
+        float** fv[] = {&h->cg.r32, &h->cg.p32, &h->cg.q32, &h->cg.z32, &h->cg.e32};
+        for (float** f : fv) {
+            if (cudaMalloc((void**)f, sizeof(float) * ld) != cudaSuccess) return fail(ESDC_ERR_NO_MEMORY);
+            cudaMemset(*f, 0, sizeof(float) * ld);
+        }
+    }
     cudaMemset(h->cg.bar, 0, sizeof(unsigned) * 2);
     cudaMemset(h->cg.status, 0, sizeof(int) * 2);
     cudaMemset(h->flags, 0, sizeof(int));
@@ -417,8 +425,12 @@ int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, i
     if (!b || !x || !(g >= 0.0) || !std::isfinite(g)) return set_err(h, ESDC_ERR_INVALID_ARG, "bad solve args");
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, sizeof(int), s));
-    CUDA_TRY(h, esdc_cg_launch(h->mesh, h->cg, g, b, x, h->opt.tol_cg, h->opt.cg_maxit, h->opt.precond,
-                               nullptr, h->flags, s));
+    if (h->opt.precision == 1)
+        CUDA_TRY(h, esdc_cg_mixed_launch(h->mesh, h->cg, g, b, x, h->opt.tol_cg, h->opt.cg_maxit,
+                                         h->opt.precond, nullptr, h->flags, s));
+    else
+        CUDA_TRY(h, esdc_cg_launch(h->mesh, h->cg, g, b, x, h->opt.tol_cg, h->opt.cg_maxit, h->opt.precond,
+                                   nullptr, h->flags, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     int st[2] = {0, 0}, flags = 0;
     CUDA_TRY(h, cudaMemcpy(st, h->cg.status, sizeof st, cudaMemcpyDeviceToHost));

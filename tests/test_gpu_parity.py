@@ -222,6 +222,24 @@ def test_errors_reported():
 
 # ---------------------------------------------------------------- precision form (FP32 ionic model)
 
+@pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5)])
+@pytest.mark.parametrize("g", [1e-3, 0.05, 2.0])
+def test_refinement_solve_matches_dct(shape, g):
+    """Precision-form solve (FP32 inner PCG, FP64 residuals): reaches the same
+    FP64 tolerance as the FP64 CG, so it meets the same bound against the DCT."""
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    s = P.Solver.from_workload(wl, cg_maxit=2000, precision="mixed")
+    m = O.Monodomain(wl)
+    rng = np.random.default_rng(6)
+    b = rng.normal(size=wl.n_nodes)
+    x0 = rng.normal(size=wl.n_nodes)
+    want = m.solve_shifted(g, b, method=O.SOLVE_DCT)
+    xd = torch.from_numpy(x0).cuda()
+    s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+    kappa = 1 + 4 * 3 * g / wl.h**2
+    assert rel(xd.cpu().numpy(), want) < 50 * kappa * 1e-14
+
 @pytest.mark.parametrize("model,mesh,M,K", [(I.MODEL_HH1952, (12, 10, 1), 3, 4), (I.MODEL_SYN19, (11, 6, 4), 4, 6)])
 def test_precision_form_one_step(model, mesh, M, K):
     """The precision form evaluates f_E, Lambda and y_inf in FP32; everything else
