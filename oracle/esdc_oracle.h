@@ -104,6 +104,10 @@ typedef struct {
     int    solver;                 /* ORC_SOLVE_*                              */
     double cg_tol; int cg_maxit;   /* for ORC_SOLVE_CG                         */
     int    ionic_off;              /* 1: I_ion = 0, h_a = 0 (diffusion only)   */
+    /* Layered anisotropic conductivity (NULL: isotropic sigma): per z-layer
+     * tensor entries [nz] sigma_xx, sigma_yy, sigma_xy, sigma_zz (in-plane
+     * fibres; sigma_xz = sigma_yz = 0). */
+    const double *lay_sxx, *lay_syy, *lay_sxy, *lay_szz;
     /* private workspace, owned by the oracle */
     void*  work;
 } orc_mono;
@@ -130,6 +134,16 @@ void orc_ionic_point(int model, const double* mp, const double* u,
 void orc_laplacian(const orc_mono* m, const double* v, double* out);
 /* Solve (I - g L) x = b with L the Laplacian above, by the chosen method. */
 int  orc_solve_shifted(const orc_mono* m, int method, double g, const double* b, double* x);
+/* The conductivity operator A = div(sigma grad) in flux form (conductivity
+ * included): sigma L for an isotropic sigma; for layered anisotropic sigma
+ *   (A v)_p = (1/h^2) [ sum_x-faces sxx (v_q - v_p) + sum_y-faces syy (v_q - v_p)
+ *                     + sum_z-faces (szz_k + szz_l)/2 (v_q - v_p)
+ *                     + sum_{a,b = +-1} (a b sxy / 2) (v_{i+a,j+b} - v_p) ],
+ * with terms of absent neighbours dropped (zero flux through boundary faces). */
+void orc_conductivity(const orc_mono* m, const double* v, double* out);
+/* Solve (I - g A) x = b.  Isotropic sigma: the chosen method on sigma L.
+ * Layered sigma: CG or dense (a DCT request falls back to CG). */
+int  orc_solve_A(const orc_mono* m, int method, double g, const double* b, double* x);
 
 /* ------------------------------------------------------------------ */
 /* Scalar test equation y' = (lI + lE + le) y  (Sec. 4, eq. (test))    */

@@ -51,7 +51,8 @@ class _Mono(C.Structure):
                 ("nbox", C.c_int), ("box", C.c_void_p), ("amp", C.c_void_p),
                 ("t_on", C.c_void_p), ("t_off", C.c_void_p),
                 ("solver", C.c_int), ("cg_tol", C.c_double), ("cg_maxit", C.c_int),
-                ("ionic_off", C.c_int), ("work", C.c_void_p)]
+                ("ionic_off", C.c_int), ("lay_sxx", C.c_void_p), ("lay_syy", C.c_void_p),
+                ("lay_sxy", C.c_void_p), ("lay_szz", C.c_void_p), ("work", C.c_void_p)]
 
 
 _D = C.POINTER(C.c_double)
@@ -77,6 +78,8 @@ def lib():
         L.orc_ionic_rest.argtypes = [C.c_int, _D, C.c_double, _D]
         L.orc_laplacian.argtypes = [C.POINTER(_Mono), _D, _D]
         L.orc_solve_shifted.argtypes = [C.POINTER(_Mono), C.c_int, C.c_double, _D, _D]
+        L.orc_conductivity.argtypes = [C.POINTER(_Mono), _D, _D]
+        L.orc_solve_A.argtypes = [C.POINTER(_Mono), C.c_int, C.c_double, _D, _D]
         L.orc_stability_R1.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
                                        C.c_double, C.c_int]
         L.orc_stability_R1.restype = C.c_double
@@ -173,9 +176,19 @@ class Monodomain:
                       np.ascontiguousarray(wl.t_on, np.float64),
                       np.ascontiguousarray(wl.t_off, np.float64)]
         mp, box, amp, ton, toff = self._keep
+        lay = [None] * 4
+        layers = getattr(wl, "layers", None)
+        if layers is not None:
+            lay_arrs = [np.ascontiguousarray(layers[k], np.float64) for k in ("sxx", "syy", "sxy", "szz")]
+            assert all(len(a) == wl.nz for a in lay_arrs)
+            self._keep += lay_arrs
+            lay = [a.ctypes.data for a in lay_arrs]
+            if solver == SOLVE_DCT:
+                solver = SOLVE_CG        # DCT-II does not diagonalise the layered operator
         self.m = _Mono(wl.dim, wl.nx, wl.ny, wl.nz, wl.h, wl.sigma, wl.chi, wl.Cm, wl.model,
                        mp.ctypes.data, len(mp), len(amp), box.ctypes.data, amp.ctypes.data,
-                       ton.ctypes.data, toff.ctypes.data, solver, cg_tol, cg_maxit, int(ionic_off), None)
+                       ton.ctypes.data, toff.ctypes.data, solver, cg_tol, cg_maxit, int(ionic_off),
+                       lay[0], lay[1], lay[2], lay[3], None)
         self.P = _Problem()
         if lib().orc_mono_problem(C.byref(self.m), C.byref(self.P)):
             raise ValueError("invalid monodomain description")
@@ -198,6 +211,24 @@ class Monodomain:
         out = np.zeros(self.N)
         lib().orc_laplacian(C.byref(self.m), _p(v), _p(out))
         return out
+
+    def conductivity(self, v: np.ndarray) -> np.ndarray:
+        """A v with A = div(sigma grad) (conductivity included)."""
+        v = np.ascontiguousarray(v, np.float64)
+        out = np.zeros(self.N)
+        lib().orc_conductivity(C.byref(self.m), _p(v), _p(out))
+        return out
+
+    def solve_A(self, g: float, b: np.ndarray, x0: np.ndarray | None = None,
+                method: int | None = None) -> np.ndarray:
+        """Solve (I - g A) x = b."""
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(self.N) if x0 is None else np.array(x0, np.float64)
+        rc = lib().orc_solve_A(C.byref(self.m), self.m.solver if method is None else method,
+                               float(g), _p(b), _p(x))
+        if rc:
+            raise RuntimeError(f"oracle solve failed ({rc})")
+        return x
 
     def solve_shifted(self, g: float, b: np.ndarray, x0: np.ndarray | None = None,
                       method: int | None = None) -> np.ndarray:

@@ -10,6 +10,12 @@
  * (Sec. 5); the second-order stencil is this build's reading (it is also
  * diagonalised by DCT-II, so the paper's solver applies to it unchanged).
  *
+ * The layered anisotropic operator (orc_conductivity) keeps the same flux form:
+ * the in-plane cross term sigma_xy V_xy uses the four diagonal neighbours, each
+ * with weight a b sigma_xy/(2 h^2), and terms of absent neighbours are dropped,
+ * so the matrix stays symmetric with zero row sums (reading of the conormal
+ * zero-flux condition; checked by dense eigenvalues in the tests).
+ *
  * Solvers for (I - g L) x = b:
  *   ORC_SOLVE_DCT   exact: orthonormal DCT-II along each axis, divide by the
  *                   eigenvalues 1 - g sum_axes mu_k, mu_k = -(4/h^2) sin^2(pi k/(2n)),
@@ -40,6 +46,40 @@ void orc_laplacian(const orc_mono* m, const double* v, double* out)
                 if (iy < ny - 1) s += v[p + nx] - v[p];
                 if (iz > 0)      s += v[p - (int64_t)nx * ny] - v[p];
                 if (iz < nz - 1) s += v[p + (int64_t)nx * ny] - v[p];
+                out[p] = s * ih2;
+            }
+}
+
+static int is_layered(const orc_mono* m) { return m->lay_sxx != NULL; }
+
+void orc_conductivity(const orc_mono* m, const double* v, double* out)
+{
+    const int nx = m->nx, ny = m->ny, nz = m->nz;
+    const int64_t N = mesh_n(m);
+    if (!is_layered(m)) {
+        orc_laplacian(m, v, out);
+        for (int64_t p = 0; p < N; ++p) out[p] *= m->sigma;
+        return;
+    }
+    const double ih2 = 1.0 / (m->h * m->h);
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    #pragma omp parallel for schedule(static)
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                int64_t p = ix + sy * iy + sz * iz;
+                double s = 0.0;
+                const double sxx = m->lay_sxx[iz], syy = m->lay_syy[iz], sxy = m->lay_sxy[iz];
+                if (ix > 0)      s += sxx * (v[p - 1] - v[p]);
+                if (ix < nx - 1) s += sxx * (v[p + 1] - v[p]);
+                if (iy > 0)      s += syy * (v[p - sy] - v[p]);
+                if (iy < ny - 1) s += syy * (v[p + sy] - v[p]);
+                if (iz > 0)      s += 0.5 * (m->lay_szz[iz] + m->lay_szz[iz - 1]) * (v[p - sz] - v[p]);
+                if (iz < nz - 1) s += 0.5 * (m->lay_szz[iz] + m->lay_szz[iz + 1]) * (v[p + sz] - v[p]);
+                for (int a = -1; a <= 1; a += 2)
+                    for (int b = -1; b <= 1; b += 2)
+                        if (ix + a >= 0 && ix + a < nx && iy + b >= 0 && iy + b < ny)
+                            s += 0.5 * sxy * a * b * (v[p + a + sy * b] - v[p]);
                 out[p] = s * ih2;
             }
 }
@@ -127,26 +167,40 @@ static double dot(int64_t n, const double* a, const double* b)
     return s;
 }
 
-static void apply_shifted(const orc_mono* m, double g, const double* v, double* out)
+/* out = v - g L v (use_A = 0) or v - g A v (use_A = 1) */
+static void apply_shifted_op(const orc_mono* m, int use_A, double g, const double* v, double* out)
 {
-    orc_laplacian(m, v, out);
+    if (use_A) orc_conductivity(m, v, out);
+    else orc_laplacian(m, v, out);
     const int64_t N = mesh_n(m);
     for (int64_t i = 0; i < N; ++i) out[i] = v[i] - g * out[i];
 }
 
+static void apply_shifted(const orc_mono* m, double g, const double* v, double* out)
+{
+    apply_shifted_op(m, 0, g, v, out);
+}
+
+static int solve_cg_op(const orc_mono* m, int use_A, double g, const double* b, double* x);
+
 static int solve_cg(const orc_mono* m, double g, const double* b, double* x)
+{
+    return solve_cg_op(m, 0, g, b, x);
+}
+
+static int solve_cg_op(const orc_mono* m, int use_A, double g, const double* b, double* x)
 {
     const int64_t N = mesh_n(m);
     double* r = malloc(sizeof(double) * N);
     double* p = malloc(sizeof(double) * N);
     double* q = malloc(sizeof(double) * N);
-    apply_shifted(m, g, x, q);
+    apply_shifted_op(m, use_A, g, x, q);
     for (int64_t i = 0; i < N; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
     double rr = dot(N, r, r), bb = dot(N, b, b);
     double tol2 = m->cg_tol * m->cg_tol * bb;
     int it = 0, ok = (rr <= tol2);
     while (!ok && it < m->cg_maxit) {
-        apply_shifted(m, g, p, q);
+        apply_shifted_op(m, use_A, g, p, q);
         double alpha = rr / dot(N, p, q);
         for (int64_t i = 0; i < N; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         double rr_new = dot(N, r, r);
@@ -162,10 +216,10 @@ static int solve_cg(const orc_mono* m, double g, const double* b, double* x)
 
 /* ---------- dense Cholesky (tiny meshes) ---------- */
 
-typedef struct { double g; double* Lf; } dense_fac;
+typedef struct { double g; int use_A; double* Lf; } dense_fac;
 typedef struct { int nf; dense_fac f[16]; } dense_cache;
 
-static double* dense_factor(const orc_mono* m, double g)
+static double* dense_factor(const orc_mono* m, int use_A, double g)
 {
     const int64_t N = mesh_n(m);
     double* A = calloc((size_t)(N * N), sizeof(double));
@@ -173,7 +227,7 @@ static double* dense_factor(const orc_mono* m, double g)
     double* col = malloc(sizeof(double) * N);
     for (int64_t j = 0; j < N; ++j) {          /* column j = (I - g L) e_j */
         e[j] = 1.0;
-        apply_shifted(m, g, e, col);
+        apply_shifted_op(m, use_A, g, e, col);
         for (int64_t i = 0; i < N; ++i) A[i * N + j] = col[i];
         e[j] = 0.0;
     }
@@ -194,18 +248,18 @@ static double* dense_factor(const orc_mono* m, double g)
     return A;
 }
 
-static int solve_dense(orc_mono* m, double g, const double* b, double* x)
+static int solve_dense(orc_mono* m, int use_A, double g, const double* b, double* x)
 {
     const int64_t N = mesh_n(m);
     if (N > 2048) return -2;
     dense_cache* dc = m->work;
     if (!dc) { dc = calloc(1, sizeof(dense_cache)); m->work = dc; }
     double* Lf = NULL;
-    for (int i = 0; i < dc->nf; ++i) if (dc->f[i].g == g) Lf = dc->f[i].Lf;
+    for (int i = 0; i < dc->nf; ++i) if (dc->f[i].g == g && dc->f[i].use_A == use_A) Lf = dc->f[i].Lf;
     if (!Lf) {
-        Lf = dense_factor(m, g);
+        Lf = dense_factor(m, use_A, g);
         if (!Lf) return -3;
-        if (dc->nf < 16) { dc->f[dc->nf].g = g; dc->f[dc->nf].Lf = Lf; dc->nf++; }
+        if (dc->nf < 16) { dc->f[dc->nf].g = g; dc->f[dc->nf].use_A = use_A; dc->f[dc->nf].Lf = Lf; dc->nf++; }
     }
     for (int64_t i = 0; i < N; ++i) {           /* L y = b */
         double s = b[i];
@@ -227,8 +281,15 @@ int orc_solve_shifted(const orc_mono* m, int method, double g, const double* b, 
 {
     if (method == ORC_SOLVE_DCT) return solve_dct(m, g, b, x);
     if (method == ORC_SOLVE_CG) return solve_cg(m, g, b, x);
-    if (method == ORC_SOLVE_DENSE) return solve_dense((orc_mono*)m, g, b, x);
+    if (method == ORC_SOLVE_DENSE) return solve_dense((orc_mono*)m, 0, g, b, x);
     return -1;
+}
+
+int orc_solve_A(const orc_mono* m, int method, double g, const double* b, double* x)
+{
+    if (!is_layered(m)) return orc_solve_shifted(m, method, g * m->sigma, b, x);
+    if (method == ORC_SOLVE_DENSE) return solve_dense((orc_mono*)m, 1, g, b, x);
+    return solve_cg_op(m, 1, g, b, x);
 }
 
 void orc_mono_free(orc_mono* m)

@@ -196,14 +196,14 @@ done:
 /* ------------------------------------------------------------------ */
 static int64_t mono_N(const orc_mono* m) { return (int64_t)m->nx * m->ny * m->nz; }
 
-/* f_I = ((chi C_m)^{-1} A V, 0, 0) with A = sigma L */
+/* f_I = ((chi C_m)^{-1} A V, 0, 0) with A = div(sigma grad) (orc_conductivity) */
 static void mono_fI(const orc_problem* P, const double* y, double* out)
 {
     const orc_mono* m = P->ctx;
     const int64_t N = mono_N(m);
     memset(out, 0, sizeof(double) * P->n);
-    orc_laplacian(m, y, out);
-    const double s = m->sigma / (m->chi * m->Cm);
+    orc_conductivity(m, y, out);
+    const double s = 1.0 / (m->chi * m->Cm);
     for (int64_t p = 0; p < N; ++p) out[p] *= s;
 }
 
@@ -212,8 +212,8 @@ static int mono_solve(const orc_problem* P, double gamma, const double* rhs, dou
     const orc_mono* m = P->ctx;
     const int64_t N = mono_N(m);
     memcpy(x + N, rhs + N, sizeof(double) * (P->n - N));   /* non-V rows: x = rhs */
-    const double g = gamma * m->sigma / (m->chi * m->Cm);
-    return orc_solve_shifted(m, m->solver, g, rhs, x);
+    const double g = gamma / (m->chi * m->Cm);
+    return orc_solve_A(m, m->solver, g, rhs, x);
 }
 
 static double stim_at(const orc_mono* m, double t, int ix, int iy, int iz)

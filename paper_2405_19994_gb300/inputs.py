@@ -87,6 +87,8 @@ class Workload:
     sigma: float = 0.17
     chi: float = 140.0
     Cm: float = 0.01
+    # layered anisotropic conductivity: {"sxx","syy","sxy","szz"} -> [nz] arrays, or None
+    layers: dict | None = None
     # stimulus boxes: [x0, x1, y0, y1, z0, z1] node index ranges (half-open)
     boxes: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 6), np.int32))
     amp: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
@@ -116,8 +118,23 @@ class Workload:
         b[:, 3] = np.minimum(b[:, 3], ny)
         b[:, 5] = np.minimum(b[:, 5], nz)
         dim = 1 if (ny == 1 and nz == 1) else (2 if nz == 1 else 3)
+        layers = self.layers
+        if layers is not None and nz != self.nz:     # same fibre rotation over the new depth
+            sl = float(np.max(layers["sxx"] + layers["syy"] - layers["szz"]))
+            layers = fibre_layers(nz, sigma_l=sl, sigma_t=float(layers["szz"][0]))
         return dataclasses.replace(self, name=name or f"{self.name}@{nx}x{ny}x{nz}",
-                                   nx=nx, ny=ny, nz=nz, dim=dim, boxes=b)
+                                   nx=nx, ny=ny, nz=nz, dim=dim, boxes=b, layers=layers)
+
+
+def fibre_layers(nz: int, sigma_l: float = 0.17, sigma_t: float = 0.02,
+                 theta0_deg: float = -60.0, theta1_deg: float = 60.0) -> dict:
+    """Conductivity tensor of fibres lying in the xy-plane whose angle rotates
+    linearly through the depth, theta(z) from theta0 (bottom layer) to theta1
+    (top layer): sigma = sigma_t I + (sigma_l - sigma_t) f f^T, f = (cos, sin, 0)."""
+    th = np.deg2rad(np.linspace(theta0_deg, theta1_deg, nz)) if nz > 1 else np.array([np.deg2rad(theta0_deg)])
+    d = sigma_l - sigma_t
+    return {"sxx": sigma_t + d * np.cos(th) ** 2, "syy": sigma_t + d * np.sin(th) ** 2,
+            "sxy": d * np.sin(th) * np.cos(th), "szz": np.full(nz, sigma_t)}
 
 
 def hh_sheet_32() -> Workload:
@@ -133,6 +150,18 @@ def syn19_slab() -> Workload:
                     model=MODEL_SYN19, params=syn19_params(), V0=-83.4,
                     M=4, K=6, dt=0.05, T=50.0,
                     boxes=np.array([[0, 2, 0, 128, 0, 32]], np.int32),
+                    amp=np.array([0.5]), t_on=np.array([0.0]), t_off=np.array([1.0]))
+
+
+def hh_aniso_slab() -> Workload:
+    """The precision-form workload: 3D 256x256x64 (4,194,304 nodes), h = 0.2 mm,
+    Hodgkin-Huxley, fibres rotating from -60 to +60 degrees through the depth
+    (sigma_l = 0.17, sigma_t = 0.02 mS/mm), planar stimulus on the two cell
+    layers at x = 0 for [0, 1) ms, M = 4, K = 6, dt = 0.05 ms, T = 10 ms."""
+    return Workload(name="hh_aniso_slab_256x256x64", dim=3, nx=256, ny=256, nz=64, h=0.2,
+                    model=MODEL_HH1952, params=hh1952_params(), V0=-75.0,
+                    M=4, K=6, dt=0.05, T=10.0, layers=fibre_layers(64),
+                    boxes=np.array([[0, 2, 0, 256, 0, 64]], np.int32),
                     amp=np.array([0.5]), t_on=np.array([0.0]), t_off=np.array([1.0]))
 
 

@@ -61,3 +61,84 @@ def test_solvers_agree_and_solve(orc, shape):
         assert np.abs(r).max() < 1e-13 * np.abs(b).max()
     np.testing.assert_allclose(xs[0], xs[2], atol=1e-13)
     np.testing.assert_allclose(xs[1], xs[2], atol=1e-13)
+
+
+# ---------------------------------------------------------------- layered anisotropic conductivity
+
+def _aniso(nx, ny, nz, h=0.3, sl=0.17, st=0.02):
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.h = h
+    wl.layers = I.fibre_layers(nz, sl, st)
+    return wl, O.Monodomain(wl, solver=O.SOLVE_CG)
+
+
+def test_aniso_operator_exact_on_quadratics(orc):
+    # Interior nodes: central differences are exact for quadratics, so
+    # A x^2 = 2 sxx, A y^2 = 2 syy, A (x y) = 2 sxy, A z^2 = 2 szz (per layer).
+    nx, ny, nz, h = 9, 8, 7, 0.3
+    wl, m = _aniso(nx, ny, nz, h)
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    x = ((ix + 0.5) * h).transpose(2, 1, 0).reshape(-1)
+    y = ((iy + 0.5) * h).transpose(2, 1, 0).reshape(-1)
+    z = ((iz + 0.5) * h).transpose(2, 1, 0).reshape(-1)
+    kz = iz.transpose(2, 1, 0).reshape(-1)
+    inner = ((ix > 0) & (ix < nx - 1) & (iy > 0) & (iy < ny - 1) & (iz > 0) & (iz < nz - 1)).transpose(2, 1, 0).reshape(-1)
+    L = wl.layers
+    for f, want in ((x * x, 2 * L["sxx"][kz]), (y * y, 2 * L["syy"][kz]), (x * y, 2 * L["sxy"][kz]),
+                    (z * z, 2 * L["szz"][kz])):
+        got = m.conductivity(f)
+        np.testing.assert_allclose(got[inner], want[inner], rtol=0, atol=1e-11)
+
+
+def test_aniso_operator_symmetric_nsd_constant_nullspace(orc):
+    nx, ny, nz = 6, 5, 4
+    wl, m = _aniso(nx, ny, nz, h=0.5, sl=0.3, st=0.01)       # strong anisotropy
+    N = nx * ny * nz
+    A = np.stack([m.conductivity(e) for e in np.eye(N)], axis=1)
+    np.testing.assert_allclose(A, A.T, atol=1e-14)
+    ev = np.linalg.eigvalsh(A)
+    assert ev.max() < 1e-12 and ev[-2] < -1e-4
+    np.testing.assert_allclose(A @ np.ones(N), 0.0, atol=1e-13)
+
+
+def test_aniso_reduces_to_isotropic(orc):
+    nx, ny, nz = 7, 6, 3
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    iso = O.Monodomain(wl)
+    wl2 = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl2.layers = {"sxx": np.full(nz, wl.sigma), "syy": np.full(nz, wl.sigma), "sxy": np.zeros(nz),
+                  "szz": np.full(nz, wl.sigma)}
+    lay = O.Monodomain(wl2, solver=O.SOLVE_CG)
+    v = np.random.default_rng(3).normal(size=nx * ny * nz)
+    np.testing.assert_allclose(lay.conductivity(v), wl.sigma * iso.laplacian(v), rtol=0, atol=1e-12)
+
+
+def test_aniso_solves_agree(orc):
+    wl, m = _aniso(8, 7, 5)
+    b = np.random.default_rng(4).normal(size=8 * 7 * 5)
+    g = 0.02
+    x_cg = m.solve_A(g, b, method=O.SOLVE_CG)
+    x_de = m.solve_A(g, b, method=O.SOLVE_DENSE)
+    np.testing.assert_allclose(x_cg, x_de, atol=1e-13)
+    r = x_cg - g * m.conductivity(x_cg) - b
+    assert np.abs(r).max() < 1e-13
+
+
+def test_aniso_second_order_consistency(orc):
+    # smooth field, interior nodes: error of A f against div(sigma grad f) falls ~4x per halving of h
+    errs = []
+    for n, h in ((12, 0.2), (24, 0.1)):
+        wl, m = _aniso(n, n, 3, h)
+        ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(3), indexing="ij")
+        x = ((ix + 0.5) * h).transpose(2, 1, 0).reshape(-1)
+        y = ((iy + 0.5) * h).transpose(2, 1, 0).reshape(-1)
+        kz = iz.transpose(2, 1, 0).reshape(-1)
+        f = np.sin(1.3 * x) * np.cos(0.7 * y)
+        fxx = -1.69 * f
+        fyy = -0.49 * f
+        fxy = -1.3 * 0.7 * np.cos(1.3 * x) * np.sin(0.7 * y)
+        L = wl.layers
+        want = L["sxx"][kz] * fxx + L["syy"][kz] * fyy + 2 * L["sxy"][kz] * fxy
+        inner = ((ix > 0) & (ix < n - 1) & (iy > 0) & (iy < n - 1) & (iz == 1)).transpose(2, 1, 0).reshape(-1)
+        errs.append(np.abs(m.conductivity(f) - want)[inner].max())
+    assert 3.3 < errs[0] / errs[1] < 4.8, errs
