@@ -174,7 +174,7 @@ def run_ours(args):
         dist.init_process_group("gloo")
         pg = dist
     wl = I.syn19_slab()
-    if args.nz != wl.nz:                     # smaller slab for profiler captures
+    if args.nz and args.nz != wl.nz:         # smaller slab for profiler captures
         wl = wl.with_mesh(wl.nx, wl.ny, args.nz)
     M, K, dt = wl.M, wl.K, wl.dt
     N = wl.n_nodes
@@ -319,21 +319,168 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def _activation_update(act, v_old, v_new, t_old, dt, level=-40.0):
+    """First upward crossing of `level`, linear interpolation between step ends."""
+    import torch
+    hit = (v_old < level) & (v_new >= level) & torch.isnan(act)
+    frac = (level - v_old) / torch.clamp(v_new - v_old, min=1e-300)
+    act[hit] = (t_old + frac * dt)[hit]
+
+
+def _simulate(solver, wl, n_steps, record=True):
+    """Run n_steps from rest; per-step CUDA-event timing of the sweeps only.
+    Returns (V at the end [N], activation times [N] or None, sweep ms total)."""
+    import torch
+    N, dt = wl.n_nodes, wl.dt
+    y = solver.new_state()
+    solver.init_state(y, wl.V0)
+    stream = torch.cuda.current_stream()
+    act = torch.full((N,), float("nan"), dtype=torch.float64, device=y.device) if record else None
+    v_old = y[0, :N].clone() if record else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+    t = 0.0
+    for n in range(n_steps):
+        ev[n][0].record(stream)
+        solver.sweep(y, t, dt, wl.M, wl.K)
+        ev[n][1].record(stream)
+        if record:
+            v_new = y[0, :N]
+            _activation_update(act, v_old, v_new, t, dt)
+            v_old.copy_(v_new)
+        t += dt
+    torch.cuda.synchronize()
+    rc = solver.residual()[0]
+    if rc != 0:
+        raise RuntimeError(f"run failed with code {rc}")
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    return y[0, :N].clone(), act, ms
+
+
+def _v_errors(v, ref, act=None, act_ref=None):
+    import torch
+    out = {"V_max_abs_mV": float((v - ref).abs().max()),
+           "V_max_rel": float((v - ref).abs().max() / ref.abs().max()),
+           "V_l2_rel": float(torch.linalg.vector_norm(v - ref) / torch.linalg.vector_norm(ref))}
+    if act is not None:
+        both = ~torch.isnan(act) & ~torch.isnan(act_ref)
+        only = torch.isnan(act) ^ torch.isnan(act_ref)
+        d = (act - act_ref)[both].abs()
+        out.update({"act_max_abs_ms": float(d.max()) if d.numel() else 0.0,
+                    "act_mean_abs_ms": float(d.mean()) if d.numel() else 0.0,
+                    "activated_nodes": int(both.sum()), "activated_in_one_only": int(only.sum())})
+    return out
+
+
+def run_precision_form(args):
+    """The precision form (FP32 ionic model, FP64 state / quadrature / residual,
+    refinement CG) on the anisotropic HH slab, against the FP64 path on the
+    same GPU over the whole simulated interval, and against the oracle on a
+    reduced mesh (the cpu_baseline leg)."""
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1 and rank != 0:
+        return                                         # single-GPU comparison; replicas add nothing here
+    wl = I.hh_aniso_slab()
+    if args.nz and args.nz != wl.nz:
+        wl = wl.with_mesh(wl.nx, wl.ny, args.nz)
+    n_steps = wl.n_steps if args.steps is None else args.steps
+    N = wl.n_nodes
+    runs = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for prec in ("fp64", "mixed"):
+        s = P.Solver.from_workload(wl, M_max=wl.M, precision=prec)
+        _simulate(s, wl, args.warmup, record=False)                 # warm-up (clocks, caches, first launches)
+        s.profile(True)
+        v, act, ms = _simulate(s, wl, n_steps)
+        prof = s.profile_read()
+        s.profile(False)
+        runs[prec] = {"V": v, "act": act, "ms": ms, "prof": prof, "cg": s.stats(wl.K * wl.M).tolist()}
+        s.close()
+    clk = clocks.stop()
+    r64, rmx = runs["fp64"], runs["mixed"]
+    err = _v_errors(rmx["V"], r64["V"], rmx["act"], r64["act"])
+
+    cpu, oracle_err = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = wl.with_mesh(32, 32, 8)
+        m = oracle.Monodomain(sub)
+        y = m.init_state()
+        act_o = np.full(sub.n_nodes, np.nan)
+        t = 0.0
+        c0 = time.perf_counter()
+        for n in range(sub.n_steps):
+            v_old = y[0].copy()
+            y, _, _, _ = m.step(y, t, sub.dt, sub.M, sub.K)
+            hit = (v_old < -40.0) & (y[0] >= -40.0) & np.isnan(act_o)
+            act_o[hit] = t + (-40.0 - v_old[hit]) / (y[0][hit] - v_old[hit]) * sub.dt
+            t += sub.dt
+        cel = time.perf_counter() - c0
+        cpu = {"value": sub.n_nodes * sub.n_steps / cel, "unit": UNIT, "cores": oracle.oracle.threads(),
+               "kind": "oracle", "sample": f"the full {sub.n_steps}-step run of the {sub.nx}x{sub.ny}x{sub.nz} "
+                                           "reduction of the workload (same physics, fibres and stimulus)"}
+        vo = torch.from_numpy(y[0]).cuda()
+        ao = torch.from_numpy(act_o).cuda()
+        oracle_err = {"mesh": f"{sub.nx}x{sub.ny}x{sub.nz}", "steps": sub.n_steps}
+        for prec in ("fp64", "mixed"):
+            s = P.Solver.from_workload(sub, M_max=sub.M, precision=prec)
+            v, act, _ = _simulate(s, sub, sub.n_steps)
+            s.close()
+            oracle_err[prec] = _v_errors(v, vo, act, ao)
+
+    launches = int(sum(v[1] for v in rmx["prof"].values()))
+    ms_step = rmx["ms"] / n_steps
+    line = {
+        "metric": METRIC, "value": N * n_steps / (rmx["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": n_steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": wl.name, "form": "precision", "nodes": N, "M": wl.M, "K": wl.K, "dt_ms": wl.dt,
+                   "T_ms": n_steps * wl.dt, "model": "hh1952", "conductivity": "layered, fibres -60..60 deg",
+                   "l2": "inputs larger than L2 (state + workspace ~1.5 GB)"},
+        "s_per_sim_ms": ms_step * 1e-3 / wl.dt,
+        "fp64": {"value": N * n_steps / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"] / n_steps,
+                 "kernels_ms_per_step": {k: v[0] / n_steps for k, v in r64["prof"].items()},
+                 "cg_iters_last_step": r64["cg"]},
+        "mixed": {"kernels_ms_per_step": {k: v[0] / n_steps for k, v in rmx["prof"].items()},
+                  "cg_iters_last_step": rmx["cg"]},
+        "speedup_vs_fp64_gpu": r64["ms"] / rmx["ms"],
+        "v_error_mixed_vs_fp64_gpu": err,
+        "v_error_vs_oracle_reduced_mesh": oracle_err,
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 40; the precision form runs its whole interval)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nz", type=int, default=32, help="slab depth (32 = the benchmark workload)")
+    ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
+    ap.add_argument("--form", choices=["plain", "precision"], default="plain",
+                    help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.steps is None and args.form == "plain":
+        args.steps = 40
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "precision":
+        run_precision_form(args)
     else:
         run_ours(args)
 

@@ -119,6 +119,21 @@ const char* esdc_last_error(const esdc_handle* h);
 int esdc_set_stimulus(esdc_handle* h, int nbox, const int* box, const double* amp,
                       const double* t_on, const double* t_off);
 
+/*
+ * Layered anisotropic conductivity: per z-layer tensor entries sigma_xx[k],
+ * sigma_yy[k], sigma_xy[k], sigma_zz[k] (host arrays of length nz, mS/mm,
+ * copied; sigma_xz = sigma_yz = 0, i.e. fibres in the xy-plane, e.g. rotating
+ * through the depth).  Replaces the scalar sigma of esdc_create in f_I and in
+ * the diffusion solves: A = div(sigma grad) in flux form, with the in-plane
+ * cross term on the four diagonal neighbours (weight a b sigma_xy/(2h^2)) and
+ * zero flux through boundary faces; z faces use the mean of the two layers'
+ * sigma_zz.  Every layer must be positive definite.  All four pointers NULL
+ * return to the scalar sigma.  Synchronises the device.
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA.
+ */
+int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double* syy,
+                                 const double* sxy, const double* szz);
+
 /* Reports the number of states per node (1 + m_1 + m_2), the number of mesh
  * nodes and the row pitch ld (in doubles) of a state buffer. */
 int esdc_state_size(const esdc_handle* h, int* n_state, int64_t* n_nodes, int64_t* ld);
@@ -207,7 +222,8 @@ int esdc_coefficients(esdc_handle* h, const double* z, int64_t n, int M, double*
 
 /*
  * Diffusion solve (I - g L) x = b on the handle's mesh (the implicit step of
- * eq. (def_P) with g = dt d_i sigma/(chi C_m)): b, x device [n_nodes]; x holds
+ * eq. (def_P) with g = dt d_i sigma/(chi C_m)); with a layered conductivity,
+ * (I - g A) x = b with g = dt d_i/(chi C_m).  b, x device [n_nodes]; x holds
  * the initial guess on entry and the solution on return.  iters (host,
  * optional) receives the iteration count; synchronises `stream`.  Returns
  * ESDC_ERR_CG_NOT_CONVERGED if cg_maxit was reached.  With precision = 1 the

@@ -15,6 +15,7 @@
 #include <cooperative_groups.h>
 
 #include "esdc_internal.h"
+#include "esdc_fmath.cuh"
 
 namespace {
 
@@ -149,10 +150,62 @@ __device__ __forceinline__ NodeIdx node_idx(const MeshDev& m, int p)
 // (I - g L) v at node p (L: mirrored-ghost 3/5/7-point Laplacian) and the
 // number of in-domain neighbours.  The vectors are rewritten by other blocks
 // between phases, so neighbour values are read with __ldcg (L2, coherent).
+// Layered anisotropic operator (A v)_p (coefficients include sigma and 1/h^2).
+__device__ __forceinline__ double layered_A(const MeshDev& m, const double* v, int p, NodeIdx n, double vp)
+{
+    const int sxy = m.nx * m.ny;
+    const double cxx = __ldg(m.lay + n.iz), cyy = __ldg(m.lay + m.nz + n.iz), cd = __ldg(m.lay + 2 * m.nz + n.iz);
+    double s = 0.0;
+    if (n.ix > 0)        s = fma(cxx, __ldcg(v + p - 1) - vp, s);
+    if (n.ix < m.nx - 1) s = fma(cxx, __ldcg(v + p + 1) - vp, s);
+    if (n.iy > 0)        s = fma(cyy, __ldcg(v + p - m.nx) - vp, s);
+    if (n.iy < m.ny - 1) s = fma(cyy, __ldcg(v + p + m.nx) - vp, s);
+    if (n.iz > 0)        s = fma(__ldg(m.lay + 3 * m.nz + n.iz - 1), __ldcg(v + p - sxy) - vp, s);
+    if (n.iz < m.nz - 1) s = fma(__ldg(m.lay + 3 * m.nz + n.iz), __ldcg(v + p + sxy) - vp, s);
+    const bool xm = n.ix > 0, xp = n.ix < m.nx - 1, ym = n.iy > 0, yp = n.iy < m.ny - 1;
+    double c = 0.0;
+    if (xp && yp) c += __ldcg(v + p + 1 + m.nx) - vp;
+    if (xm && ym) c += __ldcg(v + p - 1 - m.nx) - vp;
+    if (xp && ym) c -= __ldcg(v + p + 1 - m.nx) - vp;
+    if (xm && yp) c -= __ldcg(v + p - 1 + m.nx) - vp;
+    return fma(cd, c, s);
+}
+
+__device__ __forceinline__ float layered_A_f(const MeshDev& m, const float* v, int p, NodeIdx n, float vp)
+{
+    const int sxy = m.nx * m.ny;
+    const float cxx = __ldg(m.layf + n.iz), cyy = __ldg(m.layf + m.nz + n.iz), cd = __ldg(m.layf + 2 * m.nz + n.iz);
+    float s = 0.0f;
+    if (n.ix > 0)        s = fmaf(cxx, __ldcg(v + p - 1) - vp, s);
+    if (n.ix < m.nx - 1) s = fmaf(cxx, __ldcg(v + p + 1) - vp, s);
+    if (n.iy > 0)        s = fmaf(cyy, __ldcg(v + p - m.nx) - vp, s);
+    if (n.iy < m.ny - 1) s = fmaf(cyy, __ldcg(v + p + m.nx) - vp, s);
+    if (n.iz > 0)        s = fmaf(__ldg(m.layf + 3 * m.nz + n.iz - 1), __ldcg(v + p - sxy) - vp, s);
+    if (n.iz < m.nz - 1) s = fmaf(__ldg(m.layf + 3 * m.nz + n.iz), __ldcg(v + p + sxy) - vp, s);
+    const bool xm = n.ix > 0, xp = n.ix < m.nx - 1, ym = n.iy > 0, yp = n.iy < m.ny - 1;
+    float c = 0.0f;
+    if (xp && yp) c += __ldcg(v + p + 1 + m.nx) - vp;
+    if (xm && ym) c += __ldcg(v + p - 1 - m.nx) - vp;
+    if (xp && ym) c -= __ldcg(v + p + 1 - m.nx) - vp;
+    if (xm && yp) c -= __ldcg(v + p - 1 + m.nx) - vp;
+    return fmaf(cd, c, s);
+}
+
+// Jacobi factor 1/diag(I - g A) at node p with c in-domain face neighbours.
+__device__ __forceinline__ double jacobi(const MeshDev& m, const double* dinv, int p, int c, double g)
+{
+    if (m.lay) return esdc::esdc_rcp(fma(g, __ldg(m.wdiag + p), 1.0));
+    return dinv[c];
+}
+
 __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, int p,
                                            NodeIdx n, double gih2, int* nnb)
 {
     const double vp = __ldcg(v + p);
+    if (m.lay) {                       // layered conductivity: gih2 carries g only
+        *nnb = 0;
+        return fma(-gih2, layered_A(m, v, p, n, vp), vp);
+    }
     const int sxy = m.nx * m.ny;
     double s = 0.0;
     int c = 0;
@@ -182,6 +235,10 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
 __device__ __forceinline__ float apply_op_f(const MeshDev& m, const float* v, int p, NodeIdx n, float gih2, int* nnb)
 {
     const float vp = __ldcg(v + p);
+    if (m.lay) {
+        *nnb = 0;
+        return fmaf(-gih2, layered_A_f(m, v, p, n, vp), vp);
+    }
     const int sxy = m.nx * m.ny;
     float s = 0.0f;
     int c = 0;
@@ -203,7 +260,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     double* part = a.part;
-    const double gih2 = a.g * m.ih2;
+    const double gih2 = m.lay ? a.g : a.g * m.ih2;     // layered coefficients carry 1/h^2
     __shared__ double bs[3];
     unsigned target = 0;
 
@@ -216,7 +273,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
             double ax = apply_op(m, a.x, p, n, gih2, &c);
             double bp = a.b[p];
             double rp = bp - ax;
-            double zp = a.precond ? a.dinv[c] * rp : rp;
+            double zp = a.precond ? jacobi(m, a.dinv, p, c, a.g) * rp : rp;
             a.r[p] = rp;
             a.z[p] = zp;
             a.p[p] = 0.0;
@@ -296,7 +353,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
                             NodeIdx n = node_idx(m, p);
                             int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
                                     (n.iz > 0) + (n.iz < m.nz - 1);
-                            zq = a.dinv[c] * rp;
+                            zq = jacobi(m, a.dinv, p, c, a.g) * rp;
                         }
                         a.z[p] = zq;
                         v[0] = fma(rp, zq, v[0]);
@@ -347,7 +404,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArg
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     double* part = a.part;
-    const double gih2 = a.g * m.ih2;
+    const double gih2 = m.lay ? a.g : a.g * m.ih2;     // layered coefficients carry 1/h^2
     const float gih2f = (float)gih2;
     __shared__ double bs[3];
     unsigned target = 0;
@@ -386,7 +443,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArg
                     NodeIdx n = node_idx(m, p);
                     int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
                             (n.iz > 0) + (n.iz < m.nz - 1);
-                    zp = f.dinv[c] * rp;
+                    zp = (m.lay ? (float)jacobi(m, a.dinv, p, c, a.g) : f.dinv[c]) * rp;
                 }
                 f.r[p] = rp; f.z[p] = zp; f.p[p] = 0.0f; f.q[p] = 0.0f; f.e[p] = 0.0f;
                 v[0] += (double)(rp * zp);
@@ -465,7 +522,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArg
                                 NodeIdx n = node_idx(m, p);
                                 int c = (n.ix > 0) + (n.ix < m.nx - 1) + (n.iy > 0) + (n.iy < m.ny - 1) +
                                         (n.iz > 0) + (n.iz < m.nz - 1);
-                                zp = f.dinv[c] * rp;
+                                zp = (m.lay ? 1.0f / fmaf((float)a.g, (float)__ldg(m.wdiag + p), 1.0f) : f.dinv[c]) * rp;
                             }
                             f.z[p] = zp;
                             acc0 = fmaf(rp, zp, acc0);

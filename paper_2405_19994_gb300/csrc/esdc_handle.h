@@ -43,6 +43,8 @@ struct esdc_handle {
     ModelDev mp{};
     ModelDevF mpf{};
     double sigma = 0, chi = 0, Cm = 0, D = 0;
+    double *lay = nullptr, *wdiag = nullptr;   // layered conductivity (see MeshDev)
+    float* layf = nullptr;
     esdc_options opt{};
     // workspace
     double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,

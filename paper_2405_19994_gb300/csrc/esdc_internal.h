@@ -42,6 +42,12 @@ struct MeshDev {
     int N;            // nx*ny*nz
     int64_t ld;       // row pitch of state arrays (doubles)
     double ih2;       // 1/h^2
+    // Layered anisotropic conductivity (nullptr: scalar sigma, plain stencil):
+    // lay[0..nz) sxx/h^2, [nz..2nz) syy/h^2, [2nz..3nz) sxy/(2h^2),
+    // [3nz..4nz) face sigma_zz/h^2 between layers k and k+1.
+    const double* lay = nullptr;
+    const double* wdiag = nullptr;   // [N] -diag(A) (Jacobi weights), layered case
+    const float* layf = nullptr;     // FP32 copy of lay (precision form)
 };
 
 struct StimDev {

@@ -24,12 +24,31 @@ __device__ __forceinline__ void node_xyz(const MeshDev& m, int p, int& ix, int& 
     iy = r - iz * m.ny;
 }
 
-// L v at node p: (1/h^2) sum over in-domain neighbours of (v_q - v_p).
+// L v at node p: (1/h^2) sum over in-domain neighbours of (v_q - v_p); with a
+// layered conductivity, A v (the coefficients then include sigma and 1/h^2,
+// and the in-plane diagonal neighbours carry the sigma_xy cross term).
 __device__ __forceinline__ double lap(const MeshDev& m, const double* __restrict__ v, int p,
                                       int ix, int iy, int iz)
 {
     const double vp = v[p];
     const int sxy = m.nx * m.ny;
+    if (m.lay) {
+        const double cxx = __ldg(m.lay + iz), cyy = __ldg(m.lay + m.nz + iz), cd = __ldg(m.lay + 2 * m.nz + iz);
+        double s = 0.0;
+        if (ix > 0)        s = fma(cxx, v[p - 1] - vp, s);
+        if (ix < m.nx - 1) s = fma(cxx, v[p + 1] - vp, s);
+        if (iy > 0)        s = fma(cyy, v[p - m.nx] - vp, s);
+        if (iy < m.ny - 1) s = fma(cyy, v[p + m.nx] - vp, s);
+        if (iz > 0)        s = fma(__ldg(m.lay + 3 * m.nz + iz - 1), v[p - sxy] - vp, s);
+        if (iz < m.nz - 1) s = fma(__ldg(m.lay + 3 * m.nz + iz), v[p + sxy] - vp, s);
+        const bool xm = ix > 0, xp = ix < m.nx - 1, ym = iy > 0, yp = iy < m.ny - 1;
+        double c = 0.0;
+        if (xp && yp) c += v[p + 1 + m.nx] - vp;
+        if (xm && ym) c += v[p - 1 - m.nx] - vp;
+        if (xp && ym) c -= v[p + 1 - m.nx] - vp;
+        if (xm && yp) c -= v[p - 1 + m.nx] - vp;
+        return fma(cd, c, s);
+    }
     double s = 0.0;
     if (ix > 0)        s += v[p - 1] - vp;
     if (ix < m.nx - 1) s += v[p + 1] - vp;

@@ -76,13 +76,13 @@ extern "C" int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, cons
     double* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return ESDC_ERR_CUDA;
 
-    MeshDev m;
+    MeshDev m{};                                  // scalar conductivity only
     m.nx = mesh->nx; m.ny = mesh->ny; m.nz = mesh->nz;
     m.N = (int)N;
     m.ld = N;
     m.ih2 = 1.0 / (mesh->h * mesh->h);
 
-    CgWork w;
+    CgWork w{};
     w.r = base;
     w.p = base + kVec;
     w.q = base + 2 * kVec;

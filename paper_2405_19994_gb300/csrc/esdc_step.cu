@@ -29,6 +29,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "esdc_internal.h"
 #include "esdc_kernels.cuh"
@@ -71,6 +72,31 @@ __global__ void k_math(const double* x, int64_t n, double* ex, double* rc)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         ex[e] = esdc::esdc_exp(x[e]);
         rc[e] = esdc::esdc_rcp(x[e]);
+    }
+}
+
+// -diag(A) of the layered operator: sum of the coefficients of the present
+// neighbours (faces, and a b sigma_xy/(2h^2) for the in-plane diagonals).
+__global__ void k_wdiag(MeshDev m, double* w)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        node_xyz(m, p, ix, iy, iz);
+        const double cxx = m.lay[iz], cyy = m.lay[m.nz + iz], cd = m.lay[2 * m.nz + iz];
+        double s = 0.0;
+        if (ix > 0) s += cxx;
+        if (ix < m.nx - 1) s += cxx;
+        if (iy > 0) s += cyy;
+        if (iy < m.ny - 1) s += cyy;
+        if (iz > 0) s += m.lay[3 * m.nz + iz - 1];
+        if (iz < m.nz - 1) s += m.lay[3 * m.nz + iz];
+        const bool xm = ix > 0, xp = ix < m.nx - 1, ym = iy > 0, yp = iy < m.ny - 1;
+        double c = 0.0;
+        if (xp && yp) c += 1.0;
+        if (xm && ym) c += 1.0;
+        if (xp && ym) c -= 1.0;
+        if (xm && yp) c -= 1.0;
+        w[p] = s + cd * c;
     }
 }
 
@@ -126,6 +152,9 @@ void free_all(esdc_handle* h)
 {
     for (auto& e : h->prof_ev)
         if (e) cudaEventDestroy(e);
+    if (h->lay) cudaFree(h->lay);
+    if (h->layf) cudaFree(h->layf);
+    if (h->wdiag) cudaFree(h->wdiag);
     void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev, h->Vprev,
                     h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.r32, h->cg.p32, h->cg.q32, h->cg.z32,
                     h->cg.e32, h->cg.part, h->cg.bar, h->cg.status,
@@ -276,6 +305,52 @@ int esdc_set_stimulus(esdc_handle* h, int nbox, const int* box, const double* am
         st.amp[b] = amp[b]; st.t_on[b] = t_on[b]; st.t_off[b] = t_off[b];
     }
     h->stim = st;
+    return ESDC_OK;
+}
+
+int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double* syy, const double* sxy,
+                                 const double* szz)
+{
+    if (!h) return ESDC_ERR_INVALID_ARG;
+    if (!sxx && !syy && !sxy && !szz) {                 // back to the scalar sigma
+        if (h->lay) cudaFree(h->lay);
+        if (h->layf) cudaFree(h->layf);
+        if (h->wdiag) cudaFree(h->wdiag);
+        h->lay = h->wdiag = nullptr;
+        h->layf = nullptr;
+        h->mesh.lay = nullptr; h->mesh.wdiag = nullptr; h->mesh.layf = nullptr;
+        h->D = h->sigma / (h->chi * h->Cm);
+        return ESDC_OK;
+    }
+    if (!sxx || !syy || !sxy || !szz) return set_err(h, ESDC_ERR_INVALID_ARG, "all four layer arrays are needed");
+    const int nz = h->mesh.nz;
+    const double ih2 = h->mesh.ih2;
+    std::vector<double> c(4 * (size_t)nz, 0.0);
+    for (int k = 0; k < nz; ++k) {
+        const double a = sxx[k], b = syy[k], d = sxy[k], e = szz[k];
+        if (!(a > 0.0) || !(b > 0.0) || !(e > 0.0) || !std::isfinite(d) || !(a * b - d * d > 0.0) ||
+            !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(e))
+            return set_err(h, ESDC_ERR_INVALID_ARG, "layer %d: conductivity tensor not positive definite", k);
+        c[k] = a * ih2;
+        c[nz + k] = b * ih2;
+        c[2 * nz + k] = 0.5 * d * ih2;
+        c[3 * nz + k] = (k + 1 < nz) ? 0.5 * (e + szz[k + 1]) * ih2 : 0.0;
+    }
+    std::vector<float> cf(c.begin(), c.end());
+    if (!h->lay) {
+        CUDA_TRY(h, cudaMalloc((void**)&h->lay, sizeof(double) * 4 * nz));
+        CUDA_TRY(h, cudaMalloc((void**)&h->layf, sizeof(float) * 4 * nz));
+        CUDA_TRY(h, cudaMalloc((void**)&h->wdiag, sizeof(double) * h->mesh.ld));
+    }
+    CUDA_TRY(h, cudaMemcpy(h->lay, c.data(), sizeof(double) * 4 * nz, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->layf, cf.data(), sizeof(float) * 4 * nz, cudaMemcpyHostToDevice));
+    h->mesh.lay = h->lay;
+    h->mesh.layf = h->layf;
+    h->mesh.wdiag = h->wdiag;
+    k_wdiag<<<grid_for(h, 256), 256>>>(h->mesh, h->wdiag);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaDeviceSynchronize());
+    h->D = 1.0 / (h->chi * h->Cm);                      // sigma now lives in the coefficients
     return ESDC_OK;
 }
 

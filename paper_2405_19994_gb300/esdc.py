@@ -58,6 +58,8 @@ def lib() -> C.CDLL:
             "esdc_set_stimulus": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(_D), C.POINTER(_D),
                                             C.POINTER(_D)]),
             "esdc_state_size": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(_I64), C.POINTER(_I64)]),
+            "esdc_set_conductivity_layers": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
+                                                       C.POINTER(_D)]),
             "esdc_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
             "esdc_sweep": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
             "esdc_sweep_host": (C.c_int, [_VP, _VP, _I64, _D, _D, C.c_int, C.c_int, _VP]),
@@ -138,6 +140,8 @@ class Solver:
     def from_workload(cls, wl, **kw) -> "Solver":
         s = cls(wl.dim, wl.nx, wl.ny, wl.nz, wl.h, wl.sigma, wl.chi, wl.Cm, wl.model, wl.params, **kw)
         s.set_stimulus(wl.boxes, wl.amp, wl.t_on, wl.t_off)
+        if getattr(wl, "layers", None) is not None:
+            s.set_conductivity_layers(wl.layers)
         return s
 
     def _check(self, rc: int):
@@ -164,6 +168,14 @@ class Solver:
         self._check(lib().esdc_set_stimulus(self._h, n, b.ctypes.data_as(C.POINTER(C.c_int)),
                                             a.ctypes.data_as(C.POINTER(_D)), on.ctypes.data_as(C.POINTER(_D)),
                                             off.ctypes.data_as(C.POINTER(_D))))
+
+    def set_conductivity_layers(self, layers):
+        """layers: {"sxx","syy","sxy","szz"} -> arrays of length nz, or None for the scalar sigma."""
+        if layers is None:
+            self._check(lib().esdc_set_conductivity_layers(self._h, None, None, None, None))
+            return
+        arrs = [np.ascontiguousarray(layers[k], np.float64) for k in ("sxx", "syy", "sxy", "szz")]
+        self._check(lib().esdc_set_conductivity_layers(self._h, *[a.ctypes.data_as(C.POINTER(_D)) for a in arrs]))
 
     def new_state(self, device=None):
         import torch

@@ -278,6 +278,50 @@ def test_precision_form_hh_sheet_run():
     assert err < 1e-4, err
 
 
+# ---------------------------------------------------------------- layered anisotropic conductivity
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(13, 11, 5), (40, 33, 3), (9, 9, 1)])
+def test_layered_solve_matches_oracle(precision, shape):
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.layers = I.fibre_layers(nz)
+    s = P.Solver.from_workload(wl, cg_maxit=2000, precision=precision)
+    m = O.Monodomain(wl, solver=O.SOLVE_CG, cg_tol=1e-15)
+    rng = np.random.default_rng(8)
+    b = rng.normal(size=wl.n_nodes)
+    g = 0.4
+    want = m.solve_A(g, b)
+    xd = torch.zeros(wl.n_nodes, dtype=torch.float64, device="cuda")
+    s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+    assert rel(xd.cpu().numpy(), want) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_layered_one_step_matches_oracle(precision, tol):
+    """HH on a 3D slab with fibres rotating through the depth (the precision-form
+    workload's physics, reduced mesh), one step from a mid-upstroke state.
+
+    The start state comes from the oracle (rest, then 24 stimulated steps), not
+    from random gates: HH with arbitrary gate values is far stiffer than any
+    physical state, and at dt = 0.05 ms the sweep diverges from it on both sides."""
+    wl = I.hh_aniso_slab().with_mesh(14, 12, 6)
+    m = O.Monodomain(wl, cg_tol=1e-15)
+    y0, t0 = m.init_state(), 0.0
+    for _ in range(24):
+        y0, _, _, _ = m.step(y0, t0, wl.dt, wl.M, wl.K)
+        t0 += wl.dt
+    assert y0[0].max() > 0.0 and y0[0].min() < -60.0              # a front is on the mesh
+    s = P.Solver.from_workload(wl, M_max=wl.M, precision=precision)
+    yd = to_dev(s, y0)
+    s.sweep(yd, t0, wl.dt, wl.M, wl.K)
+    assert s.residual()[0] == 0
+    got = from_dev(s, yd)
+    want, _, _, _ = m.step(y0, t0, wl.dt, wl.M, wl.K)
+    assert np.abs(got[0] - want[0]).max() <= tol * np.abs(want[0]).max()
+    assert np.abs(got[1:] - want[1:]).max() <= tol
+
+
 # ---------------------------------------------------------------- full workloads
 
 def test_hh_sheet_full_run_matches_oracle():
