@@ -15,137 +15,10 @@
 #include <cooperative_groups.h>
 
 #include "esdc_internal.h"
+#include "esdc_cg_common.cuh"
 #include "esdc_fmath.cuh"
 
 namespace {
-
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // give up a barrier wait after 1 s
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned load_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-struct CgArgs {
-    MeshDev m;
-    double g;
-    double dinv[7];          // inverse diagonal of I - g L by neighbour count
-    const double* b;
-    double* x;
-    double *r, *p, *q, *z;
-    double* part;            // [6][nblocks]: setup r.z, r.r, b.b | p.q | r.z, r.r
-    unsigned* bar;           // barrier arrival counter
-    int* status;             // [0] iterations, [1] flags
-    int* iter_log;
-    int* flags;
-    double tol2;
-    int maxit;
-    int precond;
-};
-
-// Grid barrier on one monotonic arrival counter (zeroed before the launch):
-// barrier number b is passed once the counter reaches b * gridDim.x.  Thread 0
-// of each block adds its arrival and polls with acquire loads, tightly at
-// first, then with short sleeps; after 1 s of waiting it raises TIMEOUT and
-// returns false, and the caller must return from the kernel.
-__device__ bool grid_barrier(unsigned* bar, unsigned& target, int* flags)
-{
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        target += gridDim.x;
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int ok = 1;
-        if (load_acquire(bar) < target) {
-            const unsigned long long t0 = global_ns();
-            unsigned spins = 0;
-            while (load_acquire(bar) < target) {
-                if (++spins > 32) __nanosleep(32);
-                if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
-                    ok = 0;
-                    atomicOr(flags, ESDC_FLAG_TIMEOUT);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
-// Block sum of up to three values in a fixed order: every thread stores its
-// value, lane l of warp 0 adds the values of lane l of all warps (in warp
-// order), then warp 0 reduces its 32 sums with a shuffle tree.  Few FP64 adds
-// per thread: the FP64 pipe is the scarce unit.
-template <int NV>
-__device__ void block_sum(double (&v)[NV], double* out)
-{
-    __shared__ double sh[NV][32][33];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[k][lane][wid] = v[k];
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = sh[k][lane][0];
-            for (int w = 1; w < nw; ++w) s += sh[k][lane][w];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) out[k] = s;
-        }
-    }
-    __syncthreads();
-}
-
-// Every block sums the partials of all blocks: lane l of warp 0 adds partials
-// l, l+32, ... in order, then a shuffle tree; the result is broadcast through
-// shared memory, so every block obtains the same bits.  The partials were
-// written by other blocks before the last barrier; __ldcg reads them from L2,
-// past this SM's L1.
-template <int NV>
-__device__ void grid_total(const double* part, int off0, double (&tot)[NV])
-{
-    __shared__ double res[NV];
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const double* pk = part + (size_t)(off0 + k) * gridDim.x;
-            double s = 0.0;
-            for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(pk + b);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) res[k] = s;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = res[k];
-    __syncthreads();
-}
-
-struct NodeIdx { int ix, iy, iz; };
-
-__device__ __forceinline__ NodeIdx node_idx(const MeshDev& m, int p)
-{
-    NodeIdx n;
-    int r = p / m.nx;
-    n.ix = p - r * m.nx;
-    n.iz = r / m.ny;
-    n.iy = r - n.iz * m.ny;
-    return n;
-}
 
 // (I - g L) v at node p (L: mirrored-ghost 3/5/7-point Laplacian) and the
 // number of in-domain neighbours.  The vectors are rewritten by other blocks
@@ -328,9 +201,8 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
             if (threadIdx.x == 0) part[3 * gridDim.x + blockIdx.x] = bs[0];
         }
         if (!grid_barrier(a.bar, target, a.flags)) return;
-        double pq[1];
-        grid_total<1>(part, 3, pq);
-        const double alpha = rz / pq[0];
+        double pq[1], alpha;
+        grid_total_q<1, 1>(part, 3, pq, rz, alpha);
         // [B] x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z, r.r (slots 4, 5)
         {
             double v[2] = {0.0, 0.0};
@@ -366,8 +238,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
         }
         if (!grid_barrier(a.bar, target, a.flags)) return;
         double t2[2];
-        grid_total<2>(part, 4, t2);
-        beta = t2[0] / rz;
+        grid_total_q<2, 2>(part, 4, t2, rz, beta);
         rz = t2[0];
         rr = t2[1];
         ++it;
@@ -496,9 +367,9 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArg
                 if (threadIdx.x == 0) part[4 * gridDim.x + blockIdx.x] = bs[0];
             }
             if (!grid_barrier(a.bar, target, a.flags)) return;
-            double pq[1];
-            grid_total<1>(part, 4, pq);
-            const float alpha = (float)(rz / pq[0]);
+            double pq[1], alpha64;
+            grid_total_q<1, 1>(part, 4, pq, rz, alpha64);
+            const float alpha = (float)alpha64;
             // [B] e += alpha p, r -= alpha q, z = D^{-1} r; partials r.z, r.r
             {
                 constexpr int U = ESDC_CG_UNROLL;
@@ -536,8 +407,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArg
             }
             if (!grid_barrier(a.bar, target, a.flags)) return;
             double t2[2];
-            grid_total<2>(part, 5, t2);
-            beta = t2[0] / rz;
+            grid_total_q<2, 2>(part, 5, t2, rz, beta);
             rz = t2[0];
             rri = t2[1];
             ++inner;
@@ -596,6 +466,10 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
                            double* x, double tol, int maxit, int precond, int* iter_log,
                            int* flags, cudaStream_t s)
 {
+    if (esdc_cg4_eligible(mesh, b, x)) {
+        CgArgsHost hq{mesh, w, g, b, x, tol, maxit, precond, iter_log, flags};
+        return esdc_cg4_launch(hq, false, s);
+    }
     CgArgs a;
     a.m = mesh;
     a.g = g;
@@ -622,6 +496,10 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
 cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b, double* x,
                                  double tol, int maxit, int precond, int* iter_log, int* flags, cudaStream_t s)
 {
+    if (esdc_cg4_eligible(mesh, b, x)) {
+        CgArgsHost hq{mesh, w, g, b, x, tol, maxit, precond, iter_log, flags};
+        return esdc_cg4_launch(hq, true, s);
+    }
     CgArgs a;
     a.m = mesh;
     a.g = g;

@@ -91,3 +91,22 @@ cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g,
                                  int* flags, cudaStream_t s);
 // Blocks to use for a cooperative CG launch on this device.
 int esdc_cg_blocks(const MeshDev& mesh, int threads);
+
+// Quad form of the solves (four x-consecutive nodes per thread, diagonal and
+// Jacobi tables in shared memory): used when nx is a multiple of 4, b and x are
+// 16-byte aligned and the layered operator has at most ESDC_CG4_MAX_LAYERS
+// layers; esdc_cg_launch and esdc_cg_mixed_launch dispatch to it.
+#define ESDC_CG4_MAX_LAYERS 256
+struct CgArgsHost {
+    MeshDev mesh;
+    CgWork w;
+    double g;
+    const double* b;
+    double* x;
+    double tol;
+    int maxit, precond;
+    int* iter_log;
+    int* flags;
+};
+bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x);
+cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s);
