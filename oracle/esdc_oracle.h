@@ -84,6 +84,16 @@ int orc_hsdc_step(const orc_problem* P, int M, int K, double tol, int plain_sdc,
                   double t_n, double dt, const double* y_n, double* y_next,
                   double* colloc, double* resid, orc_stats* st);
 
+/* The same step started from a given iterate instead of y^0 = 1 (x) y_n:
+ * colloc_in [M*n] holds y_{n,1..M}^0 (y_{n,0} = y_n).  G^0 and E^0 are
+ * evaluated on that iterate with Lambda_n = Lambda(y_n), so the step is the
+ * single-step sweep of eq. prec_picard applied to it.  One such sweep per
+ * slice, with y_n the previous slice's last node, is the Q^par iteration of
+ * eq. def_Q (Sec. 3.2).  colloc_in = NULL is orc_hsdc_step. */
+int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain_sdc,
+                       double t_n, double dt, const double* y_n, const double* colloc_in,
+                       double* y_next, double* colloc, double* resid, orc_stats* st);
+
 /* ------------------------------------------------------------------ */
 /* Monodomain problem on a uniform cell-centred mesh (Sec. 2)          */
 /* ------------------------------------------------------------------ */

@@ -71,6 +71,8 @@ def lib():
         L.orc_aij.argtypes = [C.c_int, _D, _D, C.c_double, _D]
         L.orc_hsdc_step.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_double, C.c_int,
                                     C.c_double, C.c_double, _D, _D, _D, _D, C.POINTER(_Stats)]
+        L.orc_hsdc_step_from.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_double, C.c_int,
+                                         C.c_double, C.c_double, _D, _D, _D, _D, _D, C.POINTER(_Stats)]
         L.orc_mono_problem.argtypes = [C.POINTER(_Mono), C.POINTER(_Problem)]
         L.orc_mono_free.argtypes = [C.POINTER(_Mono)]
         L.orc_mono_init.argtypes = [C.POINTER(_Mono), C.c_double, _D]
@@ -241,17 +243,25 @@ class Monodomain:
         return x
 
     def step(self, y_n: np.ndarray, t_n: float, dt: float, M: int, K: int, tol: float = 0.0,
-             plain_sdc: bool = False, want_colloc: bool = False, want_resid: bool = False):
-        """One HSDC step; returns (y_next[ns, N], stats dict, colloc, resid)."""
+             plain_sdc: bool = False, want_colloc: bool = False, want_resid: bool = False,
+             colloc_in: np.ndarray | None = None):
+        """One HSDC step; returns (y_next[ns, N], stats dict, colloc, resid).
+
+        colloc_in [M, ns, N] (optional) starts the sweeps from that iterate
+        instead of y^0 = 1 (x) y_n (orc_hsdc_step_from)."""
         y_n = np.ascontiguousarray(y_n, np.float64).reshape(-1)
         n = len(y_n)
         y1 = np.zeros(n)
         col = np.zeros(M * n) if want_colloc else None
         res = np.zeros(M * n) if want_resid else None
+        cin = None if colloc_in is None else np.ascontiguousarray(colloc_in, np.float64).reshape(-1)
+        if cin is not None and len(cin) != M * n:
+            raise ValueError("colloc_in must hold M x n_state x N values")
         st = _Stats()
-        rc = lib().orc_hsdc_step(C.byref(self.P), M, K, tol, int(plain_sdc), float(t_n), float(dt),
-                                 _p(y_n), _p(y1), _p(col) if col is not None else None,
-                                 _p(res) if res is not None else None, C.byref(st))
+        rc = lib().orc_hsdc_step_from(C.byref(self.P), M, K, tol, int(plain_sdc), float(t_n), float(dt),
+                                      _p(y_n), _p(cin) if cin is not None else None, _p(y1),
+                                      _p(col) if col is not None else None,
+                                      _p(res) if res is not None else None, C.byref(st))
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
         stats = dict(sweeps=st.sweeps_done, res_inf=st.res_inf, y_inf=st.y_inf)
@@ -259,6 +269,25 @@ class Monodomain:
         return (y1.reshape(shp), stats,
                 None if col is None else col.reshape((M,) + shp),
                 None if res is None else res.reshape((M,) + shp))
+
+    def qpar(self, y0: np.ndarray, t0: float, dt: float, P: int, M: int, iters: int):
+        """Q^par iteration (eq. prec_picard_seq with Q = Q^par, eq. def_Q) for P
+        consecutive steps from y0 at t0, started from z^0 = 1 (x) y0 in every
+        slice (the paper's Burn-in is not specified).  Iteration k+1: every
+        slice p runs one sweep from its iterate z_p^k with y_{p,0} = y0 (p = 0)
+        or the last node y_{p-1,M}^k of the previous slice's iterate.
+        Returns the iterates [P, M, ns, N] after `iters` iterations."""
+        y0 = np.asarray(y0, np.float64).reshape(self.ns, self.N)
+        Z = np.broadcast_to(y0, (P, M, self.ns, self.N)).copy()
+        for _ in range(iters):
+            ends = Z[:, M - 1].copy()
+            newZ = np.empty_like(Z)
+            for p in range(P):
+                yn = y0 if p == 0 else ends[p - 1]
+                _, _, col, _ = self.step(yn, t0 + p * dt, dt, M, 1, want_colloc=True, colloc_in=Z[p])
+                newZ[p] = col
+            Z = newZ
+        return Z
 
     def run(self, y0: np.ndarray, t0: float, dt: float, nsteps: int, M: int, K: int):
         y = np.array(y0, np.float64)

@@ -77,6 +77,13 @@ int orc_hsdc_step(const orc_problem* P, int M, int K, double tol, int plain_sdc,
                   double t_n, double dt, const double* y_n, double* y_next,
                   double* colloc, double* resid, orc_stats* st)
 {
+    return orc_hsdc_step_from(P, M, K, tol, plain_sdc, t_n, dt, y_n, NULL, y_next, colloc, resid, st);
+}
+
+int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain_sdc,
+                       double t_n, double dt, const double* y_n, const double* colloc_in,
+                       double* y_next, double* colloc, double* resid, orc_stats* st)
+{
     if (M < 1 || M > ORC_MMAX || K < 0 || !(dt > 0.0)) return -1;
     const int64_t n = P->n;
     double c[ORC_MMAX + 1], d[ORC_MMAX + 1], w[ORC_MMAX * ORC_MMAX], a0[ORC_MMAX * ORC_MMAX];
@@ -118,8 +125,9 @@ int orc_hsdc_step(const orc_problem* P, int M, int K, double tol, int plain_sdc,
     double* R    = ALLOC((int64_t)M * n);
     int rc = 0;
 
-    /* y^0 = 1 (x) y_n (eq. prec_picard) */
-    for (int j = 0; j <= M; ++j) memcpy(Y + j * n, y_n, sizeof(double) * n);
+    /* y^0 = 1 (x) y_n (eq. prec_picard), or the given iterate with y_{n,0} = y_n */
+    for (int j = 0; j <= M; ++j)
+        memcpy(Y + j * n, (j > 0 && colloc_in) ? colloc_in + (int64_t)(j - 1) * n : y_n, sizeof(double) * n);
     for (int j = 1; j <= M; ++j) {
         eval_g(P, t_n + c[j] * dt, Y + j * n, y_n, lam_n, G + (j - 1) * n, t1, t2, t3);
         eval_E_explicit(P, t_n + c[j - 1] * dt, Y + (j - 1) * n, y_n, lam_n, phi1 + (j - 1) * n,

@@ -257,3 +257,69 @@ def test_syn19_planar_wave_acceptance(orc):
         assert y[7:].min() > -1e-9 and y[7:].max() < 1 + 1e-9
     assert np.all(np.isfinite(act)) and np.all(np.diff(act) >= 0)
     assert y[0].max() < -80.0
+
+
+# ---------------------------------------------------------------- sweeps from a given iterate; Q^par
+
+def test_step_from_spread_iterate_is_the_plain_step(orc):
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.hh_sheet_32().with_mesh(10, 8, 1)
+    m = O.Monodomain(wl)
+    y0 = m.init_state()
+    a, _, ca, _ = m.step(y0, 0.0, wl.dt, wl.M, 3, want_colloc=True)
+    spread = np.broadcast_to(y0, (wl.M,) + y0.shape).copy()
+    b, _, cb, _ = m.step(y0, 0.0, wl.dt, wl.M, 3, want_colloc=True, colloc_in=spread)
+    assert np.array_equal(a, b) and np.array_equal(ca, cb)
+
+
+def test_step_from_iterate_continues_the_sweeps(orc):
+    # K1 sweeps, then K2 sweeps from that iterate, is K1 + K2 sweeps (same y_n)
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.hh_sheet_32().with_mesh(9, 7, 1)
+    m = O.Monodomain(wl)
+    y0 = I.random_state(wl, seed=3)
+    y0[1:] = m.init_state()[1:]                      # physical gates
+    _, _, c5, _ = m.step(y0, 0.2, wl.dt, wl.M, 5, want_colloc=True)
+    _, _, c2, _ = m.step(y0, 0.2, wl.dt, wl.M, 2, want_colloc=True)
+    _, _, c23, _ = m.step(y0, 0.2, wl.dt, wl.M, 3, want_colloc=True, colloc_in=c2)
+    assert np.array_equal(c5, c23)
+
+
+def test_qpar_single_slice_is_k_sweeps(orc):
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.hh_sheet_32().with_mesh(8, 8, 1)
+    m = O.Monodomain(wl)
+    y0 = m.init_state()
+    Z = m.qpar(y0, 0.0, wl.dt, 1, wl.M, 4)
+    _, _, c, _ = m.step(y0, 0.0, wl.dt, wl.M, 4, want_colloc=True)
+    assert np.array_equal(Z[0], c)
+
+
+def test_qpar_fixed_point_is_sequential_collocation(orc):
+    # Q^par converges to the solution of the P-step system eq. def_D: each slice
+    # the collocation solution started from the previous slice's end value.
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.hh_sheet_32().with_mesh(6, 6, 1)
+    m = O.Monodomain(wl)
+    y0 = m.init_state()
+    P, M = 4, wl.M
+    Z = m.qpar(y0, 0.0, wl.dt, P, M, 40)
+    y, t = y0, 0.0
+    for p in range(P):
+        y_next, _, col, _ = m.step(y, t, wl.dt, M, 40, want_colloc=True)
+        np.testing.assert_allclose(Z[p], col, rtol=0, atol=1e-12 * np.abs(col).max())
+        y, t = y_next, t + wl.dt
+
+
+def test_qpar_first_iteration_sweeps_every_slice_from_y0(orc):
+    # From z^0 = 1 (x) y0, the first Q^par iteration gives every slice p one
+    # sweep from y0 at its own start time t0 + p dt: Q^par is block-diagonal
+    # (eq. def_Q), so no slice sees another slice's new values within an iteration.
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.hh_sheet_32().with_mesh(6, 6, 1)
+    m = O.Monodomain(wl)
+    y0 = m.init_state()
+    Z1 = m.qpar(y0, 0.0, wl.dt, 3, wl.M, 1)
+    for p in range(3):
+        _, _, col, _ = m.step(y0, p * wl.dt, wl.dt, wl.M, 1, want_colloc=True)
+        assert np.array_equal(Z1[p], col)
