@@ -459,6 +459,170 @@ def run_precision_form(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch_form(args):
+    """The batching form: the 64-tissue ragged Hodgkin-Huxley batch stepped by one
+    batched launch sequence (recorded CUDA graph, autotuned launch shape) against
+    the same tissues stepped one at a time, (a) as batches of one tissue (the
+    same kernels: results must be identical bit for bit) and (b) through the
+    single-tissue entry point esdc_sweep."""
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1 and rank != 0:
+        return
+    wls = I.hh_batch()
+    w0 = wls[0]
+    M, K, dt = w0.M, w0.K, w0.dt
+    steps = args.steps if args.steps is not None else 20
+    nodes = int(sum(w.n_nodes for w in wls))
+    stream = torch.cuda.current_stream()
+
+    def timed(step_fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(n):
+            step_fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # ---- batched
+    b = P.Batch.from_workloads(wls, M_max=M)
+    scratch = b.new_state()
+    b.tune(scratch, w0.V0, 0.0, dt, M, K, reps=2)
+    shape = b.shape()
+    del scratch
+    yb = b.new_state()
+    b.init_state(yb, w0.V0)
+    t = [0.0]
+
+    def step_b(k):
+        b.sweep(yb, t[0], dt, M, K)
+        t[0] += dt
+    for k in range(args.warmup):
+        step_b(k)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_b = timed(step_b, steps)
+    clk = clocks.stop()
+    rc, res, _ = b.residual()
+    if rc != 0:
+        raise RuntimeError(f"batched step failed with code {rc}")
+    graph = b.graph_active()
+    iters = b.stats(K, M)
+
+    # ---- one tissue at a time, as batches of one (same kernels)
+    singles = [P.Batch.from_workloads([w], M_max=M) for w in wls]
+    for s1 in singles:
+        s1.set_shape(*shape[:2], 1)
+    ys = [s1.new_state() for s1 in singles]
+    for s1, y1 in zip(singles, ys):
+        s1.init_state(y1, w0.V0)
+    t1 = [0.0]
+
+    def step_1(k):
+        for s1, y1 in zip(singles, ys):
+            s1.sweep(y1, t1[0], dt, M, K)
+        t1[0] += dt
+    for k in range(args.warmup):
+        step_1(k)
+    ms_1 = timed(step_1, steps)
+    for s1 in singles:
+        if s1.residual()[0] != 0:
+            raise RuntimeError("single-tissue batch failed")
+    identical = all(torch.equal(b.tissue(yb, k), singles[k].tissue(ys[k], 0)) for k in range(len(wls)))
+    for s1 in singles:
+        s1.close()
+    del ys
+
+    # ---- one tissue at a time through esdc_sweep
+    solvers = [P.Solver.from_workload(w, M_max=M) for w in wls]
+    yv = [s.new_state() for s in solvers]
+    for s, y in zip(solvers, yv):
+        s.init_state(y, w0.V0)
+    t2 = [0.0]
+
+    def step_2(k):
+        for s, y in zip(solvers, yv):
+            s.sweep(y, t2[0], dt, M, K)
+        t2[0] += dt
+    for k in range(args.warmup):
+        step_2(k)
+    ms_2 = timed(step_2, steps)
+    maxdiff = 0.0
+    for k, (s, y) in enumerate(zip(solvers, yv)):
+        if s.residual()[0] != 0:
+            raise RuntimeError("single-tissue solver failed")
+        ref = b.tissue(yb, k)
+        maxdiff = max(maxdiff, float((y[:, :wls[k].n_nodes] - ref).abs().max() / ref.abs().max()))
+        s.close()
+
+    # ---- end to end: host state, copies inside the timed region (pinned host buffer)
+    yh = torch.empty_like(yb, device="cpu").pin_memory()
+    yh.copy_(yb)
+    n_e2e = max(1, min(steps, 10))
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    for k in range(n_e2e):
+        yb.copy_(yh, non_blocking=True)
+        b.sweep(yb, t[0], dt, M, K)
+        yh.copy_(yb, non_blocking=True)
+        torch.cuda.synchronize()
+        t[0] += dt
+    e2e_s = time.perf_counter() - c0
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sample = wls[:4]
+        c0 = time.perf_counter()
+        done = 0
+        for w in sample:
+            m = oracle.Monodomain(w)
+            y = m.init_state()
+            tt = 0.0
+            for _ in range(2):
+                y, _, _, _ = m.step(y, tt, w.dt, w.M, w.K)
+                tt += w.dt
+            done += 2 * w.n_nodes
+        cel = time.perf_counter() - c0
+        cpu = {"value": done / cel, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
+               "sample": "2 steps from rest of each of the first 4 tissues of the batch"}
+    launches_per_step = 1 + K * (M + 1) + K * M + 1
+    line = {
+        "metric": METRIC, "value": nodes * steps / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_b / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hh_batch_64 (64 2D HH tissues, sides U[64,512], sigma U[0.05,0.3], seed 4)",
+                   "form": "batch", "tissues": len(wls), "nodes": nodes, "M": M, "K": K, "dt_ms": dt,
+                   "l2": "inputs larger than L2 (batch state and workspace ~3.7 GB)"},
+        "s_per_sim_ms": ms_b / steps * 1e-3 / dt,
+        "launch_shape": {"node_waves": shape[0], "cg_threads": shape[1], "cg_blocks": shape[2]},
+        "graph": graph,
+        "graph_error": b.graph_error() or None,
+        "looped_batches_of_one": {"value": nodes * steps / (ms_1 * 1e-3), "ms_per_step": ms_1 / steps,
+                                  "identical_to_batched": bool(identical)},
+        "looped_single_solver": {"value": nodes * steps / (ms_2 * 1e-3), "ms_per_step": ms_2 / steps,
+                                 "max_rel_diff_vs_batched": maxdiff},
+        "speedup_vs_looped_batches_of_one": ms_1 / ms_b,
+        "speedup_vs_looped_single_solver": ms_2 / ms_b,
+        "cg_iters_last_step_max": int(iters.max()),
+        "residual_max": float(res.max()),
+        "cpu_baseline": cpu,
+        "e2e": {"value": nodes * n_e2e / e2e_s, "unit": UNIT, "steps": n_e2e,
+                "h2d_bytes_per_step": int(yb.numel() * 8), "d2h_bytes_per_step": int(yb.numel() * 8)},
+        "gpu_launches": launches_per_step * steps,
+        "clocks": clk,
+    }
+    b.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,8 +634,9 @@ def main():
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
-    ap.add_argument("--form", choices=["plain", "precision"], default="plain",
-                    help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms)")
+    ap.add_argument("--form", choices=["plain", "precision", "batch"], default="plain",
+                    help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
+                         "batch: the 64-tissue ragged HH batch against looped single-tissue steps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -481,6 +646,8 @@ def main():
         run_reference(args)
     elif args.form == "precision":
         run_precision_form(args)
+    elif args.form == "batch":
+        run_batch_form(args)
     else:
         run_ours(args)
 

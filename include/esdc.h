@@ -279,6 +279,86 @@ int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* st
 int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, const double* b, double* x,
                                 double tol, int maxit, int precond, int* iters, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Ragged batches (many tissues per launch).
+ *
+ * A batch holds n tissues that share the ionic model, its parameters, chi,
+ * C_m and the options, but each has its own mesh (any dim/size), scalar
+ * conductivity sigma[b], stimulus and start time.  One esdc_batch_sweep
+ * advances every tissue by one HSDC step (the same method and arithmetic as
+ * esdc_sweep, Sec. 3.1) with the launches of a single step: the node kernels
+ * cover all tissues, and each diffusion solve is one cooperative launch that
+ * runs all tissues' CG iterations side by side, each with its own step sizes
+ * and stop test.  The launches of a step are recorded once in a CUDA graph and
+ * replayed.  Every reduction is fixed per 512-node tile and per tissue, so a
+ * tissue's results are identical bit for bit whatever the rest of the batch and
+ * whatever launch shape the autotuner picks.  The paper batches its
+ * time-parallel slices across processors (Sec. 3.2); batching tissues is this
+ * library's own use of the same step.
+ *
+ * State layout: one device array y[n_state][ld] for the whole batch; tissue b
+ * occupies columns [offset_b, offset_b + N_b), offset_b a multiple of 512
+ * (esdc_batch_layout); the padding columns are never read as mesh nodes.
+ * Batches run the FP64 path (options.precision must be 0) with scalar
+ * conductivities.
+ * ------------------------------------------------------------------------ */
+typedef struct esdc_batch esdc_batch;
+
+/* meshes[n], sigma[n] (mS/mm) are host arrays, copied.  Errors as esdc_create;
+ * ESDC_ERR_UNSUPPORTED for precision != 0 or more tissues than one CG block
+ * can track (about 19,000 single-tile tissues on 152 SMs). */
+int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, double chi, double Cm, int model,
+                      const double* params, int n_params, const esdc_options* opt, esdc_batch** out);
+void esdc_batch_destroy(esdc_batch* b);
+const char* esdc_batch_last_error(const esdc_batch* b);
+
+/* Stimulus of tissue `tissue` (0-based), in the form of esdc_set_stimulus.
+ * Synchronises the device.  Errors: INVALID_ARG, CUDA. */
+int esdc_batch_set_stimulus(esdc_batch* b, int tissue, int nbox, const int* box, const double* amp,
+                            const double* t_on, const double* t_off);
+
+/* n_state, the row pitch ld of the batch state, and (optional, host [n]) the
+ * first column of every tissue. */
+int esdc_batch_layout(const esdc_batch* b, int* n_state, int64_t* ld, int64_t* offsets);
+
+/* Every column of y (device, [n_state][ld]) at the model's rest state at V0. */
+int esdc_batch_init_state(esdc_batch* b, double* y, double V0, void* stream);
+
+/* One HSDC step of every tissue, in place on y (device, [n_state][ld]).
+ * t (host, [n]) holds each tissue's t_n; dt, M (<= M_max) and K are shared.
+ * Stream-ordered, no synchronisation.  The first call for a given (y, M, K,
+ * dt) records the step's launches in a CUDA graph on a stream of the batch's
+ * own and later calls launch that graph on `stream` (falling back to direct
+ * launches if the driver cannot record them).  Errors: INVALID_ARG, CUDA. */
+int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M, int K, void* stream);
+
+/* Per tissue (host [n], optional): max |r| of the collocation residual and
+ * max |y| of the last step.  Synchronises that step's stream.  Returns
+ * NONFINITE, CG_NOT_CONVERGED or DEVICE_TIMEOUT if any tissue raised it. */
+int esdc_batch_residual(esdc_batch* b, double* res_inf, double* y_inf);
+
+/* CG iterations of the last step, [K*M][n] (solve-major), at most n_entries. */
+int esdc_batch_stats(esdc_batch* b, int* cg_iters, int n_entries);
+
+/* Graph recording on (default) or off. */
+int esdc_batch_set_graph(esdc_batch* b, int on);
+/* 1 if the last step ran from a recorded graph. */
+int esdc_batch_graph_active(const esdc_batch* b);
+/* Why recording failed ("" if it did not). */
+const char* esdc_batch_graph_error(const esdc_batch* b);
+
+/* Launch shape: node-kernel grid in waves of the resident capacity (1..8), CG
+ * block size (256 or 512) and CG blocks per SM (1..4, within occupancy).  No
+ * effect on results. */
+int esdc_batch_set_shape(esdc_batch* b, int node_waves, int cg_threads, int cg_blocks_per_sm);
+int esdc_batch_get_shape(const esdc_batch* b, int* node_waves, int* cg_threads, int* cg_blocks);
+
+/* Autotuner: times `reps` steps of the batch itself (from rest at V0, time t,
+ * on the caller's scratch state y_scratch of the batch's layout) for each
+ * candidate launch shape and keeps the fastest.  Synchronises. */
+int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, double dt, int M, int K, int reps,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,4 +2,4 @@
 spectral deferred correction (HSDC, "ES-SDC") step for the monodomain equation
 of arXiv 2405.19994, behind the C ABI of include/esdc.h."""
 from . import inputs  # noqa: F401
-from .esdc import Solver, EsdcError, lib  # noqa: F401
+from .esdc import Batch, Solver, EsdcError, lib  # noqa: F401

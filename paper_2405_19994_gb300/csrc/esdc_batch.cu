@@ -1,0 +1,1023 @@
+// Ragged batches: many tissues (meshes of different sizes and conductivities,
+// each with its own stimulus and start time) advanced by one HSDC step with the
+// same launches a single tissue needs.
+//
+// Layout.  The tissues are concatenated in every SoA array; tissue b occupies
+// nodes [off_b, off_b + N_b) with off_b a multiple of ESDC_TILE (512), so every
+// tile of 512 nodes belongs to exactly one tissue.  Node kernels find a node's
+// tissue from its tile and skip the padding at the end of each tissue.
+//
+// Determinism.  Every dot product of the CG is reduced first over one tile, in
+// an order fixed by the tile alone (lane l of a warp adds nodes l, l+32, ...,
+// then a fixed shuffle tree), then over the tiles of the tissue in tile order.
+// The result of every tissue is therefore independent of which other tissues
+// share the batch and of the launch shape (blocks, threads, tiles per warp);
+// the residual norms are maxima and order-free.  A batch of many tissues gives
+// bit for bit the results of the same tissues stepped one at a time, and the
+// launch-shape autotuner may choose any configuration without changing a bit.
+//
+// CG.  One cooperative launch solves all tissues' systems (I - dt d_i D_b L_b) x = b
+// together: the grid meets at the same barriers, each tissue has its own alpha,
+// beta and stop test, and a tissue that has converged drops out of the work.
+// Each block owns a contiguous range of tiles, hence few tissues; it reduces
+// only their totals.  The block holding a tissue's first tile records its
+// outcome, and the loop ends after the barrier at which every tissue has
+// recorded one.
+//
+// Graphs.  The launches of a step (set-up, K (M+1) node launches, K M solves,
+// residual) are captured once per (state buffer, M, K, dt) in a CUDA graph and
+// replayed; the only per-step data, the stimulus windows at the collocation
+// times, are copied to the device before each replay.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "esdc_kernels.cuh"
+#include "esdc_cg_common.cuh"
+
+namespace {
+
+std::mutex g_bconst_mu;
+bool g_bconst_done[64] = {false};
+
+constexpr int kMaxBlockTissues = 128;     // tissues one CG block may touch
+
+// ---------------------------------------------------------------- kernels
+template <class Model>
+__global__ void k_init_b(int64_t n, int64_t ld, ModelDev mp, double V0, double* y)
+{
+    constexpr int NS = Model::NS;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double u[NS];
+        Model::rest(mp.p, V0, u);
+        for (int s = 0; s < NS; ++s) y[s * ld + p] = u[s];
+    }
+}
+
+// Per-tissue residual maxima.  Warp w walks a contiguous range of 32-node
+// groups (a group never spans two tiles); running maxima are flushed to the
+// tissue's slots when the tissue changes.
+template <class Model, int M>
+__global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long long* rmax)
+{
+    constexpr int NS = Model::NS;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long ng = (long long)a.m.N >> 5;
+    const long long g0 = gw * ng / nw, g1 = (gw + 1) * ng / nw;
+    double rm[NS], ym[NS];
+    int cur = -1;
+    bool bad = false;
+    auto flush = [&](int b) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double r = rm[s], y = ym[s];
+            for (int o = 16; o > 0; o >>= 1) {
+                r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+                y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
+            }
+            if (lane == 0) {
+                atomicMax(rmax + (size_t)b * 2 * NS + s, (unsigned long long)__double_as_longlong(r));
+                atomicMax(rmax + (size_t)b * 2 * NS + NS + s, (unsigned long long)__double_as_longlong(y));
+            }
+        }
+    };
+    for (long long gi = g0; gi < g1; ++gi) {
+        const int p = (int)(gi * 32 + lane);
+        const int b = __ldg(a.tile_tissue + (p >> ESDC_TILE_SHIFT));      // the same for the whole warp
+        if (b != cur) {
+            if (cur >= 0) flush(cur);
+            cur = b;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) { rm[s] = 0.0; ym[s] = 0.0; }
+        }
+        const TissueDev* T = a.tis + b;
+        if (p - T->off < T->N) {
+#pragma unroll 1
+            for (int s = 0; s < NS; ++s) {
+                double r, y;
+                bad |= !residual_state<Model, M>(a, p, s, r, y);
+                rm[s] = fmax(rm[s], r);
+                ym[s] = fmax(ym[s], y);
+            }
+        }
+    }
+    if (cur >= 0) flush(cur);
+    if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+}
+
+struct BCgArgs {
+    const TissueDev* tis;
+    const int* tile_tissue;
+    int ntis, ntiles;
+    double gfac;                 // dt d_i: tissue b solves (I - gfac D_b L_b) x = b
+    const double* b;
+    double* x;
+    double *r, *p, *q, *z;
+    double* part;                // [6][ntiles] tile partials: set-up r.z, r.r, b.b | p.q | r.z, r.r
+    unsigned* bar;
+    int* flags;
+    int* done_at;                // [ntis] iteration after which the tissue stopped (INT_MAX: running)
+    int* status;                 // [ntis][2] iterations, flag bits of the last solve
+    int* iter_log;               // [ntis] iterations (optional)
+    double tol2;
+    int maxit, precond;
+};
+
+// Tile partials: lane l of the warp adds nodes l, l + 32, ... of the tile in
+// order; then a fixed shuffle tree.  All lanes return the tile's sum.
+__device__ __forceinline__ double warp_tree(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct BlockTissues {
+    int lo, n;                   // tissues lo .. lo+n-1 touch this block's tiles
+    long long t0, t1;            // this block's tiles
+};
+
+// Per-tissue totals of nv tile-partial slots for the block's tissues: warp w
+// reduces tissues w, w + nwarps, ...; lane l adds tiles l, l + 32, ... of the
+// tissue in order, then the fixed tree.  tot[k * nv + v] in shared memory.
+__device__ void tissue_totals(const BCgArgs& a, const BlockTissues& bt, const bool* active, int slot0, int nv,
+                              double* tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = w; k < bt.n; k += nw) {
+        if (!active[k]) continue;
+        const TissueDev* T = a.tis + bt.lo + k;
+        const int t0 = T->tile0, nt = T->ntile;
+        for (int v = 0; v < nv; ++v) {
+            const double* pv = a.part + (size_t)(slot0 + v) * a.ntiles + t0;
+            double s = 0.0;
+            for (int j = lane; j < nt; j += 32) s += __ldcg(pv + j);
+            s = warp_tree(s);
+            if (lane == 0) tot[k * nv + v] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Node work of one tile: lane l handles nodes tile*512 + l + 32u, u = 0..15.
+struct TileGeo {
+    int base, nx, ny, nz, N, off;
+};
+
+__global__ void __launch_bounds__(512) k_cgb(BCgArgs a)
+{
+    constexpr int U = ESDC_TILE / 32;
+    __shared__ bool s_active[kMaxBlockTissues];
+    __shared__ double s_gih2[kMaxBlockTissues], s_diag[kMaxBlockTissues][8], s_dinv[kMaxBlockTissues][8];
+    __shared__ double s_rz[kMaxBlockTissues], s_stop[kMaxBlockTissues];
+    __shared__ double s_alpha[kMaxBlockTissues], s_beta[kMaxBlockTissues];
+    __shared__ double s_tot[kMaxBlockTissues * 3];
+    __shared__ int s_exit;
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const long long nwt = (long long)gridDim.x * nwb;
+    BlockTissues bt;
+    bt.t0 = (long long)blockIdx.x * nwb * a.ntiles / nwt;
+    bt.t1 = (long long)(blockIdx.x + 1) * nwb * a.ntiles / nwt;
+    const long long wt0 = ((long long)blockIdx.x * nwb + w) * a.ntiles / nwt;
+    const long long wt1 = ((long long)blockIdx.x * nwb + w + 1) * a.ntiles / nwt;
+    if (bt.t1 > bt.t0) {
+        bt.lo = a.tile_tissue[bt.t0];
+        bt.n = a.tile_tissue[bt.t1 - 1] - bt.lo + 1;
+    } else {
+        bt.lo = 0;
+        bt.n = 0;
+    }
+    if (bt.n > kMaxBlockTissues) {
+        // The host sizes the grid so that this cannot happen.  Leaving now makes
+        // the other blocks give up at their next barrier wait (bounded) and
+        // report DEVICE_TIMEOUT; no shared-memory slot is ever out of range.
+        if (threadIdx.x == 0) atomicOr(a.flags, ESDC_FLAG_TIMEOUT);
+        return;
+    }
+    for (int k = threadIdx.x; k < bt.n; k += blockDim.x) {
+        const TissueDev* T = a.tis + bt.lo + k;
+        const double gih2 = a.gfac * T->D * T->ih2;
+        s_gih2[k] = gih2;
+        for (int c = 0; c < 8; ++c) {
+            s_diag[k][c] = 1.0 + gih2 * c;
+            s_dinv[k][c] = a.precond ? 1.0 / (1.0 + gih2 * c) : 1.0;
+        }
+        s_active[k] = true;
+        if (T->tile0 >= bt.t0 && T->tile0 < bt.t1) a.done_at[bt.lo + k] = INT_MAX;   // this block records it
+    }
+    __syncthreads();
+
+    // Stencil at node p of the tile's tissue: returns (I - g L) v and the Jacobi factor.
+    auto op = [&](const double* v, int p, const TileGeo& G, int k, double& dinv) -> double {
+        const int q = p - G.off;
+        const int r = q / G.nx;
+        const int ix = q - r * G.nx;
+        const int iz = r / G.ny;
+        const int iy = r - iz * G.ny;
+        const int sxy = G.nx * G.ny;
+        const double vp = __ldcg(v + p);
+        double s = 0.0;
+        int c = 0;
+        if (ix > 0)        { s += __ldcg(v + p - 1); ++c; }
+        if (ix < G.nx - 1) { s += __ldcg(v + p + 1); ++c; }
+        if (iy > 0)        { s += __ldcg(v + p - G.nx); ++c; }
+        if (iy < G.ny - 1) { s += __ldcg(v + p + G.nx); ++c; }
+        if (iz > 0)        { s += __ldcg(v + p - sxy); ++c; }
+        if (iz < G.nz - 1) { s += __ldcg(v + p + sxy); ++c; }
+        dinv = s_dinv[k][c];
+        return fma(s_diag[k][c], vp, -(s_gih2[k] * s));
+    };
+    auto tile_geo = [&](long long t, int& k) -> TileGeo {
+        const int b = a.tile_tissue[t];
+        k = b - bt.lo;
+        const TissueDev* T = a.tis + b;
+        TileGeo G;
+        G.base = (int)(t << ESDC_TILE_SHIFT);
+        G.nx = T->nx; G.ny = T->ny; G.nz = T->nz; G.N = T->N; G.off = T->off;
+        return G;
+    };
+    unsigned target = 0;
+
+    // [S] r = b - A x, z = D^{-1} r; tile partials r.z, r.r, b.b (slots 0-2)
+    for (long long t = wt0; t < wt1; ++t) {
+        int k;
+        const TileGeo G = tile_geo(t, k);
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+#pragma unroll 4
+        for (int u = 0; u < U; ++u) {
+            const int p = G.base + lane + 32 * u;
+            if (p - G.off >= G.N) continue;
+            double dinv;
+            const double ax = op(a.x, p, G, k, dinv);
+            const double bp = __ldcg(a.b + p);
+            const double rp = bp - ax;
+            const double zp = dinv * rp;
+            a.r[p] = rp;
+            a.z[p] = zp;
+            v0 = fma(rp, zp, v0);
+            v1 = fma(rp, rp, v1);
+            v2 = fma(bp, bp, v2);
+        }
+        v0 = warp_tree(v0); v1 = warp_tree(v1); v2 = warp_tree(v2);
+        if (lane == 0) {
+            a.part[t] = v0;
+            a.part[(size_t)a.ntiles + t] = v1;
+            a.part[2 * (size_t)a.ntiles + t] = v2;
+        }
+    }
+    if (!grid_barrier(a.bar, target, a.flags)) return;
+    tissue_totals(a, bt, s_active, 0, 3, s_tot);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < bt.n; ++k) {
+            const double rz = s_tot[3 * k], rr = s_tot[3 * k + 1], stop = a.tol2 * s_tot[3 * k + 2];
+            s_rz[k] = rz; s_stop[k] = stop;
+            const bool bad = !isfinite(rr) || !isfinite(stop);
+            const bool conv = rr <= stop;
+            if (bad || conv) {
+                s_active[k] = false;
+                const TissueDev* T = a.tis + bt.lo + k;
+                if (T->tile0 >= bt.t0 && T->tile0 < bt.t1) {
+                    a.done_at[bt.lo + k] = -1;
+                    a.status[2 * (bt.lo + k)] = 0;
+                    a.status[2 * (bt.lo + k) + 1] = bad ? ESDC_FLAG_NONFINITE : 0;
+                    if (a.iter_log) a.iter_log[bt.lo + k] = 0;
+                    if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    for (int it = 0;; ++it) {
+        if (it > a.maxit) {                   // cannot happen: every tissue stops by maxit
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+            break;
+        }
+        // [A] p = z + beta p, q = A z + beta q (first: p = z, q = A z); tile partials p.q (slot 3)
+        for (long long t = wt0; t < wt1; ++t) {
+            int k;
+            const TileGeo G = tile_geo(t, k);
+            if (!s_active[k]) continue;
+            const double beta = s_beta[k];
+            double v = 0.0;
+#pragma unroll 4
+            for (int u = 0; u < U; ++u) {
+                const int p = G.base + lane + 32 * u;
+                if (p - G.off >= G.N) continue;
+                double dinv;
+                const double az = op(a.z, p, G, k, dinv);
+                const double zp = __ldcg(a.z + p);
+                double pp = zp, qp = az;
+                if (it > 0) {
+                    pp = fma(beta, a.p[p], zp);
+                    qp = fma(beta, a.q[p], az);
+                }
+                a.p[p] = pp;
+                a.q[p] = qp;
+                v = fma(pp, qp, v);
+            }
+            v = warp_tree(v);
+            if (lane == 0) a.part[3 * (size_t)a.ntiles + t] = v;
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        // every tissue has stopped by the previous iteration: leave (the same decision in every block)
+        if (threadIdx.x < 32) {
+            bool all = true;
+            for (int b = threadIdx.x; b < a.ntis; b += 32) all &= __ldcg(a.done_at + b) <= it - 1;
+            all = __all_sync(0xffffffffu, all);
+            if (threadIdx.x == 0) s_exit = all;
+        }
+        __syncthreads();
+        if (s_exit) break;
+        tissue_totals(a, bt, s_active, 3, 1, s_tot);
+        for (int k = threadIdx.x; k < bt.n; k += blockDim.x)
+            if (s_active[k]) s_alpha[k] = s_rz[k] / s_tot[k];
+        __syncthreads();
+        // [B] x += alpha p, r -= alpha q, z = D^{-1} r; tile partials r.z, r.r (slots 4-5)
+        for (long long t = wt0; t < wt1; ++t) {
+            int k;
+            const TileGeo G = tile_geo(t, k);
+            if (!s_active[k]) continue;
+            const double alpha = s_alpha[k];
+            double v0 = 0.0, v1 = 0.0;
+#pragma unroll 4
+            for (int u = 0; u < U; ++u) {
+                const int p = G.base + lane + 32 * u;
+                const int q = p - G.off;
+                if (q >= G.N) continue;
+                const double rp = fma(-alpha, a.q[p], a.r[p]);
+                a.x[p] = fma(alpha, a.p[p], a.x[p]);
+                a.r[p] = rp;
+                double zq = rp;
+                if (a.precond) {
+                    const int rr = q / G.nx;
+                    const int ix = q - rr * G.nx;
+                    const int iz = rr / G.ny;
+                    const int iy = rr - iz * G.ny;
+                    const int c = (ix > 0) + (ix < G.nx - 1) + (iy > 0) + (iy < G.ny - 1) + (iz > 0) + (iz < G.nz - 1);
+                    zq = s_dinv[k][c] * rp;
+                }
+                a.z[p] = zq;
+                v0 = fma(rp, zq, v0);
+                v1 = fma(rp, rp, v1);
+            }
+            v0 = warp_tree(v0); v1 = warp_tree(v1);
+            if (lane == 0) {
+                a.part[4 * (size_t)a.ntiles + t] = v0;
+                a.part[5 * (size_t)a.ntiles + t] = v1;
+            }
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        tissue_totals(a, bt, s_active, 4, 2, s_tot);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < bt.n; ++k) {
+                if (!s_active[k]) continue;
+                const double rz = s_tot[2 * k], rr = s_tot[2 * k + 1];
+                s_beta[k] = rz / s_rz[k];
+                s_rz[k] = rz;
+
+                const bool bad = !isfinite(rr);
+                const bool conv = rr <= s_stop[k];
+                const bool maxed = it + 1 >= a.maxit;
+                if (bad || conv || maxed) {
+                    s_active[k] = false;
+                    const TissueDev* T = a.tis + bt.lo + k;
+                    if (T->tile0 >= bt.t0 && T->tile0 < bt.t1) {
+                        const int f = bad ? ESDC_FLAG_NONFINITE : (conv ? 0 : ESDC_FLAG_CG_MAXIT);
+                        a.done_at[bt.lo + k] = it;
+                        a.status[2 * (bt.lo + k)] = it + 1;
+                        a.status[2 * (bt.lo + k) + 1] = f;
+                        if (a.iter_log) a.iter_log[bt.lo + k] = it + 1;
+                        if (f) atomicOr(a.flags, f);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host
+template <class F>
+int occupancy(F kernel, int threads)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) return 0;
+    return per_sm;
+}
+
+}  // namespace
+
+struct esdc_batch {
+    int device = 0, sms = 152;
+    int model = 0, NS = 0, NA = 0, NG = 0;
+    int ntis = 0, ntiles = 0;
+    int64_t ld = 0;
+    double chi = 0, Cm = 0;
+    esdc_options opt{};
+    ColloData col[ESDC_MMAX];
+    ModelDev mp{};
+    ModelDevF mpf{};
+    std::vector<TissueDev> tis_h;
+    std::vector<unsigned> on_h;            // [ntis][ESDC_MMAX + 1]
+    TissueDev* tis = nullptr;
+    int* tile_tissue = nullptr;
+    unsigned* tis_on = nullptr;
+    double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,
+           *LAMN = nullptr, *rhs = nullptr, *Vprev = nullptr;
+    double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr;
+    unsigned* bar = nullptr;
+    int *done_at = nullptr, *status = nullptr, *cg_log = nullptr, *flags = nullptr;
+    int cg_log_len = 0;
+    unsigned long long* rmax = nullptr;    // [ntis][2 NS]
+    // launch shapes (esdc_batch_tune)
+    int node_waves = 1, cg_threads = 512, cg_blocks = 0;
+    int occ_node[ESDC_MMAX + 1] = {0}, occ_setup[ESDC_MMAX + 1] = {0}, occ_res[ESDC_MMAX + 1] = {0};
+    // graph of one step
+    bool use_graph = true, graph_failed = false;
+    cudaStream_t cap_stream = nullptr;     // private stream the step is recorded on
+    cudaGraphExec_t gexec = nullptr;
+    const double* g_y = nullptr;
+    int g_M = 0, g_K = 0;
+    double g_dt = 0.0;
+    char graph_err[128] = {0};
+    // last step
+    int last_M = 0, last_K = 0;
+    cudaStream_t last_stream = nullptr;
+    char err[256] = {0};
+};
+
+namespace {
+
+int set_berr(esdc_batch* b, int code, const char* msg)
+{
+    std::snprintf(b->err, sizeof b->err, "%s", msg);
+    return code;
+}
+
+void free_batch(esdc_batch* b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    void* ptrs[] = {b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
+                    b->rhs, b->Vprev, b->r, b->p, b->q, b->z, b->part, b->bar, b->done_at, b->status,
+                    b->cg_log, b->flags, b->rmax};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int grid_nodes(const esdc_batch* b, int occ, int waves)
+{
+    long long cap = (long long)b->sms * (occ < 1 ? 1 : occ) * waves;
+    long long need = (b->ld + 127) / 128;
+    return (int)std::max(1LL, std::min(cap, need));
+}
+
+// Largest number of tissues one CG block touches for a grid of nb blocks.
+int max_block_tissues(const esdc_batch* b, int nb, int threads)
+{
+    const int nwb = threads / 32;
+    const long long nwt = (long long)nb * nwb;
+    int worst = 0;
+    for (int blk = 0; blk < nb; ++blk) {
+        const long long t0 = (long long)blk * nwb * b->ntiles / nwt, t1 = (long long)(blk + 1) * nwb * b->ntiles / nwt;
+        if (t1 <= t0) continue;
+        int lo = 0, hi = 0;
+        for (int k = 0; k < b->ntis; ++k) {                // tissues are in tile order
+            if (b->tis_h[k].tile0 <= t0) lo = k;
+            if (b->tis_h[k].tile0 <= t1 - 1) hi = k;
+        }
+        worst = std::max(worst, hi - lo + 1);
+    }
+    return worst;
+}
+
+int cg_grid(const esdc_batch* b, int threads, int per_sm_wanted)
+{
+    const int occ = occupancy(k_cgb, threads);
+    if (occ < 1) return 0;
+    int per_sm = std::min(occ, per_sm_wanted);
+    long long nb = (long long)b->sms * per_sm;
+    const long long need = ((long long)b->ntiles + threads / 32 - 1) / (threads / 32);
+    nb = std::max(1LL, std::min(nb, need));
+    while (nb > 1 && max_block_tissues(b, (int)nb, threads) > kMaxBlockTissues) --nb;
+    return (int)nb;
+}
+
+cudaError_t launch_cgb(esdc_batch* b, double gfac, const double* rhs, double* x, int* log, cudaStream_t s)
+{
+    BCgArgs a;
+    a.tis = b->tis;
+    a.tile_tissue = b->tile_tissue;
+    a.ntis = b->ntis;
+    a.ntiles = b->ntiles;
+    a.gfac = gfac;
+    a.b = rhs;
+    a.x = x;
+    a.r = b->r; a.p = b->p; a.q = b->q; a.z = b->z;
+    a.part = b->part;
+    a.bar = b->bar;
+    a.flags = b->flags;
+    a.done_at = b->done_at;
+    a.status = b->status;
+    a.iter_log = log;
+    a.tol2 = b->opt.tol_cg * b->opt.tol_cg;
+    a.maxit = b->opt.cg_maxit;
+    a.precond = b->opt.precond;
+    void* args[] = {&a};
+    cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void*)k_cgb, dim3(b->cg_blocks), dim3(b->cg_threads), args, 0, s);
+}
+
+// Occupancy of the step kernels (queried before any stream capture).
+template <class Model, int M>
+void batch_prime(esdc_batch* b)
+{
+    if (b->occ_node[M]) return;
+    b->occ_node[M] = occupancy(k_node<Model, M, false, true>, 128);
+    b->occ_setup[M] = occupancy(k_setup<Model, M, false, true>, 128);
+    b->occ_res[M] = occupancy(k_residual_b<Model, M>, 128);
+}
+
+template <class Model, int M>
+cudaError_t batch_step(esdc_batch* b, double* y, double dt, int K, cudaStream_t s)
+{
+    const int T = 128;
+    batch_prime<Model, M>(b);
+    const ColloData* C = &b->col[M - 1];
+    StepArgs a{};
+    a.m.nx = 1; a.m.ny = 1; a.m.nz = 1;
+    a.m.N = (int)b->ld;
+    a.m.ld = b->ld;
+    a.m.ih2 = 1.0;
+    a.mp = b->mp;
+    a.mpf = b->mpf;
+    a.Vprev = b->Vprev;
+    a.dt = dt;
+    a.inv_Cm = 1.0 / b->Cm;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) a.dS0[i][j] = dt * C->S0[i][j];
+    for (int i = 0; i <= M; ++i) a.dtd[i] = dt * C->d[i];
+    a.yn = y;
+    a.Y = b->Y; a.FI = b->FI; a.S = b->S; a.PHI = b->PHI; a.LAMN = b->LAMN; a.rhs = b->rhs;
+    a.R = nullptr;
+    a.rmax = nullptr;
+    a.flags = b->flags;
+    a.tis = b->tis;
+    a.tile_tissue = b->tile_tissue;
+    a.tis_on = b->tis_on;
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->flags, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->rmax, 0, sizeof(unsigned long long) * 2 * b->NS * b->ntis, s)) != cudaSuccess)
+        return e;
+    a.Gnew = b->G0;
+    a.Gold = b->G0;
+    k_setup<Model, M, false, true><<<grid_nodes(b, b->occ_setup[M], b->node_waves), T, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    double* Gold = b->G0;
+    double* Gnew = b->G1;
+    const int nb_node = grid_nodes(b, b->occ_node[M], b->node_waves);
+    for (int k = 0; k < K; ++k) {
+        a.Gold = Gold;
+        a.Gnew = Gnew;
+        for (int i = 1; i <= M + 1; ++i) {
+            a.i = i;
+            a.k = k;
+            a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
+            k_node<Model, M, false, true><<<nb_node, T, 0, s>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (i <= M) {
+                double* Vi = b->Y + (int64_t)(i - 1) * b->NS * b->ld;
+                const int slot = k * M + (i - 1);
+                int* log = (slot + 1) * b->ntis <= b->cg_log_len ? b->cg_log + (size_t)slot * b->ntis : nullptr;
+                if ((e = launch_cgb(b, dt * C->d[i], b->rhs, Vi, log, s)) != cudaSuccess) return e;
+            }
+        }
+        std::swap(Gold, Gnew);
+    }
+    a.Gold = Gold;
+    a.yout = y;
+    k_residual_b<Model, M><<<grid_nodes(b, b->occ_res[M], b->node_waves), T, 0, s>>>(a, b->rmax);
+    return cudaGetLastError();
+}
+
+template <class Model>
+cudaError_t batch_step_M(esdc_batch* b, double* y, double dt, int M, int K, cudaStream_t s)
+{
+    switch (M) {
+        case 1: return batch_step<Model, 1>(b, y, dt, K, s);
+        case 2: return batch_step<Model, 2>(b, y, dt, K, s);
+        case 3: return batch_step<Model, 3>(b, y, dt, K, s);
+        case 4: return batch_step<Model, 4>(b, y, dt, K, s);
+        case 5: return batch_step<Model, 5>(b, y, dt, K, s);
+        case 6: return batch_step<Model, 6>(b, y, dt, K, s);
+        case 7: return batch_step<Model, 7>(b, y, dt, K, s);
+        case 8: return batch_step<Model, 8>(b, y, dt, K, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Model>
+void batch_prime_M(esdc_batch* b, int M)
+{
+    switch (M) {
+        case 1: batch_prime<Model, 1>(b); break;
+        case 2: batch_prime<Model, 2>(b); break;
+        case 3: batch_prime<Model, 3>(b); break;
+        case 4: batch_prime<Model, 4>(b); break;
+        case 5: batch_prime<Model, 5>(b); break;
+        case 6: batch_prime<Model, 6>(b); break;
+        case 7: batch_prime<Model, 7>(b); break;
+        case 8: batch_prime<Model, 8>(b); break;
+        default: break;
+    }
+}
+
+cudaError_t batch_launch(esdc_batch* b, double* y, double dt, int M, int K, cudaStream_t s)
+{
+    return b->model == ESDC_MODEL_HH1952 ? batch_step_M<esdc::HH1952>(b, y, dt, M, K, s)
+                                         : batch_step_M<esdc::SYN19>(b, y, dt, M, K, s);
+}
+
+void drop_graph(esdc_batch* b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_y = nullptr;
+}
+
+// Records one step in a graph for (y, M, K, dt).  The recording runs on the
+// batch's own stream (the legacy default stream cannot be recorded); the graph
+// is then launched on the caller's stream.  On failure the reason is kept and
+// the batch falls back to direct launches for good (graph_failed).
+bool capture(esdc_batch* b, double* y, double dt, int M, int K)
+{
+    drop_graph(b);
+    if (b->model == ESDC_MODEL_HH1952) batch_prime_M<esdc::HH1952>(b, M);
+    else batch_prime_M<esdc::SYN19>(b, M);
+    auto fail = [&](const char* what, cudaError_t e) {
+        std::snprintf(b->graph_err, sizeof b->graph_err, "%s: %s", what, cudaGetErrorString(e));
+        cudaGetLastError();
+        return false;
+    };
+    cudaError_t e;
+    if (!b->cap_stream && (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail("stream", e);
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return fail("begin capture", e);
+    const cudaError_t el = batch_launch(b, y, dt, M, K, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (el != cudaSuccess || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return fail("capture", el != cudaSuccess ? el : e);
+    }
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        return fail("instantiate", e);
+    }
+    b->g_y = y; b->g_M = M; b->g_K = K; b->g_dt = dt;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, double chi, double Cm, int model,
+                      const double* params, int n_params, const esdc_options* opt, esdc_batch** out)
+{
+    if (!out) return ESDC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || !meshes || !sigma || !params) return ESDC_ERR_INVALID_ARG;
+    if (!(chi > 0.0) || !(Cm > 0.0) || !std::isfinite(chi) || !std::isfinite(Cm)) return ESDC_ERR_INVALID_ARG;
+    long long total = 0;
+    for (int k = 0; k < n; ++k) {
+        const esdc_mesh& m = meshes[k];
+        if (m.dim < 1 || m.dim > 3 || m.nx < 1 || m.ny < 1 || m.nz < 1) return ESDC_ERR_INVALID_ARG;
+        if ((m.dim < 3 && m.nz != 1) || (m.dim < 2 && m.ny != 1)) return ESDC_ERR_INVALID_ARG;
+        if (!(m.h > 0.0) || !std::isfinite(m.h)) return ESDC_ERR_INVALID_ARG;
+        if (!(sigma[k] >= 0.0) || !std::isfinite(sigma[k])) return ESDC_ERR_INVALID_ARG;
+        const long long N = (long long)m.nx * m.ny * m.nz;
+        total += (N + ESDC_TILE - 1) / ESDC_TILE * ESDC_TILE;
+        if (total > 0x7fffffffLL - ESDC_TILE) return ESDC_ERR_TOO_LARGE;
+    }
+    ModelDev mp{};
+    ModelDevF mpf{};
+    int NS = 0, NG = 0;
+    const int rc = esdc_model_setup(model, params, n_params, &mp, &mpf, &NS, &NG);
+    if (rc != ESDC_OK) return rc;
+    esdc_options o;
+    esdc_default_options(&o);
+    if (opt) o = *opt;
+    if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
+    if (o.precision != 0) return ESDC_ERR_UNSUPPORTED;            // batches run the FP64 path
+
+    esdc_batch* b = new (std::nothrow) esdc_batch();
+    if (!b) return ESDC_ERR_NO_MEMORY;
+    auto fail = [&](int code) { free_batch(b); delete b; return code; };
+    b->opt = o;
+    b->model = model; b->NS = NS; b->NG = NG; b->NA = NS - 1 - NG;
+    b->chi = chi; b->Cm = Cm;
+    b->mp = mp; b->mpf = mpf;
+    b->ntis = n;
+    b->tis_h.resize(n);
+    int tile = 0;
+    for (int k = 0; k < n; ++k) {
+        TissueDev& T = b->tis_h[k];
+        std::memset(&T, 0, sizeof T);
+        T.nx = meshes[k].nx; T.ny = meshes[k].ny; T.nz = meshes[k].nz;
+        T.N = T.nx * T.ny * T.nz;
+        T.off = tile * ESDC_TILE;
+        T.tile0 = tile;
+        T.ntile = (T.N + ESDC_TILE - 1) / ESDC_TILE;
+        T.ih2 = 1.0 / (meshes[k].h * meshes[k].h);
+        T.D = sigma[k] / (chi * Cm);
+        tile += T.ntile;
+    }
+    b->ntiles = tile;
+    b->ld = (int64_t)tile * ESDC_TILE;
+    b->on_h.assign((size_t)n * (ESDC_MMAX + 1), 0u);
+    for (int M = 1; M <= ESDC_MMAX; ++M)
+        if (esdc_colloc_build(M, &b->col[M - 1])) return fail(ESDC_ERR_CUDA);
+    if (cudaGetDevice(&b->device) != cudaSuccess) return fail(ESDC_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+        return fail(ESDC_ERR_CUDA);
+    {
+        std::lock_guard<std::mutex> lk(g_bconst_mu);
+        if (upload_constants_local(g_bconst_done, b->device) != cudaSuccess) return fail(ESDC_ERR_CUDA);
+    }
+    const int64_t ld = b->ld, Mx = o.M_max;
+    struct { double** p; int64_t n; } bufs[] = {
+        {&b->Y, Mx * NS * ld}, {&b->G0, Mx * NS * ld}, {&b->G1, Mx * NS * ld}, {&b->FI, Mx * ld},
+        {&b->S, Mx * Mx * NG * ld}, {&b->PHI, Mx * NG * ld}, {&b->LAMN, NG * ld}, {&b->rhs, ld},
+        {&b->Vprev, ld}, {&b->r, ld}, {&b->p, ld}, {&b->q, ld}, {&b->z, ld}, {&b->part, 6LL * tile}};
+    for (auto& bf : bufs) {
+        cudaError_t e = cudaMalloc((void**)bf.p, sizeof(double) * bf.n);
+        if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA);
+        cudaMemset(*bf.p, 0, sizeof(double) * bf.n);
+    }
+    b->cg_log_len = 64 * ESDC_MMAX * n;
+    if (cudaMalloc((void**)&b->tis, sizeof(TissueDev) * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->tile_tissue, sizeof(int) * tile) != cudaSuccess ||
+        cudaMalloc((void**)&b->tis_on, sizeof(unsigned) * b->on_h.size()) != cudaSuccess ||
+        cudaMalloc((void**)&b->bar, sizeof(unsigned) * 2) != cudaSuccess ||
+        cudaMalloc((void**)&b->done_at, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->status, sizeof(int) * 2 * n) != cudaSuccess ||
+        cudaMalloc((void**)&b->cg_log, sizeof(int) * b->cg_log_len) != cudaSuccess ||
+        cudaMalloc((void**)&b->flags, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&b->rmax, sizeof(unsigned long long) * 2 * NS * n) != cudaSuccess)
+        return fail(ESDC_ERR_NO_MEMORY);
+    std::vector<int> tt(tile);
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < b->tis_h[k].ntile; ++j) tt[b->tis_h[k].tile0 + j] = k;
+    if (cudaMemcpy(b->tis, b->tis_h.data(), sizeof(TissueDev) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tile_tissue, tt.data(), sizeof(int) * tile, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(ESDC_ERR_CUDA);
+    cudaMemset(b->tis_on, 0, sizeof(unsigned) * b->on_h.size());
+    cudaMemset(b->bar, 0, sizeof(unsigned) * 2);
+    cudaMemset(b->status, 0, sizeof(int) * 2 * n);
+    cudaMemset(b->cg_log, 0, sizeof(int) * b->cg_log_len);
+    cudaMemset(b->flags, 0, sizeof(int));
+    b->cg_threads = 512;
+    b->cg_blocks = cg_grid(b, b->cg_threads, 1);
+    if (b->cg_blocks < 1) return fail(ESDC_ERR_CUDA);
+    if (max_block_tissues(b, b->cg_blocks, b->cg_threads) > kMaxBlockTissues) return fail(ESDC_ERR_UNSUPPORTED);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(ESDC_ERR_CUDA);
+    *out = b;
+    return ESDC_OK;
+}
+
+void esdc_batch_destroy(esdc_batch* b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    delete b;
+}
+
+const char* esdc_batch_last_error(const esdc_batch* b) { return b ? b->err : "null batch"; }
+
+int esdc_batch_set_stimulus(esdc_batch* b, int tissue, int nbox, const int* box, const double* amp,
+                            const double* t_on, const double* t_off)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (tissue < 0 || tissue >= b->ntis) return set_berr(b, ESDC_ERR_INVALID_ARG, "tissue out of range");
+    if (nbox < 0 || nbox > ESDC_MAXBOX) return set_berr(b, ESDC_ERR_INVALID_ARG, "nbox out of range");
+    if (nbox > 0 && (!box || !amp || !t_on || !t_off)) return set_berr(b, ESDC_ERR_INVALID_ARG, "null stimulus array");
+    StimDev st{};
+    st.nbox = nbox;
+    for (int k = 0; k < nbox; ++k) {
+        for (int c = 0; c < 6; ++c) st.box[k][c] = box[6 * k + c];
+        st.amp[k] = amp[k]; st.t_on[k] = t_on[k]; st.t_off[k] = t_off[k];
+        if (!std::isfinite(amp[k]) || std::isnan(t_on[k]) || std::isnan(t_off[k]))
+            return set_berr(b, ESDC_ERR_INVALID_ARG, "non-finite stimulus value");
+    }
+    b->tis_h[tissue].st = st;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(b->tis + tissue, &b->tis_h[tissue], sizeof(TissueDev), cudaMemcpyHostToDevice) != cudaSuccess)
+        return set_berr(b, ESDC_ERR_CUDA, "stimulus upload failed");
+    return ESDC_OK;
+}
+
+int esdc_batch_layout(const esdc_batch* b, int* n_state, int64_t* ld, int64_t* offsets)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (n_state) *n_state = b->NS;
+    if (ld) *ld = b->ld;
+    if (offsets)
+        for (int k = 0; k < b->ntis; ++k) offsets[k] = b->tis_h[k].off;
+    return ESDC_OK;
+}
+
+int esdc_batch_init_state(esdc_batch* b, double* y, double V0, void* stream)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (!y || !std::isfinite(V0)) return set_berr(b, ESDC_ERR_INVALID_ARG, "bad init arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)std::min<int64_t>((b->ld + 127) / 128, (int64_t)b->sms * 16);
+    if (b->model == ESDC_MODEL_HH1952) k_init_b<esdc::HH1952><<<nb, 128, 0, s>>>(b->ld, b->ld, b->mp, V0, y);
+    else k_init_b<esdc::SYN19><<<nb, 128, 0, s>>>(b->ld, b->ld, b->mp, V0, y);
+    if (cudaGetLastError() != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "init launch failed");
+    return ESDC_OK;
+}
+
+int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M, int K, void* stream)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (!y || !t) return set_berr(b, ESDC_ERR_INVALID_ARG, "null state or time array");
+    if (M < 1 || M > b->opt.M_max || K < 1 || K > 64) return set_berr(b, ESDC_ERR_INVALID_ARG, "M or K out of range");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_berr(b, ESDC_ERR_INVALID_ARG, "dt must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ColloData& C = b->col[M - 1];
+    for (int k = 0; k < b->ntis; ++k) {
+        if (!std::isfinite(t[k])) return set_berr(b, ESDC_ERR_INVALID_ARG, "non-finite time");
+        const StimDev& st = b->tis_h[k].st;
+        for (int i = 0; i <= M; ++i) {
+            const double tj = t[k] + C.c[i] * dt;
+            unsigned on = 0;
+            for (int q = 0; q < st.nbox; ++q)
+                if (tj >= st.t_on[q] && tj < st.t_off[q]) on |= 1u << q;
+            b->on_h[(size_t)k * (ESDC_MMAX + 1) + i] = on;
+        }
+    }
+    // pageable source: the copy has left on_h when the call returns
+    if (cudaMemcpyAsync(b->tis_on, b->on_h.data(), sizeof(unsigned) * b->on_h.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return set_berr(b, ESDC_ERR_CUDA, "stimulus window upload failed");
+    b->last_M = M; b->last_K = K; b->last_stream = s;
+    if (b->use_graph && !b->graph_failed) {
+        if (!(b->gexec && b->g_y == y && b->g_M == M && b->g_K == K && b->g_dt == dt)) {
+            if (!capture(b, y, dt, M, K)) b->graph_failed = true;
+        }
+        if (b->gexec) {
+            if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "graph launch failed");
+            return ESDC_OK;
+        }
+    }
+    if (batch_launch(b, y, dt, M, K, s) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "step launch failed");
+    return ESDC_OK;
+}
+
+int esdc_batch_residual(esdc_batch* b, double* res_inf, double* y_inf)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->last_stream) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "step failed");
+    std::vector<unsigned long long> rm((size_t)2 * b->NS * b->ntis);
+    int flags = 0;
+    if (cudaMemcpy(rm.data(), b->rmax, sizeof(unsigned long long) * rm.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&flags, b->flags, sizeof flags, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_berr(b, ESDC_ERR_CUDA, "reading the residual failed");
+    for (int k = 0; k < b->ntis; ++k) {
+        double r = 0.0, y = 0.0;
+        for (int s = 0; s < b->NS; ++s) {
+            double v;
+            unsigned long long u = rm[(size_t)k * 2 * b->NS + s];
+            std::memcpy(&v, &u, sizeof v);
+            r = std::max(r, v);
+            u = rm[(size_t)k * 2 * b->NS + b->NS + s];
+            std::memcpy(&v, &u, sizeof v);
+            y = std::max(y, v);
+        }
+        if (res_inf) res_inf[k] = r;
+        if (y_inf) y_inf[k] = y;
+    }
+    if (flags & ESDC_FLAG_TIMEOUT) return set_berr(b, ESDC_ERR_DEVICE_TIMEOUT, "CG grid barrier timed out");
+    if (flags & ESDC_FLAG_NONFINITE) return set_berr(b, ESDC_ERR_NONFINITE, "non-finite value in the step");
+    if (flags & ESDC_FLAG_CG_MAXIT) return set_berr(b, ESDC_ERR_CG_NOT_CONVERGED, "CG hit cg_maxit");
+    return ESDC_OK;
+}
+
+int esdc_batch_stats(esdc_batch* b, int* cg_iters, int n_entries)
+{
+    if (!b || !cg_iters || n_entries < 0) return ESDC_ERR_INVALID_ARG;
+    const int n = std::min(n_entries, b->last_K * b->last_M * b->ntis);
+    if (cudaStreamSynchronize(b->last_stream) != cudaSuccess ||
+        (n > 0 && cudaMemcpy(cg_iters, b->cg_log, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess))
+        return set_berr(b, ESDC_ERR_CUDA, "reading the statistics failed");
+    return ESDC_OK;
+}
+
+int esdc_batch_set_graph(esdc_batch* b, int on)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    b->use_graph = on != 0;
+    b->graph_failed = false;
+    return ESDC_OK;
+}
+
+int esdc_batch_graph_active(const esdc_batch* b)
+{
+    return (b && b->gexec && !b->graph_failed) ? 1 : 0;
+}
+
+const char* esdc_batch_graph_error(const esdc_batch* b)
+{
+    return b ? b->graph_err : "null batch";
+}
+
+int esdc_batch_get_shape(const esdc_batch* b, int* node_waves, int* cg_threads, int* cg_blocks)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (node_waves) *node_waves = b->node_waves;
+    if (cg_threads) *cg_threads = b->cg_threads;
+    if (cg_blocks) *cg_blocks = b->cg_blocks;
+    return ESDC_OK;
+}
+
+int esdc_batch_set_shape(esdc_batch* b, int node_waves, int cg_threads, int cg_blocks_per_sm)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (node_waves < 1 || node_waves > 8 || (cg_threads != 256 && cg_threads != 512) || cg_blocks_per_sm < 1 ||
+        cg_blocks_per_sm > 4)
+        return set_berr(b, ESDC_ERR_INVALID_ARG, "launch shape out of range");
+    const int nb = cg_grid(b, cg_threads, cg_blocks_per_sm);
+    if (nb < 1) return set_berr(b, ESDC_ERR_CUDA, "CG occupancy query failed");
+    if (max_block_tissues(b, nb, cg_threads) > kMaxBlockTissues)
+        return set_berr(b, ESDC_ERR_UNSUPPORTED, "too many tissues per CG block for this shape");
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    b->node_waves = node_waves;
+    b->cg_threads = cg_threads;
+    b->cg_blocks = nb;
+    return ESDC_OK;
+}
+
+int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, double dt, int M, int K, int reps,
+                    void* stream)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (!y_scratch || reps < 1 || reps > 100 || !std::isfinite(V0))
+        return set_berr(b, ESDC_ERR_INVALID_ARG, "bad tuning arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    struct Shape { int waves, threads, per_sm; };
+    const Shape cand[] = {{1, 512, 1}, {2, 512, 1}, {4, 512, 1}, {1, 256, 1}, {1, 256, 2}, {2, 256, 2}, {4, 256, 2}};
+    std::vector<double> tv(b->ntis, t);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return set_berr(b, ESDC_ERR_CUDA, "event creation failed");
+    }
+    float best = 1e30f;
+    Shape pick = {b->node_waves, b->cg_threads, 0};
+    int pick_blocks = b->cg_blocks;
+    int rc = ESDC_OK;
+    for (const Shape& c : cand) {
+        if (esdc_batch_set_shape(b, c.waves, c.threads, c.per_sm) != ESDC_OK) continue;
+        rc = esdc_batch_init_state(b, y_scratch, V0, stream);
+        if (rc == ESDC_OK) rc = esdc_batch_sweep(b, y_scratch, tv.data(), dt, M, K, stream);   // capture, warm-up
+        if (rc == ESDC_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = ESDC_ERR_CUDA;
+        for (int r = 0; r < reps && rc == ESDC_OK; ++r) rc = esdc_batch_sweep(b, y_scratch, tv.data(), dt, M, K, stream);
+        if (rc == ESDC_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            rc = ESDC_ERR_CUDA;
+        if (rc != ESDC_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = c; pick_blocks = b->cg_blocks; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ESDC_OK) return rc;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    b->node_waves = pick.waves;
+    b->cg_threads = pick.threads;
+    b->cg_blocks = pick_blocks;
+    return ESDC_OK;
+}
+
+}  // extern "C"

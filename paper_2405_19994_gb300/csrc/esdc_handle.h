@@ -32,6 +32,10 @@ struct StepArgs {
     double* R;             // residual vectors (optional)
     unsigned long long* rmax;   // [NS] per-state max |r| (as ordered bits), [NS] max |y|
     int* flags;
+    // ragged batches (batched kernels only)
+    const TissueDev* tis;
+    const int* tile_tissue;     // [tiles] tissue of each tile
+    const unsigned* tis_on;     // [tissues][ESDC_MMAX + 1] stimulus window bits per collocation time
 };
 
 struct esdc_handle {

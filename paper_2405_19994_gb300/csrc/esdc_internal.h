@@ -33,6 +33,9 @@ struct ColloData {
     int nb[5];
 };
 
+struct ModelDev;
+struct ModelDevF;
+
 // Fills ColloData for 1 <= M <= 8.  Returns 0 on success.
 int esdc_colloc_build(int M, ColloData* out);
 
@@ -64,6 +67,19 @@ struct ModelDevF {            // FP32 copy of the parameters (precision form)
     float p[ESDC_NPMAX];
 };
 
+// Ragged batches: meshes concatenated in the state arrays, each starting on a
+// tile boundary; tiles are also the unit of every deterministic reduction.
+#define ESDC_TILE_SHIFT 9
+#define ESDC_TILE (1 << ESDC_TILE_SHIFT)   // 512 nodes
+
+struct TissueDev {
+    int nx, ny, nz, N;
+    int off;                 // first node in the concatenated arrays (multiple of ESDC_TILE)
+    int tile0, ntile;        // its tiles
+    double ih2, D;           // 1/h^2, sigma / (chi C_m)
+    StimDev st;
+};
+
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
 struct CgWork {
     double *r, *p, *q, *z;          // [ld] each
@@ -74,6 +90,10 @@ struct CgWork {
     int max_blocks;
     int threads;
 };
+
+// Validates ionic-model parameters and fills the device parameter blocks;
+// returns ESDC_OK or ESDC_ERR_INVALID_ARG.
+int esdc_model_setup(int model, const double* params, int n_params, ModelDev* mp, ModelDevF* mpf, int* NS, int* NG);
 
 #define ESDC_FLAG_CG_MAXIT   1
 #define ESDC_FLAG_TIMEOUT    2

@@ -113,82 +113,118 @@ __device__ __forceinline__ double phi1(double y)
 // ------------------------------------------------------------------ set-up
 // Lambda_n, dt S_ij(dt Lambda_n), dt d_i phi_1(d_i dt Lambda_n) (tables carry the
 // step size); y^0 = 1 (x) y_n; G_j^0 = g_n(t_{n,j}, y_n); FI_j^0 = f_I(y_n).
+// Batched form: nodes of a ragged batch of meshes, concatenated in ESDC_TILE-node
+// tiles; the tissue of a node is found from its tile.
+struct BatchNode {
+    MeshDev m;               // the node's own mesh (ld: the pitch of the concatenated arrays)
+    const TissueDev* T;
+    const unsigned* on;      // stimulus window bits of the tissue, per collocation time
+    int ix, iy, iz;
+};
+
+__device__ __forceinline__ bool batch_node(const StepArgs& a, int p, BatchNode& n)
+{
+    const int b = __ldg(a.tile_tissue + (p >> ESDC_TILE_SHIFT));
+    const TissueDev* T = a.tis + b;
+    const int q = p - (int)T->off;
+    if (q >= T->N) return false;              // padding at the end of the tissue's last tile
+    n.m = a.m;
+    n.m.nx = T->nx; n.m.ny = T->ny; n.m.nz = T->nz; n.m.N = T->N; n.m.ih2 = T->ih2;
+    n.m.lay = nullptr; n.m.wdiag = nullptr; n.m.layf = nullptr;
+    n.T = T;
+    n.on = a.tis_on + (size_t)b * (ESDC_MMAX + 1);
+    node_xyz(n.m, q, n.ix, n.iy, n.iz);
+    return true;
+}
+
 template <class Model, int M, bool MIXED>
-__global__ void __launch_bounds__(128) k_setup(StepArgs a)
+__device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
+                                           const unsigned* on, double D, int p, int ix, int iy, int iz)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const MeshDev& m = a.m;
     const ColloData& C = c_col[M - 1];
-    const int64_t ld = m.ld;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        node_xyz(m, p, ix, iy, iz);
-        double u[NS];
+    const int64_t ld = a.m.ld;
+    double u[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) u[s] = a.yn[s * ld + p];
-        const double fi = a.D * lap(m, a.yn, p, ix, iy, iz);
-        double mI, ha[NA > 0 ? NA : 1];
-        float uf[NS];
+    for (int s = 0; s < NS; ++s) u[s] = a.yn[s * ld + p];
+    const double fi = D * lap(m, a.yn, p, ix, iy, iz);
+    double mI, ha[NA > 0 ? NA : 1];
+    float uf[NS];
+    if (MIXED) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) uf[s] = (float)u[s];
+        float mIf, haf[NA > 0 ? NA : 1];
+        Model::currents_f(a.mpf.p, uf, mIf, haf);
+        mI = mIf;
+#pragma unroll
+        for (int s = 0; s < NA; ++s) ha[s] = haf[s];
+    } else {
+        Model::currents(a.mp.p, u, mI, ha);
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        double* Yj = a.Y + (int64_t)j * NS * ld;
+        double* Gj = a.Gnew + (int64_t)j * NS * ld;
+        Gj[p] = fi + (stim_at(st, on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
+        Yj[p] = u[0];
+#pragma unroll
+        for (int s = 1; s <= NA; ++s) { Gj[s * ld + p] = ha[s - 1]; Yj[s * ld + p] = u[s]; }
+        a.FI[(int64_t)j * ld + p] = fi;
+    }
+#pragma unroll 1
+    for (int g = 0; g < NG; ++g) {
+        const int s = 1 + NA + g;
+        double lam, yinf;
         if (MIXED) {
-#pragma unroll
-            for (int s = 0; s < NS; ++s) uf[s] = (float)u[s];
-            float mIf, haf[NA > 0 ? NA : 1];
-            Model::currents_f(a.mpf.p, uf, mIf, haf);
-            mI = mIf;
-#pragma unroll
-            for (int s = 0; s < NA; ++s) ha[s] = haf[s];
+            float lf, yf;
+            Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
+            lam = lf; yinf = yf;
         } else {
-            Model::currents(a.mp.p, u, mI, ha);
+            Model::gate(a.mp.p, g, u[0], lam, yinf);
         }
+        const double us = a.yn[s * ld + p];
+        const double g0 = lam * (us - yinf);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            double* Yj = a.Y + (int64_t)j * NS * ld;
-            double* Gj = a.Gnew + (int64_t)j * NS * ld;
-            Gj[p] = fi + (stim_at(a.st, a.stim_on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
-            Yj[p] = u[0];
-#pragma unroll
-            for (int s = 1; s <= NA; ++s) { Gj[s * ld + p] = ha[s - 1]; Yj[s * ld + p] = u[s]; }
-            a.FI[(int64_t)j * ld + p] = fi;
+            a.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
+            a.Y[((int64_t)j * NS + s) * ld + p] = us;
         }
-#pragma unroll 1
-        for (int g = 0; g < NG; ++g) {
-            const int s = 1 + NA + g;
-            double lam, yinf;
-            if (MIXED) {
-                float lf, yf;
-                Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
-                lam = lf; yinf = yf;
-            } else {
-                Model::gate(a.mp.p, g, u[0], lam, yinf);
-            }
-            const double us = a.yn[s * ld + p];
-            const double g0 = lam * (us - yinf);
+        const double z = a.dt * lam;
+        a.LAMN[(int64_t)g * ld + p] = lam;
+        double aprev[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) aprev[j] = 0.0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            double ph[M];
+            phi_all<M>(C.c[i + 1] * z, ph);
+            const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
+            a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
 #pragma unroll
             for (int j = 0; j < M; ++j) {
-                a.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
-                a.Y[((int64_t)j * NS + s) * ld + p] = us;
+                double aij = 0.0;
+#pragma unroll
+                for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
+                aij *= a.dt;                                                 // dt a_ij
+                a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
+                aprev[j] = aij;
             }
-            const double z = a.dt * lam;
-            a.LAMN[(int64_t)g * ld + p] = lam;
-            double aprev[M];
-#pragma unroll
-            for (int j = 0; j < M; ++j) aprev[j] = 0.0;
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                double ph[M];
-                phi_all<M>(C.c[i + 1] * z, ph);
-                const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
-                a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    double aij = 0.0;
-#pragma unroll
-                    for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
-                    aij *= a.dt;                                                 // dt a_ij
-                    a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
-                    aprev[j] = aij;
-                }
-            }
+        }
+    }
+}
+
+template <class Model, int M, bool MIXED, bool BATCH>
+__global__ void __launch_bounds__(128) k_setup(StepArgs a)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
+        if (!BATCH) {
+            int ix, iy, iz;
+            node_xyz(a.m, p, ix, iy, iz);
+            setup_body<Model, M, MIXED>(a, a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+        } else {
+            BatchNode n;
+            if (!batch_node(a, p, n)) continue;
+            setup_body<Model, M, MIXED>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
         }
     }
 }
@@ -202,99 +238,111 @@ __global__ void __launch_bounds__(128) k_setup(StepArgs a)
 #define ESDC_NODE_MINBLOCKS 5      // 5 x 128 threads per SM: at most 102 registers
 #endif
 template <class Model, int M, bool MIXED>
-__global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
+__device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
+                                          const unsigned* on, double D, int p, int ix, int iy, int iz)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const MeshDev& m = a.m;
-    const int64_t ld = m.ld;
+    const int64_t ld = a.m.ld;
     const int i = a.i;
     const bool eval = i >= 2;                 // G at y_{i-1}^{k+1}
     const bool quad = i <= M;                 // explicit rows of y_i^{k+1}
     const int jm = i - 2;                     // 0-based index of node i-1
     const int ii = i - 1;                     // 0-based index of node i
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        node_xyz(m, p, ix, iy, iz);
-        const double* src = eval ? a.Y + (int64_t)jm * NS * ld : a.yn;   // y_{i-1}^{k+1}
-        double u[NS];
+    const double* src = eval ? a.Y + (int64_t)jm * NS * ld : a.yn;   // y_{i-1}^{k+1}
+    double u[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) u[s] = src[s * ld + p];
-        const double* Gp = a.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
-        double* Gq = a.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
-        double* Yi = a.Y + (int64_t)ii * NS * ld;
-        const double dtd = quad ? a.dtd[i] : 0.0;
+    for (int s = 0; s < NS; ++s) u[s] = src[s * ld + p];
+    const double* Gp = a.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
+    double* Gq = a.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
+    double* Yi = a.Y + (int64_t)ii * NS * ld;
+    const double dtd = quad ? a.dtd[i] : 0.0;
 
-        // ---- V row and auxiliaries
-        double dlt0 = 0.0, ha[NA > 0 ? NA : 1];
-        float uf[NS];
+    // ---- V row and auxiliaries
+    double dlt0 = 0.0, ha[NA > 0 ? NA : 1];
+    float uf[NS];
+    if (eval) {
+        const double fi = D * lap(m, src, p, ix, iy, iz);
+        double mI;
+        if (MIXED) {                      // precision form: the ionic model in FP32
+#pragma unroll
+            for (int s = 0; s < NS; ++s) uf[s] = (float)u[s];
+            float mIf, haf[NA > 0 ? NA : 1];
+            Model::currents_f(a.mpf.p, uf, mIf, haf);
+            mI = mIf;
+#pragma unroll
+            for (int s = 0; s < NA; ++s) ha[s] = haf[s];
+        } else {
+            Model::currents(a.mp.p, u, mI, ha);
+        }
+        const double fE = (stim_at(st, on[i - 1], ix, iy, iz) + mI) * a.inv_Cm;
+        const double fi_old = a.FI[(int64_t)jm * ld + p];
+        a.FI[(int64_t)jm * ld + p] = fi;
+        Gq[p] = fi + fE;
+        dlt0 = fE - (Gp[p] - fi_old);
+#pragma unroll
+        for (int s = 1; s <= NA; ++s) Gq[s * ld + p] = ha[s - 1];
+    }
+    if (quad) {
+        // Initial guess of the V_i solve: V_i^k moved by the change the previous
+        // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
+        // starting point of CG changes; the solution is the same.
+        const double vik = Yi[p];
+        if (eval) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
+        a.Vprev[p] = vik;
+        double q = u[0];
+#pragma unroll
+        for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
+        a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
+#pragma unroll
+        for (int s = 1; s <= NA; ++s) {
+            const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
+            double qa = u[s];
+#pragma unroll
+            for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
+            Yi[s * ld + p] = fma(dtd, dl, qa);
+        }
+    }
+    // ---- gates, one at a time
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int s = 1 + NA + g;
+        double dl = 0.0;
         if (eval) {
-            const double fi = a.D * lap(m, src, p, ix, iy, iz);
-            double mI;
-            if (MIXED) {                      // precision form: the ionic model in FP32
-#pragma unroll
-                for (int s = 0; s < NS; ++s) uf[s] = (float)u[s];
-                float mIf, haf[NA > 0 ? NA : 1];
-                Model::currents_f(a.mpf.p, uf, mIf, haf);
-                mI = mIf;
-#pragma unroll
-                for (int s = 0; s < NA; ++s) ha[s] = haf[s];
+            double lam, yinf;
+            if (MIXED) {
+                float lf, yf;
+                Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
+                lam = lf; yinf = yf;
             } else {
-                Model::currents(a.mp.p, u, mI, ha);
+                Model::gate(a.mp.p, g, u[0], lam, yinf);
             }
-            const double fE = (stim_at(a.st, a.stim_on[i - 1], ix, iy, iz) + mI) * a.inv_Cm;
-            const double fi_old = a.FI[(int64_t)jm * ld + p];
-            a.FI[(int64_t)jm * ld + p] = fi;
-            Gq[p] = fi + fE;
-            dlt0 = fE - (Gp[p] - fi_old);
-#pragma unroll
-            for (int s = 1; s <= NA; ++s) Gq[s * ld + p] = ha[s - 1];
+            const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
+            Gq[s * ld + p] = gn;
+            dl = gn - Gp[s * ld + p];
         }
         if (quad) {
-            // Initial guess of the V_i solve: V_i^k moved by the change the previous
-            // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
-            // starting point of CG changes; the solution is the same.
-            const double vik = Yi[p];
-            if (eval) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
-            a.Vprev[p] = vik;
-            double q = u[0];
+            double qg = u[s];
 #pragma unroll
-            for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
-            a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
-#pragma unroll
-            for (int s = 1; s <= NA; ++s) {
-                const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
-                double qa = u[s];
-#pragma unroll
-                for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
-                Yi[s * ld + p] = fma(dtd, dl, qa);
-            }
+            for (int j = 0; j < M; ++j)
+                qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
+                         a.Gold[((int64_t)j * NS + s) * ld + p], qg);
+            Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
         }
-        // ---- gates, one at a time
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            const int s = 1 + NA + g;
-            double dl = 0.0;
-            if (eval) {
-                double lam, yinf;
-                if (MIXED) {
-                    float lf, yf;
-                    Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
-                    lam = lf; yinf = yf;
-                } else {
-                    Model::gate(a.mp.p, g, u[0], lam, yinf);
-                }
-                const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
-                Gq[s * ld + p] = gn;
-                dl = gn - Gp[s * ld + p];
-            }
-            if (quad) {
-                double qg = u[s];
-#pragma unroll
-                for (int j = 0; j < M; ++j)
-                    qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
-                             a.Gold[((int64_t)j * NS + s) * ld + p], qg);
-                Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
-            }
+    }
+}
+
+template <class Model, int M, bool MIXED, bool BATCH>
+__global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
+        if (!BATCH) {
+            int ix, iy, iz;
+            node_xyz(a.m, p, ix, iy, iz);
+            node_body<Model, M, MIXED>(a, a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+        } else {
+            BatchNode n;
+            if (!batch_node(a, p, n)) continue;
+            node_body<Model, M, MIXED>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
         }
     }
 }
@@ -303,43 +351,55 @@ __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
 // r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C), accumulated over i from the row
 // differences dt S_ij = dt (a_ij - a_{i-1,j});
 // per-state max |r| and max |y|; y_{n+1} = y_M.
+// One state s of one node: the residual recursion over the M nodes, the
+// largest |r_i| and |y| (y_n included), and y_{n+1} = y_{n,M} (c_M = 1).
+// Returns false if a residual or iterate is not finite.
+template <class Model, int M>
+__device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, double& rmax, double& ymax)
+{
+    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
+    const int64_t ld = a.m.ld;
+    const int g = s - 1 - NA;
+    const double yns = a.yn[s * ld + p];
+    bool ok = true;
+    ymax = fabs(yns);
+    rmax = 0.0;
+    // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
+    double r = 0.0, yprev = yns;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        double q = 0.0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
+            q = fma(sij, a.Gold[((int64_t)j * NS + s) * ld + p], q);
+        }
+        const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
+        r += q - (yi - yprev);
+        yprev = yi;
+        if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
+        ok &= isfinite(r) && isfinite(yi);
+        rmax = fmax(rmax, fabs(r));
+        ymax = fmax(ymax, fabs(yi));
+    }
+    // y_n was read above by this thread only, so y may alias y_{n+1}.
+    a.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
+    return ok;
+}
+
 template <class Model, int M>
 __global__ void __launch_bounds__(128) k_residual(StepArgs a)
 {
-    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const MeshDev& m = a.m;
-    const ColloData& C = c_col[M - 1];
-    const int64_t ld = m.ld;
+    constexpr int NS = Model::NS;
     __shared__ double smax[2 * ESDC_NSMAX];
     for (int s = threadIdx.x; s < 2 * NS; s += blockDim.x) smax[s] = 0.0;
     __syncthreads();
     bool bad = false;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
-            const int g = s - 1 - NA;
-            const double yns = a.yn[s * ld + p];
-            double ymax = fabs(yns), rmax = 0.0;
-            // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
-            double r = 0.0, yprev = yns;
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                double q = 0.0;
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
-                    q = fma(sij, a.Gold[((int64_t)j * NS + s) * ld + p], q);
-                }
-                const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
-                r += q - (yi - yprev);
-                yprev = yi;
-                if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
-                bad |= !isfinite(r) || !isfinite(yi);
-                rmax = fmax(rmax, fabs(r));
-                ymax = fmax(ymax, fabs(yi));
-            }
-            // y_{n+1} = y_{n,M} (c_M = 1); y_n was read above by this thread only.
-            a.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
+            double rmax, ymax;
+            bad |= !residual_state<Model, M>(a, p, s, rmax, ymax);
             // shared-memory max of non-negative doubles through their bit patterns
             atomicMax((unsigned long long*)&smax[s], (unsigned long long)__double_as_longlong(rmax));
             atomicMax((unsigned long long*)&smax[NS + s], (unsigned long long)__double_as_longlong(ymax));
@@ -399,9 +459,9 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     const int T = 128;
     static int occ_setup = 0, occ_node = 0, occ_res = 0;    // blocks/SM per (model, M) instantiation
     if (!occ_setup) {
-        occ_node = blocks_per_sm(k_node<Model, M, MIXED>, T);
+        occ_node = blocks_per_sm(k_node<Model, M, MIXED, false>, T);
         occ_res = blocks_per_sm(k_residual<Model, M>, T);
-        occ_setup = blocks_per_sm(k_setup<Model, M, MIXED>, T);
+        occ_setup = blocks_per_sm(k_setup<Model, M, MIXED, false>, T);
     }
     const int nb_setup = resident_grid(h, occ_setup, T);
     const int nb_node = resident_grid(h, occ_node, T);
@@ -422,7 +482,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     a.Gnew = h->G0;
     a.Gold = h->G0;
     prof_begin(h, 0, s);
-    k_setup<Model, M, MIXED><<<nb_setup, T, 0, s>>>(a);
+    k_setup<Model, M, MIXED, false><<<nb_setup, T, 0, s>>>(a);
     prof_end(h, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -437,7 +497,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
             // first sweep: y^0 = y_n, so the change grows with the node time c_i
             a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
             prof_begin(h, 1, s);
-            k_node<Model, M, MIXED><<<nb_node, T, 0, s>>>(a);
+            k_node<Model, M, MIXED, false><<<nb_node, T, 0, s>>>(a);
             prof_end(h, s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (i <= M) {

@@ -165,6 +165,36 @@ void free_all(esdc_handle* h)
 
 }  // namespace
 
+// Validates the ionic-model parameters and fills the device parameter blocks
+// (FP64, with host reciprocals of the constant divisors of SYN19, and FP32).
+int esdc_model_setup(int model, const double* params, int n_params, ModelDev* mp, ModelDevF* mpf, int* NS, int* NG)
+{
+    const int need = model == ESDC_MODEL_HH1952 ? 7 : model == ESDC_MODEL_SYN19 ? 88 : -1;
+    if (need < 0 || !params || n_params != need) return ESDC_ERR_INVALID_ARG;
+    for (int k = 0; k < n_params; ++k)
+        if (!std::isfinite(params[k])) return ESDC_ERR_INVALID_ARG;
+    if (model == ESDC_MODEL_SYN19) {
+        for (int q = 0; q < 12; ++q)
+            if (params[6 * q + 1] == 0.0 || params[6 * q + 5] == 0.0 || !(params[6 * q + 2] > 0.0))
+                return ESDC_ERR_INVALID_ARG;
+        for (int l = 0; l < 6; ++l)
+            if (!(params[82 + l] > 0.0)) return ESDC_ERR_INVALID_ARG;
+    }
+    *mp = ModelDev{};
+    for (int k = 0; k < n_params; ++k) mp->p[k] = params[k];
+    if (model == ESDC_MODEL_SYN19) {
+        for (int q = 0; q < 12; ++q) {
+            mp->p[88 + q] = 1.0 / params[6 * q + 1];
+            mp->p[100 + q] = 1.0 / params[6 * q + 5];
+        }
+        for (int l = 0; l < 6; ++l) mp->p[112 + l] = 1.0 / params[82 + l];
+    }
+    for (int k = 0; k < ESDC_NPMAX; ++k) mpf->p[k] = (float)mp->p[k];
+    *NS = model == ESDC_MODEL_HH1952 ? 4 : 19;
+    *NG = model == ESDC_MODEL_HH1952 ? 3 : 12;
+    return ESDC_OK;
+}
+
 extern "C" {
 
 void esdc_default_options(esdc_options* opt)
@@ -192,16 +222,15 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     if (!(sigma >= 0.0) || !(chi > 0.0) || !(Cm > 0.0) || !std::isfinite(sigma) || !std::isfinite(chi) ||
         !std::isfinite(Cm))
         return ESDC_ERR_INVALID_ARG;
-    int need = model == ESDC_MODEL_HH1952 ? 7 : model == ESDC_MODEL_SYN19 ? 88 : -1;
-    if (need < 0 || n_params != need) return ESDC_ERR_INVALID_ARG;
-    for (int k = 0; k < n_params; ++k)
-        if (!std::isfinite(params[k])) return ESDC_ERR_INVALID_ARG;
-    if (model == ESDC_MODEL_SYN19) {
-        for (int q = 0; q < 12; ++q)
-            if (params[6 * q + 1] == 0.0 || params[6 * q + 5] == 0.0 || !(params[6 * q + 2] > 0.0))
-                return ESDC_ERR_INVALID_ARG;
-        for (int l = 0; l < 6; ++l)
-            if (!(params[82 + l] > 0.0)) return ESDC_ERR_INVALID_ARG;
+    ModelDev mp{};
+    ModelDevF mpf{};
+    int64_t NS = 0, NG = 0;              // they size the workspace below
+    {
+        int ns = 0, ng = 0;
+        const int mrc = esdc_model_setup(model, params, n_params, &mp, &mpf, &ns, &ng);
+        if (mrc != ESDC_OK) return mrc;
+        NS = ns;
+        NG = ng;
     }
     esdc_options o;
     esdc_default_options(&o);
@@ -213,8 +242,8 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     if (!h) return ESDC_ERR_NO_MEMORY;
     h->opt = o;
     h->model = model;
-    h->NS = model == ESDC_MODEL_HH1952 ? 4 : 19;
-    h->NG = model == ESDC_MODEL_HH1952 ? 3 : 12;
+    h->NS = NS;
+    h->NG = NG;
     h->NA = h->NS - 1 - h->NG;
     h->sigma = sigma; h->chi = chi; h->Cm = Cm;
     h->D = sigma / (chi * Cm);
@@ -222,15 +251,8 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     h->mesh.N = (int)N;
     h->mesh.ld = (N + 31) / 32 * 32;
     h->mesh.ih2 = 1.0 / (mesh->h * mesh->h);
-    for (int k = 0; k < n_params; ++k) h->mp.p[k] = params[k];
-    if (model == ESDC_MODEL_SYN19) {             // reciprocals of the constant divisors
-        for (int q = 0; q < 12; ++q) {
-            h->mp.p[88 + q] = 1.0 / params[6 * q + 1];
-            h->mp.p[100 + q] = 1.0 / params[6 * q + 5];
-        }
-        for (int l = 0; l < 6; ++l) h->mp.p[112 + l] = 1.0 / params[82 + l];
-    }
-    for (int k = 0; k < ESDC_NPMAX; ++k) h->mpf.p[k] = (float)h->mp.p[k];
+    h->mp = mp;
+    h->mpf = mpf;
 
     auto fail = [&](int code) { free_all(h); delete h; return code; };
     for (int M = 1; M <= ESDC_MMAX; ++M)
@@ -243,7 +265,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
         if (upload_constants_local(g_const_done, h->device) != cudaSuccess) return fail(ESDC_ERR_CUDA);
     }
 
-    const int64_t ld = h->mesh.ld, NS = h->NS, NG = h->NG, Mx = o.M_max;
+    const int64_t ld = h->mesh.ld, Mx = o.M_max;
     struct { double** p; int64_t n; } bufs[] = {
         {&h->Y, Mx * NS * ld}, {&h->G0, Mx * NS * ld}, {&h->G1, Mx * NS * ld}, {&h->FI, Mx * ld},
         {&h->S, Mx * Mx * NG * ld}, {&h->PHI, Mx * NG * ld}, {&h->LAMN, NG * ld}, {&h->rhs, ld},

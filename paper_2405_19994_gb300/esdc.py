@@ -75,6 +75,23 @@ def lib() -> C.CDLL:
             "esdc_math_check": (C.c_int, [_VP, _I64, _VP, _VP, _VP]),
             "esdc_diffusion_solve_static": (C.c_int, [C.POINTER(esdc_mesh), _D, _VP, _VP, _D, C.c_int, C.c_int,
                                                       C.POINTER(C.c_int), _VP]),
+            "esdc_batch_create": (C.c_int, [C.c_int, C.POINTER(esdc_mesh), C.POINTER(_D), _D, _D, C.c_int,
+                                            C.POINTER(_D), C.c_int, C.POINTER(esdc_options), C.POINTER(_VP)]),
+            "esdc_batch_destroy": (None, [_VP]),
+            "esdc_batch_last_error": (C.c_char_p, [_VP]),
+            "esdc_batch_set_stimulus": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_D),
+                                                  C.POINTER(_D), C.POINTER(_D)]),
+            "esdc_batch_layout": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(_I64), C.POINTER(_I64)]),
+            "esdc_batch_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
+            "esdc_batch_sweep": (C.c_int, [_VP, _VP, C.POINTER(_D), _D, C.c_int, C.c_int, _VP]),
+            "esdc_batch_residual": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D)]),
+            "esdc_batch_stats": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
+            "esdc_batch_set_graph": (C.c_int, [_VP, C.c_int]),
+            "esdc_batch_graph_active": (C.c_int, [_VP]),
+            "esdc_batch_graph_error": (C.c_char_p, [_VP]),
+            "esdc_batch_set_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+            "esdc_batch_get_shape": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "esdc_batch_tune": (C.c_int, [_VP, _VP, _D, _D, _D, C.c_int, C.c_int, C.c_int, _VP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -250,3 +267,118 @@ class Solver:
         fE, lam, yinf = (torch.empty_like(y) for _ in range(3))
         self._check(lib().esdc_ionic(self._h, _ptr(y), _ptr(fE), _ptr(lam), _ptr(yinf), _stream(stream)))
         return fE, lam, yinf
+
+
+class Batch:
+    """A ragged batch of tissues stepped together (``esdc_batch_*``).
+
+    The tissues share the ionic model, chi, C_m and the options; each has its
+    own mesh, scalar conductivity, stimulus and start time.  The state of the
+    whole batch is one device tensor [n_state, ld]; tissue b occupies columns
+    offsets[b] .. offsets[b] + n_nodes[b]."""
+
+    def __init__(self, meshes, sigmas, chi: float, Cm: float, model: int, params, M_max: int = 8,
+                 tol_cg: float = 1e-14, cg_maxit: int = 200, precond: bool = True):
+        self._b = None
+        L = lib()
+        n = len(meshes)
+        arr = (esdc_mesh * n)(*[esdc_mesh(*m) for m in meshes])
+        sig = np.ascontiguousarray(sigmas, np.float64)
+        opt = esdc_options()
+        L.esdc_default_options(C.byref(opt))
+        opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond = M_max, tol_cg, cg_maxit, int(precond)
+        p = np.ascontiguousarray(params, np.float64)
+        out = _VP()
+        rc = L.esdc_batch_create(n, arr, sig.ctypes.data_as(C.POINTER(_D)), chi, Cm, model,
+                                 p.ctypes.data_as(C.POINTER(_D)), len(p), C.byref(opt), C.byref(out))
+        if rc != ESDC_OK:
+            raise EsdcError(rc, "esdc_batch_create failed")
+        self._b = out.value
+        self.n = n
+        ns, ld = C.c_int(), _I64()
+        offs = np.zeros(n, np.int64)
+        self._check(L.esdc_batch_layout(self._b, C.byref(ns), C.byref(ld), offs.ctypes.data_as(C.POINTER(_I64))))
+        self.n_state, self.ld, self.offsets = ns.value, ld.value, offs
+        self.n_nodes = np.array([m[1] * m[2] * m[3] for m in meshes], np.int64)
+
+    @classmethod
+    def from_workloads(cls, wls, **kw) -> "Batch":
+        """All workloads must share model, parameters, chi and C_m."""
+        w0 = wls[0]
+        meshes = [(w.dim, w.nx, w.ny, w.nz, w.h) for w in wls]
+        b = cls(meshes, [w.sigma for w in wls], w0.chi, w0.Cm, w0.model, w0.params, **kw)
+        for k, w in enumerate(wls):
+            b.set_stimulus(k, w.boxes, w.amp, w.t_on, w.t_off)
+        return b
+
+    def _check(self, rc: int):
+        if rc != ESDC_OK:
+            msg = lib().esdc_batch_last_error(self._b).decode() if self._b else ""
+            raise EsdcError(rc, msg)
+
+    def close(self):
+        if self._b:
+            lib().esdc_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stimulus(self, tissue: int, boxes, amp, t_on, t_off):
+        box = np.ascontiguousarray(np.asarray(boxes, np.int32).reshape(-1))
+        a, on, off = (np.ascontiguousarray(v, np.float64) for v in (amp, t_on, t_off))
+        self._check(lib().esdc_batch_set_stimulus(self._b, tissue, len(a), box.ctypes.data_as(C.POINTER(C.c_int)),
+                                                  a.ctypes.data_as(C.POINTER(_D)), on.ctypes.data_as(C.POINTER(_D)),
+                                                  off.ctypes.data_as(C.POINTER(_D))))
+
+    def new_state(self):
+        import torch
+        return torch.zeros((self.n_state, self.ld), dtype=torch.float64, device="cuda")
+
+    def init_state(self, y, V0: float, stream=None):
+        self._check(lib().esdc_batch_init_state(self._b, _ptr(y), V0, _stream(stream)))
+
+    def sweep(self, y, t, dt: float, M: int, K: int, stream=None):
+        tv = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (self.n,)))
+        self._check(lib().esdc_batch_sweep(self._b, _ptr(y), tv.ctypes.data_as(C.POINTER(_D)), dt, M, K,
+                                           _stream(stream)))
+
+    def residual(self):
+        """(return code, res_inf[n], y_inf[n]); does not raise on solver flags."""
+        r = np.zeros(self.n)
+        y = np.zeros(self.n)
+        rc = lib().esdc_batch_residual(self._b, r.ctypes.data_as(C.POINTER(_D)), y.ctypes.data_as(C.POINTER(_D)))
+        return rc, r, y
+
+    def stats(self, K: int, M: int) -> np.ndarray:
+        out = np.zeros(K * M * self.n, np.int32)
+        self._check(lib().esdc_batch_stats(self._b, out.ctypes.data_as(C.POINTER(C.c_int)), len(out)))
+        return out.reshape(K * M, self.n)
+
+    def set_graph(self, on: bool):
+        self._check(lib().esdc_batch_set_graph(self._b, int(on)))
+
+    def graph_active(self) -> bool:
+        return bool(lib().esdc_batch_graph_active(self._b))
+
+    def graph_error(self) -> str:
+        return lib().esdc_batch_graph_error(self._b).decode()
+
+    def set_shape(self, node_waves: int, cg_threads: int, cg_blocks_per_sm: int):
+        self._check(lib().esdc_batch_set_shape(self._b, node_waves, cg_threads, cg_blocks_per_sm))
+
+    def shape(self):
+        w, t, b = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().esdc_batch_get_shape(self._b, C.byref(w), C.byref(t), C.byref(b)))
+        return w.value, t.value, b.value
+
+    def tune(self, y_scratch, V0: float, t: float, dt: float, M: int, K: int, reps: int = 3, stream=None):
+        self._check(lib().esdc_batch_tune(self._b, _ptr(y_scratch), V0, t, dt, M, K, reps, _stream(stream)))
+
+    def tissue(self, y, b: int):
+        """View of tissue b's columns of a batch state."""
+        o = int(self.offsets[b])
+        return y[:, o:o + int(self.n_nodes[b])]

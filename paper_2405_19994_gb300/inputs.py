@@ -180,3 +180,25 @@ def random_state(wl: Workload, seed: int, ld: int | None = None) -> np.ndarray:
     y[0, :N] = -85.0 + 115.0 / (1.0 + np.exp((ix - x0) / width)) + rng.normal(0.0, 0.5, N)
     y[1:, :N] = rng.uniform(0.0, 1.0, (wl.n_state - 1, N))
     return y
+
+
+def hh_batch(n: int = 64, seed: int = 4, side: tuple = (64, 512), sigma: tuple = (0.05, 0.3),
+             patch: int = 8) -> list:
+    """The ragged batch of the batching form: n seeded 2D Hodgkin-Huxley tissues,
+    each side length drawn uniformly from side[0]..side[1] (nx and ny
+    independently), sigma uniformly from sigma[0]..sigma[1] mS/mm, and a
+    patch x patch stimulus (0.5 uA/mm^2 for [0, 1) ms) at a uniformly drawn
+    position.  h = 0.25 mm, rest -75 mV, M = 3, K = 4, dt = 0.025 ms, T = 4 ms."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nx, ny = (int(v) for v in rng.integers(side[0], side[1] + 1, size=2))
+        sg = float(rng.uniform(*sigma))
+        px, py = min(patch, nx), min(patch, ny)
+        x0 = int(rng.integers(0, nx - px + 1))
+        y0 = int(rng.integers(0, ny - py + 1))
+        out.append(Workload(name=f"hh_batch[{k}]_{nx}x{ny}", dim=2 if ny > 1 else 1, nx=nx, ny=ny, nz=1, h=0.25,
+                            model=MODEL_HH1952, params=hh1952_params(), V0=-75.0, M=3, K=4, dt=0.025, T=4.0,
+                            sigma=sg, boxes=np.array([[x0, x0 + px, y0, y0 + py, 0, 1]], np.int32),
+                            amp=np.array([0.5]), t_on=np.array([0.0]), t_off=np.array([1.0])))
+    return out

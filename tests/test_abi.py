@@ -87,3 +87,35 @@ def test_no_product_import_of_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "esdc_oracle" not in txt and "liborc" not in txt, f
+
+
+def test_batch_invalid_arguments_rejected_without_gpu(L):
+    from paper_2405_19994_gb300 import esdc as E
+    from paper_2405_19994_gb300 import inputs as I
+    p = I.hh1952_params()
+    pp = p.ctypes.data_as(C.POINTER(C.c_double))
+    out = C.c_void_p(1)
+    meshes = (E.esdc_mesh * 2)(E.esdc_mesh(2, 8, 8, 1, 0.25), E.esdc_mesh(2, 5, 3, 1, 0.25))
+    sig = np.array([0.1, 0.2])
+    sp = sig.ctypes.data_as(C.POINTER(C.c_double))
+
+    def create(n=2, m=meshes, s=sp, chi=140.0, Cm=0.01, model=0, params=pp, npar=7, optp=None):
+        return L.esdc_batch_create(n, m, s, chi, Cm, model, params, npar, optp, C.byref(out))
+
+    assert create(n=0) == -1 and out.value is None
+    assert create(m=None) == -1
+    assert create(s=None) == -1
+    assert create(chi=0.0) == -1
+    assert create(npar=6) == -1
+    bad = np.array([0.1, -1.0])
+    assert create(s=bad.ctypes.data_as(C.POINTER(C.c_double))) == -1
+    bm = (E.esdc_mesh * 2)(E.esdc_mesh(2, 8, 8, 3, 0.25), E.esdc_mesh(2, 5, 3, 1, 0.25))
+    assert create(m=bm) == -1                                  # 2D mesh with nz != 1
+    opt = E.esdc_options(); L.esdc_default_options(C.byref(opt))
+    opt.precision = 1
+    assert create(optp=C.byref(opt)) == -6                     # batches run the FP64 path
+    assert L.esdc_batch_sweep(None, None, None, 0.1, 3, 4, None) == -1
+    assert L.esdc_batch_residual(None, None, None) == -1
+    assert L.esdc_batch_layout(None, None, None, None) == -1
+    L.esdc_batch_destroy(None)
+    assert L.esdc_batch_last_error(None) == b"null batch"

@@ -1,0 +1,172 @@
+"""Ragged batches (esdc_batch_*): every tissue of a batch against the FP64 oracle
+run on that tissue alone, and bit-for-bit identity of the batched results with
+the same tissues stepped one at a time, across launch shapes, with and without
+the recorded CUDA graph."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+import paper_2405_19994_gb300 as P  # noqa: E402
+from paper_2405_19994_gb300 import inputs as I  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    P.lib()
+
+
+def small_batch():
+    """Seven ragged tissues: odd and even sides, a 1D strip, one single-tile tissue,
+    and one spanning several tiles; stimulus patches at seeded positions."""
+    wls = I.hh_batch(n=5, seed=11, side=(3, 41), sigma=(0.05, 0.3), patch=4)
+    wls.append(I.hh_batch(n=1, seed=12, side=(37, 37))[0].with_mesh(37, 1, 1))      # 1D strip
+    wls.append(I.hh_batch(n=1, seed=13, side=(48, 48))[0])                          # 2304 nodes, 5 tiles
+    return wls
+
+
+def run_batch(wls, steps, shape=None, graph=True, t0=0.0):
+    b = P.Batch.from_workloads(wls, M_max=3)
+    if shape:
+        b.set_shape(*shape)
+    b.set_graph(graph)
+    y = b.new_state()
+    b.init_state(y, -75.0)
+    w0 = wls[0]
+    t = t0
+    for _ in range(steps):
+        b.sweep(y, t, w0.dt, w0.M, w0.K)
+        t += w0.dt
+    rc, r, ym = b.residual()
+    assert rc == 0, P.esdc.ERRORS.get(rc)
+    torch.cuda.synchronize()
+    out = [b.tissue(y, k).cpu().numpy().copy() for k in range(len(wls))]
+    graph_used = (b.graph_active(), b.graph_error())
+    b.close()
+    return out, r, graph_used
+
+
+def test_batch_matches_oracle_per_tissue():
+    wls = small_batch()
+    steps = 8
+    got, res, _ = run_batch(wls, steps)
+    for k, w in enumerate(wls):
+        m = O.Monodomain(w)
+        y = m.init_state()
+        t = 0.0
+        for _ in range(steps):
+            y, st, _, _ = m.step(y, t, w.dt, w.M, w.K)
+            t += w.dt
+        err = np.abs(got[k][0] - y[0]).max() / np.abs(y[0]).max()
+        assert err < 1e-12, (k, w.name, err)
+        assert np.abs(got[k][1:] - y[1:]).max() < 1e-12, (k, w.name)
+
+
+def test_batch_bitwise_equals_one_at_a_time():
+    wls = small_batch()
+    steps = 6
+    batched, _, _ = run_batch(wls, steps)
+    for k, w in enumerate(wls):
+        alone, _, _ = run_batch([w], steps)
+        assert np.array_equal(batched[k], alone[0]), (k, w.name)
+
+
+@pytest.mark.parametrize("shape", [(1, 512, 1), (2, 256, 2), (4, 256, 1)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_results_independent_of_launch_shape_and_graph(shape, graph):
+    wls = small_batch()
+    ref, _, _ = run_batch(wls, 4)
+    got, _, used = run_batch(wls, 4, shape=shape, graph=graph)
+    for k in range(len(wls)):
+        assert np.array_equal(ref[k], got[k]), (shape, graph, k)
+    if not graph:
+        assert not used[0]
+    else:
+        assert used[0], "the step was not recorded in a CUDA graph: " + used[1]
+
+
+def test_batch_matches_single_tissue_solver():
+    """Against esdc_sweep on each tissue (a different CG reduction order, so the
+    agreement is to the CG tolerance rather than bitwise)."""
+    wls = small_batch()
+    steps = 5
+    got, _, _ = run_batch(wls, steps)
+    for k, w in enumerate(wls):
+        s = P.Solver.from_workload(w, M_max=3)
+        y = s.new_state()
+        s.init_state(y, w.V0)
+        t = 0.0
+        for _ in range(steps):
+            s.sweep(y, t, w.dt, w.M, w.K)
+            t += w.dt
+        assert s.residual()[0] == 0
+        torch.cuda.synchronize()
+        ys = y[:, :w.n_nodes].cpu().numpy()
+        assert np.abs(got[k] - ys).max() < 1e-11 * max(1.0, np.abs(ys).max()), k
+        s.close()
+
+
+def test_batch_per_tissue_start_times_and_stimulus_windows():
+    """Tissues at different t_n: a tissue whose window has passed is not stimulated."""
+    wls = small_batch()[:3]
+    b = P.Batch.from_workloads(wls, M_max=3)
+    y = b.new_state()
+    b.init_state(y, -75.0)
+    w0 = wls[0]
+    tv = np.array([0.0, 5.0, 0.5])
+    for _ in range(4):
+        b.sweep(y, tv, w0.dt, w0.M, w0.K)
+        tv = tv + w0.dt
+    assert b.residual()[0] == 0
+    torch.cuda.synchronize()
+    for k, w in enumerate(wls):
+        m = O.Monodomain(w)
+        yo = m.init_state()
+        t = [0.0, 5.0, 0.5][k]
+        for _ in range(4):
+            yo, _, _, _ = m.step(yo, t, w.dt, w.M, w.K)
+            t += w.dt
+        got = b.tissue(y, k).cpu().numpy()
+        assert np.abs(got[0] - yo[0]).max() < 1e-12 * np.abs(yo[0]).max(), k
+    b.close()
+
+
+def test_batch_tuner_keeps_results():
+    wls = small_batch()
+    ref, _, _ = run_batch(wls, 3)
+    b = P.Batch.from_workloads(wls, M_max=3)
+    scratch = b.new_state()
+    w0 = wls[0]
+    b.tune(scratch, -75.0, 0.0, w0.dt, w0.M, w0.K, reps=1)
+    waves, threads, blocks = b.shape()
+    assert waves in (1, 2, 4) and threads in (256, 512) and blocks >= 1
+    y = b.new_state()
+    b.init_state(y, -75.0)
+    t = 0.0
+    for _ in range(3):
+        b.sweep(y, t, w0.dt, w0.M, w0.K)
+        t += w0.dt
+    assert b.residual()[0] == 0
+    torch.cuda.synchronize()
+    for k in range(len(wls)):
+        assert np.array_equal(b.tissue(y, k).cpu().numpy(), ref[k]), k
+    b.close()
+
+
+def test_batch_cg_maxit_reported_per_batch():
+    wls = small_batch()[:2]
+    b = P.Batch.from_workloads(wls, M_max=3, cg_maxit=1)
+    y = b.new_state()
+    b.init_state(y, -75.0)
+    w0 = wls[0]
+    b.sweep(y, 0.0, w0.dt, w0.M, w0.K)
+    rc, _, _ = b.residual()
+    assert rc == -3
+    it = b.stats(w0.K, w0.M)
+    assert it.max() <= 1
+    b.close()
