@@ -594,6 +594,8 @@ def run_batch_form(args):
         cpu = {"value": done / cel, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
                "sample": "2 steps from rest of each of the first 4 tissues of the batch"}
     launches_per_step = 1 + K * (M + 1) + K * M + 1
+    # ---- Batch B: P = 16 time slices x M = 3 of one 512 x 512 tissue under Q^par
+    qb = run_qpar_batch(args, P, I, torch, timed)
     line = {
         "metric": METRIC, "value": nodes * steps / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_b / steps, "higher_is_better": True, "scaling": "weak",
@@ -618,9 +620,60 @@ def run_batch_form(args):
                 "h2d_bytes_per_step": int(yb.numel() * 8), "d2h_bytes_per_step": int(yb.numel() * 8)},
         "gpu_launches": launches_per_step * steps,
         "clocks": clk,
+        "qpar_batch_b": qb,
     }
     b.close()
     print(json.dumps(line), flush=True)
+
+
+def run_qpar_batch(args, P, I, torch, timed):
+    """Batch B: one 2D 512 x 512 Hodgkin-Huxley tissue (h = 0.25 mm, corner
+    stimulus), P = 16 consecutive steps as time slices, M = 3, 4 Q^par
+    iterations per solve (eq. def_Q), batched against looping the slices one at a
+    time (same kernels: identical results)."""
+    w = I.hh_sheet_32().with_mesh(512, 512, 1, name="hh_sheet_512")
+    Pn, M, iters, dt = 16, w.M, 4, w.dt
+    reps = 5
+    b = P.Batch.from_workloads([w] * Pn, M_max=M)
+    yin, yout = b.new_state(), b.new_state()
+    y0 = b.new_state()
+    b.init_state(y0, w.V0)
+
+    def solve_b(k):
+        yin.copy_(y0)
+        b.qpar(yin, yout, 0.0, dt, M, iters)
+    for k in range(max(2, args.warmup)):
+        solve_b(k)
+    ms_b = timed(solve_b, reps)
+    if b.residual()[0] != 0:
+        raise RuntimeError("Q^par batch failed")
+    graph = b.graph_active()
+    singles = [P.Batch.from_workloads([w], M_max=M) for _ in range(Pn)]
+    yi = [s.new_state() for s in singles]
+    yo = [s.new_state() for s in singles]
+    y0s = b.tissue(y0, 0).clone()
+
+    def solve_1(k):
+        ends = None
+        for it in range(iters):
+            for p, s in enumerate(singles):
+                s.tissue(yi[p], 0).copy_(y0s if (p == 0 or ends is None) else ends[p - 1])
+                s.sweep_from(yi[p], yo[p], p * dt, dt, M, 1, from_iterate=it > 0)
+            ends = [s.tissue(yo[p], 0) for p, s in enumerate(singles)]
+            ends = [e.clone() for e in ends]
+    for k in range(max(2, args.warmup)):
+        solve_1(k)
+    ms_1 = timed(solve_1, reps)
+    identical = all(torch.equal(b.tissue(yout, p), singles[p].tissue(yo[p], 0)) for p in range(Pn))
+    for s in singles:
+        s.close()
+    b.close()
+    nodes = Pn * w.n_nodes
+    return {"workload": "hh_sheet_512 (512x512 HH, corner stimulus), P=16 slices x M=3, 4 Q^par iterations",
+            "ms_per_solve": ms_b / reps, "node_updates_per_s": nodes / (ms_b / reps * 1e-3),
+            "slice_sweeps_per_s": Pn * iters / (ms_b / reps * 1e-3), "graph": graph,
+            "looped_slices": {"ms_per_solve": ms_1 / reps, "identical_to_batched": bool(identical)},
+            "speedup_vs_looped_slices": ms_1 / ms_b}
 
 
 def main():

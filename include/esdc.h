@@ -332,6 +332,28 @@ int esdc_batch_init_state(esdc_batch* b, double* y, double V0, void* stream);
  * launches if the driver cannot record them).  Errors: INVALID_ARG, CUDA. */
 int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M, int K, void* stream);
 
+/* As esdc_batch_sweep with a separate output: y_n from y_in, y_{n+1} of every
+ * tissue to y_out (both device [n_state][ld]; they may be the same array).
+ * from_iterate != 0 starts the sweeps not from y^0 = 1 (x) y_n but from the
+ * collocation iterate y_{n,1..M} that the previous call (same M) left in the
+ * batch, with y_{n,0} = y_n now taken from y_in: G and f_I are evaluated on
+ * that iterate with Lambda_n = Lambda(y_n).  This is one Q^par sweep
+ * (eq. def_Q): the paper's parallel preconditioner applies the single-step
+ * sweep to every time slice at once.  Errors: INVALID_ARG, CUDA. */
+int esdc_batch_sweep_from(esdc_batch* b, const double* y_in, double* y_out, const double* t, double dt, int M, int K,
+                          int from_iterate, void* stream);
+
+/* `iters` iterations of Q^par (eq. prec_picard_seq with Q = Q^par, eq. def_Q)
+ * over P = n consecutive time steps, the tissues of the batch being the time
+ * slices (they must share mesh and conductivity).  On entry slice 0 of y_in
+ * holds y0 at time t0; slice p covers [t0 + p dt, t0 + (p+1) dt].  The first
+ * iteration starts every slice from z^0 = 1 (x) y0; iteration k+1 runs one
+ * sweep in every slice from its iterate with y_{p,0} = y_{p-1,M} of iteration
+ * k (y_{0,0} = y0).  On return y_out slice p holds y_{p,M}; y_in slices 1..P-1
+ * are overwritten (y_{p,0} of a next iteration).  Stream-ordered.
+ * Errors: INVALID_ARG, CUDA. */
+int esdc_batch_qpar(esdc_batch* b, double* y_in, double* y_out, double t0, double dt, int M, int iters, void* stream);
+
 /* Per tissue (host [n], optional): max |r| of the collocation residual and
  * max |y| of the last step.  Synchronises that step's stream.  Returns
  * NONFINITE, CG_NOT_CONVERGED or DEVICE_TIMEOUT if any tissue raised it. */

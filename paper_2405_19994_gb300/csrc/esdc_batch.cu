@@ -60,6 +60,17 @@ __global__ void k_init_b(int64_t n, int64_t ld, ModelDev mp, double V0, double* 
     }
 }
 
+// Set-up from the iterate in Y (Q^par iterations after the first).
+template <class Model, int M>
+__global__ void __launch_bounds__(128) k_setup_iter(StepArgs a)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
+        BatchNode n;
+        if (!batch_node(a, p, n)) continue;
+        setup_iter_body<Model, M>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+    }
+}
+
 // Per-tissue residual maxima.  Warp w walks a contiguous range of 32-node
 // groups (a group never spans two tiles); running maxima are flushed to the
 // tissue's slots when the tissue changes.
@@ -440,14 +451,19 @@ struct esdc_batch {
     unsigned long long* rmax = nullptr;    // [ntis][2 NS]
     // launch shapes (esdc_batch_tune)
     int node_waves = 1, cg_threads = 512, cg_blocks = 0;
-    int occ_node[ESDC_MMAX + 1] = {0}, occ_setup[ESDC_MMAX + 1] = {0}, occ_res[ESDC_MMAX + 1] = {0};
+    int occ_node[ESDC_MMAX + 1] = {0}, occ_setup[ESDC_MMAX + 1] = {0}, occ_res[ESDC_MMAX + 1] = {0},
+        occ_iter[ESDC_MMAX + 1] = {0};
     // graph of one step
     bool use_graph = true, graph_failed = false;
     cudaStream_t cap_stream = nullptr;     // private stream the step is recorded on
-    cudaGraphExec_t gexec = nullptr;
-    const double* g_y = nullptr;
-    int g_M = 0, g_K = 0;
-    double g_dt = 0.0;
+    struct Graph {                         // one per set-up kind (from y_n / from the iterate)
+        cudaGraphExec_t exec = nullptr;
+        const double* yin = nullptr;
+        double* yout = nullptr;
+        int M = 0, K = 0;
+        double dt = 0.0;
+    } graphs[2];
+    bool last_graph = false;
     char graph_err[128] = {0};
     // last step
     int last_M = 0, last_K = 0;
@@ -465,7 +481,8 @@ int set_berr(esdc_batch* b, int code, const char* msg)
 
 void free_batch(esdc_batch* b)
 {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto& g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     void* ptrs[] = {b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
                     b->rhs, b->Vprev, b->r, b->p, b->q, b->z, b->part, b->bar, b->done_at, b->status,
@@ -546,10 +563,15 @@ void batch_prime(esdc_batch* b)
     b->occ_node[M] = occupancy(k_node<Model, M, false, true>, 128);
     b->occ_setup[M] = occupancy(k_setup<Model, M, false, true>, 128);
     b->occ_res[M] = occupancy(k_residual_b<Model, M>, 128);
+    b->occ_iter[M] = occupancy(k_setup_iter<Model, M>, 128);
 }
 
+// One step of every tissue: y_{n+1} of tissue b to yout (may alias yin).
+// from_iter: start from the iterate left in Y by the previous step with the new
+// y_n in yin (a Q^par iteration); otherwise from y^0 = 1 (x) y_n.
 template <class Model, int M>
-cudaError_t batch_step(esdc_batch* b, double* y, double dt, int K, cudaStream_t s)
+cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from_iter, double dt, int K,
+                       cudaStream_t s)
 {
     const int T = 128;
     batch_prime<Model, M>(b);
@@ -567,7 +589,7 @@ cudaError_t batch_step(esdc_batch* b, double* y, double dt, int K, cudaStream_t 
     for (int i = 0; i < M; ++i)
         for (int j = 0; j < M; ++j) a.dS0[i][j] = dt * C->S0[i][j];
     for (int i = 0; i <= M; ++i) a.dtd[i] = dt * C->d[i];
-    a.yn = y;
+    a.yn = yin;
     a.Y = b->Y; a.FI = b->FI; a.S = b->S; a.PHI = b->PHI; a.LAMN = b->LAMN; a.rhs = b->rhs;
     a.R = nullptr;
     a.rmax = nullptr;
@@ -582,7 +604,8 @@ cudaError_t batch_step(esdc_batch* b, double* y, double dt, int K, cudaStream_t 
         return e;
     a.Gnew = b->G0;
     a.Gold = b->G0;
-    k_setup<Model, M, false, true><<<grid_nodes(b, b->occ_setup[M], b->node_waves), T, 0, s>>>(a);
+    if (from_iter) k_setup_iter<Model, M><<<grid_nodes(b, b->occ_iter[M], b->node_waves), T, 0, s>>>(a);
+    else k_setup<Model, M, false, true><<<grid_nodes(b, b->occ_setup[M], b->node_waves), T, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     double* Gold = b->G0;
     double* Gnew = b->G1;
@@ -593,7 +616,7 @@ cudaError_t batch_step(esdc_batch* b, double* y, double dt, int K, cudaStream_t 
         for (int i = 1; i <= M + 1; ++i) {
             a.i = i;
             a.k = k;
-            a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
+            a.rho = (i >= 2 && i <= M) ? (k == 0 && !from_iter ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
             k_node<Model, M, false, true><<<nb_node, T, 0, s>>>(a);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (i <= M) {
@@ -606,23 +629,24 @@ cudaError_t batch_step(esdc_batch* b, double* y, double dt, int K, cudaStream_t 
         std::swap(Gold, Gnew);
     }
     a.Gold = Gold;
-    a.yout = y;
+    a.yout = yout;
     k_residual_b<Model, M><<<grid_nodes(b, b->occ_res[M], b->node_waves), T, 0, s>>>(a, b->rmax);
     return cudaGetLastError();
 }
 
 template <class Model>
-cudaError_t batch_step_M(esdc_batch* b, double* y, double dt, int M, int K, cudaStream_t s)
+cudaError_t batch_step_M(esdc_batch* b, const double* yin, double* yout, bool fi, double dt, int M, int K,
+                         cudaStream_t s)
 {
     switch (M) {
-        case 1: return batch_step<Model, 1>(b, y, dt, K, s);
-        case 2: return batch_step<Model, 2>(b, y, dt, K, s);
-        case 3: return batch_step<Model, 3>(b, y, dt, K, s);
-        case 4: return batch_step<Model, 4>(b, y, dt, K, s);
-        case 5: return batch_step<Model, 5>(b, y, dt, K, s);
-        case 6: return batch_step<Model, 6>(b, y, dt, K, s);
-        case 7: return batch_step<Model, 7>(b, y, dt, K, s);
-        case 8: return batch_step<Model, 8>(b, y, dt, K, s);
+        case 1: return batch_step<Model, 1>(b, yin, yout, fi, dt, K, s);
+        case 2: return batch_step<Model, 2>(b, yin, yout, fi, dt, K, s);
+        case 3: return batch_step<Model, 3>(b, yin, yout, fi, dt, K, s);
+        case 4: return batch_step<Model, 4>(b, yin, yout, fi, dt, K, s);
+        case 5: return batch_step<Model, 5>(b, yin, yout, fi, dt, K, s);
+        case 6: return batch_step<Model, 6>(b, yin, yout, fi, dt, K, s);
+        case 7: return batch_step<Model, 7>(b, yin, yout, fi, dt, K, s);
+        case 8: return batch_step<Model, 8>(b, yin, yout, fi, dt, K, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -643,26 +667,31 @@ void batch_prime_M(esdc_batch* b, int M)
     }
 }
 
-cudaError_t batch_launch(esdc_batch* b, double* y, double dt, int M, int K, cudaStream_t s)
+cudaError_t batch_launch(esdc_batch* b, const double* yin, double* yout, bool fi, double dt, int M, int K,
+                         cudaStream_t s)
 {
-    return b->model == ESDC_MODEL_HH1952 ? batch_step_M<esdc::HH1952>(b, y, dt, M, K, s)
-                                         : batch_step_M<esdc::SYN19>(b, y, dt, M, K, s);
+    return b->model == ESDC_MODEL_HH1952 ? batch_step_M<esdc::HH1952>(b, yin, yout, fi, dt, M, K, s)
+                                         : batch_step_M<esdc::SYN19>(b, yin, yout, fi, dt, M, K, s);
 }
 
 void drop_graph(esdc_batch* b)
 {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-    b->g_y = nullptr;
+    for (auto& g : b->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = esdc_batch::Graph{};
+    }
+    b->last_graph = false;
 }
 
 // Records one step in a graph for (y, M, K, dt).  The recording runs on the
 // batch's own stream (the legacy default stream cannot be recorded); the graph
 // is then launched on the caller's stream.  On failure the reason is kept and
 // the batch falls back to direct launches for good (graph_failed).
-bool capture(esdc_batch* b, double* y, double dt, int M, int K)
+bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, double dt, int M, int K)
 {
-    drop_graph(b);
+    esdc_batch::Graph& G = b->graphs[fi ? 1 : 0];
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G = esdc_batch::Graph{};
     if (b->model == ESDC_MODEL_HH1952) batch_prime_M<esdc::HH1952>(b, M);
     else batch_prime_M<esdc::SYN19>(b, M);
     auto fail = [&](const char* what, cudaError_t e) {
@@ -676,20 +705,58 @@ bool capture(esdc_batch* b, double* y, double dt, int M, int K)
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return fail("begin capture", e);
-    const cudaError_t el = batch_launch(b, y, dt, M, K, b->cap_stream);
+    const cudaError_t el = batch_launch(b, yin, yout, fi, dt, M, K, b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (el != cudaSuccess || e != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         return fail("capture", el != cudaSuccess ? el : e);
     }
-    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    e = cudaGraphInstantiate(&G.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        b->gexec = nullptr;
+        G.exec = nullptr;
         return fail("instantiate", e);
     }
-    b->g_y = y; b->g_M = M; b->g_K = K; b->g_dt = dt;
+    G.yin = yin; G.yout = yout; G.M = M; G.K = K; G.dt = dt;
     return true;
+}
+
+// Stimulus windows of every tissue at its collocation times, then the step.
+int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const double* t, double dt, int M, int K,
+               cudaStream_t s)
+{
+    const ColloData& C = b->col[M - 1];
+    for (int k = 0; k < b->ntis; ++k) {
+        if (!std::isfinite(t[k])) return set_berr(b, ESDC_ERR_INVALID_ARG, "non-finite time");
+        const StimDev& st = b->tis_h[k].st;
+        for (int i = 0; i <= M; ++i) {
+            const double tj = t[k] + C.c[i] * dt;
+            unsigned on = 0;
+            for (int q = 0; q < st.nbox; ++q)
+                if (tj >= st.t_on[q] && tj < st.t_off[q]) on |= 1u << q;
+            b->on_h[(size_t)k * (ESDC_MMAX + 1) + i] = on;
+        }
+    }
+    // pageable source: the copy has left on_h when the call returns
+    if (cudaMemcpyAsync(b->tis_on, b->on_h.data(), sizeof(unsigned) * b->on_h.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return set_berr(b, ESDC_ERR_CUDA, "stimulus window upload failed");
+    b->last_M = M; b->last_K = K; b->last_stream = s;
+    b->last_graph = false;
+    if (b->use_graph && !b->graph_failed) {
+        const esdc_batch::Graph& G = b->graphs[fi ? 1 : 0];
+        if (!(G.exec && G.yin == yin && G.yout == yout && G.M == M && G.K == K && G.dt == dt)) {
+            if (!capture(b, yin, yout, fi, dt, M, K)) b->graph_failed = true;
+        }
+        if (b->graphs[fi ? 1 : 0].exec && !b->graph_failed) {
+            if (cudaGraphLaunch(b->graphs[fi ? 1 : 0].exec, s) != cudaSuccess)
+                return set_berr(b, ESDC_ERR_CUDA, "graph launch failed");
+            b->last_graph = true;
+            return ESDC_OK;
+        }
+    }
+    if (batch_launch(b, yin, yout, fi, dt, M, K, s) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "step launch failed");
+    return ESDC_OK;
 }
 
 }  // namespace
@@ -860,34 +927,47 @@ int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M
     if (!y || !t) return set_berr(b, ESDC_ERR_INVALID_ARG, "null state or time array");
     if (M < 1 || M > b->opt.M_max || K < 1 || K > 64) return set_berr(b, ESDC_ERR_INVALID_ARG, "M or K out of range");
     if (!(dt > 0.0) || !std::isfinite(dt)) return set_berr(b, ESDC_ERR_INVALID_ARG, "dt must be positive");
+    return sweep_impl(b, y, y, false, t, dt, M, K, (cudaStream_t)stream);
+}
+
+int esdc_batch_sweep_from(esdc_batch* b, const double* y_in, double* y_out, const double* t, double dt, int M, int K,
+                          int from_iterate, void* stream)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (!y_in || !y_out || !t) return set_berr(b, ESDC_ERR_INVALID_ARG, "null state or time array");
+    if (M < 1 || M > b->opt.M_max || K < 1 || K > 64) return set_berr(b, ESDC_ERR_INVALID_ARG, "M or K out of range");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_berr(b, ESDC_ERR_INVALID_ARG, "dt must be positive");
+    if (from_iterate && b->last_M != M) return set_berr(b, ESDC_ERR_INVALID_ARG, "no iterate of this M to start from");
+    return sweep_impl(b, y_in, y_out, from_iterate != 0, t, dt, M, K, (cudaStream_t)stream);
+}
+
+int esdc_batch_qpar(esdc_batch* b, double* y_in, double* y_out, double t0, double dt, int M, int iters, void* stream)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (!y_in || !y_out || y_in == y_out || iters < 1) return set_berr(b, ESDC_ERR_INVALID_ARG, "bad Q^par arguments");
+    const TissueDev& T0 = b->tis_h[0];
+    for (const TissueDev& T : b->tis_h)
+        if (T.nx != T0.nx || T.ny != T0.ny || T.nz != T0.nz || T.D != T0.D || T.ih2 != T0.ih2)
+            return set_berr(b, ESDC_ERR_INVALID_ARG, "Q^par slices must share mesh and conductivity");
     cudaStream_t s = (cudaStream_t)stream;
-    const ColloData& C = b->col[M - 1];
-    for (int k = 0; k < b->ntis; ++k) {
-        if (!std::isfinite(t[k])) return set_berr(b, ESDC_ERR_INVALID_ARG, "non-finite time");
-        const StimDev& st = b->tis_h[k].st;
-        for (int i = 0; i <= M; ++i) {
-            const double tj = t[k] + C.c[i] * dt;
-            unsigned on = 0;
-            for (int q = 0; q < st.nbox; ++q)
-                if (tj >= st.t_on[q] && tj < st.t_off[q]) on |= 1u << q;
-            b->on_h[(size_t)k * (ESDC_MMAX + 1) + i] = on;
-        }
+    const int P = b->ntis;
+    const size_t slice = (size_t)T0.ntile * ESDC_TILE;       // columns per slice
+    const size_t pitch = sizeof(double) * b->ld;
+    std::vector<double> t(P);
+    for (int p = 0; p < P; ++p) t[p] = t0 + p * dt;
+    // z^0 = 1 (x) y0 in every slice: y_in[p] = y_in[0]
+    for (int p = 1; p < P; ++p)
+        if (cudaMemcpy2DAsync(y_in + p * slice, pitch, y_in, pitch, sizeof(double) * slice, b->NS,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return set_berr(b, ESDC_ERR_CUDA, "slice copy failed");
+    for (int k = 0; k < iters; ++k) {
+        const int rc = esdc_batch_sweep_from(b, y_in, y_out, t.data(), dt, M, 1, k > 0, stream);
+        if (rc != ESDC_OK) return rc;
+        // y_{p+1,0} <- y_{p,M} for the next iteration (slice 0 keeps y0)
+        if (P > 1 && cudaMemcpy2DAsync(y_in + slice, pitch, y_out, pitch, sizeof(double) * slice * (P - 1), b->NS,
+                                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return set_berr(b, ESDC_ERR_CUDA, "slice shift failed");
     }
-    // pageable source: the copy has left on_h when the call returns
-    if (cudaMemcpyAsync(b->tis_on, b->on_h.data(), sizeof(unsigned) * b->on_h.size(), cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return set_berr(b, ESDC_ERR_CUDA, "stimulus window upload failed");
-    b->last_M = M; b->last_K = K; b->last_stream = s;
-    if (b->use_graph && !b->graph_failed) {
-        if (!(b->gexec && b->g_y == y && b->g_M == M && b->g_K == K && b->g_dt == dt)) {
-            if (!capture(b, y, dt, M, K)) b->graph_failed = true;
-        }
-        if (b->gexec) {
-            if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "graph launch failed");
-            return ESDC_OK;
-        }
-    }
-    if (batch_launch(b, y, dt, M, K, s) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "step launch failed");
     return ESDC_OK;
 }
 
@@ -942,7 +1022,7 @@ int esdc_batch_set_graph(esdc_batch* b, int on)
 
 int esdc_batch_graph_active(const esdc_batch* b)
 {
-    return (b && b->gexec && !b->graph_failed) ? 1 : 0;
+    return (b && b->last_graph) ? 1 : 0;
 }
 
 const char* esdc_batch_graph_error(const esdc_batch* b)

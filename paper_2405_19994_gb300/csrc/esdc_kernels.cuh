@@ -137,12 +137,82 @@ __device__ __forceinline__ bool batch_node(const StepArgs& a, int p, BatchNode& 
     return true;
 }
 
+// Per-step tables of gate g at node p: Lambda_n, dt d_i phi_1(d_i dt Lambda_n)
+// and dt S_ij(dt Lambda_n) (App. A).
+template <int M>
+__device__ __forceinline__ void gate_tables(const StepArgs& a, int g, int NG, double lam, int p)
+{
+    const ColloData& C = c_col[M - 1];
+    const int64_t ld = a.m.ld;
+    const double z = a.dt * lam;
+    a.LAMN[(int64_t)g * ld + p] = lam;
+    double aprev[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) aprev[j] = 0.0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        double ph[M];
+        phi_all<M>(C.c[i + 1] * z, ph);
+        const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
+        a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            double aij = 0.0;
+#pragma unroll
+            for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
+            aij *= a.dt;                                                 // dt a_ij
+            a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
+            aprev[j] = aij;
+        }
+    }
+}
+
+// Set-up from a given iterate (the Q^par iteration of Sec. 3.2): y_{n,0} = y_n
+// is new, y_{n,1..M} are the iterate in Y.  Lambda_n = Lambda(y_n) and the
+// tables as in the plain set-up; G_j = g_n(t_{n,j}, y_j) and FI_j = f_I(y_j) on
+// the iterate (the plain set-up's G^0 with y_j in place of y_n).
+template <class Model, int M>
+__device__ __forceinline__ void setup_iter_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
+                                                const unsigned* on, double D, int p, int ix, int iy, int iz)
+{
+    constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
+    const int64_t ld = a.m.ld;
+    const double vn = a.yn[p];
+#pragma unroll 1
+    for (int g = 0; g < NG; ++g) {
+        double lam, yinf;
+        Model::gate(a.mp.p, g, vn, lam, yinf);
+        gate_tables<M>(a, g, NG, lam, p);
+    }
+#pragma unroll 1
+    for (int j = 0; j < M; ++j) {
+        const double* Yj = a.Y + (int64_t)j * NS * ld;
+        double* Gj = a.Gnew + (int64_t)j * NS * ld;
+        double u[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) u[s] = Yj[s * ld + p];
+        const double fi = D * lap(m, Yj, p, ix, iy, iz);
+        double mI, ha[NA > 0 ? NA : 1];
+        Model::currents(a.mp.p, u, mI, ha);
+        Gj[p] = fi + (stim_at(st, on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
+#pragma unroll
+        for (int s = 1; s <= NA; ++s) Gj[s * ld + p] = ha[s - 1];
+        a.FI[(int64_t)j * ld + p] = fi;
+#pragma unroll 1
+        for (int g = 0; g < NG; ++g) {
+            const int s = 1 + NA + g;
+            double lam, yinf;
+            Model::gate(a.mp.p, g, u[0], lam, yinf);
+            Gj[s * ld + p] = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
+        }
+    }
+}
+
 template <class Model, int M, bool MIXED>
 __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
                                            const unsigned* on, double D, int p, int ix, int iy, int iz)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
-    const ColloData& C = c_col[M - 1];
     const int64_t ld = a.m.ld;
     double u[NS];
 #pragma unroll
@@ -189,27 +259,7 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, 
             a.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
             a.Y[((int64_t)j * NS + s) * ld + p] = us;
         }
-        const double z = a.dt * lam;
-        a.LAMN[(int64_t)g * ld + p] = lam;
-        double aprev[M];
-#pragma unroll
-        for (int j = 0; j < M; ++j) aprev[j] = 0.0;
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-            double ph[M];
-            phi_all<M>(C.c[i + 1] * z, ph);
-            const double p1 = (i == 0) ? ph[0] : phi1(C.d[i + 1] * z);
-            a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
-#pragma unroll
-            for (int j = 0; j < M; ++j) {
-                double aij = 0.0;
-#pragma unroll
-                for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
-                aij *= a.dt;                                                 // dt a_ij
-                a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
-                aprev[j] = aij;
-            }
-        }
+        gate_tables<M>(a, g, NG, lam, p);
     }
 }
 

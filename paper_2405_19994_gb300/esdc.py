@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
             "esdc_batch_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
             "esdc_batch_sweep": (C.c_int, [_VP, _VP, C.POINTER(_D), _D, C.c_int, C.c_int, _VP]),
             "esdc_batch_residual": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D)]),
+            "esdc_batch_sweep_from": (C.c_int, [_VP, _VP, _VP, C.POINTER(_D), _D, C.c_int, C.c_int, C.c_int, _VP]),
+            "esdc_batch_qpar": (C.c_int, [_VP, _VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
             "esdc_batch_stats": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
             "esdc_batch_set_graph": (C.c_int, [_VP, C.c_int]),
             "esdc_batch_graph_active": (C.c_int, [_VP]),
@@ -345,6 +347,15 @@ class Batch:
         tv = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (self.n,)))
         self._check(lib().esdc_batch_sweep(self._b, _ptr(y), tv.ctypes.data_as(C.POINTER(_D)), dt, M, K,
                                            _stream(stream)))
+
+    def sweep_from(self, y_in, y_out, t, dt: float, M: int, K: int, from_iterate: bool, stream=None):
+        tv = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (self.n,)))
+        self._check(lib().esdc_batch_sweep_from(self._b, _ptr(y_in), _ptr(y_out), tv.ctypes.data_as(C.POINTER(_D)),
+                                                dt, M, K, int(from_iterate), _stream(stream)))
+
+    def qpar(self, y_in, y_out, t0: float, dt: float, M: int, iters: int, stream=None):
+        """Q^par iterations over the batch's tissues as time slices (esdc_batch_qpar)."""
+        self._check(lib().esdc_batch_qpar(self._b, _ptr(y_in), _ptr(y_out), t0, dt, M, iters, _stream(stream)))
 
     def residual(self):
         """(return code, res_inf[n], y_inf[n]); does not raise on solver flags."""

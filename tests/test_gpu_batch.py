@@ -170,3 +170,73 @@ def test_batch_cg_maxit_reported_per_batch():
     it = b.stats(w0.K, w0.M)
     assert it.max() <= 1
     b.close()
+
+
+# ---------------------------------------------------------------- Q^par: time slices as the batch
+
+def qpar_setup(P=4, nx=10, ny=8):
+    w = I.hh_sheet_32().with_mesh(nx, ny, 1)
+    m = O.Monodomain(w)
+    y0, t0 = m.init_state(), 0.0
+    for _ in range(16):                               # a state inside the stimulus window, mid-upstroke
+        y0, _, _, _ = m.step(y0, t0, w.dt, w.M, w.K)
+        t0 += w.dt
+    return w, m, y0, t0
+
+
+def test_qpar_matches_oracle():
+    P_, iters = 4, 3
+    w, m, y0, t0 = qpar_setup(P_)
+    b = P.Batch.from_workloads([w] * P_, M_max=w.M)
+    yin, yout = b.new_state(), b.new_state()
+    b.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    b.qpar(yin, yout, t0, w.dt, w.M, iters)
+    assert b.residual()[0] == 0
+    Z = m.qpar(y0, t0, w.dt, P_, w.M, iters)
+    torch.cuda.synchronize()
+    for p in range(P_):
+        got = b.tissue(yout, p).cpu().numpy()
+        want = Z[p, w.M - 1]
+        assert np.abs(got[0] - want[0]).max() < 1e-12 * np.abs(want[0]).max(), p
+        assert np.abs(got[1:] - want[1:]).max() < 1e-12, p
+    b.close()
+
+
+def test_qpar_bitwise_equals_looped_slices():
+    P_, iters = 4, 3
+    w, m, y0, t0 = qpar_setup(P_)
+    b = P.Batch.from_workloads([w] * P_, M_max=w.M)
+    yin, yout = b.new_state(), b.new_state()
+    b.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    b.qpar(yin, yout, t0, w.dt, w.M, iters)
+    assert b.residual()[0] == 0
+    torch.cuda.synchronize()
+    singles = [P.Batch.from_workloads([w], M_max=w.M) for _ in range(P_)]
+    yi = [s.new_state() for s in singles]
+    yo = [s.new_state() for s in singles]
+    y0d = torch.from_numpy(y0).cuda()
+    ends = None
+    for k in range(iters):
+        for p, s in enumerate(singles):
+            src = y0d if (p == 0 or ends is None) else ends[p - 1]
+            s.tissue(yi[p], 0).copy_(src)
+            s.sweep_from(yi[p], yo[p], t0 + p * w.dt, w.dt, w.M, 1, from_iterate=k > 0)
+        ends = [s.tissue(yo[p], 0).clone() for p, s in enumerate(singles)]
+    for p, s in enumerate(singles):
+        assert s.residual()[0] == 0
+        assert torch.equal(b.tissue(yout, p), s.tissue(yo[p], 0)), p
+        s.close()
+    b.close()
+
+
+def test_qpar_one_slice_is_k_sweeps_of_the_step():
+    w, m, y0, t0 = qpar_setup(1)
+    b = P.Batch.from_workloads([w], M_max=w.M)
+    yin, yout = b.new_state(), b.new_state()
+    b.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    b.qpar(yin, yout, t0, w.dt, w.M, w.K)
+    want, _, _, _ = m.step(y0, t0, w.dt, w.M, w.K)
+    assert b.residual()[0] == 0
+    got = b.tissue(yout, 0).cpu().numpy()
+    assert np.abs(got[0] - want[0]).max() < 1e-12 * np.abs(want[0]).max()
+    b.close()
