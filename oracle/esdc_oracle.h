@@ -118,6 +118,9 @@ typedef struct {
      * tensor entries [nz] sigma_xx, sigma_yy, sigma_xy, sigma_zz (in-plane
      * fibres; sigma_xz = sigma_yz = 0). */
     const double *lay_sxx, *lay_syy, *lay_sxy, *lay_szz;
+    /* Heterogeneous isotropic conductivity (NULL: sigma): one value per node,
+     * [N] mS/mm; the flux through a face uses the mean of its two nodes. */
+    const double* sig_node;
     /* private workspace, owned by the oracle */
     void*  work;
 } orc_mono;
@@ -145,14 +148,17 @@ void orc_laplacian(const orc_mono* m, const double* v, double* out);
 /* Solve (I - g L) x = b with L the Laplacian above, by the chosen method. */
 int  orc_solve_shifted(const orc_mono* m, int method, double g, const double* b, double* x);
 /* The conductivity operator A = div(sigma grad) in flux form (conductivity
- * included): sigma L for an isotropic sigma; for layered anisotropic sigma
+ * included): sigma L for an isotropic sigma; for a per-node field
+ *   (A v)_p = (1/h^2) sum_{q in nbr(p)} (sigma_p + sigma_q)/2 (v_q - v_p);
+ * for layered anisotropic sigma
  *   (A v)_p = (1/h^2) [ sum_x-faces sxx (v_q - v_p) + sum_y-faces syy (v_q - v_p)
  *                     + sum_z-faces (szz_k + szz_l)/2 (v_q - v_p)
  *                     + sum_{a,b = +-1} (a b sxy / 2) (v_{i+a,j+b} - v_p) ],
  * with terms of absent neighbours dropped (zero flux through boundary faces). */
 void orc_conductivity(const orc_mono* m, const double* v, double* out);
 /* Solve (I - g A) x = b.  Isotropic sigma: the chosen method on sigma L.
- * Layered sigma: CG or dense (a DCT request falls back to CG). */
+ * Layered sigma or a per-node field: CG or dense (a DCT request falls back
+ * to CG). */
 int  orc_solve_A(const orc_mono* m, int method, double g, const double* b, double* x);
 
 /* ------------------------------------------------------------------ */

@@ -52,7 +52,8 @@ class _Mono(C.Structure):
                 ("t_on", C.c_void_p), ("t_off", C.c_void_p),
                 ("solver", C.c_int), ("cg_tol", C.c_double), ("cg_maxit", C.c_int),
                 ("ionic_off", C.c_int), ("lay_sxx", C.c_void_p), ("lay_syy", C.c_void_p),
-                ("lay_sxy", C.c_void_p), ("lay_szz", C.c_void_p), ("work", C.c_void_p)]
+                ("lay_sxy", C.c_void_p), ("lay_szz", C.c_void_p), ("sig_node", C.c_void_p),
+                ("work", C.c_void_p)]
 
 
 _D = C.POINTER(C.c_double)
@@ -187,10 +188,19 @@ class Monodomain:
             lay = [a.ctypes.data for a in lay_arrs]
             if solver == SOLVE_DCT:
                 solver = SOLVE_CG        # DCT-II does not diagonalise the layered operator
+        field = getattr(wl, "sigma_field", None)
+        fptr = None
+        if field is not None:
+            f = np.ascontiguousarray(field, np.float64).reshape(-1)
+            assert len(f) == wl.n_nodes and layers is None
+            self._keep.append(f)
+            fptr = f.ctypes.data
+            if solver == SOLVE_DCT:
+                solver = SOLVE_CG        # nor a heterogeneous one
         self.m = _Mono(wl.dim, wl.nx, wl.ny, wl.nz, wl.h, wl.sigma, wl.chi, wl.Cm, wl.model,
                        mp.ctypes.data, len(mp), len(amp), box.ctypes.data, amp.ctypes.data,
                        ton.ctypes.data, toff.ctypes.data, solver, cg_tol, cg_maxit, int(ionic_off),
-                       lay[0], lay[1], lay[2], lay[3], None)
+                       lay[0], lay[1], lay[2], lay[3], fptr, None)
         self.P = _Problem()
         if lib().orc_mono_problem(C.byref(self.m), C.byref(self.P)):
             raise ValueError("invalid monodomain description")

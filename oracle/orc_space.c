@@ -51,18 +51,37 @@ void orc_laplacian(const orc_mono* m, const double* v, double* out)
 }
 
 static int is_layered(const orc_mono* m) { return m->lay_sxx != NULL; }
+static int is_field(const orc_mono* m) { return m->sig_node != NULL; }
 
 void orc_conductivity(const orc_mono* m, const double* v, double* out)
 {
     const int nx = m->nx, ny = m->ny, nz = m->nz;
     const int64_t N = mesh_n(m);
+    const double ih2 = 1.0 / (m->h * m->h);
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    if (is_field(m)) {
+        const double* sg = m->sig_node;
+        #pragma omp parallel for schedule(static)
+        for (int iz = 0; iz < nz; ++iz)
+            for (int iy = 0; iy < ny; ++iy)
+                for (int ix = 0; ix < nx; ++ix) {
+                    int64_t p = ix + sy * iy + sz * iz;
+                    double s = 0.0;
+                    if (ix > 0)      s += 0.5 * (sg[p] + sg[p - 1]) * (v[p - 1] - v[p]);
+                    if (ix < nx - 1) s += 0.5 * (sg[p] + sg[p + 1]) * (v[p + 1] - v[p]);
+                    if (iy > 0)      s += 0.5 * (sg[p] + sg[p - sy]) * (v[p - sy] - v[p]);
+                    if (iy < ny - 1) s += 0.5 * (sg[p] + sg[p + sy]) * (v[p + sy] - v[p]);
+                    if (iz > 0)      s += 0.5 * (sg[p] + sg[p - sz]) * (v[p - sz] - v[p]);
+                    if (iz < nz - 1) s += 0.5 * (sg[p] + sg[p + sz]) * (v[p + sz] - v[p]);
+                    out[p] = s * ih2;
+                }
+        return;
+    }
     if (!is_layered(m)) {
         orc_laplacian(m, v, out);
         for (int64_t p = 0; p < N; ++p) out[p] *= m->sigma;
         return;
     }
-    const double ih2 = 1.0 / (m->h * m->h);
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
     #pragma omp parallel for schedule(static)
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
@@ -287,7 +306,7 @@ int orc_solve_shifted(const orc_mono* m, int method, double g, const double* b, 
 
 int orc_solve_A(const orc_mono* m, int method, double g, const double* b, double* x)
 {
-    if (!is_layered(m)) return orc_solve_shifted(m, method, g * m->sigma, b, x);
+    if (!is_layered(m) && !is_field(m)) return orc_solve_shifted(m, method, g * m->sigma, b, x);
     if (method == ORC_SOLVE_DENSE) return solve_dense((orc_mono*)m, 1, g, b, x);
     return solve_cg_op(m, 1, g, b, x);
 }

@@ -89,6 +89,8 @@ class Workload:
     Cm: float = 0.01
     # layered anisotropic conductivity: {"sxx","syy","sxy","szz"} -> [nz] arrays, or None
     layers: dict | None = None
+    # heterogeneous isotropic conductivity: one value per node [N] (mS/mm), or None
+    sigma_field: np.ndarray | None = None
     # stimulus boxes: [x0, x1, y0, y1, z0, z1] node index ranges (half-open)
     boxes: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 6), np.int32))
     amp: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
@@ -122,8 +124,11 @@ class Workload:
         if layers is not None and nz != self.nz:     # same fibre rotation over the new depth
             sl = float(np.max(layers["sxx"] + layers["syy"] - layers["szz"]))
             layers = fibre_layers(nz, sigma_l=sl, sigma_t=float(layers["szz"][0]))
+        field = self.sigma_field
+        if field is not None and (nx, ny, nz) != (self.nx, self.ny, self.nz):
+            field = None                                # a per-node field does not carry over
         return dataclasses.replace(self, name=name or f"{self.name}@{nx}x{ny}x{nz}",
-                                   nx=nx, ny=ny, nz=nz, dim=dim, boxes=b, layers=layers)
+                                   nx=nx, ny=ny, nz=nz, dim=dim, boxes=b, layers=layers, sigma_field=field)
 
 
 def fibre_layers(nz: int, sigma_l: float = 0.17, sigma_t: float = 0.02,
@@ -202,3 +207,30 @@ def hh_batch(n: int = 64, seed: int = 4, side: tuple = (64, 512), sigma: tuple =
                             sigma=sg, boxes=np.array([[x0, x0 + px, y0, y0 + py, 0, 1]], np.int32),
                             amp=np.array([0.5]), t_on=np.array([0.0]), t_off=np.array([1.0])))
     return out
+
+
+def lognormal_field(nx: int, ny: int, nz: int = 1, seed: int = 5, sigma0: float = 0.17, amp: float = 0.3,
+                    corr: float = 8.0) -> np.ndarray:
+    """A smooth log-normal conductivity field sigma0 exp(amp g) [nz*ny*nx],
+    g a seeded Gaussian random field of unit variance with Gaussian covariance
+    of correlation length `corr` nodes (white noise filtered in Fourier space)."""
+    rng = np.random.default_rng(seed)
+    w = rng.normal(size=(nz, ny, nx))
+    k = [np.fft.fftfreq(n) for n in (nz, ny, nx)]
+    kz, ky, kx = np.meshgrid(*k, indexing="ij")
+    filt = np.exp(-0.5 * (2 * np.pi * corr) ** 2 * (kx ** 2 + ky ** 2 + (kz ** 2 if nz > 1 else 0.0)) / 2)
+    g = np.real(np.fft.ifftn(np.fft.fftn(w) * filt))
+    g = (g - g.mean()) / max(g.std(), 1e-300)
+    return (sigma0 * np.exp(amp * g)).reshape(-1)
+
+
+def hh_field_sheet(n: int = 256, seed: int = 5) -> Workload:
+    """The differentiation-form tissue: 2D n x n, h = 0.25 mm, Hodgkin-Huxley,
+    conductivity 0.17 exp(0.3 g) mS/mm with g a smooth seeded Gaussian field,
+    corner stimulus (4x4 nodes, 0.5 uA/mm^2, [0, 1) ms), M = 3, K = 4,
+    dt = 0.025 ms, T = 20 ms."""
+    return Workload(name=f"hh_field_sheet_{n}", dim=2, nx=n, ny=n, nz=1, h=0.25,
+                    model=MODEL_HH1952, params=hh1952_params(), V0=-75.0, M=3, K=4, dt=0.025, T=20.0,
+                    sigma_field=lognormal_field(n, n, 1, seed=seed),
+                    boxes=np.array([[0, 4, 0, 4, 0, 1]], np.int32),
+                    amp=np.array([0.5]), t_on=np.array([0.0]), t_off=np.array([1.0]))

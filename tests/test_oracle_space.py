@@ -142,3 +142,74 @@ def test_aniso_second_order_consistency(orc):
         inner = ((ix > 0) & (ix < n - 1) & (iy > 0) & (iy < n - 1) & (iz == 1)).transpose(2, 1, 0).reshape(-1)
         errs.append(np.abs(m.conductivity(f) - want)[inner].max())
     assert 3.3 < errs[0] / errs[1] < 4.8, errs
+
+
+# ---------------------------------------------------------------- per-node conductivity field
+
+def _field(nx, ny, nz, h=0.3, field=None, seed=0):
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.h = h
+    wl.sigma_field = (I.lognormal_field(nx, ny, nz, seed=seed, corr=2.0) if field is None
+                      else np.asarray(field, np.float64))
+    return wl, O.Monodomain(wl, solver=O.SOLVE_CG)
+
+
+def test_field_constant_is_scalar_sigma(orc):
+    nx, ny, nz = 7, 6, 3
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    iso = O.Monodomain(wl)
+    _, fm = _field(nx, ny, nz, h=wl.h, field=np.full(nx * ny * nz, 0.23))
+    v = np.random.default_rng(5).normal(size=nx * ny * nz)
+    np.testing.assert_allclose(fm.conductivity(v), 0.23 * iso.laplacian(v), rtol=0, atol=1e-12)
+
+
+def test_field_operator_symmetric_nsd_constant_nullspace(orc):
+    nx, ny, nz = 6, 5, 3
+    wl, m = _field(nx, ny, nz, h=0.5, seed=2)
+    N = nx * ny * nz
+    A = np.stack([m.conductivity(e) for e in np.eye(N)], axis=1)
+    np.testing.assert_allclose(A, A.T, atol=1e-14)
+    ev = np.linalg.eigvalsh(A)
+    assert ev.max() < 1e-12 and ev[-2] < -1e-4
+    np.testing.assert_allclose(A @ np.ones(N), 0.0, atol=1e-13)
+    # brute force: sum over the faces of the quadratic form, face sigma = mean of its two nodes
+    v = np.random.default_rng(6).normal(size=N)
+    s = wl.sigma_field
+    q = 0.0
+    for p in range(N):
+        ix, iy, iz = p % nx, (p // nx) % ny, p // (nx * ny)
+        for d, ok in ((1, ix < nx - 1), (nx, iy < ny - 1), (nx * ny, iz < nz - 1)):
+            if ok:
+                q -= 0.5 * (s[p] + s[p + d]) * (v[p + d] - v[p]) ** 2
+    assert abs(v @ A @ v - q / 0.25) < 1e-10 * abs(q)
+
+
+def test_field_second_order_consistency(orc):
+    # div(sigma grad f) for smooth sigma and f, interior nodes: error falls ~4x per halving of h
+    errs = []
+    for n, h in ((16, 0.2), (32, 0.1)):
+        ix, iy = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+        x = (ix + 0.5) * h
+        y = (iy + 0.5) * h
+        sig = 0.1 + 0.05 * np.sin(0.9 * x) * np.cos(0.6 * y)
+        f = np.cos(1.1 * x) * np.sin(0.8 * y)
+        wl, m = _field(n, n, 1, h=h, field=sig.reshape(-1))
+        sx = 0.05 * 0.9 * np.cos(0.9 * x) * np.cos(0.6 * y)
+        sy = -0.05 * 0.6 * np.sin(0.9 * x) * np.sin(0.6 * y)
+        fx = -1.1 * np.sin(1.1 * x) * np.sin(0.8 * y)
+        fy = 0.8 * np.cos(1.1 * x) * np.cos(0.8 * y)
+        lapf = -(1.21 + 0.64) * f
+        want = sig * lapf + sx * fx + sy * fy
+        got = m.conductivity(f.reshape(-1)).reshape(n, n)
+        errs.append(np.abs(got - want)[1:-1, 1:-1].max())
+    assert 3.3 < errs[0] / errs[1] < 4.8, errs
+
+
+def test_field_solves_agree(orc):
+    wl, m = _field(8, 7, 2, seed=3)
+    b = np.random.default_rng(4).normal(size=8 * 7 * 2)
+    g = 0.03
+    x_cg = m.solve_A(g, b, method=O.SOLVE_CG)
+    x_de = m.solve_A(g, b, method=O.SOLVE_DENSE)
+    np.testing.assert_allclose(x_cg, x_de, atol=1e-13)
+    assert np.abs(x_cg - g * m.conductivity(x_cg) - b).max() < 1e-13
