@@ -131,6 +131,17 @@ int esdc_set_stimulus(esdc_handle* h, int nbox, const int* box, const double* am
  * return to the scalar sigma.  Synchronises the device.
  * Errors: INVALID_ARG, NO_MEMORY, CUDA.
  */
+/*
+ * Heterogeneous isotropic conductivity: sigma[p] (host array of N values,
+ * mS/mm, copied, all positive) at every mesh node.  Replaces the scalar sigma
+ * (and any layers) in f_I and in the diffusion solves:
+ *   (A v)_p = (1/h^2) sum_{q in nbr(p)} (sigma_p + sigma_q)/2 (v_q - v_p),
+ * zero flux through boundary faces.  sigma = NULL returns to the scalar sigma.
+ * FP64 path only (options.precision = 0).  Synchronises the device.
+ * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
+ */
+int esdc_set_conductivity_field(esdc_handle* h, const double* sigma);
+
 int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double* syy,
                                  const double* sxy, const double* szz);
 

@@ -64,10 +64,25 @@ __device__ __forceinline__ float layered_A_f(const MeshDev& m, const float* v, i
     return fmaf(cd, c, s);
 }
 
+// Heterogeneous operator (A v)_p, face conductivity (sigma_p + sigma_q)/2.
+__device__ __forceinline__ double field_A(const MeshDev& m, const double* v, int p, NodeIdx n, double vp)
+{
+    const int sxy = m.nx * m.ny;
+    const double sp = __ldg(m.sig + p);
+    double s = 0.0;
+    if (n.ix > 0)        s = fma(sp + __ldg(m.sig + p - 1), __ldcg(v + p - 1) - vp, s);
+    if (n.ix < m.nx - 1) s = fma(sp + __ldg(m.sig + p + 1), __ldcg(v + p + 1) - vp, s);
+    if (n.iy > 0)        s = fma(sp + __ldg(m.sig + p - m.nx), __ldcg(v + p - m.nx) - vp, s);
+    if (n.iy < m.ny - 1) s = fma(sp + __ldg(m.sig + p + m.nx), __ldcg(v + p + m.nx) - vp, s);
+    if (n.iz > 0)        s = fma(sp + __ldg(m.sig + p - sxy), __ldcg(v + p - sxy) - vp, s);
+    if (n.iz < m.nz - 1) s = fma(sp + __ldg(m.sig + p + sxy), __ldcg(v + p + sxy) - vp, s);
+    return 0.5 * m.ih2 * s;
+}
+
 // Jacobi factor 1/diag(I - g A) at node p with c in-domain face neighbours.
 __device__ __forceinline__ double jacobi(const MeshDev& m, const double* dinv, int p, int c, double g)
 {
-    if (m.lay) return esdc::esdc_rcp(fma(g, __ldg(m.wdiag + p), 1.0));
+    if (m.lay || m.sig) return esdc::esdc_rcp(fma(g, __ldg(m.wdiag + p), 1.0));
     return dinv[c];
 }
 
@@ -78,6 +93,10 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
     if (m.lay) {                       // layered conductivity: gih2 carries g only
         *nnb = 0;
         return fma(-gih2, layered_A(m, v, p, n, vp), vp);
+    }
+    if (m.sig) {                       // conductivity field: likewise
+        *nnb = 0;
+        return fma(-gih2, field_A(m, v, p, n, vp), vp);
     }
     const int sxy = m.nx * m.ny;
     double s = 0.0;
@@ -133,7 +152,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     double* part = a.part;
-    const double gih2 = m.lay ? a.g : a.g * m.ih2;     // layered coefficients carry 1/h^2
+    const double gih2 = (m.lay || m.sig) ? a.g : a.g * m.ih2;     // layered coefficients carry 1/h^2
     __shared__ double bs[3];
     unsigned target = 0;
 
@@ -275,7 +294,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg_mixed(CgArgs a, CgMixArg
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     double* part = a.part;
-    const double gih2 = m.lay ? a.g : a.g * m.ih2;     // layered coefficients carry 1/h^2
+    const double gih2 = (m.lay || m.sig) ? a.g : a.g * m.ih2;     // layered coefficients carry 1/h^2
     const float gih2f = (float)gih2;
     __shared__ double bs[3];
     unsigned target = 0;

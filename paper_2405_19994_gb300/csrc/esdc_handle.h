@@ -48,6 +48,7 @@ struct esdc_handle {
     ModelDevF mpf{};
     double sigma = 0, chi = 0, Cm = 0, D = 0;
     double *lay = nullptr, *wdiag = nullptr;   // layered conductivity (see MeshDev)
+    double* sigf = nullptr;                    // conductivity field (see MeshDev)
     float* layf = nullptr;
     esdc_options opt{};
     // workspace

@@ -49,8 +49,11 @@ struct MeshDev {
     // lay[0..nz) sxx/h^2, [nz..2nz) syy/h^2, [2nz..3nz) sxy/(2h^2),
     // [3nz..4nz) face sigma_zz/h^2 between layers k and k+1.
     const double* lay = nullptr;
-    const double* wdiag = nullptr;   // [N] -diag(A) (Jacobi weights), layered case
+    const double* wdiag = nullptr;   // [N] -diag(A) (Jacobi weights), layered or field case
     const float* layf = nullptr;     // FP32 copy of lay (precision form)
+    // Heterogeneous isotropic conductivity (nullptr: scalar sigma): sigma per
+    // node [N] (mS/mm); a face carries the mean of its two nodes.
+    const double* sig = nullptr;
 };
 
 struct StimDev {

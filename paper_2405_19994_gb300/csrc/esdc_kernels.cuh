@@ -26,12 +26,24 @@ __device__ __forceinline__ void node_xyz(const MeshDev& m, int p, int& ix, int& 
 
 // L v at node p: (1/h^2) sum over in-domain neighbours of (v_q - v_p); with a
 // layered conductivity, A v (the coefficients then include sigma and 1/h^2,
-// and the in-plane diagonal neighbours carry the sigma_xy cross term).
+// and the in-plane diagonal neighbours carry the sigma_xy cross term); with a
+// per-node conductivity field, A v with face conductivities (sigma_p + sigma_q)/2.
 __device__ __forceinline__ double lap(const MeshDev& m, const double* __restrict__ v, int p,
                                       int ix, int iy, int iz)
 {
     const double vp = v[p];
     const int sxy = m.nx * m.ny;
+    if (m.sig) {                       // (A v)_p = (1/h^2) sum_q (sigma_p + sigma_q)/2 (v_q - v_p)
+        const double sp = __ldg(m.sig + p);
+        double s = 0.0;
+        if (ix > 0)        s = fma(sp + __ldg(m.sig + p - 1), v[p - 1] - vp, s);
+        if (ix < m.nx - 1) s = fma(sp + __ldg(m.sig + p + 1), v[p + 1] - vp, s);
+        if (iy > 0)        s = fma(sp + __ldg(m.sig + p - m.nx), v[p - m.nx] - vp, s);
+        if (iy < m.ny - 1) s = fma(sp + __ldg(m.sig + p + m.nx), v[p + m.nx] - vp, s);
+        if (iz > 0)        s = fma(sp + __ldg(m.sig + p - sxy), v[p - sxy] - vp, s);
+        if (iz < m.nz - 1) s = fma(sp + __ldg(m.sig + p + sxy), v[p + sxy] - vp, s);
+        return 0.5 * m.ih2 * s;
+    }
     if (m.lay) {
         const double cxx = __ldg(m.lay + iz), cyy = __ldg(m.lay + m.nz + iz), cd = __ldg(m.lay + 2 * m.nz + iz);
         double s = 0.0;

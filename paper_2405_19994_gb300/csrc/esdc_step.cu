@@ -76,12 +76,26 @@ __global__ void k_math(const double* x, int64_t n, double* ex, double* rc)
 }
 
 // -diag(A) of the layered operator: sum of the coefficients of the present
-// neighbours (faces, and a b sigma_xy/(2h^2) for the in-plane diagonals).
+// neighbours (faces, and a b sigma_xy/(2h^2) for the in-plane diagonals); of
+// the field operator: sum over present faces of (sigma_p + sigma_q)/(2h^2).
 __global__ void k_wdiag(MeshDev m, double* w)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
         int ix, iy, iz;
         node_xyz(m, p, ix, iy, iz);
+        if (m.sig) {
+            const int sxy = m.nx * m.ny;
+            const double sp = m.sig[p];
+            double s = 0.0;
+            if (ix > 0) s += sp + m.sig[p - 1];
+            if (ix < m.nx - 1) s += sp + m.sig[p + 1];
+            if (iy > 0) s += sp + m.sig[p - m.nx];
+            if (iy < m.ny - 1) s += sp + m.sig[p + m.nx];
+            if (iz > 0) s += sp + m.sig[p - sxy];
+            if (iz < m.nz - 1) s += sp + m.sig[p + sxy];
+            w[p] = 0.5 * m.ih2 * s;
+            continue;
+        }
         const double cxx = m.lay[iz], cyy = m.lay[m.nz + iz], cd = m.lay[2 * m.nz + iz];
         double s = 0.0;
         if (ix > 0) s += cxx;
@@ -155,6 +169,7 @@ void free_all(esdc_handle* h)
     if (h->lay) cudaFree(h->lay);
     if (h->layf) cudaFree(h->layf);
     if (h->wdiag) cudaFree(h->wdiag);
+    if (h->sigf) cudaFree(h->sigf);
     void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev, h->Vprev,
                     h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.r32, h->cg.p32, h->cg.q32, h->cg.z32,
                     h->cg.e32, h->cg.part, h->cg.bar, h->cg.status,
@@ -334,17 +349,27 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
                                  const double* szz)
 {
     if (!h) return ESDC_ERR_INVALID_ARG;
-    if (!sxx && !syy && !sxy && !szz) {                 // back to the scalar sigma
-        if (h->lay) cudaFree(h->lay);
+    if (!sxx && !syy && !sxy && !szz) {                 // back to the scalar sigma (or the field)
+        if (!h->lay) return ESDC_OK;
+        cudaFree(h->lay);
         if (h->layf) cudaFree(h->layf);
-        if (h->wdiag) cudaFree(h->wdiag);
-        h->lay = h->wdiag = nullptr;
+        h->lay = nullptr;
         h->layf = nullptr;
-        h->mesh.lay = nullptr; h->mesh.wdiag = nullptr; h->mesh.layf = nullptr;
-        h->D = h->sigma / (h->chi * h->Cm);
+        h->mesh.lay = nullptr; h->mesh.layf = nullptr;
+        if (!h->sigf) {
+            if (h->wdiag) cudaFree(h->wdiag);
+            h->wdiag = nullptr;
+            h->mesh.wdiag = nullptr;
+            h->D = h->sigma / (h->chi * h->Cm);
+        }
         return ESDC_OK;
     }
     if (!sxx || !syy || !sxy || !szz) return set_err(h, ESDC_ERR_INVALID_ARG, "all four layer arrays are needed");
+    if (h->sigf) {                                       // layers replace a conductivity field
+        cudaFree(h->sigf);
+        h->sigf = nullptr;
+        h->mesh.sig = nullptr;
+    }
     const int nz = h->mesh.nz;
     const double ih2 = h->mesh.ih2;
     std::vector<double> c(4 * (size_t)nz, 0.0);
@@ -373,6 +398,39 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaDeviceSynchronize());
     h->D = 1.0 / (h->chi * h->Cm);                      // sigma now lives in the coefficients
+    return ESDC_OK;
+}
+
+int esdc_set_conductivity_field(esdc_handle* h, const double* sigma)
+{
+    if (!h) return ESDC_ERR_INVALID_ARG;
+    if (!sigma) {                                        // back to the scalar sigma
+        if (h->sigf) cudaFree(h->sigf);
+        if (h->wdiag && !h->lay) { cudaFree(h->wdiag); h->wdiag = nullptr; h->mesh.wdiag = nullptr; }
+        h->sigf = nullptr;
+        h->mesh.sig = nullptr;
+        if (!h->lay) h->D = h->sigma / (h->chi * h->Cm);
+        return ESDC_OK;
+    }
+    if (h->opt.precision != 0)
+        return set_err(h, ESDC_ERR_UNSUPPORTED, "a conductivity field runs on the FP64 path only");
+    const int64_t N = h->mesh.N;
+    for (int64_t p = 0; p < N; ++p)
+        if (!(sigma[p] > 0.0) || !std::isfinite(sigma[p]))
+            return set_err(h, ESDC_ERR_INVALID_ARG, "sigma[%lld] must be positive and finite", (long long)p);
+    if (h->lay) {                                        // a field replaces the layers
+        const int rc = esdc_set_conductivity_layers(h, nullptr, nullptr, nullptr, nullptr);
+        if (rc != ESDC_OK) return rc;
+    }
+    if (!h->sigf) CUDA_TRY(h, cudaMalloc((void**)&h->sigf, sizeof(double) * h->mesh.ld));
+    if (!h->wdiag) CUDA_TRY(h, cudaMalloc((void**)&h->wdiag, sizeof(double) * h->mesh.ld));
+    CUDA_TRY(h, cudaMemcpy(h->sigf, sigma, sizeof(double) * N, cudaMemcpyHostToDevice));
+    h->mesh.sig = h->sigf;
+    h->mesh.wdiag = h->wdiag;
+    k_wdiag<<<grid_for(h, 256), 256>>>(h->mesh, h->wdiag);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaDeviceSynchronize());
+    h->D = 1.0 / (h->chi * h->Cm);                      // sigma now lives in the field
     return ESDC_OK;
 }
 

@@ -60,6 +60,7 @@ def lib() -> C.CDLL:
             "esdc_state_size": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(_I64), C.POINTER(_I64)]),
             "esdc_set_conductivity_layers": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
                                                        C.POINTER(_D)]),
+            "esdc_set_conductivity_field": (C.c_int, [_VP, C.POINTER(_D)]),
             "esdc_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
             "esdc_sweep": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
             "esdc_sweep_host": (C.c_int, [_VP, _VP, _I64, _D, _D, C.c_int, C.c_int, _VP]),
@@ -161,6 +162,8 @@ class Solver:
         s.set_stimulus(wl.boxes, wl.amp, wl.t_on, wl.t_off)
         if getattr(wl, "layers", None) is not None:
             s.set_conductivity_layers(wl.layers)
+        if getattr(wl, "sigma_field", None) is not None:
+            s.set_conductivity_field(wl.sigma_field)
         return s
 
     def _check(self, rc: int):
@@ -195,6 +198,16 @@ class Solver:
             return
         arrs = [np.ascontiguousarray(layers[k], np.float64) for k in ("sxx", "syy", "sxy", "szz")]
         self._check(lib().esdc_set_conductivity_layers(self._h, *[a.ctypes.data_as(C.POINTER(_D)) for a in arrs]))
+
+    def set_conductivity_field(self, sigma):
+        """Per-node conductivity [N] (mS/mm), or None for the scalar sigma."""
+        if sigma is None:
+            self._check(lib().esdc_set_conductivity_field(self._h, None))
+            return
+        f = np.ascontiguousarray(sigma, np.float64).reshape(-1)
+        if len(f) != self.n_nodes:
+            raise ValueError("the field needs one value per mesh node")
+        self._check(lib().esdc_set_conductivity_field(self._h, f.ctypes.data_as(C.POINTER(_D))))
 
     def new_state(self, device=None):
         import torch

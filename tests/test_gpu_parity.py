@@ -363,3 +363,49 @@ def test_syn19_slab_full_size_one_step():
         scale = max(np.abs(want[srow]).max(), 1e-3)
         assert np.abs(got[srow] - want[srow]).max() / scale < 1e-11, srow
     assert abs(res_inf - st["res_inf"]) <= 1e-9 * max(st["res_inf"], 1e-6)
+
+
+# ---------------------------------------------------------------- heterogeneous conductivity field
+
+@pytest.mark.parametrize("shape", [(13, 11, 1), (32, 24, 1), (9, 8, 5)])
+def test_field_solve_matches_oracle(shape):
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.sigma_field = I.lognormal_field(nx, ny, nz, seed=7, corr=3.0)
+    s = P.Solver.from_workload(wl, cg_maxit=2000)
+    m = O.Monodomain(wl, solver=O.SOLVE_CG, cg_tol=1e-15)
+    b = np.random.default_rng(9).normal(size=wl.n_nodes)
+    g = 0.3
+    want = m.solve_A(g, b)
+    xd = torch.zeros(wl.n_nodes, dtype=torch.float64, device="cuda")
+    s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+    assert rel(xd.cpu().numpy(), want) < 1e-12
+
+
+def test_field_run_matches_oracle():
+    """HH on a 2D sheet with a log-normal conductivity field, corner stimulus:
+    40 steps from rest against the oracle (the differentiation-form physics on a
+    reduced mesh)."""
+    wl = I.hh_field_sheet(32)
+    s = P.Solver.from_workload(wl)
+    y = s.new_state()
+    s.init_state(y, wl.V0)
+    m = O.Monodomain(wl, cg_tol=1e-15)
+    ref = m.init_state()
+    t = 0.0
+    for _ in range(40):
+        s.sweep(y, t, wl.dt, wl.M, wl.K)
+        ref, _, _, _ = m.step(ref, t, wl.dt, wl.M, wl.K)
+        t += wl.dt
+    assert s.residual()[0] == 0
+    got = from_dev(s, y)
+    assert rel(got[0], ref[0]) < 1e-10
+    assert np.abs(got[0]).max() > 0.0 and ref[0].max() > -60.0       # the corner has fired
+
+
+def test_field_rejected_in_precision_form():
+    wl = I.hh_sheet_32().with_mesh(8, 8, 1)
+    s = P.Solver.from_workload(wl, precision="mixed")
+    with pytest.raises(P.EsdcError) as e:
+        s.set_conductivity_field(np.full(64, 0.2))
+    assert e.value.code == -6
