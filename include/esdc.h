@@ -291,6 +291,44 @@ int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, const double* b
                                 double tol, int maxit, int precond, int* iters, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Differentiation: the discrete adjoint of the step.
+ *
+ * The adjoint is the reverse-mode derivative of exactly the arithmetic of
+ * esdc_sweep (the sweep of eq. def_P with the tables of App. A), written by
+ * hand: sweeps and nodes in reverse order, one adjoint CG solve per implicit
+ * row (the operator is symmetric), analytic Hodgkin-Huxley derivatives, and
+ * phi_k' = phi_k - k phi_{k+1} for the Lambda_n-dependence of the tables.
+ * Supported: Hodgkin-Huxley, FP64 path, a per-node conductivity field
+ * (esdc_set_conductivity_field), M <= 7.  The paper has no adjoint; this is
+ * the library's own use of its step.
+ * ------------------------------------------------------------------------ */
+
+/* Replaces the ionic-model parameters (same count and rules as esdc_create),
+ * e.g. to perturb g_Na and g_K.  Errors: INVALID_ARG. */
+int esdc_set_params(esdc_handle* h, const double* params, int n_params);
+
+/* Forward run of nsteps steps from y (device [n_state][ld], in: y_0 at t0,
+ * out: y_nsteps) keeping a checkpoint of every step's input in ckpt (device,
+ * caller-owned, [nsteps][n_state][ld]) and, after every step n, V at the
+ * nsens sensor nodes sens (device int [nsens]) in traces (device
+ * [nsteps][nsens]).  Stream-ordered.  Errors: INVALID_ARG, UNSUPPORTED, and
+ * those of esdc_sweep. */
+int esdc_adjoint_forward(esdc_handle* h, double* y, double t0, double dt, int M, int K, int nsteps, int nsens,
+                         const int* sens, double* traces, double* ckpt, void* stream);
+
+/* Gradients of a loss L through its derivative dtraces = dL/dtraces (device
+ * [nsteps][nsens]) and, optionally, dy_final = dL/dy_nsteps (device
+ * [n_state][ld] or NULL): gsig (device [N]) = dL/dsigma per node, gpar (host
+ * [2]) = dL/d(g_Na, g_K), gy0 (device [n_state][ld] or NULL) = dL/dy_0.
+ * Recomputes every step from ckpt (esdc_adjoint_forward with the same
+ * arguments and parameters) and reverses it.  Allocates its workspace and
+ * synchronises the stream.  Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA,
+ * CG_NOT_CONVERGED, NONFINITE, DEVICE_TIMEOUT. */
+int esdc_adjoint_backward(esdc_handle* h, const double* ckpt, double t0, double dt, int M, int K, int nsteps,
+                          int nsens, const int* sens, const double* dtraces, const double* dy_final, double* gy0,
+                          double* gsig, double* gpar, void* stream);
+
+/* ------------------------------------------------------------------------
  * Ragged batches (many tissues per launch).
  *
  * A batch holds n tissues that share the ionic model, its parameters, chi,

@@ -1,7 +1,9 @@
 // Internal: the handle and the per-launch argument block shared by the
 // translation units of the step (FP64 and precision-form instantiations).
 #pragma once
+#include <cstdarg>
 #include <cstdint>
+#include <cstdio>
 #include <cuda_runtime.h>
 
 #include "esdc_internal.h"
@@ -55,6 +57,9 @@ struct esdc_handle {
     double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,
            *LAMN = nullptr, *rhs = nullptr, *R = nullptr, *ydev = nullptr, *Vprev = nullptr;
     CgWork cg{};
+    // adjoint recording (set only inside esdc_adjoint_backward): Y^{1..K},
+    // G^{0..K}, FI^{0..K} of one step, each block [M][NS][ld] or [M][ld]
+    double *tapeY = nullptr, *tapeG = nullptr, *tapeFI = nullptr;
     unsigned long long* rmax = nullptr;   // [2*NS]
     int* flags = nullptr;                 // [1]
     int* cg_log = nullptr;                // [K_log] iteration counts of the last step
@@ -74,6 +79,26 @@ struct esdc_handle {
     char err[256] = {0};
 };
 
+
+// Records a formatted message on the handle and returns code.
+__attribute__((format(printf, 3, 4))) inline int set_err(esdc_handle* h, int code, const char* fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof h->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return set_err((h), e_ == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA, \
+                           "%s: %s", #call, cudaGetErrorString(e_));                           \
+    } while (0)
 
 // Kernel-class timing (esdc_profile).
 // Folds the recorded event pairs into the per-class totals (synchronises them).

@@ -548,6 +548,14 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     prof_end(h, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // Adjoint recording (esdc_adjoint_*): G^0 and FI^0 after the set-up, and
+    // Y^{k+1}, G^{k+1}, FI^{k+1} after every sweep.
+    const int64_t tY = (int64_t)M * h->NS * h->mesh.ld, tF = (int64_t)M * h->mesh.ld;
+    if (h->tapeY) {
+        if ((e = cudaMemcpyAsync(h->tapeG, h->G0, sizeof(double) * tY, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h->tapeFI, h->FI, sizeof(double) * tF, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return e;
+    }
     double* Gold = h->G0;
     double* Gnew = h->G1;
     for (int k = 0; k < K; ++k) {
@@ -574,6 +582,15 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
                 prof_end(h, s);
                 if (e != cudaSuccess) return e;
             }
+        }
+        if (h->tapeY) {
+            if ((e = cudaMemcpyAsync(h->tapeY + k * tY, h->Y, sizeof(double) * tY, cudaMemcpyDeviceToDevice, s)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(h->tapeG + (k + 1) * tY, Gnew, sizeof(double) * tY, cudaMemcpyDeviceToDevice,
+                                     s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(h->tapeFI + (k + 1) * tF, h->FI, sizeof(double) * tF, cudaMemcpyDeviceToDevice,
+                                     s)) != cudaSuccess)
+                return e;
         }
         double* t = Gold; Gold = Gnew; Gnew = t;
     }

@@ -90,6 +90,54 @@ struct HH1952 {
         lam = -sum;
         yinf = al / sum;
     }
+    // Derivatives for the adjoint.  d(-I_ion)/du (u = V, m, h, n) and
+    // d(-I_ion)/d(gNa, gK).
+    __device__ static void currents_d(const double* __restrict__ mp, const double* u, double* dmI, double* dpar)
+    {
+        const double V = u[0], m = u[1], h = u[2], n = u[3];
+        const double m2 = m * m, n3 = n * n * n;
+        dmI[0] = -(mp[0] * m2 * m * h + mp[1] * n3 * n + mp[2]);
+        dmI[1] = -3.0 * mp[0] * m2 * h * (V - mp[3]);
+        dmI[2] = -mp[0] * m2 * m * (V - mp[3]);
+        dmI[3] = -4.0 * mp[1] * n3 * (V - mp[4]);
+        dpar[0] = -m2 * m * h * (V - mp[3]);
+        dpar[1] = -n3 * n * (V - mp[4]);
+    }
+    // Lambda, w_inf of gate q and their derivatives in V.  With f(x) = x/(e^x - 1),
+    // f'(x) = f (1 - f - x)/x, or its Taylor series -1/2 + x/6 - x^3/180 near 0.
+    __device__ static void gate_d(const double* __restrict__ mp, int q, double V, double& lam, double& yinf,
+                                  double& dlam, double& dyinf)
+    {
+        const double v = V - mp[6];
+        auto fprime = [](double x, double f) {
+            return fabs(x) < 1e-3 ? -0.5 + x * (1.0 / 6.0 - x * x * (1.0 / 180.0)) : f * (1.0 - f - x) / x;
+        };
+        double al, be, dal, dbe;
+        if (q == 0) {
+            const double x = (25.0 - v) * 0.1;
+            al = x_over_expm1(x);
+            dal = -0.1 * fprime(x, al);
+            be = 4.0 * exp(v * (-1.0 / 18.0));
+            dbe = be * (-1.0 / 18.0);
+        } else if (q == 1) {
+            al = 0.07 * exp(v * (-0.05));
+            dal = -0.05 * al;
+            be = 1.0 / (exp((30.0 - v) * 0.1) + 1.0);
+            dbe = 0.1 * be * (1.0 - be);
+        } else {
+            const double x = (10.0 - v) * 0.1;
+            const double f = x_over_expm1(x);
+            al = 0.1 * f;
+            dal = 0.1 * (-0.1) * fprime(x, f);
+            be = 0.125 * exp(v * (-0.0125));
+            dbe = be * (-0.0125);
+        }
+        const double sum = al + be;
+        lam = -sum;
+        yinf = al / sum;
+        dlam = -(dal + dbe);
+        dyinf = (dal * be - al * dbe) / (sum * sum);
+    }
     // Resting state at V0: gates at w_inf(V0).
     __device__ static void rest(const double* mp, double V0, double* u)
     {

@@ -135,26 +135,6 @@ __global__ void k_coef(const double* z, int64_t n, double* out)
 
 namespace {
 
-int set_err(esdc_handle* h, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
-int set_err(esdc_handle* h, int code, const char* fmt, ...)
-{
-    if (h) {
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(h->err, sizeof h->err, fmt, ap);
-        va_end(ap);
-    }
-    return code;
-}
-
-#define CUDA_TRY(h, call)                                                                      \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
-            return set_err((h), e_ == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA, \
-                           "%s: %s", #call, cudaGetErrorString(e_));                           \
-    } while (0)
-
 int grid_for(const esdc_handle* h, int threads)
 {
     long long need = ((long long)h->mesh.N + threads - 1) / threads;

@@ -76,6 +76,11 @@ def lib() -> C.CDLL:
             "esdc_math_check": (C.c_int, [_VP, _I64, _VP, _VP, _VP]),
             "esdc_diffusion_solve_static": (C.c_int, [C.POINTER(esdc_mesh), _D, _VP, _VP, _D, C.c_int, C.c_int,
                                                       C.POINTER(C.c_int), _VP]),
+            "esdc_set_params": (C.c_int, [_VP, C.POINTER(_D), C.c_int]),
+            "esdc_adjoint_forward": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP,
+                                               _VP]),
+            "esdc_adjoint_backward": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP,
+                                                _VP, _VP, C.POINTER(_D), _VP]),
             "esdc_batch_create": (C.c_int, [C.c_int, C.POINTER(esdc_mesh), C.POINTER(_D), _D, _D, C.c_int,
                                             C.POINTER(_D), C.c_int, C.POINTER(esdc_options), C.POINTER(_VP)]),
             "esdc_batch_destroy": (None, [_VP]),
@@ -155,6 +160,7 @@ class Solver:
         self._check(L.esdc_state_size(self._h, C.byref(ns), C.byref(nn), C.byref(ld)))
         self.n_state, self.n_nodes, self.ld = ns.value, nn.value, ld.value
         self.M_max = M_max
+        self.params = p.copy()
 
     @classmethod
     def from_workload(cls, wl, **kw) -> "Solver":
@@ -208,6 +214,32 @@ class Solver:
         if len(f) != self.n_nodes:
             raise ValueError("the field needs one value per mesh node")
         self._check(lib().esdc_set_conductivity_field(self._h, f.ctypes.data_as(C.POINTER(_D))))
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float64)
+        self._check(lib().esdc_set_params(self._h, p.ctypes.data_as(C.POINTER(_D)), len(p)))
+        self.params = p.copy()
+
+    def adjoint_forward(self, y, t0: float, dt: float, M: int, K: int, nsteps: int, sens, traces, ckpt, stream=None):
+        """esdc_adjoint_forward: y in/out, traces [nsteps, nsens], ckpt [nsteps, n_state, ld]."""
+        import torch
+        assert sens.dtype == torch.int32 and sens.is_cuda and sens.is_contiguous()
+        self._check(lib().esdc_adjoint_forward(self._h, _ptr(y), t0, dt, M, K, nsteps, sens.numel(), sens.data_ptr(),
+                                               _ptr(traces) if sens.numel() else None, _ptr(ckpt), _stream(stream)))
+
+    def adjoint_backward(self, ckpt, t0: float, dt: float, M: int, K: int, nsteps: int, sens, dtraces,
+                         dy_final=None, want_y0: bool = False, stream=None):
+        """esdc_adjoint_backward: returns (dL/dsigma [N], dL/d(g_Na, g_K) [2], dL/dy0 or None)."""
+        import torch
+        gsig = torch.zeros(self.n_nodes, dtype=torch.float64, device="cuda")
+        gy0 = torch.zeros((self.n_state, self.ld), dtype=torch.float64, device="cuda") if want_y0 else None
+        gpar = np.zeros(2)
+        self._check(lib().esdc_adjoint_backward(
+            self._h, _ptr(ckpt), t0, dt, M, K, nsteps, sens.numel(), sens.data_ptr(),
+            _ptr(dtraces) if sens.numel() else None, _ptr(dy_final) if dy_final is not None else None,
+            _ptr(gy0) if gy0 is not None else None, _ptr(gsig), gpar.ctypes.data_as(C.POINTER(_D)),
+            _stream(stream)))
+        return gsig, gpar, gy0
 
     def new_state(self, device=None):
         import torch
@@ -406,3 +438,34 @@ class Batch:
         """View of tissue b's columns of a batch state."""
         o = int(self.offsets[b])
         return y[:, o:o + int(self.n_nodes[b])]
+
+
+def sensor_traces(solver: "Solver", sigma, g_na, g_k, y0, t0: float, dt: float, M: int, K: int, nsteps: int, sens):
+    """V at the sensor nodes after each of nsteps HSDC steps from y0, as a
+    differentiable function of the conductivity field sigma [N] and the maximal
+    conductances g_Na, g_K (0-d tensors): the backward pass is the library's
+    discrete adjoint (esdc_adjoint_backward), with one checkpoint per step."""
+    import torch
+
+    class _Traces(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, sig, gna, gk):
+            p = solver.params.copy()
+            p[0], p[1] = float(gna), float(gk)
+            solver.set_params(p)
+            solver.set_conductivity_field(sig.detach().cpu().numpy())
+            y = y0.clone()
+            traces = torch.empty((nsteps, sens.numel()), dtype=torch.float64, device="cuda")
+            ckpt = torch.empty((nsteps, solver.n_state, solver.ld), dtype=torch.float64, device="cuda")
+            solver.adjoint_forward(y, t0, dt, M, K, nsteps, sens, traces, ckpt)
+            ctx.ckpt = ckpt
+            ctx.sig_device = sig.device
+            return traces
+
+        @staticmethod
+        def backward(ctx, dtr):
+            gsig, gpar, _ = solver.adjoint_backward(ctx.ckpt, t0, dt, M, K, nsteps, sens, dtr.contiguous())
+            one = torch.ones((), dtype=torch.float64)
+            return gsig.to(ctx.sig_device), one * gpar[0], one * gpar[1]
+
+    return _Traces.apply(sigma, g_na, g_k)
