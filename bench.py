@@ -676,6 +676,107 @@ def run_qpar_batch(args, P, I, torch, timed):
             "speedup_vs_looped_slices": ms_1 / ms_b}
 
 
+def run_adjoint_form(args):
+    """The differentiation form: 2D 256 x 256 HH tissue with a log-normal
+    conductivity field, M = 3, K = 4, dt = 0.025 ms, T = 20 ms (800 steps), loss
+    = half the squared misfit of V at 64 seeded sensor nodes after every step
+    against a seeded target run (another field, g_Na x 1.05, g_K x 0.95).
+    Times the forward run (with one checkpoint per step) and the adjoint
+    (recomputation + reverse sweeps), and checks the gradient along a seeded
+    direction of the field against central differences of the forward map."""
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1 and rank != 0:
+        return
+    n = args.nz if args.nz else 256                       # side length (the flag is reused for this 2D form)
+    wl = I.hh_field_sheet(n)
+    nsteps = args.steps if args.steps is not None else wl.n_steps
+    rng = np.random.default_rng(5)
+    sens_h = np.sort(rng.choice(wl.n_nodes, size=64, replace=False)).astype(np.int32)
+    sens = torch.from_numpy(sens_h).cuda()
+    s = P.Solver.from_workload(wl, M_max=wl.M)
+    y0 = s.new_state()
+    s.init_state(y0, wl.V0)
+    tr = torch.empty((nsteps, 64), dtype=torch.float64, device="cuda")
+    ck = torch.empty((nsteps, s.n_state, s.ld), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def forward(sig, params):
+        s.set_params(params)
+        s.set_conductivity_field(sig)
+        y = y0.clone()
+        s.adjoint_forward(y, 0.0, wl.dt, wl.M, wl.K, nsteps, sens, tr, ck)
+        torch.cuda.synchronize()
+        if s.residual()[0] != 0:
+            raise RuntimeError("forward run failed")
+        return tr.clone()
+
+    p_t = wl.params.copy()
+    p_t[0] *= 1.05
+    p_t[1] *= 0.95
+    target = forward(I.lognormal_field(n, n, 1, seed=55), p_t)
+    forward(wl.sigma_field, wl.params)                     # warm-up
+    clocks = ClockSampler(local)
+    clocks.start()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    trs = forward(wl.sigma_field, wl.params)
+    e[1].record(stream)
+    dtr = (trs - target).contiguous()
+    gsig, gpar, _ = s.adjoint_backward(ck, 0.0, wl.dt, wl.M, wl.K, nsteps, sens, dtr)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_f, ms_b = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    loss = 0.5 * float((dtr ** 2).sum())
+
+    # gradient check along a seeded direction of the field (central differences, eps = 1e-6)
+    eps = 1e-6
+    d = wl.sigma_field * np.random.default_rng(7).normal(size=wl.n_nodes)
+    Lp = 0.5 * float(((forward(wl.sigma_field + eps * d, wl.params) - target) ** 2).sum())
+    Lm = 0.5 * float(((forward(wl.sigma_field - eps * d, wl.params) - target) ** 2).sum())
+    fd = (Lp - Lm) / (2 * eps)
+    ad = float(gsig.cpu().numpy() @ d)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = I.hh_field_sheet(32)
+        m = oracle.Monodomain(sub, cg_tol=1e-15)
+        y = m.init_state()
+        t = 0.0
+        c0 = time.perf_counter()
+        for _ in range(80):
+            y, _, _, _ = m.step(y, t, sub.dt, sub.M, sub.K)
+            t += sub.dt
+        cel = time.perf_counter() - c0
+        cpu = {"value": sub.n_nodes * 80 / cel, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
+               "sample": "80 forward steps of the 32x32 field sheet (the oracle has no adjoint; forward only)"}
+    nodes = wl.n_nodes
+    line = {
+        "metric": METRIC, "value": nodes * nsteps / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": nsteps, "warmup": 1, "ms_per_step": (ms_f + ms_b) / nsteps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"hh_field_sheet_{n} (log-normal sigma field, seed 5)", "form": "adjoint",
+                   "nodes": nodes, "M": wl.M, "K": wl.K, "dt_ms": wl.dt, "T_ms": nsteps * wl.dt, "sensors": 64,
+                   "value_is": "node-updates/s of forward + backward together"},
+        "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+        "forward_node_updates_per_s": nodes * nsteps / (ms_f * 1e-3),
+        "loss": loss, "dL_dgNa": float(gpar[0]), "dL_dgK": float(gpar[1]),
+        "grad_check_field": {"adjoint": ad, "central_difference": fd, "rel_err": abs(ad - fd) / abs(fd), "eps": eps},
+        "checkpoint_bytes": int(ck.numel() * 8),
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -687,9 +788,10 @@ def main():
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
-    ap.add_argument("--form", choices=["plain", "precision", "batch"], default="plain",
+    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint"], default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
-                         "batch: the 64-tissue ragged HH batch against looped single-tissue steps")
+                         "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "
+                         "adjoint: forward + discrete adjoint on the 256x256 HH conductivity-field sheet")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -701,6 +803,8 @@ def main():
         run_precision_form(args)
     elif args.form == "batch":
         run_batch_form(args)
+    elif args.form == "adjoint":
+        run_adjoint_form(args)
     else:
         run_ours(args)
 
