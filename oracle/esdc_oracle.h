@@ -94,6 +94,14 @@ int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain
                        double t_n, double dt, const double* y_n, const double* colloc_in,
                        double* y_next, double* colloc, double* resid, orc_stats* st);
 
+/* The FAS form of the step (Sec. 3.2, Algorithm HSDC): a correction tau
+ * [M*n] (rows 1..M; NULL = 0) is added to the right-hand side 1 (x) y_n of
+ * the collocation system, so the sweeps solve P(y^{k+1}) = (P - C)(y^k) +
+ * 1 (x) y_n + tau and the residual is r_i = y_n + tau_i + dt sum_j a_ij G_j - y_i. */
+int orc_hsdc_step_tau(const orc_problem* P, int M, int K, double tol, int plain_sdc,
+                      double t_n, double dt, const double* y_n, const double* colloc_in, const double* tau,
+                      double* y_next, double* colloc, double* resid, orc_stats* st);
+
 /* ------------------------------------------------------------------ */
 /* Monodomain problem on a uniform cell-centred mesh (Sec. 2)          */
 /* ------------------------------------------------------------------ */

@@ -74,6 +74,8 @@ def lib():
                                     C.c_double, C.c_double, _D, _D, _D, _D, C.POINTER(_Stats)]
         L.orc_hsdc_step_from.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_double, C.c_int,
                                          C.c_double, C.c_double, _D, _D, _D, _D, _D, C.POINTER(_Stats)]
+        L.orc_hsdc_step_tau.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_double, C.c_int,
+                                        C.c_double, C.c_double, _D, _D, _D, _D, _D, _D, C.POINTER(_Stats)]
         L.orc_mono_problem.argtypes = [C.POINTER(_Mono), C.POINTER(_Problem)]
         L.orc_mono_free.argtypes = [C.POINTER(_Mono)]
         L.orc_mono_init.argtypes = [C.POINTER(_Mono), C.c_double, _D]
@@ -94,6 +96,19 @@ def lib():
 def _p(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(_D)
+
+
+def lagrange_matrix(nodes: np.ndarray, points: np.ndarray) -> np.ndarray:
+    """L[i, j] = l_j(points[i]), l_j the Lagrange basis through `nodes` (the
+    interpolator I_l of Sec. 3.2, product form)."""
+    nodes = np.asarray(nodes, np.float64)
+    L = np.ones((len(points), len(nodes)))
+    for i, x in enumerate(points):
+        for j, cj in enumerate(nodes):
+            for k, ck in enumerate(nodes):
+                if k != j:
+                    L[i, j] *= (x - ck) / (cj - ck)
+    return L
 
 
 def radau_nodes(M: int) -> np.ndarray:
@@ -254,11 +269,13 @@ class Monodomain:
 
     def step(self, y_n: np.ndarray, t_n: float, dt: float, M: int, K: int, tol: float = 0.0,
              plain_sdc: bool = False, want_colloc: bool = False, want_resid: bool = False,
-             colloc_in: np.ndarray | None = None):
+             colloc_in: np.ndarray | None = None, tau: np.ndarray | None = None):
         """One HSDC step; returns (y_next[ns, N], stats dict, colloc, resid).
 
         colloc_in [M, ns, N] (optional) starts the sweeps from that iterate
-        instead of y^0 = 1 (x) y_n (orc_hsdc_step_from)."""
+        instead of y^0 = 1 (x) y_n (orc_hsdc_step_from); tau [M, ns, N]
+        (optional) is the FAS correction added to the right-hand side
+        (orc_hsdc_step_tau).  K = 0 returns the residual at the given iterate."""
         y_n = np.ascontiguousarray(y_n, np.float64).reshape(-1)
         n = len(y_n)
         y1 = np.zeros(n)
@@ -267,11 +284,15 @@ class Monodomain:
         cin = None if colloc_in is None else np.ascontiguousarray(colloc_in, np.float64).reshape(-1)
         if cin is not None and len(cin) != M * n:
             raise ValueError("colloc_in must hold M x n_state x N values")
+        tv = None if tau is None else np.ascontiguousarray(tau, np.float64).reshape(-1)
+        if tv is not None and len(tv) != M * n:
+            raise ValueError("tau must hold M x n_state x N values")
         st = _Stats()
-        rc = lib().orc_hsdc_step_from(C.byref(self.P), M, K, tol, int(plain_sdc), float(t_n), float(dt),
-                                      _p(y_n), _p(cin) if cin is not None else None, _p(y1),
-                                      _p(col) if col is not None else None,
-                                      _p(res) if res is not None else None, C.byref(st))
+        rc = lib().orc_hsdc_step_tau(C.byref(self.P), M, K, tol, int(plain_sdc), float(t_n), float(dt),
+                                     _p(y_n), _p(cin) if cin is not None else None,
+                                     _p(tv) if tv is not None else None, _p(y1),
+                                     _p(col) if col is not None else None,
+                                     _p(res) if res is not None else None, C.byref(st))
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
         stats = dict(sweeps=st.sweeps_done, res_inf=st.res_inf, y_inf=st.y_inf)
@@ -297,6 +318,49 @@ class Monodomain:
                 _, _, col, _ = self.step(yn, t0 + p * dt, dt, M, 1, want_colloc=True, colloc_in=Z[p])
                 newZ[p] = col
             Z = newZ
+        return Z
+
+    def hsdc2(self, y0: np.ndarray, t0: float, dt: float, P: int, M1: int, M2: int, iters: int,
+              Z0: np.ndarray | None = None):
+        """Algorithm HSDC (Sec. 3.2) with two levels, M = M1, M2 (M1 > M2 Radau
+        nodes), over P consecutive steps from y0 at t0, without Burn-in (not
+        specified: z^0 = 1 (x) y0 in every slice).  One iteration:
+          tau = S D_1(z) - D_2(S z), per slice S R_1(z_p) - R_2(S z_p), with R the
+                collocation residual vectors (the slice couplings cancel, and
+                row 0 of tau vanishes because c_M = 1 on both levels);
+          coarse: one Q^seq sweep from S z with tau: slice p starts from the
+                new end value of slice p-1;
+          fine:   one Q^par sweep from z + T(z_2 - S z): slice p starts from the
+                corrected end value of slice p-1 of that iterate.
+        S interpolates the fine node values at the coarse nodes, T the coarse
+        ones at the fine nodes (Lagrange through c_1..c_M).  Z0 [P, M1, ns, N]
+        (optional) replaces z^0, with row 0 of slice p the end of slice p-1.
+        Returns the fine iterates [P, M1, ns, N]."""
+        y0 = np.asarray(y0, np.float64).reshape(self.ns, self.N)
+        R = lagrange_matrix(radau_nodes(M1)[1:], radau_nodes(M2)[1:])       # [M2, M1]
+        T = lagrange_matrix(radau_nodes(M2)[1:], radau_nodes(M1)[1:])       # [M1, M2]
+        Z = np.broadcast_to(y0, (P, M1, self.ns, self.N)).copy() if Z0 is None else np.array(Z0, np.float64)
+        Y0 = np.broadcast_to(y0, (P, self.ns, self.N)).copy()              # row 0 of every slice
+        if Z0 is not None:
+            Y0[1:] = Z[:-1, M1 - 1]
+        for _ in range(iters):
+            SZ = np.einsum("ij,pjsn->pisn", R, Z)
+            tau = np.empty((P, M2, self.ns, self.N))
+            for p in range(P):
+                _, _, _, r1 = self.step(Y0[p], t0 + p * dt, dt, M1, 0, want_resid=True, colloc_in=Z[p])
+                _, _, _, r2 = self.step(Y0[p], t0 + p * dt, dt, M2, 0, want_resid=True, colloc_in=SZ[p])
+                tau[p] = np.einsum("ij,jsn->isn", R, r1) - r2
+            Z2 = np.empty_like(SZ)
+            for p in range(P):                                             # Q^seq on the coarse level
+                yi = y0 if p == 0 else Z2[p - 1, M2 - 1]
+                _, _, Z2[p], _ = self.step(yi, t0 + p * dt, dt, M2, 1, want_colloc=True, colloc_in=SZ[p],
+                                           tau=tau[p])
+            W = Z + np.einsum("ij,pjsn->pisn", T, Z2 - SZ)                 # coarse-grid correction
+            Znew = np.empty_like(Z)
+            for p in range(P):                                             # Q^par on the fine level
+                Y0[p] = y0 if p == 0 else W[p - 1, M1 - 1]
+                _, _, Znew[p], _ = self.step(Y0[p], t0 + p * dt, dt, M1, 1, want_colloc=True, colloc_in=W[p])
+            Z = Znew
         return Z
 
     def run(self, y0: np.ndarray, t0: float, dt: float, nsteps: int, M: int, K: int):

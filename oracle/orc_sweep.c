@@ -84,6 +84,13 @@ int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain
                        double t_n, double dt, const double* y_n, const double* colloc_in,
                        double* y_next, double* colloc, double* resid, orc_stats* st)
 {
+    return orc_hsdc_step_tau(P, M, K, tol, plain_sdc, t_n, dt, y_n, colloc_in, NULL, y_next, colloc, resid, st);
+}
+
+int orc_hsdc_step_tau(const orc_problem* P, int M, int K, double tol, int plain_sdc,
+                      double t_n, double dt, const double* y_n, const double* colloc_in, const double* tau,
+                      double* y_next, double* colloc, double* resid, orc_stats* st)
+{
     if (M < 1 || M > ORC_MMAX || K < 0 || !(dt > 0.0)) return -1;
     const int64_t n = P->n;
     double c[ORC_MMAX + 1], d[ORC_MMAX + 1], w[ORC_MMAX * ORC_MMAX], a0[ORC_MMAX * ORC_MMAX];
@@ -151,7 +158,7 @@ int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain
                 for (int j = 1; j < i; ++j)
                     corr += d[j] * (En[(j - 1) * n + e] - E[(j - 1) * n + e]);
                 corr += d[i] * (Ex[e] - E[(i - 1) * n + e]);
-                rhs[e] = y_n[e] + dt * s + dt * corr;
+                rhs[e] = y_n[e] + dt * s + dt * corr + (tau ? tau[(i - 1) * n + e] : 0.0);
             }
             double* yi = Yn + i * n;
             memcpy(yi, Y + i * n, sizeof(double) * n);            /* initial guess y_i^k */
@@ -172,7 +179,7 @@ int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain
                 double s = 0.0;
                 for (int j = 1; j <= M; ++j)
                     s += a[((i - 1) * M + (j - 1)) * n + e] * G[(j - 1) * n + e];
-                double r = y_n[e] + dt * s - Y[i * n + e];
+                double r = y_n[e] + dt * s - Y[i * n + e] + (tau ? tau[(i - 1) * n + e] : 0.0);
                 R[(i - 1) * n + e] = r;
                 if (fabs(r) > res_inf) res_inf = fabs(r);
                 if (fabs(Y[i * n + e]) > y_inf) y_inf = fabs(Y[i * n + e]);
@@ -185,7 +192,7 @@ int orc_hsdc_step_from(const orc_problem* P, int M, int K, double tol, int plain
                 double s = 0.0;
                 for (int j = 1; j <= M; ++j)
                     s += a[((i - 1) * M + (j - 1)) * n + e] * G[(j - 1) * n + e];
-                R[(i - 1) * n + e] = y_n[e] + dt * s - Y[i * n + e];
+                R[(i - 1) * n + e] = y_n[e] + dt * s - Y[i * n + e] + (tau ? tau[(i - 1) * n + e] : 0.0);
             }
     }
     memcpy(y_next, Y + M * n, sizeof(double) * n);

@@ -323,3 +323,82 @@ def test_qpar_first_iteration_sweeps_every_slice_from_y0(orc):
     for p in range(3):
         _, _, col, _ = m.step(y0, p * wl.dt, wl.dt, wl.M, 1, want_colloc=True)
         assert np.array_equal(Z1[p], col)
+
+
+# ---------------------------------------------------------------- two-level HSDC (Algorithm HSDC, FAS in M)
+
+def _hsdc_case():
+    from paper_2405_19994_gb300 import inputs as I
+    wl = I.hh_sheet_32().with_mesh(6, 6, 1)
+    m = O.Monodomain(wl)
+    return wl, m, m.init_state()
+
+
+def _sequential_collocation(m, y0, dt, P, M):
+    out, y, t = [], y0, 0.0
+    for _ in range(P):
+        yn, _, col, _ = m.step(y, t, dt, M, 60, want_colloc=True)
+        out.append(col)
+        y, t = yn, t + dt
+    return np.array(out)
+
+
+def test_lagrange_interpolation_matrix_exact_for_polynomials(orc):
+    # interpolation through M nodes reproduces polynomials of degree < M at any point
+    c3, c2 = O.radau_nodes(3)[1:], O.radau_nodes(2)[1:]
+    x = np.linspace(0, 1, 7)
+    L = O.lagrange_matrix(c3, x)
+    for deg in range(3):
+        np.testing.assert_allclose(L @ c3 ** deg, x ** deg, atol=1e-14)
+    np.testing.assert_allclose(O.lagrange_matrix(c3, c3), np.eye(3), atol=1e-15)
+    np.testing.assert_allclose(O.lagrange_matrix(c2, c3).sum(axis=1), 1.0, atol=1e-15)
+
+
+def test_hsdc2_fixed_point_is_sequential_collocation(orc):
+    wl, m, y0 = _hsdc_case()
+    P, M1, M2 = 4, 3, 2
+    Z = m.hsdc2(y0, 0.0, wl.dt, P, M1, M2, 14)
+    ref = _sequential_collocation(m, y0, wl.dt, P, M1)
+    assert np.abs(Z - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_hsdc2_converged_solution_is_left_unchanged(orc):
+    # FAS consistency: at the fine solution the tau-corrected coarse problem is
+    # solved by the restricted fine solution, so the coarse correction vanishes.
+    wl, m, y0 = _hsdc_case()
+    P, M1, M2 = 3, 3, 2
+    ref = _sequential_collocation(m, y0, wl.dt, P, M1)
+    Z = m.hsdc2(y0, 0.0, wl.dt, P, M1, M2, 1, Z0=ref)
+    assert np.abs(Z - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_hsdc2_converges_faster_than_qpar(orc):
+    # the sequential coarse sweep carries every slice's initial value across all
+    # slices in one iteration; Q^par alone moves it one slice per iteration
+    wl, m, y0 = _hsdc_case()
+    P, M1, M2, it = 4, 3, 2, 3
+    ref = _sequential_collocation(m, y0, wl.dt, P, M1)
+    e_h = np.abs(m.hsdc2(y0, 0.0, wl.dt, P, M1, M2, it) - ref).max()
+    e_q = np.abs(m.qpar(y0, 0.0, wl.dt, P, M1, it) - ref).max()
+    assert e_h < 1e-3 * e_q, (e_h, e_q)
+
+
+def test_step_tau_zero_is_the_plain_sweep(orc):
+    wl, m, y0 = _hsdc_case()
+    _, _, a, ra = m.step(y0, 0.0, wl.dt, 3, 2, want_colloc=True, want_resid=True)
+    _, _, b, rb = m.step(y0, 0.0, wl.dt, 3, 2, want_colloc=True, want_resid=True, tau=np.zeros((3,) + y0.shape))
+    assert np.array_equal(a, b) and np.array_equal(ra, rb)
+
+
+def test_step_tau_shifts_the_collocation_solution(orc):
+    # the converged sweep with tau solves C(y) = 1 (x) y_n + tau: its residual
+    # (which includes tau) vanishes, and tau = r(y*) makes y* (the plain
+    # solution's perturbation) the new fixed point
+    wl, m, y0 = _hsdc_case()
+    M = 3
+    _, _, ystar, _ = m.step(y0, 0.0, wl.dt, M, 60, want_colloc=True)
+    Yp = ystar * (1 + 1e-3 * np.random.default_rng(2).normal(size=ystar.shape))
+    _, _, _, r = m.step(y0, 0.0, wl.dt, M, 0, want_resid=True, colloc_in=Yp)
+    # with tau = -r(Yp) the collocation system C(y) = 1 (x) y_n + tau is solved by Yp
+    _, _, Z, rz = m.step(y0, 0.0, wl.dt, M, 60, want_colloc=True, want_resid=True, colloc_in=Yp, tau=-r)
+    assert np.abs(Z - Yp).max() < 1e-11 * np.abs(Yp).max()
