@@ -403,6 +403,45 @@ int esdc_batch_sweep_from(esdc_batch* b, const double* y_in, double* y_out, cons
  * Errors: INVALID_ARG, CUDA. */
 int esdc_batch_qpar(esdc_batch* b, double* y_in, double* y_out, double t0, double dt, int M, int iters, void* stream);
 
+/* The general form of esdc_batch_sweep_from: tau (device [M][n_state][ld] or
+ * NULL) is the FAS correction of Algorithm HSDC (Sec. 3.2), added to the
+ * right-hand side 1 (x) y_n of every tissue's collocation system; K = 0 (with
+ * from_iterate) only evaluates the residual at the iterate; want_residual
+ * keeps the residual vectors r_i = y_n + tau_i + dt sum_j a_ij G_j - y_i
+ * (esdc_batch_iterate).  Errors: INVALID_ARG, NO_MEMORY, CUDA. */
+int esdc_batch_sweep_ex(esdc_batch* b, const double* y_in, double* y_out, const double* tau, const double* t, double dt,
+                        int M, int K, int from_iterate, int want_residual, void* stream);
+
+/* Device pointers, owned by the batch, of its collocation iterate
+ * y_{n,1..M} ([M_max][n_state][ld], node j at row block j-1) and of the kept
+ * residual vectors (same layout; NULL until a call asked for them).  Writing
+ * the iterate sets the starting point of the next from_iterate sweep. */
+int esdc_batch_iterate(esdc_batch* b, double** Y, double** R);
+
+/* dst_i = beta dst_i + sum_j W[i][j] src_j for the collocation rows i < Md,
+ * j < Ms of every state and of the first n_cols columns (src [Ms][n_state]
+ * [src_ld], dst [Md][n_state][dst_ld], both device, distinct; W host
+ * [Md][Ms]).  With W the Lagrange matrix between two node sets this is the
+ * interpolator I_l of Sec. 3.2 (restriction and prolongation in M).
+ * Stream-ordered.  Errors: INVALID_ARG, CUDA. */
+int esdc_interp(const double* src, int Ms, int64_t src_ld, double* dst, int Md, int64_t dst_ld, int n_state,
+                int64_t n_cols, const double* W, double beta, void* stream);
+
+/* Algorithm HSDC (Sec. 3.2) with two levels M = M1, M2 (M2 < M1) over the
+ * P = n tissues of `fine` as consecutive time slices (shared mesh and
+ * conductivity), without Burn-in (z^0 = 1 (x) y0).  coarse[p] (p < P) are
+ * single-tissue batches of the same mesh with M_max >= M2 (the coarse level,
+ * swept one slice after another by Q^seq).  The restriction S and the
+ * prolongation T are the Lagrange interpolators between the two levels' Radau
+ * nodes c_1..c_M.  One iteration: tau = S R_1(z) - R_2(S z) per
+ * slice, one Q^seq sweep with tau on the coarse level, the coarse-grid
+ * correction z += T (z_2 - S z), one Q^par sweep on the fine level.  y_in
+ * slice 0 holds y0 at t0 on entry; on return the fine iterate is in
+ * esdc_batch_iterate(fine) and y_out slice p holds y_{p,M1}.  Synchronises.
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA and those of the sweeps. */
+int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double* y_out, double t0, double dt, int M1,
+               int M2, int iters, void* stream);
+
 /* Per tissue (host [n], optional): max |r| of the collocation residual and
  * max |y| of the last step.  Synchronises that step's stream.  Returns
  * NONFINITE, CG_NOT_CONVERGED or DEVICE_TIMEOUT if any tissue raised it. */

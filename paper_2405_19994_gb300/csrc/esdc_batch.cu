@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
 #pragma unroll 1
             for (int s = 0; s < NS; ++s) {
                 double r, y;
-                bad |= !residual_state<Model, M>(a, p, s, r, y);
+                bad |= !residual_state<Model, M, true>(a, p, s, r, y);
                 rm[s] = fmax(rm[s], r);
                 ym[s] = fmax(ym[s], y);
             }
@@ -122,6 +122,31 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
     }
     if (cur >= 0) flush(cur);
     if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+}
+
+// dst_i = beta dst_i + sum_j W_ij src_j for collocation rows i < Md, j < Ms,
+// every state and column (the interpolators I_l of Sec. 3.2 between node sets).
+struct InterpArgs {
+    const double* src;
+    double* dst;
+    int64_t sld, dld, ncols;
+    int Ms, Md, ns;
+    double beta;
+    double W[ESDC_MMAX][ESDC_MMAX];
+};
+
+__global__ void k_interp(InterpArgs a)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.ncols; c += (int64_t)gridDim.x * blockDim.x)
+        for (int s = 0; s < a.ns; ++s) {
+            double v[ESDC_MMAX];
+            for (int j = 0; j < a.Ms; ++j) v[j] = a.src[((int64_t)j * a.ns + s) * a.sld + c];
+            for (int i = 0; i < a.Md; ++i) {
+                double acc = a.beta != 0.0 ? a.beta * a.dst[((int64_t)i * a.ns + s) * a.dld + c] : 0.0;
+                for (int j = 0; j < a.Ms; ++j) acc = fma(a.W[i][j], v[j], acc);
+                a.dst[((int64_t)i * a.ns + s) * a.dld + c] = acc;
+            }
+        }
 }
 
 struct BCgArgs {
@@ -444,6 +469,7 @@ struct esdc_batch {
     unsigned* tis_on = nullptr;
     double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,
            *LAMN = nullptr, *rhs = nullptr, *Vprev = nullptr;
+    double* R = nullptr;                   // residual vectors [M_max][NS][ld] (allocated on first request)
     double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr;
     unsigned* bar = nullptr;
     int *done_at = nullptr, *status = nullptr, *cg_log = nullptr, *flags = nullptr;
@@ -460,6 +486,8 @@ struct esdc_batch {
         cudaGraphExec_t exec = nullptr;
         const double* yin = nullptr;
         double* yout = nullptr;
+        const double* tau = nullptr;
+        bool keepR = false;
         int M = 0, K = 0;
         double dt = 0.0;
     } graphs[2];
@@ -484,7 +512,7 @@ void free_batch(esdc_batch* b)
     for (auto& g : b->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    void* ptrs[] = {b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
+    void* ptrs[] = {b->R, b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
                     b->rhs, b->Vprev, b->r, b->p, b->q, b->z, b->part, b->bar, b->done_at, b->status,
                     b->cg_log, b->flags, b->rmax};
     for (void* p : ptrs)
@@ -570,8 +598,8 @@ void batch_prime(esdc_batch* b)
 // from_iter: start from the iterate left in Y by the previous step with the new
 // y_n in yin (a Q^par iteration); otherwise from y^0 = 1 (x) y_n.
 template <class Model, int M>
-cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from_iter, double dt, int K,
-                       cudaStream_t s)
+cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from_iter, const double* tau, bool keepR,
+                       double dt, int K, cudaStream_t s)
 {
     const int T = 128;
     batch_prime<Model, M>(b);
@@ -591,7 +619,8 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
     for (int i = 0; i <= M; ++i) a.dtd[i] = dt * C->d[i];
     a.yn = yin;
     a.Y = b->Y; a.FI = b->FI; a.S = b->S; a.PHI = b->PHI; a.LAMN = b->LAMN; a.rhs = b->rhs;
-    a.R = nullptr;
+    a.R = keepR ? b->R : nullptr;
+    a.tau = tau;
     a.rmax = nullptr;
     a.flags = b->flags;
     a.tis = b->tis;
@@ -635,18 +664,18 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
 }
 
 template <class Model>
-cudaError_t batch_step_M(esdc_batch* b, const double* yin, double* yout, bool fi, double dt, int M, int K,
-                         cudaStream_t s)
+cudaError_t batch_step_M(esdc_batch* b, const double* yin, double* yout, bool fi, const double* tau, bool keepR,
+                         double dt, int M, int K, cudaStream_t s)
 {
     switch (M) {
-        case 1: return batch_step<Model, 1>(b, yin, yout, fi, dt, K, s);
-        case 2: return batch_step<Model, 2>(b, yin, yout, fi, dt, K, s);
-        case 3: return batch_step<Model, 3>(b, yin, yout, fi, dt, K, s);
-        case 4: return batch_step<Model, 4>(b, yin, yout, fi, dt, K, s);
-        case 5: return batch_step<Model, 5>(b, yin, yout, fi, dt, K, s);
-        case 6: return batch_step<Model, 6>(b, yin, yout, fi, dt, K, s);
-        case 7: return batch_step<Model, 7>(b, yin, yout, fi, dt, K, s);
-        case 8: return batch_step<Model, 8>(b, yin, yout, fi, dt, K, s);
+        case 1: return batch_step<Model, 1>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 2: return batch_step<Model, 2>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 3: return batch_step<Model, 3>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 4: return batch_step<Model, 4>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 5: return batch_step<Model, 5>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 6: return batch_step<Model, 6>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 7: return batch_step<Model, 7>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 8: return batch_step<Model, 8>(b, yin, yout, fi, tau, keepR, dt, K, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -667,11 +696,11 @@ void batch_prime_M(esdc_batch* b, int M)
     }
 }
 
-cudaError_t batch_launch(esdc_batch* b, const double* yin, double* yout, bool fi, double dt, int M, int K,
-                         cudaStream_t s)
+cudaError_t batch_launch(esdc_batch* b, const double* yin, double* yout, bool fi, const double* tau, bool keepR,
+                         double dt, int M, int K, cudaStream_t s)
 {
-    return b->model == ESDC_MODEL_HH1952 ? batch_step_M<esdc::HH1952>(b, yin, yout, fi, dt, M, K, s)
-                                         : batch_step_M<esdc::SYN19>(b, yin, yout, fi, dt, M, K, s);
+    return b->model == ESDC_MODEL_HH1952 ? batch_step_M<esdc::HH1952>(b, yin, yout, fi, tau, keepR, dt, M, K, s)
+                                         : batch_step_M<esdc::SYN19>(b, yin, yout, fi, tau, keepR, dt, M, K, s);
 }
 
 void drop_graph(esdc_batch* b)
@@ -687,7 +716,8 @@ void drop_graph(esdc_batch* b)
 // batch's own stream (the legacy default stream cannot be recorded); the graph
 // is then launched on the caller's stream.  On failure the reason is kept and
 // the batch falls back to direct launches for good (graph_failed).
-bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, double dt, int M, int K)
+bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, const double* tau, bool keepR, double dt, int M,
+             int K)
 {
     esdc_batch::Graph& G = b->graphs[fi ? 1 : 0];
     if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -705,7 +735,7 @@ bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, double dt,
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return fail("begin capture", e);
-    const cudaError_t el = batch_launch(b, yin, yout, fi, dt, M, K, b->cap_stream);
+    const cudaError_t el = batch_launch(b, yin, yout, fi, tau, keepR, dt, M, K, b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (el != cudaSuccess || e != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
@@ -717,13 +747,13 @@ bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, double dt,
         G.exec = nullptr;
         return fail("instantiate", e);
     }
-    G.yin = yin; G.yout = yout; G.M = M; G.K = K; G.dt = dt;
+    G.yin = yin; G.yout = yout; G.tau = tau; G.keepR = keepR; G.M = M; G.K = K; G.dt = dt;
     return true;
 }
 
 // Stimulus windows of every tissue at its collocation times, then the step.
-int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const double* t, double dt, int M, int K,
-               cudaStream_t s)
+int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const double* tau, bool keepR, const double* t,
+               double dt, int M, int K, cudaStream_t s)
 {
     const ColloData& C = b->col[M - 1];
     for (int k = 0; k < b->ntis; ++k) {
@@ -745,8 +775,9 @@ int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const do
     b->last_graph = false;
     if (b->use_graph && !b->graph_failed) {
         const esdc_batch::Graph& G = b->graphs[fi ? 1 : 0];
-        if (!(G.exec && G.yin == yin && G.yout == yout && G.M == M && G.K == K && G.dt == dt)) {
-            if (!capture(b, yin, yout, fi, dt, M, K)) b->graph_failed = true;
+        if (!(G.exec && G.yin == yin && G.yout == yout && G.tau == tau && G.keepR == keepR && G.M == M && G.K == K &&
+              G.dt == dt)) {
+            if (!capture(b, yin, yout, fi, tau, keepR, dt, M, K)) b->graph_failed = true;
         }
         if (b->graphs[fi ? 1 : 0].exec && !b->graph_failed) {
             if (cudaGraphLaunch(b->graphs[fi ? 1 : 0].exec, s) != cudaSuccess)
@@ -755,7 +786,8 @@ int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const do
             return ESDC_OK;
         }
     }
-    if (batch_launch(b, yin, yout, fi, dt, M, K, s) != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "step launch failed");
+    if (batch_launch(b, yin, yout, fi, tau, keepR, dt, M, K, s) != cudaSuccess)
+        return set_berr(b, ESDC_ERR_CUDA, "step launch failed");
     return ESDC_OK;
 }
 
@@ -927,18 +959,40 @@ int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M
     if (!y || !t) return set_berr(b, ESDC_ERR_INVALID_ARG, "null state or time array");
     if (M < 1 || M > b->opt.M_max || K < 1 || K > 64) return set_berr(b, ESDC_ERR_INVALID_ARG, "M or K out of range");
     if (!(dt > 0.0) || !std::isfinite(dt)) return set_berr(b, ESDC_ERR_INVALID_ARG, "dt must be positive");
-    return sweep_impl(b, y, y, false, t, dt, M, K, (cudaStream_t)stream);
+    return sweep_impl(b, y, y, false, nullptr, false, t, dt, M, K, (cudaStream_t)stream);
+}
+
+int esdc_batch_sweep_ex(esdc_batch* b, const double* y_in, double* y_out, const double* tau, const double* t, double dt,
+                        int M, int K, int from_iterate, int want_residual, void* stream)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (!y_in || !y_out || !t) return set_berr(b, ESDC_ERR_INVALID_ARG, "null state or time array");
+    if (M < 1 || M > b->opt.M_max || K < 0 || K > 64 || (K == 0 && !from_iterate))
+        return set_berr(b, ESDC_ERR_INVALID_ARG, "M or K out of range");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_berr(b, ESDC_ERR_INVALID_ARG, "dt must be positive");
+    if (want_residual && !b->R) {
+        const size_t n = (size_t)b->opt.M_max * b->NS * b->ld;
+        if (cudaMalloc((void**)&b->R, sizeof(double) * n) != cudaSuccess)
+            return set_berr(b, ESDC_ERR_NO_MEMORY, "residual buffer");
+        cudaMemset(b->R, 0, sizeof(double) * n);
+    }
+    return sweep_impl(b, y_in, y_out, from_iterate != 0, tau, want_residual != 0, t, dt, M, K, (cudaStream_t)stream);
 }
 
 int esdc_batch_sweep_from(esdc_batch* b, const double* y_in, double* y_out, const double* t, double dt, int M, int K,
                           int from_iterate, void* stream)
 {
     if (!b) return ESDC_ERR_INVALID_ARG;
-    if (!y_in || !y_out || !t) return set_berr(b, ESDC_ERR_INVALID_ARG, "null state or time array");
-    if (M < 1 || M > b->opt.M_max || K < 1 || K > 64) return set_berr(b, ESDC_ERR_INVALID_ARG, "M or K out of range");
-    if (!(dt > 0.0) || !std::isfinite(dt)) return set_berr(b, ESDC_ERR_INVALID_ARG, "dt must be positive");
-    if (from_iterate && b->last_M != M) return set_berr(b, ESDC_ERR_INVALID_ARG, "no iterate of this M to start from");
-    return sweep_impl(b, y_in, y_out, from_iterate != 0, t, dt, M, K, (cudaStream_t)stream);
+    if (K < 1) return set_berr(b, ESDC_ERR_INVALID_ARG, "K out of range");
+    return esdc_batch_sweep_ex(b, y_in, y_out, nullptr, t, dt, M, K, from_iterate, 0, stream);
+}
+
+int esdc_batch_iterate(esdc_batch* b, double** Y, double** R)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (Y) *Y = b->Y;
+    if (R) *R = b->R;
+    return ESDC_OK;
 }
 
 int esdc_batch_qpar(esdc_batch* b, double* y_in, double* y_out, double t0, double dt, int M, int iters, void* stream)
@@ -1098,6 +1152,180 @@ int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, doubl
     b->cg_threads = pick.threads;
     b->cg_blocks = pick_blocks;
     return ESDC_OK;
+}
+
+int esdc_interp(const double* src, int Ms, int64_t src_ld, double* dst, int Md, int64_t dst_ld, int n_state,
+                int64_t n_cols, const double* W, double beta, void* stream)
+{
+    if (!src || !dst || !W || Ms < 1 || Md < 1 || Ms > ESDC_MMAX || Md > ESDC_MMAX || n_state < 1 || n_cols < 0 ||
+        src_ld < n_cols || dst_ld < n_cols || !std::isfinite(beta))
+        return ESDC_ERR_INVALID_ARG;
+    if (n_cols == 0) return ESDC_OK;
+    if (src == dst) return ESDC_ERR_INVALID_ARG;              // rows are read before they are written, per column only
+    InterpArgs a{};
+    a.src = src; a.dst = dst; a.sld = src_ld; a.dld = dst_ld; a.ncols = n_cols;
+    a.Ms = Ms; a.Md = Md; a.ns = n_state; a.beta = beta;
+    for (int i = 0; i < Md; ++i)
+        for (int j = 0; j < Ms; ++j) {
+            if (!std::isfinite(W[i * Ms + j])) return ESDC_ERR_INVALID_ARG;
+            a.W[i][j] = W[i * Ms + j];
+        }
+    const long long nb = std::min<long long>((n_cols + 255) / 256, 152LL * 8);
+    k_interp<<<(int)nb, 256, 0, (cudaStream_t)stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ESDC_OK : ESDC_ERR_CUDA;
+}
+
+int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double* y_out, double t0, double dt, int M1,
+               int M2, int iters, void* stream)
+{
+    if (!fine || !coarse || !y_in || !y_out || y_in == y_out || iters < 1 || M2 < 1 || M2 >= M1 ||
+        M1 > fine->opt.M_max)
+        return fine ? set_berr(fine, ESDC_ERR_INVALID_ARG, "bad two-level arguments") : ESDC_ERR_INVALID_ARG;
+    // Lagrange matrices between the Radau nodes c_1..c_M of the two levels
+    // (Sec. 3.2: I_l(y, s) = sum_j l_j(s) y_j): restriction S [M2][M1], prolongation T [M1][M2]
+    const double* cf = fine->col[M1 - 1].c + 1;
+    const double* cc = fine->col[M2 - 1].c + 1;
+    auto lagrange = [](const double* nodes, int n, const double* pts, int m, double* W) {
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double l = 1.0;
+                for (int k = 0; k < n; ++k)
+                    if (k != j) l *= (pts[i] - nodes[k]) / (nodes[j] - nodes[k]);
+                W[i * n + j] = l;
+            }
+    };
+    std::vector<double> Rv((size_t)M2 * M1), Tv((size_t)M1 * M2);
+    lagrange(cf, M1, cc, M2, Rv.data());
+    lagrange(cc, M2, cf, M1, Tv.data());
+    const double* Rmat = Rv.data();
+    const double* Tmat = Tv.data();
+    const int P = fine->ntis, NSt = fine->NS;
+    const TissueDev& T0 = fine->tis_h[0];
+    for (const TissueDev& T : fine->tis_h)
+        if (T.nx != T0.nx || T.ny != T0.ny || T.nz != T0.nz || T.D != T0.D || T.ih2 != T0.ih2)
+            return set_berr(fine, ESDC_ERR_INVALID_ARG, "slices must share mesh and conductivity");
+    const int64_t slice = (int64_t)T0.ntile * ESDC_TILE, ldf = fine->ld;
+    for (int p = 0; p < P; ++p) {
+        const esdc_batch* c = coarse[p];
+        if (!c || c->ntis != 1 || c->ld != slice || c->NS != NSt || c->opt.M_max < M2 || c->tis_h[0].N != T0.N ||
+            c->tis_h[0].D != T0.D || c->tis_h[0].ih2 != T0.ih2)
+            return set_berr(fine, ESDC_ERR_INVALID_ARG, "coarse level: one single-slice batch per slice, same mesh");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t pitchf = sizeof(double) * ldf, pitchc = sizeof(double) * slice;
+    const int64_t rowsf = (int64_t)NSt * ldf, rowsc = (int64_t)NSt * slice;
+    // scratch: per slice SZ, tau, y_in, y_out of the coarse level; a time per slice
+    struct Scratch {
+        std::vector<void*> p;
+        ~Scratch() { for (void* q : p) cudaFree(q); }
+    } sc;
+    auto alloc = [&](double** q, int64_t n) {
+        if (cudaMalloc((void**)q, sizeof(double) * n) != cudaSuccess) return false;
+        sc.p.push_back(*q);
+        return true;
+    };
+    double *SZ = nullptr, *TAU = nullptr, *YIC = nullptr, *YOC = nullptr, *ytmp = nullptr;
+    if (!alloc(&SZ, (int64_t)P * M2 * rowsc) || !alloc(&TAU, (int64_t)P * M2 * rowsc) || !alloc(&YIC, rowsc) ||
+        !alloc(&YOC, (int64_t)P * rowsc) || !alloc(&ytmp, rowsf))
+        return set_berr(fine, ESDC_ERR_NO_MEMORY, "two-level scratch");
+    std::vector<double> tf(P);
+    for (int p = 0; p < P; ++p) tf[p] = t0 + p * dt;
+    std::vector<double> I2(M2 * M2, 0.0), Ip(M2 * M2, 0.0);     // -I and +I
+    for (int i = 0; i < M2; ++i) { I2[i * M2 + i] = -1.0; Ip[i * M2 + i] = 1.0; }
+    // the calls below alternate between kinds of step: record no graphs
+    struct GraphsOff {
+        esdc_batch* const* c;
+        esdc_batch* f;
+        int P;
+        bool fg;
+        std::vector<char> cg;
+        GraphsOff(esdc_batch* f_, esdc_batch* const* c_, int P_) : c(c_), f(f_), P(P_), fg(f_->use_graph), cg(P_)
+        {
+            f->use_graph = false;
+            for (int p = 0; p < P; ++p) { cg[p] = c[p]->use_graph; c[p]->use_graph = false; }
+        }
+        ~GraphsOff()
+        {
+            f->use_graph = fg;
+            for (int p = 0; p < P; ++p) c[p]->use_graph = cg[p] != 0;
+        }
+    } graphs_off(fine, coarse, P);
+    double *Yf = nullptr, *Rf = nullptr;
+    int rc;
+    // z^0 = 1 (x) y0 in every slice: y_in[p] = y0, Y_j = y0
+    for (int p = 1; p < P; ++p)
+        if (cudaMemcpy2DAsync(y_in + p * slice, pitchf, y_in, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+            return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
+    // a K = 0 call allocates the residual buffer and gives the iterate pointers
+    if ((rc = esdc_batch_sweep_ex(fine, y_in, ytmp, nullptr, tf.data(), dt, M1, 0, 1, 1, stream)) != ESDC_OK) return rc;
+    esdc_batch_iterate(fine, &Yf, &Rf);
+    for (int j = 0; j < M1; ++j)
+        if (cudaMemcpyAsync(Yf + (int64_t)j * rowsf, y_in, sizeof(double) * rowsf, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+            return set_berr(fine, ESDC_ERR_CUDA, "spread failed");
+    for (int k = 0; k < iters; ++k) {
+        // fine residual vectors at the iterate
+        if ((rc = esdc_batch_sweep_ex(fine, y_in, ytmp, nullptr, tf.data(), dt, M1, 0, 1, 1, stream)) != ESDC_OK)
+            return rc;
+        for (int p = 0; p < P; ++p) {
+            esdc_batch* c = coarse[p];
+            double *Yc = nullptr, *Rc = nullptr;
+            double* SZp = SZ + (int64_t)p * M2 * rowsc;
+            double* TAUp = TAU + (int64_t)p * M2 * rowsc;
+            const double tp = tf[p];
+            // S z: restriction of the fine iterate, into the coarse iterate and a copy
+            if ((rc = esdc_interp(Yf + p * slice, M1, ldf, SZp, M2, slice, NSt, slice, Rmat, 0.0, stream)) != ESDC_OK)
+                return set_berr(fine, rc, "restriction failed");
+            // y_{p,0} of the slice in the coarse layout
+            if (cudaMemcpy2DAsync(YIC, pitchc, y_in + p * slice, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+                return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
+            esdc_batch_iterate(c, &Yc, nullptr);
+            if (cudaMemcpyAsync(Yc, SZp, sizeof(double) * M2 * rowsc, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return set_berr(fine, ESDC_ERR_CUDA, "iterate copy failed");
+            // coarse residual at S z, then tau = S R_1 - R_2
+            if ((rc = esdc_batch_sweep_ex(c, YIC, YOC + p * rowsc, nullptr, &tp, dt, M2, 0, 1, 1, stream)) != ESDC_OK)
+                return rc;
+            esdc_batch_iterate(c, nullptr, &Rc);
+            if ((rc = esdc_interp(Rf + p * slice, M1, ldf, TAUp, M2, slice, NSt, slice, Rmat, 0.0, stream)) != ESDC_OK ||
+                (rc = esdc_interp(Rc, M2, slice, TAUp, M2, slice, NSt, slice, I2.data(), 1.0, stream)) != ESDC_OK)
+                return set_berr(fine, rc, "tau failed");
+        }
+        // coarse Q^seq sweep: slice p starts from the new end value of slice p-1
+        for (int p = 0; p < P; ++p) {
+            esdc_batch* c = coarse[p];
+            double *Yc = nullptr, *Rc = nullptr;
+            esdc_batch_iterate(c, &Yc, &Rc);
+            const double* src = p == 0 ? y_in : nullptr;
+            if (p == 0) {
+                if (cudaMemcpy2DAsync(YIC, pitchc, src, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
+            } else if (cudaMemcpyAsync(YIC, YOC + (p - 1) * rowsc, sizeof(double) * rowsc, cudaMemcpyDeviceToDevice, s) !=
+                       cudaSuccess) {
+                return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
+            }
+            if (cudaMemcpyAsync(Yc, SZ + (int64_t)p * M2 * rowsc, sizeof(double) * M2 * rowsc, cudaMemcpyDeviceToDevice,
+                                s) != cudaSuccess)
+                return set_berr(fine, ESDC_ERR_CUDA, "iterate copy failed");
+            const double tp = tf[p];
+            if ((rc = esdc_batch_sweep_ex(c, YIC, YOC + p * rowsc, TAU + (int64_t)p * M2 * rowsc, &tp, dt, M2, 1, 1, 0,
+                                          stream)) != ESDC_OK)
+                return rc;
+            // coarse-grid correction of the fine iterate: z += T (z_2 - S z)
+            double* SZp = SZ + (int64_t)p * M2 * rowsc;
+            if ((rc = esdc_interp(Yc, M2, slice, SZp, M2, slice, NSt, slice, Ip.data(), -1.0, stream)) != ESDC_OK ||
+                (rc = esdc_interp(SZp, M2, slice, Yf + p * slice, M1, ldf, NSt, slice, Tmat, 1.0, stream)) != ESDC_OK)
+                return set_berr(fine, rc, "correction failed");
+        }
+        // fine Q^par sweep from the corrected iterate: y_{p,0} = its end value in slice p-1
+        if (P > 1 && cudaMemcpy2DAsync(y_in + slice, pitchf, Yf + (int64_t)(M1 - 1) * rowsf, pitchf,
+                                       sizeof(double) * slice * (P - 1), NSt, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return set_berr(fine, ESDC_ERR_CUDA, "slice shift failed");
+        if ((rc = esdc_batch_sweep_ex(fine, y_in, y_out, nullptr, tf.data(), dt, M1, 1, 1, 0, stream)) != ESDC_OK)
+            return rc;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? ESDC_OK : set_berr(fine, ESDC_ERR_CUDA, "two-level run failed");
 }
 
 }  // extern "C"

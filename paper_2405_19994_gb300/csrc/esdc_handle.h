@@ -38,6 +38,7 @@ struct StepArgs {
     const TissueDev* tis;
     const int* tile_tissue;     // [tiles] tissue of each tile
     const unsigned* tis_on;     // [tissues][ESDC_MMAX + 1] stimulus window bits per collocation time
+    const double* tau;          // FAS correction [M][NS][ld] (batched kernels; nullptr: none)
 };
 
 struct esdc_handle {

@@ -299,7 +299,9 @@ __global__ void __launch_bounds__(128) k_setup(StepArgs a)
 #ifndef ESDC_NODE_MINBLOCKS
 #define ESDC_NODE_MINBLOCKS 5      // 5 x 128 threads per SM: at most 102 registers
 #endif
-template <class Model, int M, bool MIXED>
+// TAU: batched kernels may add the FAS correction tau (a.tau, rows 1..M; the
+// recursive form adds tau_i - tau_{i-1}, tau_0 = 0, to every row of node i).
+template <class Model, int M, bool MIXED, bool TAU = false>
 __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
                                           const unsigned* on, double D, int p, int ix, int iy, int iz)
 {
@@ -310,6 +312,11 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
     const bool quad = i <= M;                 // explicit rows of y_i^{k+1}
     const int jm = i - 2;                     // 0-based index of node i-1
     const int ii = i - 1;                     // 0-based index of node i
+    auto dtau = [&](int s) -> double {
+        if (!TAU || !a.tau) return 0.0;
+        const double t1 = a.tau[((int64_t)ii * NS + s) * ld + p];
+        return ii > 0 ? t1 - a.tau[((int64_t)(ii - 1) * NS + s) * ld + p] : t1;
+    };
     const double* src = eval ? a.Y + (int64_t)jm * NS * ld : a.yn;   // y_{i-1}^{k+1}
     double u[NS];
 #pragma unroll
@@ -354,14 +361,14 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
         double q = u[0];
 #pragma unroll
         for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
-        a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
+        a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q) + dtau(0);
 #pragma unroll
         for (int s = 1; s <= NA; ++s) {
             const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
             double qa = u[s];
 #pragma unroll
             for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
-            Yi[s * ld + p] = fma(dtd, dl, qa);
+            Yi[s * ld + p] = fma(dtd, dl, qa) + dtau(s);
         }
     }
     // ---- gates, one at a time
@@ -388,7 +395,7 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
             for (int j = 0; j < M; ++j)
                 qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
                          a.Gold[((int64_t)j * NS + s) * ld + p], qg);
-            Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
+            Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg) + dtau(s);
         }
     }
 }
@@ -404,7 +411,7 @@ __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
         } else {
             BatchNode n;
             if (!batch_node(a, p, n)) continue;
-            node_body<Model, M, MIXED>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+            node_body<Model, M, MIXED, true>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
         }
     }
 }
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
 // One state s of one node: the residual recursion over the M nodes, the
 // largest |r_i| and |y| (y_n included), and y_{n+1} = y_{n,M} (c_M = 1).
 // Returns false if a residual or iterate is not finite.
-template <class Model, int M>
+template <class Model, int M, bool TAU = false>
 __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, double& rmax, double& ymax)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
@@ -438,6 +445,8 @@ __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, 
         }
         const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
         r += q - (yi - yprev);
+        if (TAU && a.tau)
+            r += a.tau[((int64_t)i * NS + s) * ld + p] - (i > 0 ? a.tau[((int64_t)(i - 1) * NS + s) * ld + p] : 0.0);
         yprev = yi;
         if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
         ok &= isfinite(r) && isfinite(yi);

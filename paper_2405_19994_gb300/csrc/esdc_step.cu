@@ -445,7 +445,7 @@ int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, voi
     CUDA_TRY(h, cudaMemsetAsync(h->rmax, 0, sizeof(unsigned long long) * 2 * ESDC_NSMAX, s));
     CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, sizeof(int), s));
     CUDA_TRY(h, cudaMemsetAsync(h->cg_log, 0, sizeof(int) * h->cg_log_len, s));
-    StepArgs a;
+    StepArgs a{};
     std::memset(&a, 0, sizeof a);
     a.m = h->mesh; a.st = h->stim; a.mp = h->mp; a.mpf = h->mpf;
     a.dt = dt; a.t_n = t; a.D = h->D; a.inv_Cm = 1.0 / h->Cm;

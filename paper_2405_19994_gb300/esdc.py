@@ -93,6 +93,11 @@ def lib() -> C.CDLL:
             "esdc_batch_residual": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D)]),
             "esdc_batch_sweep_from": (C.c_int, [_VP, _VP, _VP, C.POINTER(_D), _D, C.c_int, C.c_int, C.c_int, _VP]),
             "esdc_batch_qpar": (C.c_int, [_VP, _VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
+            "esdc_batch_sweep_ex": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(_D), _D, C.c_int, C.c_int, C.c_int, C.c_int,
+                                              _VP]),
+            "esdc_batch_iterate": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP)]),
+            "esdc_interp": (C.c_int, [_VP, C.c_int, _I64, _VP, C.c_int, _I64, C.c_int, _I64, C.POINTER(_D), _D, _VP]),
+            "esdc_hsdc2": (C.c_int, [_VP, C.POINTER(_VP), _VP, _VP, _D, _D, C.c_int, C.c_int, C.c_int, _VP]),
             "esdc_batch_stats": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
             "esdc_batch_set_graph": (C.c_int, [_VP, C.c_int]),
             "esdc_batch_graph_active": (C.c_int, [_VP]),
@@ -402,6 +407,14 @@ class Batch:
         """Q^par iterations over the batch's tissues as time slices (esdc_batch_qpar)."""
         self._check(lib().esdc_batch_qpar(self._b, _ptr(y_in), _ptr(y_out), t0, dt, M, iters, _stream(stream)))
 
+    def iterate(self, M: int):
+        """The batch's collocation iterate y_{n,1..M} as a tensor view [M, n_state, ld] (device memory
+        owned by the batch)."""
+        import torch
+        Y = _VP()
+        self._check(lib().esdc_batch_iterate(self._b, C.byref(Y), None))
+        return _device_view(Y.value, (M, self.n_state, self.ld))
+
     def residual(self):
         """(return code, res_inf[n], y_inf[n]); does not raise on solver flags."""
         r = np.zeros(self.n)
@@ -438,6 +451,27 @@ class Batch:
         """View of tissue b's columns of a batch state."""
         o = int(self.offsets[b])
         return y[:, o:o + int(self.n_nodes[b])]
+
+
+def _device_view(ptr: int, shape):
+    """A float64 CUDA tensor viewing library-owned device memory (no copy)."""
+    import torch
+
+    class _Arr:
+        pass
+    a = _Arr()
+    n = int(np.prod(shape))
+    a.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (int(ptr), False), "version": 2,
+                                  "strides": None}
+    return torch.as_tensor(a, device="cuda").view(*shape)
+
+
+def hsdc2(fine: "Batch", coarse, y_in, y_out, t0: float, dt: float, M1: int, M2: int, iters: int, stream=None):
+    """Two-level Algorithm HSDC over the fine batch's tissues as time slices
+    (esdc_hsdc2); coarse is a list of single-tissue batches, one per slice."""
+    arr = (_VP * len(coarse))(*[c._b for c in coarse])
+    rc = lib().esdc_hsdc2(fine._b, arr, _ptr(y_in), _ptr(y_out), t0, dt, M1, M2, iters, _stream(stream))
+    fine._check(rc)
 
 
 def sensor_traces(solver: "Solver", sigma, g_na, g_k, y0, t0: float, dt: float, M: int, K: int, nsteps: int, sens):

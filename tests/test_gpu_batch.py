@@ -240,3 +240,75 @@ def test_qpar_one_slice_is_k_sweeps_of_the_step():
     got = b.tissue(yout, 0).cpu().numpy()
     assert np.abs(got[0] - want[0]).max() < 1e-12 * np.abs(want[0]).max()
     b.close()
+
+
+# ---------------------------------------------------------------- FAS: tau-corrected sweeps, two-level Algorithm HSDC
+
+def test_sweep_with_tau_matches_oracle():
+    w, m, y0, t0 = qpar_setup(1)
+    M = w.M
+    rng = np.random.default_rng(17)
+    _, _, col, _ = m.step(y0, t0, w.dt, M, 2, want_colloc=True)
+    tau = 1e-3 * rng.normal(size=col.shape) * np.abs(col).max(axis=(0, 2), keepdims=True)
+    b = P.Batch.from_workloads([w], M_max=M)
+    yin, yout = b.new_state(), b.new_state()
+    b.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    Y = b.iterate(M)
+    for j in range(M):
+        Y[j, :, :w.n_nodes] = torch.from_numpy(col[j])
+    td = torch.zeros((M, b.n_state, b.ld), dtype=torch.float64, device="cuda")
+    td[:, :, :w.n_nodes] = torch.from_numpy(tau)
+    tv = np.array([t0])
+    P.lib().esdc_batch_sweep_ex(b._b, yin.data_ptr(), yout.data_ptr(), td.data_ptr(),
+                                tv.ctypes.data_as(E_D()), w.dt, M, 2, 1, 0, torch.cuda.current_stream().cuda_stream)
+    assert b.residual()[0] == 0
+    want, _, wcol, _ = m.step(y0, t0, w.dt, M, 2, want_colloc=True, colloc_in=col, tau=tau)
+    got = b.iterate(M)[:, :, :w.n_nodes].cpu().numpy()
+    assert np.abs(got - wcol).max() < 1e-12 * np.abs(wcol).max()
+    b.close()
+
+
+def E_D():
+    import ctypes
+    return ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+def test_hsdc2_matches_oracle(iters):
+    P_, M1, M2 = 4, 3, 2
+    w, m, y0, t0 = qpar_setup(P_)
+    fine = P.Batch.from_workloads([w] * P_, M_max=M1)
+    coarse = [P.Batch.from_workloads([w], M_max=M2) for _ in range(P_)]
+    yin, yout = fine.new_state(), fine.new_state()
+    fine.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    P.esdc.hsdc2(fine, coarse, yin, yout, t0, w.dt, M1, M2, iters)
+    assert fine.residual()[0] == 0
+    Z = m.hsdc2(y0, t0, w.dt, P_, M1, M2, iters)
+    Y = fine.iterate(M1)
+    for p in range(P_):
+        o = int(fine.offsets[p])
+        got = Y[:, :, o:o + w.n_nodes].cpu().numpy()
+        assert np.abs(got - Z[p]).max() < 1e-12 * np.abs(Z[p]).max(), p
+        assert np.array_equal(fine.tissue(yout, p).cpu().numpy(), got[M1 - 1]), p
+    for c in coarse:
+        c.close()
+    fine.close()
+
+
+def test_hsdc2_converges_to_sequential_collocation():
+    P_, M1, M2 = 4, 3, 2
+    w, m, y0, t0 = qpar_setup(P_)
+    fine = P.Batch.from_workloads([w] * P_, M_max=M1)
+    coarse = [P.Batch.from_workloads([w], M_max=M2) for _ in range(P_)]
+    yin, yout = fine.new_state(), fine.new_state()
+    fine.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    P.esdc.hsdc2(fine, coarse, yin, yout, t0, w.dt, M1, M2, 14)
+    y, t = y0, t0
+    for p in range(P_):
+        yn, _, col, _ = m.step(y, t, w.dt, M1, 60, want_colloc=True)
+        got = fine.tissue(yout, p).cpu().numpy()
+        assert np.abs(got - yn).max() < 1e-11 * np.abs(yn).max(), p
+        y, t = yn, t + w.dt
+    for c in coarse:
+        c.close()
+    fine.close()
