@@ -36,14 +36,14 @@ UNIT = "node-updates/s"
 #  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
 #  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu
 #  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep:
-#  191.0 + 3 x 1200.7 + 988.7 = 4781.8 flops per node per sweep
+#  191.0 + 3 x 1201.7 + 989.7 = 4785.8 flops per node per sweep
 #  (profiles/k_node_syn19_slab_128x128x16.md).
 #  Algorithmic bytes per node: node 1 reads 158 / writes 20 doubles, nodes 2..M
 #  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep, 1493 B per launch
-#  on average; DRAM traffic measured by ncu: 7045 B per sweep (1409 B per launch).
+#  on average; DRAM traffic measured by ncu: 7044 B per sweep (1409 B per launch).
 #  cg (per mesh node and iteration): [A] z (stencil), p, q -> p, q;
 #  [B] q, r, x, p -> x, r, z: 12 doubles = 96 B, plus 8 doubles per solve.
-NODE_FLOPS_PER_SWEEP = {4: 4781.8}
+NODE_FLOPS_PER_SWEEP = {4: 4785.8}
 NODE_BYTES_PER_LAUNCH = {4: 1493}
 NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {4: 1409}
 CG_BYTES_PER_NODE_ITER = 96
@@ -777,6 +777,111 @@ def run_adjoint_form(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fas_form(args):
+    """Algorithm HSDC with two levels (M = 3, 2) against single-level Q^par
+    (M = 3) on P = 16 consecutive steps of the 512 x 512 HH sheet (corner
+    stimulus, dt = 0.025 ms): the error of the last slice's end value against
+    the sequential collocation solution after each iteration, and the time per
+    iteration, both on the GPU."""
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1 and rank != 0:
+        return
+    n = args.nz if args.nz else 512
+    w = I.hh_sheet_32().with_mesh(n, n, 1, name=f"hh_sheet_{n}")
+    Pn, M1, M2, dt = 16, 3, 2, w.dt
+    iters = args.steps if args.steps is not None else 10
+    stream = torch.cuda.current_stream()
+    # state at t0 = 0.4 ms: inside the stimulus window, the upstroke under way
+    one = P.Batch.from_workloads([w], M_max=M1)
+    y0 = one.new_state()
+    one.init_state(y0, w.V0)
+    t0 = 0.0
+    for _ in range(16):
+        one.sweep(y0, t0, dt, M1, w.K)
+        t0 += dt
+    # sequential collocation reference: P steps with 40 sweeps each
+    yref = y0.clone()
+    t = t0
+    for _ in range(Pn):
+        one.sweep(yref, t, dt, M1, 40)
+        t += dt
+    if one.residual()[0] != 0:
+        raise RuntimeError("reference run failed")
+    ref = yref[0, :w.n_nodes].clone()
+
+    fine = P.Batch.from_workloads([w] * Pn, M_max=M1)
+    coarse = [P.Batch.from_workloads([w], M_max=M2) for _ in range(Pn)]
+    yin, yout = fine.new_state(), fine.new_state()
+    last = int(fine.offsets[Pn - 1])
+
+    def err():
+        v = yout[0, last:last + w.n_nodes]
+        return float((v - ref).abs().max() / ref.abs().max())
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def load():
+        yin.zero_()
+        fine.tissue(yin, 0).copy_(y0[:, :w.n_nodes])
+
+    out = {"hsdc2": [], "qpar": []}
+    for k in range(1, iters + 1):
+        load()
+        ms = timed(lambda: P.esdc.hsdc2(fine, coarse, yin, yout, t0, dt, M1, M2, k))
+        out["hsdc2"].append({"iters": k, "ms": ms, "err": err()})
+        load()
+        ms = timed(lambda: fine.qpar(yin, yout, t0, dt, M1, k))
+        if fine.residual()[0] != 0:
+            raise RuntimeError("Q^par failed")
+        out["qpar"].append({"iters": k, "ms": ms, "err": err()})
+    # Q^par needs up to P iterations to carry y0 across all slices: extend it
+    for k in (Pn, Pn + 4, Pn + 8, Pn + 12):
+        load()
+        ms = timed(lambda: fine.qpar(yin, yout, t0, dt, M1, k))
+        out["qpar"].append({"iters": k, "ms": ms, "err": err()})
+
+    def first_below(rows, tol):
+        for r in rows:
+            if r["err"] < tol:
+                return r
+        return None
+    tol = 1e-8
+    h, q = first_below(out["hsdc2"], tol), first_below(out["qpar"], tol)
+    h6, q6 = first_below(out["hsdc2"], 1e-6), first_below(out["qpar"], 1e-6)
+    nodes = Pn * w.n_nodes
+    line = {
+        "metric": METRIC, "value": (nodes / (h["ms"] * 1e-3)) if h else None, "unit": UNIT, "n_gpus": 1,
+        "steps": Pn, "warmup": 0, "ms_per_step": (h["ms"] / Pn) if h else None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"hh_sheet_{n} (corner stimulus), P=16 slices from t0={t0:.2f} ms",
+                   "form": "fas", "levels": [M1, M2], "dt_ms": dt,
+                   "value_is": "node-updates/s of the two-level solve to 1e-8 relative error of the last slice"},
+        "tolerance": tol,
+        "hsdc2_to_tol": h, "qpar_to_tol": q,
+        "speedup_hsdc2_vs_qpar_to_tol": (q["ms"] / h["ms"]) if (h and q) else None,
+        "hsdc2_to_1e-6": h6, "qpar_to_1e-6": q6,
+        "speedup_hsdc2_vs_qpar_to_1e-6": (q6["ms"] / h6["ms"]) if (h6 and q6) else None,
+        "history": out,
+    }
+    for c in coarse:
+        c.close()
+    fine.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -788,10 +893,11 @@ def main():
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
-    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint"], default="plain",
+    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas"], default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
                          "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "
-                         "adjoint: forward + discrete adjoint on the 256x256 HH conductivity-field sheet")
+                         "adjoint: forward + discrete adjoint on the 256x256 HH conductivity-field sheet; "
+                         "fas: two-level Algorithm HSDC against Q^par on 16 slices of the 512x512 HH sheet")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -805,6 +911,8 @@ def main():
         run_batch_form(args)
     elif args.form == "adjoint":
         run_adjoint_form(args)
+    elif args.form == "fas":
+        run_fas_form(args)
     else:
         run_ours(args)
 

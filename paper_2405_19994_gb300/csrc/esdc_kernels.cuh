@@ -361,14 +361,18 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
         double q = u[0];
 #pragma unroll
         for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
-        a.rhs[p] = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q) + dtau(0);
+        double rv = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
+        if (TAU) rv += dtau(0);                // (x + 0.0 is not x in IEEE arithmetic: no add without TAU)
+        a.rhs[p] = rv;
 #pragma unroll
         for (int s = 1; s <= NA; ++s) {
             const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
             double qa = u[s];
 #pragma unroll
             for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
-            Yi[s * ld + p] = fma(dtd, dl, qa) + dtau(s);
+            double ya = fma(dtd, dl, qa);
+            if (TAU) ya += dtau(s);
+            Yi[s * ld + p] = ya;
         }
     }
     // ---- gates, one at a time
@@ -395,7 +399,9 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
             for (int j = 0; j < M; ++j)
                 qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
                          a.Gold[((int64_t)j * NS + s) * ld + p], qg);
-            Yi[s * ld + p] = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg) + dtau(s);
+            double yg = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
+            if (TAU) yg += dtau(s);
+            Yi[s * ld + p] = yg;
         }
     }
 }
