@@ -113,6 +113,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, pg=None) -> float:
+    """The slowest rank's time: every rank passes its own, all get the maximum."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank: float, world_size: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world_size / (ms * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,11 +229,8 @@ def run_ours(args):
     cg_iters = solver.stats(K * M).tolist()
     if rc != 0:
         raise RuntimeError(f"timed step failed with code {rc}")
-    if pg:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = N * args.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(ms, pg)
+    value = aggregate_value(N * args.steps, ws, ms)
     ms_step = ms / args.steps
 
     # ---- end to end: the same steps through the host-buffer entry point (H2D + step + D2H)
