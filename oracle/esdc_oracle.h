@@ -129,6 +129,12 @@ typedef struct {
     /* Heterogeneous isotropic conductivity (NULL: sigma): one value per node,
      * [N] mS/mm; the flux through a face uses the mean of its two nodes. */
     const double* sig_node;
+    /* Order of the Laplacian: 2 (3-/5-/7-point, default; 0 means 2) or 4
+     * (the paper's fourth-order differences, Sec. 5: per axis
+     * (-v_{i-2} + 16 v_{i-1} - 30 v_i + 16 v_{i+1} - v_{i+2}) / (12 h^2) with
+     * mirrored ghost cells, repeated for axes shorter than the stencil).
+     * Order 4 needs the scalar sigma. */
+    int order;
     /* private workspace, owned by the oracle */
     void*  work;
 } orc_mono;
@@ -150,8 +156,10 @@ void orc_ionic_rest(int model, const double* mp, double V0, double* u);
 void orc_ionic_point(int model, const double* mp, const double* u,
                      double* fE, double* lam, double* yinf);
 
-/* Discrete Neumann Laplacian (5-/7-point, cell-centred, mirror ghosts):
- * out = (1/h^2) sum_{q in nbr(p)} (v_q - v_p).  (Sec. 2.2) */
+/* Discrete Neumann Laplacian (cell-centred, mirror ghosts).  Order 2:
+ * out = (1/h^2) sum_{q in nbr(p)} (v_q - v_p) (5-/7-point).  Order 4: the
+ * five-point fourth-order difference along every axis (see orc_mono.order).
+ * Both are diagonalised by DCT-II, so ORC_SOLVE_DCT is exact for both. (Sec. 2.2) */
 void orc_laplacian(const orc_mono* m, const double* v, double* out);
 /* Solve (I - g L) x = b with L the Laplacian above, by the chosen method. */
 int  orc_solve_shifted(const orc_mono* m, int method, double g, const double* b, double* x);

@@ -53,7 +53,7 @@ class _Mono(C.Structure):
                 ("solver", C.c_int), ("cg_tol", C.c_double), ("cg_maxit", C.c_int),
                 ("ionic_off", C.c_int), ("lay_sxx", C.c_void_p), ("lay_syy", C.c_void_p),
                 ("lay_sxy", C.c_void_p), ("lay_szz", C.c_void_p), ("sig_node", C.c_void_p),
-                ("work", C.c_void_p)]
+                ("order", C.c_int), ("work", C.c_void_p)]
 
 
 _D = C.POINTER(C.c_double)
@@ -215,7 +215,7 @@ class Monodomain:
         self.m = _Mono(wl.dim, wl.nx, wl.ny, wl.nz, wl.h, wl.sigma, wl.chi, wl.Cm, wl.model,
                        mp.ctypes.data, len(mp), len(amp), box.ctypes.data, amp.ctypes.data,
                        ton.ctypes.data, toff.ctypes.data, solver, cg_tol, cg_maxit, int(ionic_off),
-                       lay[0], lay[1], lay[2], lay[3], fptr, None)
+                       lay[0], lay[1], lay[2], lay[3], fptr, int(getattr(wl, "order", 2)), None)
         self.P = _Problem()
         if lib().orc_mono_problem(C.byref(self.m), C.byref(self.P)):
             raise ValueError("invalid monodomain description")

@@ -30,10 +30,38 @@
 
 static int64_t mesh_n(const orc_mono* m) { return (int64_t)m->nx * m->ny * m->nz; }
 
+/* Index of the cell that a (possibly ghost) index j of an axis of n cells
+ * mirrors: reflection about the outer faces, repeated while outside. */
+static int mirror(int j, int n)
+{
+    while (j < 0 || j >= n) j = j < 0 ? -j - 1 : 2 * n - 1 - j;
+    return j;
+}
+
+/* (-v_{i-2} + 16 v_{i-1} - 30 v_i + 16 v_{i+1} - v_{i+2}) along one axis (axes of one cell contribute 0). */
+static double axis4(const double* v, int64_t p, int i, int n, int64_t stride)
+{
+    if (n == 1) return 0.0;
+    const double a = v[p + (int64_t)(mirror(i - 2, n) - i) * stride], b = v[p + (int64_t)(mirror(i - 1, n) - i) * stride];
+    const double c = v[p + (int64_t)(mirror(i + 1, n) - i) * stride], d = v[p + (int64_t)(mirror(i + 2, n) - i) * stride];
+    return -a + 16.0 * b - 30.0 * v[p] + 16.0 * c - d;
+}
+
 void orc_laplacian(const orc_mono* m, const double* v, double* out)
 {
     const int nx = m->nx, ny = m->ny, nz = m->nz;
     const double ih2 = 1.0 / (m->h * m->h);
+    if (m->order == 4) {
+        const int64_t sy = nx, sz = (int64_t)nx * ny;
+        #pragma omp parallel for schedule(static)
+        for (int iz = 0; iz < nz; ++iz)
+            for (int iy = 0; iy < ny; ++iy)
+                for (int ix = 0; ix < nx; ++ix) {
+                    int64_t p = ix + sy * iy + sz * iz;
+                    out[p] = (axis4(v, p, ix, nx, 1) + axis4(v, p, iy, ny, sy) + axis4(v, p, iz, nz, sz)) * ih2 / 12.0;
+                }
+        return;
+    }
     #pragma omp parallel for schedule(static)
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
@@ -147,6 +175,18 @@ static void dct_axis(const orc_mono* m, int axis, int transpose, const double* T
     }
 }
 
+/* Eigenvalue of the 1D operator on cosine mode k of n cells, theta = pi k / n:
+ * order 2: -(4/h^2) sin^2(theta/2); order 4: (32 cos theta - 2 cos 2 theta - 30)/(12 h^2)
+ * (the stencil's symbol; the mirrored extension of a cosine mode is the mode itself). */
+static double axis_eig(int order, int k, int n, double h2)
+{
+    if (n == 1) return 0.0;
+    const double th = M_PI * k / n;
+    if (order == 4) return (32.0 * cos(th) - 2.0 * cos(2.0 * th) - 30.0) / (12.0 * h2);
+    const double s = sin(0.5 * th);
+    return -(4.0 / h2) * s * s;
+}
+
 static int solve_dct(const orc_mono* m, double g, const double* b, double* x)
 {
     const int nx = m->nx, ny = m->ny, nz = m->nz;
@@ -160,12 +200,11 @@ static int solve_dct(const orc_mono* m, double g, const double* b, double* x)
     dct_axis(m, 2, 0, Tz, x);
     const double h2 = m->h * m->h;
     for (int iz = 0; iz < nz; ++iz) {
-        double sz = sin(M_PI * iz / (2.0 * nz));
+        const double mz = axis_eig(m->order, iz, nz, h2);
         for (int iy = 0; iy < ny; ++iy) {
-            double sy = sin(M_PI * iy / (2.0 * ny));
+            const double my = axis_eig(m->order, iy, ny, h2);
             for (int ix = 0; ix < nx; ++ix) {
-                double sx = sin(M_PI * ix / (2.0 * nx));
-                double mu = -(4.0 / h2) * (sx * sx + sy * sy + sz * sz);
+                double mu = axis_eig(m->order, ix, nx, h2) + my + mz;
                 x[ix + (int64_t)nx * (iy + (int64_t)ny * iz)] /= (1.0 - g * mu);
             }
         }

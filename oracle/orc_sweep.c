@@ -281,6 +281,8 @@ int orc_mono_problem(orc_mono* m, orc_problem* P)
     if (m->dim < 1 || m->dim > 3 || m->nx < 1 || m->ny < 1 || m->nz < 1 || !(m->h > 0.0)) return -1;
     if (m->model != ORC_HH1952 && m->model != ORC_SYN19) return -1;
     if (m->n_mp < (m->model == ORC_HH1952 ? 7 : 88)) return -1;
+    if (m->order != 0 && m->order != 2 && m->order != 4) return -1;
+    if (m->order == 4 && (m->lay_sxx || m->sig_node)) return -1;   /* fourth order: scalar sigma only */
     P->n = mono_N(m) * orc_mono_nstate(m->model);
     P->ctx = m;
     P->f_I = mono_fI;

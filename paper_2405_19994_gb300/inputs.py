@@ -91,6 +91,8 @@ class Workload:
     layers: dict | None = None
     # heterogeneous isotropic conductivity: one value per node [N] (mS/mm), or None
     sigma_field: np.ndarray | None = None
+    # order of the Laplacian: 2 (3/5/7-point) or 4 (five-point fourth-order differences per axis)
+    order: int = 2
     # stimulus boxes: [x0, x1, y0, y1, z0, z1] node index ranges (half-open)
     boxes: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 6), np.int32))
     amp: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))

@@ -213,3 +213,63 @@ def test_field_solves_agree(orc):
     x_de = m.solve_A(g, b, method=O.SOLVE_DENSE)
     np.testing.assert_allclose(x_cg, x_de, atol=1e-13)
     assert np.abs(x_cg - g * m.conductivity(x_cg) - b).max() < 1e-13
+
+
+# ---------------------------------------------------------------- fourth-order Laplacian (the paper's scheme)
+
+def _mono4(nx, ny, nz, h=0.3, solver=O.SOLVE_DCT):
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.h = h
+    wl.order = 4
+    return O.Monodomain(wl, solver=solver)
+
+
+@pytest.mark.parametrize("shape,k", [((7, 1, 1), (3, 0, 0)), ((6, 5, 1), (2, 4, 0)), ((5, 4, 3), (1, 3, 2)),
+                                     ((2, 3, 1), (1, 2, 0)), ((9, 8, 4), (0, 0, 0))])
+def test_laplacian4_cosine_eigenmodes(orc, shape, k):
+    # cos(pi k (i+1/2)/n) is an eigenvector of the mirrored five-point stencil
+    # with eigenvalue (32 cos t - 2 cos 2t - 30)/(12 h^2), t = pi k/n, per axis
+    nx, ny, nz = shape
+    m = _mono4(nx, ny, nz, h=0.3)
+    v = _mode(nx, ny, nz, *k)
+    mu = sum((32 * np.cos(np.pi * kk / n) - 2 * np.cos(2 * np.pi * kk / n) - 30) / (12 * 0.09) if n > 1 else 0.0
+             for kk, n in zip(k, shape))
+    np.testing.assert_allclose(m.laplacian(v), mu * v, atol=1e-12 * max(1, abs(mu)))
+
+
+def test_laplacian4_symmetric_nsd_constant_nullspace(orc):
+    nx, ny, nz = 6, 4, 3
+    m = _mono4(nx, ny, nz, h=0.5)
+    N = nx * ny * nz
+    L = np.stack([m.laplacian(e) for e in np.eye(N)], axis=1)
+    np.testing.assert_allclose(L, L.T, atol=1e-13)
+    ev = np.linalg.eigvalsh(L)
+    assert ev.max() < 1e-12 and ev[-2] < -1e-3
+    np.testing.assert_allclose(L @ np.ones(N), 0.0, atol=1e-13)
+
+
+def test_laplacian4_fourth_order_consistency(orc):
+    # interior nodes (two cells from the boundary): the error against the exact
+    # Laplacian falls ~16x per halving of h (it is ~4x for the 5-point stencil)
+    errs = []
+    for n, h in ((16, 0.2), (32, 0.1)):
+        ix, iy = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+        x, y = (ix + 0.5) * h, (iy + 0.5) * h
+        f = np.sin(1.3 * x) * np.cos(0.7 * y)
+        m = _mono4(n, n, 1, h=h)
+        got = m.laplacian(f.reshape(-1)).reshape(n, n)
+        errs.append(np.abs(got - (-(1.69 + 0.49) * f))[2:-2, 2:-2].max())
+    assert 13.0 < errs[0] / errs[1] < 19.0, errs
+
+
+@pytest.mark.parametrize("shape", [(12, 1, 1), (9, 7, 1), (6, 5, 4), (2, 3, 2)])
+def test_laplacian4_solvers_agree_and_solve(orc, shape):
+    nx, ny, nz = shape
+    m = _mono4(nx, ny, nz, h=0.25)
+    b = np.random.default_rng(1).normal(size=nx * ny * nz)
+    g = 0.0123
+    xs = [m.solve_shifted(g, b, method=meth) for meth in (O.SOLVE_DCT, O.SOLVE_CG, O.SOLVE_DENSE)]
+    for x in xs:
+        assert np.abs(x - g * m.laplacian(x) - b).max() < 1e-13 * np.abs(b).max()
+    np.testing.assert_allclose(xs[0], xs[2], atol=1e-13)
+    np.testing.assert_allclose(xs[1], xs[2], atol=1e-13)
