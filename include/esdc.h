@@ -132,6 +132,19 @@ int esdc_set_stimulus(esdc_handle* h, int nbox, const int* box, const double* am
  * Errors: INVALID_ARG, NO_MEMORY, CUDA.
  */
 /*
+ * Order of the Laplacian of f_I and of the diffusion solves: 2 (the default
+ * 3-/5-/7-point cell-centred stencil) or 4, the fourth-order differences of
+ * the paper's experiments (Sec. 5): along every axis
+ * (-v_{i-2} + 16 v_{i-1} - 30 v_i + 16 v_{i+1} - v_{i+2}) / (12 h^2), ghost cells
+ * mirrored about the boundary faces (zero flux; the operator stays symmetric
+ * and is diagonalised by DCT-II).  Order 4 needs the scalar sigma and the FP64
+ * path; its solves use the one-node-per-thread CG with Jacobi weights from the
+ * operator's diagonal.  Synchronises the device.
+ * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
+ */
+int esdc_set_stencil_order(esdc_handle* h, int order);
+
+/*
  * Heterogeneous isotropic conductivity: sigma[p] (host array of N values,
  * mS/mm, copied, all positive) at every mesh node.  Replaces the scalar sigma
  * (and any layers) in f_I and in the diffusion solves:

@@ -82,7 +82,7 @@ __device__ __forceinline__ double field_A(const MeshDev& m, const double* v, int
 // Jacobi factor 1/diag(I - g A) at node p with c in-domain face neighbours.
 __device__ __forceinline__ double jacobi(const MeshDev& m, const double* dinv, int p, int c, double g)
 {
-    if (m.lay || m.sig) return esdc::esdc_rcp(fma(g, __ldg(m.wdiag + p), 1.0));
+    if (m.lay || m.sig || m.order == 4) return esdc::esdc_rcp(fma(g, __ldg(m.wdiag + p), 1.0));
     return dinv[c];
 }
 
@@ -97,6 +97,19 @@ __device__ __forceinline__ double apply_op(const MeshDev& m, const double* v, in
     if (m.sig) {                       // conductivity field: likewise
         *nnb = 0;
         return fma(-gih2, field_A(m, v, p, n, vp), vp);
+    }
+    if (m.order == 4) {                // fourth-order stencil: v_p - g/(12 h^2) S4 v (L2-coherent loads)
+        *nnb = 0;
+        auto ax = [&](int i, int nn, int st) -> double {
+            if (nn == 1) return 0.0;
+            const double a4 = __ldcg(v + p + (esdc_mirror(i - 2, nn) - i) * st);
+            const double b4 = __ldcg(v + p + (esdc_mirror(i - 1, nn) - i) * st);
+            const double c4 = __ldcg(v + p + (esdc_mirror(i + 1, nn) - i) * st);
+            const double d4 = __ldcg(v + p + (esdc_mirror(i + 2, nn) - i) * st);
+            return fma(16.0, b4 + c4, -(a4 + d4)) - 30.0 * vp;
+        };
+        const double s4 = ax(n.ix, m.nx, 1) + ax(n.iy, m.ny, m.nx) + ax(n.iz, m.nz, m.nx * m.ny);
+        return fma(-gih2 * (1.0 / 12.0), s4, vp);
     }
     const int sxy = m.nx * m.ny;
     double s = 0.0;

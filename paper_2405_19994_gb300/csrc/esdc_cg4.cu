@@ -545,7 +545,7 @@ int quad_blocks(const MeshDev& m, const CgWork& w)
 
 bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x)
 {
-    if (m.nx % 4 != 0 || m.N < 4 || m.sig) return false;      // a conductivity field takes the scalar path
+    if (m.nx % 4 != 0 || m.N < 4 || m.sig || m.order != 2) return false;   // field and fourth order: scalar path
     if ((reinterpret_cast<uintptr_t>(b) & 15u) || (reinterpret_cast<uintptr_t>(x) & 15u)) return false;
     if (m.lay && (m.nz > ESDC_CG4_MAX_LAYERS || !m.wdiag)) return false;
     return true;

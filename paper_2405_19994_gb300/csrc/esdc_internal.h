@@ -54,7 +54,18 @@ struct MeshDev {
     // Heterogeneous isotropic conductivity (nullptr: scalar sigma): sigma per
     // node [N] (mS/mm); a face carries the mean of its two nodes.
     const double* sig = nullptr;
+    // Order of the Laplacian (scalar sigma only): 2 (3/5/7-point) or 4 (the
+    // fourth-order five-point difference per axis with mirrored ghost cells).
+    int order = 2;
 };
+
+// Mirror image of index j on an axis of n cells (reflection about the outer
+// faces, repeated while outside: axes shorter than the stencil).
+__host__ __device__ inline int esdc_mirror(int j, int n)
+{
+    while (j < 0 || j >= n) j = j < 0 ? -j - 1 : 2 * n - 1 - j;
+    return j;
+}
 
 struct StimDev {
     int nbox;

@@ -24,6 +24,23 @@ __device__ __forceinline__ void node_xyz(const MeshDev& m, int p, int& ix, int& 
     iy = r - iz * m.ny;
 }
 
+// The fourth-order difference of the paper's experiments (Sec. 5) along one
+// axis, (-v_{i-2} + 16 v_{i-1} - 30 v_i + 16 v_{i+1} - v_{i+2}), mirrored ghost
+// cells; an axis of one cell contributes nothing.
+__device__ __forceinline__ double axis4(const double* v, int p, int i, int n, int stride)
+{
+    if (n == 1) return 0.0;
+    const double a = v[p + (esdc_mirror(i - 2, n) - i) * stride], b = v[p + (esdc_mirror(i - 1, n) - i) * stride];
+    const double c = v[p + (esdc_mirror(i + 1, n) - i) * stride], d = v[p + (esdc_mirror(i + 2, n) - i) * stride];
+    return fma(16.0, b + c, -(a + d)) - 30.0 * v[p];
+}
+
+// Sum over the axes of axis4 (times 1/(12 h^2) it is the fourth-order Laplacian).
+__device__ __forceinline__ double lap4(const double* v, int p, int ix, int iy, int iz, int nx, int ny, int nz)
+{
+    return axis4(v, p, ix, nx, 1) + axis4(v, p, iy, ny, nx) + axis4(v, p, iz, nz, nx * ny);
+}
+
 // L v at node p: (1/h^2) sum over in-domain neighbours of (v_q - v_p); with a
 // layered conductivity, A v (the coefficients then include sigma and 1/h^2,
 // and the in-plane diagonal neighbours carry the sigma_xy cross term); with a
@@ -61,6 +78,7 @@ __device__ __forceinline__ double lap(const MeshDev& m, const double* __restrict
         if (xm && yp) c -= v[p - 1 + m.nx] - vp;
         return fma(cd, c, s);
     }
+    if (m.order == 4) return lap4(v, p, ix, iy, iz, m.nx, m.ny, m.nz) * (m.ih2 * (1.0 / 12.0));
     double s = 0.0;
     if (ix > 0)        s += v[p - 1] - vp;
     if (ix < m.nx - 1) s += v[p + 1] - vp;

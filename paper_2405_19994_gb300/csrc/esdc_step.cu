@@ -83,6 +83,22 @@ __global__ void k_wdiag(MeshDev m, double* w)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
         int ix, iy, iz;
         node_xyz(m, p, ix, iy, iz);
+        if (m.order == 4) {                 // -diag of the fourth-order Laplacian: 30 less the ghosts that mirror onto p
+            const int idx[3] = {ix, iy, iz}, nn[3] = {m.nx, m.ny, m.nz};
+            double d = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                if (nn[a] == 1) continue;
+                const int i = idx[a], n = nn[a];
+                double c = -30.0;
+                if (esdc_mirror(i - 1, n) == i) c += 16.0;
+                if (esdc_mirror(i + 1, n) == i) c += 16.0;
+                if (esdc_mirror(i - 2, n) == i) c -= 1.0;
+                if (esdc_mirror(i + 2, n) == i) c -= 1.0;
+                d += c;
+            }
+            w[p] = -d * m.ih2 / 12.0;
+            continue;
+        }
         if (m.sig) {
             const int sxy = m.nx * m.ny;
             const double sp = m.sig[p];
@@ -345,6 +361,8 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
         return ESDC_OK;
     }
     if (!sxx || !syy || !sxy || !szz) return set_err(h, ESDC_ERR_INVALID_ARG, "all four layer arrays are needed");
+    if (h->mesh.order != 2)
+        return set_err(h, ESDC_ERR_UNSUPPORTED, "layered conductivity needs the second-order stencil");
     if (h->sigf) {                                       // layers replace a conductivity field
         cudaFree(h->sigf);
         h->sigf = nullptr;
@@ -381,6 +399,27 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
     return ESDC_OK;
 }
 
+int esdc_set_stencil_order(esdc_handle* h, int order)
+{
+    if (!h) return ESDC_ERR_INVALID_ARG;
+    if (order != 2 && order != 4) return set_err(h, ESDC_ERR_INVALID_ARG, "order must be 2 or 4");
+    if (order == h->mesh.order) return ESDC_OK;
+    if (order == 2) {
+        h->mesh.order = 2;
+        if (h->wdiag && !h->lay && !h->sigf) { cudaFree(h->wdiag); h->wdiag = nullptr; h->mesh.wdiag = nullptr; }
+        return ESDC_OK;
+    }
+    if (h->lay || h->sigf) return set_err(h, ESDC_ERR_UNSUPPORTED, "the fourth-order stencil needs the scalar sigma");
+    if (h->opt.precision != 0) return set_err(h, ESDC_ERR_UNSUPPORTED, "the fourth-order stencil runs on the FP64 path");
+    if (!h->wdiag) CUDA_TRY(h, cudaMalloc((void**)&h->wdiag, sizeof(double) * h->mesh.ld));
+    h->mesh.order = 4;
+    h->mesh.wdiag = h->wdiag;
+    k_wdiag<<<grid_for(h, 256), 256>>>(h->mesh, h->wdiag);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaDeviceSynchronize());
+    return ESDC_OK;
+}
+
 int esdc_set_conductivity_field(esdc_handle* h, const double* sigma)
 {
     if (!h) return ESDC_ERR_INVALID_ARG;
@@ -394,6 +433,8 @@ int esdc_set_conductivity_field(esdc_handle* h, const double* sigma)
     }
     if (h->opt.precision != 0)
         return set_err(h, ESDC_ERR_UNSUPPORTED, "a conductivity field runs on the FP64 path only");
+    if (h->mesh.order != 2)
+        return set_err(h, ESDC_ERR_UNSUPPORTED, "a conductivity field needs the second-order stencil");
     const int64_t N = h->mesh.N;
     for (int64_t p = 0; p < N; ++p)
         if (!(sigma[p] > 0.0) || !std::isfinite(sigma[p]))

@@ -61,6 +61,7 @@ def lib() -> C.CDLL:
             "esdc_set_conductivity_layers": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
                                                        C.POINTER(_D)]),
             "esdc_set_conductivity_field": (C.c_int, [_VP, C.POINTER(_D)]),
+            "esdc_set_stencil_order": (C.c_int, [_VP, C.c_int]),
             "esdc_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
             "esdc_sweep": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
             "esdc_sweep_host": (C.c_int, [_VP, _VP, _I64, _D, _D, C.c_int, C.c_int, _VP]),
@@ -175,6 +176,8 @@ class Solver:
             s.set_conductivity_layers(wl.layers)
         if getattr(wl, "sigma_field", None) is not None:
             s.set_conductivity_field(wl.sigma_field)
+        if getattr(wl, "order", 2) != 2:
+            s.set_stencil_order(wl.order)
         return s
 
     def _check(self, rc: int):
@@ -209,6 +212,10 @@ class Solver:
             return
         arrs = [np.ascontiguousarray(layers[k], np.float64) for k in ("sxx", "syy", "sxy", "szz")]
         self._check(lib().esdc_set_conductivity_layers(self._h, *[a.ctypes.data_as(C.POINTER(_D)) for a in arrs]))
+
+    def set_stencil_order(self, order: int):
+        """2: the 3/5/7-point Laplacian; 4: the fourth-order five-point differences per axis."""
+        self._check(lib().esdc_set_stencil_order(self._h, int(order)))
 
     def set_conductivity_field(self, sigma):
         """Per-node conductivity [N] (mS/mm), or None for the scalar sigma."""

@@ -409,3 +409,59 @@ def test_field_rejected_in_precision_form():
     with pytest.raises(P.EsdcError) as e:
         s.set_conductivity_field(np.full(64, 0.2))
     assert e.value.code == -6
+
+
+# ---------------------------------------------------------------- fourth-order Laplacian
+
+@pytest.mark.parametrize("shape", [(13, 11, 1), (32, 24, 1), (9, 8, 5), (2, 3, 2)])
+def test_order4_solve_matches_oracle(shape):
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.order = 4
+    s = P.Solver.from_workload(wl, cg_maxit=2000)
+    m = O.Monodomain(wl)                                   # the exact DCT-II solve
+    b = np.random.default_rng(12).normal(size=wl.n_nodes)
+    g = 0.3 * 0.17
+    want = m.solve_shifted(g, b)
+    xd = torch.zeros(wl.n_nodes, dtype=torch.float64, device="cuda")
+    s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+    assert rel(xd.cpu().numpy(), want) < 1e-12
+
+
+def test_order4_run_matches_oracle():
+    """The parity sheet (32x32 HH, corner stimulus, M=3, K=4) with the paper's
+    fourth-order differences: 60 steps against the oracle."""
+    wl = I.hh_sheet_32()
+    wl.order = 4
+    s = P.Solver.from_workload(wl)
+    y = s.new_state()
+    s.init_state(y, wl.V0)
+    m = O.Monodomain(wl)
+    ref = m.init_state()
+    t = 0.0
+    for _ in range(60):
+        s.sweep(y, t, wl.dt, wl.M, wl.K)
+        ref, _, _, _ = m.step(ref, t, wl.dt, wl.M, wl.K)
+        t += wl.dt
+    assert s.residual()[0] == 0
+    got = from_dev(s, y)
+    assert rel(got[0], ref[0]) < 1e-10
+    assert ref[0].max() > -60.0                            # the corner has fired
+
+
+def test_order4_combinations_rejected():
+    wl = I.hh_sheet_32().with_mesh(8, 8, 2)
+    s = P.Solver.from_workload(wl)
+    s.set_conductivity_layers(I.fibre_layers(2))
+    with pytest.raises(P.EsdcError) as e:
+        s.set_stencil_order(4)
+    assert e.value.code == -6
+    s2 = P.Solver.from_workload(wl, precision="mixed")
+    with pytest.raises(P.EsdcError) as e:
+        s2.set_stencil_order(4)
+    assert e.value.code == -6
+    s3 = P.Solver.from_workload(wl)
+    s3.set_stencil_order(4)
+    with pytest.raises(P.EsdcError) as e:
+        s3.set_conductivity_field(np.full(wl.n_nodes, 0.2))
+    assert e.value.code == -6
