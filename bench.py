@@ -894,6 +894,72 @@ def run_fas_form(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sheet_form(args):
+    """Config 1: the 32x32 HH parity sheet (corner stimulus, M = 3, K = 4,
+    dt = 0.025 ms, T = 4 ms, 160 steps) on the GPU, its V error at T against
+    the oracle, and the oracle's own time for the whole run on this host's
+    cores (OMP_NUM_THREADS sets how many)."""
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1 and rank != 0:
+        return
+    wl = I.hh_sheet_32()
+    n = wl.n_steps
+    s = P.Solver.from_workload(wl)
+    stream = torch.cuda.current_stream()
+
+    def run():
+        y = s.new_state()
+        s.init_state(y, wl.V0)
+        t = 0.0
+        for _ in range(n):
+            s.sweep(y, t, wl.dt, wl.M, wl.K)
+            t += wl.dt
+        return y
+    for _ in range(max(1, args.warmup)):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    y = run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if s.residual()[0] != 0:
+        raise RuntimeError("run failed")
+    got = y[0, :wl.n_nodes].cpu().numpy()
+    cpu, verr = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        m = oracle.Monodomain(wl)
+        yo = m.init_state()
+        t = 0.0
+        c0 = time.perf_counter()
+        for _ in range(n):
+            yo, _, _, _ = m.step(yo, t, wl.dt, wl.M, wl.K)
+            t += wl.dt
+        cel = time.perf_counter() - c0
+        cpu = {"value": wl.n_nodes * n / cel, "unit": UNIT, "cores": oracle.oracle.threads(), "kind": "oracle",
+               "sample": "the whole 160-step run", "s_per_sim_ms": cel / wl.T}
+        verr = float(np.abs(got - yo[0]).max() / np.abs(yo[0]).max())
+    line = {
+        "metric": METRIC, "value": wl.n_nodes * n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": n,
+        "warmup": max(1, args.warmup), "ms_per_step": ms / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "form": "sheet", "nodes": wl.n_nodes, "M": wl.M, "K": wl.K, "dt_ms": wl.dt,
+                   "T_ms": wl.T, "l2": "latency-bound parity case (1024 nodes, L2-resident)"},
+        "s_per_sim_ms": ms * 1e-3 / wl.T,
+        "V_max_rel_vs_oracle_at_T": verr,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -905,11 +971,12 @@ def main():
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
-    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas"], default="plain",
+    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet"], default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
                          "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "
                          "adjoint: forward + discrete adjoint on the 256x256 HH conductivity-field sheet; "
-                         "fas: two-level Algorithm HSDC against Q^par on 16 slices of the 512x512 HH sheet")
+                         "fas: two-level Algorithm HSDC against Q^par on 16 slices of the 512x512 HH sheet; "
+                         "sheet: the 32x32 HH parity sheet's full run against the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -925,6 +992,8 @@ def main():
         run_adjoint_form(args)
     elif args.form == "fas":
         run_fas_form(args)
+    elif args.form == "sheet":
+        run_sheet_form(args)
     else:
         run_ours(args)
 
