@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ES-SDC node-updates/s and s per simulated ms at stated V-error; % roofline"
 UNIT = "node-updates/s"
 
-# Work per unit, used for the roofline of the dominant kernel (see DESIGN.md).
+# Work per unit, used for the roofline of the dominant kernel.
 #  node kernel (SYN19, M = 4), per mesh node and sweep: the M + 1 launches of a
 #  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
 #  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu

@@ -391,7 +391,7 @@ int esdc_batch_init_state(esdc_batch* b, double* y, double V0, void* stream);
  * Stream-ordered, no synchronisation.  The first call for a given (y, M, K,
  * dt) records the step's launches in a CUDA graph on a stream of the batch's
  * own and later calls launch that graph on `stream` (falling back to direct
- * launches if the driver cannot record them).  Errors: INVALID_ARG, CUDA. */
+ * launches if the CUDA runtime cannot record them).  Errors: INVALID_ARG, CUDA. */
 int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M, int K, void* stream);
 
 /* As esdc_batch_sweep with a separate output: y_n from y_in, y_{n+1} of every

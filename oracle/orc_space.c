@@ -7,8 +7,11 @@
  * mirror ghosts (zero normal flux, eq. (monodomain) boundary condition):
  *   (L v)_p = (1/h^2) sum_{q in nbr(p)} (v_q - v_p).
  * The paper uses fourth-order differences (Sec. 2.2) and solves with DCT-II
- * (Sec. 5); the second-order stencil is this build's reading (it is also
+ * (Sec. 5); the second-order stencil is the default reading (it is also
  * diagonalised by DCT-II, so the paper's solver applies to it unchanged).
+ * orc_mono.order = 4 selects the fourth-order five-point differences per
+ * axis, with the ghost cells mirrored about the boundary faces; DCT-II
+ * diagonalises that operator too.
  *
  * The layered anisotropic operator (orc_conductivity) keeps the same flux form:
  * the in-plane cross term sigma_xy V_xy uses the four diagonal neighbours, each
