@@ -119,3 +119,34 @@ def test_batch_invalid_arguments_rejected_without_gpu(L):
     assert L.esdc_batch_layout(None, None, None, None) == -1
     L.esdc_batch_destroy(None)
     assert L.esdc_batch_last_error(None) == b"null batch"
+
+
+def test_later_entry_points_reject_invalid_arguments_without_gpu(L):
+    D = C.POINTER(C.c_double)
+    # null handles
+    assert L.esdc_set_stencil_order(None, 4) == -1
+    assert L.esdc_set_conductivity_field(None, None) == -1
+    assert L.esdc_set_conductivity_layers(None, None, None, None, None) == -1
+    assert L.esdc_set_params(None, None, 7) == -1
+    assert L.esdc_adjoint_forward(None, None, 0.0, 0.1, 3, 4, 1, 0, None, None, None, None) == -1
+    assert L.esdc_adjoint_backward(None, None, 0.0, 0.1, 3, 4, 1, 0, None, None, None, None, None, None,
+                                   None) == -1
+    assert L.esdc_batch_sweep_ex(None, None, None, None, None, 0.1, 3, 1, 0, 0, None) == -1
+    assert L.esdc_batch_sweep_from(None, None, None, None, 0.1, 3, 1, 0, None) == -1
+    assert L.esdc_batch_qpar(None, None, None, 0.0, 0.1, 3, 2, None) == -1
+    assert L.esdc_batch_iterate(None, None, None) == -1
+    assert L.esdc_hsdc2(None, None, None, None, 0.0, 0.1, 3, 2, 1, None) == -1
+    assert L.esdc_batch_set_shape(None, 1, 512, 1) == -1
+    assert L.esdc_batch_tune(None, None, -75.0, 0.0, 0.1, 3, 4, 1, None) == -1
+    assert L.esdc_batch_graph_active(None) == 0
+    # the node interpolator: null arrays, too many rows, equal source and destination
+    W = np.eye(2)
+    Wp = W.ctypes.data_as(D)
+    src, dst = C.c_void_p(16), C.c_void_p(32)
+    assert L.esdc_interp(None, 2, 4, dst, 2, 4, 1, 4, Wp, 0.0, None) == -1
+    assert L.esdc_interp(src, 9, 4, dst, 2, 4, 1, 4, Wp, 0.0, None) == -1
+    assert L.esdc_interp(src, 2, 4, src, 2, 4, 1, 4, Wp, 0.0, None) == -1
+    assert L.esdc_interp(src, 2, 2, dst, 2, 4, 1, 4, Wp, 0.0, None) == -1     # pitch shorter than the columns
+    bad = np.array([[1.0, np.nan], [0.0, 1.0]])
+    assert L.esdc_interp(src, 2, 4, dst, 2, 4, 1, 4, bad.ctypes.data_as(D), 0.0, None) == -1
+    assert L.esdc_interp(src, 2, 4, dst, 2, 4, 1, 0, Wp, 0.0, None) == 0      # nothing to do
