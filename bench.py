@@ -193,7 +193,7 @@ def run_ours(args):
         wl = wl.with_mesh(wl.nx, wl.ny, args.nz)
     M, K, dt = wl.M, wl.K, wl.dt
     N = wl.n_nodes
-    solver = P.Solver.from_workload(wl, M_max=M, precision=args.precision)
+    solver = P.Solver.from_workload(wl, M_max=M, precision=args.precision, solver=args.solver)
     y = solver.new_state()
     solver.init_state(y, wl.V0)
     stream = torch.cuda.current_stream()
@@ -308,7 +308,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "nodes": N, "n_state": wl.n_state, "M": M, "K": K, "dt_ms": dt,
-                   "precision": args.precision,
+                   "precision": args.precision, "solver": args.solver,
                    "model": "syn19 (seed 20240530)", "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (state + workspace ~2 GB per GPU)",
                    "window_ms": [args.warmup * dt, (args.warmup + args.steps) * dt]},
@@ -971,6 +971,9 @@ def main():
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
+    ap.add_argument("--solver", choices=["auto", "cg"], default="auto",
+                    help="diffusion solves of the headline step: auto (Chebyshev semi-iteration on the "
+                         "exactly known spectrum of the scalar-sigma operator) or cg (Jacobi-PCG)")
     ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet"], default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
                          "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "

@@ -84,10 +84,20 @@ typedef struct {
                           r = b - A x, FP32 inner PCG on A e = r, x += e) to the
                           same tol_cg; state, coefficient tables, quadrature and
                           residual stay FP64                                       */
+    int    solver;     /* FP64 diffusion solves of the sweep and esdc_diffusion_solve:
+                          0 = automatic: the Chebyshev semi-iteration where the
+                          spectrum of the operator I - g L of esdc_diffusion_solve
+                          is known exactly (scalar sigma, second-order stencil,
+                          nx a multiple of 4: the interval [1, 1 + (g/h^2)
+                          sum_axes 4 sin^2(pi (n-1)/(2n))], the cosine modes
+                          being its eigenvectors), the Jacobi-PCG elsewhere;
+                          1 = the (Jacobi-P)CG always.
+                          Both stop at the same ||r|| <= tol_cg ||b||.  The paper
+                          leaves the inner solver open (it uses PCG).            */
 } esdc_options;
 
 /* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1,
- * precision 0. */
+ * precision 0, solver 0. */
 void esdc_default_options(esdc_options* opt);
 
 /*
@@ -250,9 +260,9 @@ int esdc_coefficients(esdc_handle* h, const double* z, int64_t n, int M, double*
  * (I - g A) x = b with g = dt d_i/(chi C_m).  b, x device [n_nodes]; x holds
  * the initial guess on entry and the solution on return.  iters (host,
  * optional) receives the iteration count; synchronises `stream`.  Returns
- * ESDC_ERR_CG_NOT_CONVERGED if cg_maxit was reached.  With precision = 1 the
- * solve is the refinement of the precision form and iters counts the inner
- * (FP32) iterations.
+ * ESDC_ERR_CG_NOT_CONVERGED if cg_maxit was reached.  The solver is the one
+ * options.solver selects.  With precision = 1 the solve is the refinement of
+ * the precision form and iters counts the inner (FP32) iterations.
  */
 int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, int* iters,
                          void* stream);
@@ -280,8 +290,9 @@ int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* st
  * memory another framework has reserved up front, or in a loop that must not
  * enter the allocator after start-up; such callers cannot call esdc_create).
  *
- * Solves (I - g L) x = b on `mesh` like esdc_diffusion_solve (same kernel,
- * Jacobi-preconditioned when precond != 0, stop at ||r|| <= tol ||b||, at most
+ * Solves (I - g L) x = b on `mesh` like esdc_diffusion_solve with
+ * options.solver = 1 (the same CG kernel, Jacobi-preconditioned when
+ * precond != 0, stop at ||r|| <= tol ||b||, at most
  * maxit iterations; x holds the initial guess on entry), but needs no handle and
  * allocates nothing: its scratch (CG vectors, block partial sums, barrier
  * counter) lives in one fixed array compiled into the library, of

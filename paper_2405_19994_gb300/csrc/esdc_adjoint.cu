@@ -377,7 +377,8 @@ cudaError_t reverse_step(esdc_handle* h, AdjWork& w, AdjArgs& a, int K, cudaStre
                 // adjoint solve: (I - dt d_i D A) brhs = bY_{i,V}
                 if ((e = cudaMemsetAsync(w.brhs, 0, sizeof(double) * ld, s)) != cudaSuccess) return e;
                 e = esdc_cg_launch(h->mesh, h->cg, a.dt * C->d[i] * h->D, w.bY + (int64_t)(i - 1) * NSld, w.brhs,
-                                   h->opt.tol_cg, h->opt.cg_maxit, h->opt.precond, nullptr, h->flags, s);
+                                   h->opt.tol_cg, h->opt.cg_maxit, h->opt.precond, h->opt.solver, nullptr,
+                                   h->flags, s);
                 if (e != cudaSuccess) return e;
                 k_adj_rhs<M><<<nb, 128, 0, s>>>(a);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -20,6 +20,8 @@
 //
 // Requirements (checked by esdc_cg4_eligible): nx a multiple of 4, b and x
 // 16-byte aligned, and for the layered operator nz <= ESDC_CG4_MAX_LAYERS.
+#include <cmath>
+
 #include "esdc_internal.h"
 #include "esdc_cg_common.cuh"
 
@@ -350,6 +352,128 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg4(CgArgs a)
     }
 }
 
+// ---------------------------------------------------------------- Chebyshev semi-iteration
+// For the scalar-sigma second-order stencil the spectrum of B = I - g L is
+// known exactly: the cosine modes are its eigenvectors, so it lies in
+// [lmin, lmax] = [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))].  The
+// Chebyshev semi-iteration on that interval needs no dot products:
+//   x_{k+1} = x_k + d_k,  r_{k+1} = r_k - B d_k,
+//   d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1}/delta) r_{k+1},
+//   rho_0 = delta/theta, rho_{k+1} = 1/(2 theta/delta - rho_k),
+// theta, delta the centre and half-width of the interval (the coefficients are
+// precomputed on the host).  ||r_k|| <= 2 q^k ||r_0|| with
+// q = (sqrt(kappa) - 1)/(sqrt(kappa) + 1), kappa = lmax/lmin, so the number of
+// iterations to ||r|| <= tol ||b|| follows from ||r_0||; the residual is then
+// checked, and a short extension runs if rounding left it above the tolerance.
+// One grid barrier per iteration (CG needs two and three dot products), and
+// 11 FP64 operations per node: the stencil, r, x and d.
+#define ESDC_CHEB_TAB 64
+struct ChebArgs {
+    double theta, q;
+    double ca[ESDC_CHEB_TAB];   // rho_{k+1} rho_k
+    double cb[ESDC_CHEB_TAB];   // 2 rho_{k+1} / delta   (index k; the last entry is used beyond)
+};
+
+__global__ void __launch_bounds__(ESDC_CG_THREADS) k_cheb4(CgArgs a, ChebArgs c)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const MeshDev& m = a.m;
+    Tab<double> t = carve<double>(reinterpret_cast<double*>(dsm), m);
+    build_tab(m, a.g, false, t);
+    const int nq = m.N >> 2;
+    const int stride = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double* part = a.part;
+    __shared__ double bs[3];
+    unsigned target = 0;
+    double* dc = a.p;            // d_k
+    double* dn = a.q;            // d_{k+1}
+    const double inv_theta = 1.0 / c.theta;
+
+    // r = b - B x, d_0 = r / theta; partials r.r, b.b
+    {
+        double v[2] = {0.0, 0.0};
+        for (int qi = tid; qi < nq; qi += stride) {
+            const Geo G = geo(m, qi);
+            const DiagIdx di = diag_idx<false>(G);
+            Q4<double> xc, bx;
+            apply4<double, false>(m, t, a.x, G, di, xc, bx);
+            const Q4<double> b = ld4(a.b + G.p);
+            Q4<double> r, d;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                r.v[j] = b.v[j] - bx.v[j];
+                d.v[j] = r.v[j] * inv_theta;
+                v[0] = fma(r.v[j], r.v[j], v[0]);
+                v[1] = fma(b.v[j], b.v[j], v[1]);
+            }
+            st4(a.r + G.p, r);
+            st4(dc + G.p, d);
+        }
+        block_sum<2>(v, bs);
+        if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[k * gridDim.x + blockIdx.x] = bs[k];
+    }
+    if (!grid_barrier(a.bar, target, a.flags)) return;
+    double tot[2];
+    grid_total<2>(part, 0, tot);
+    const double stop = a.tol2 * tot[1];
+    bool done = tot[0] <= stop;
+    bool bad = !isfinite(tot[0]) || !isfinite(stop);
+    // iterations the bound asks for: 2 q^k ||r_0|| <= tol ||b||  (the same value in every thread)
+    int k_need = 1;
+    if (!done && !bad && c.q > 0.0) {
+        const double kd = stop > 0.0 ? ceil(log(0.5 * sqrt(stop / tot[0])) / log(c.q)) : (double)a.maxit;
+        k_need = kd < (double)a.maxit ? (int)kd : a.maxit;     // tol 0: run to the cap
+    }
+    if (k_need < 1) k_need = 1;
+    int it = 0;
+    int chunk_end = k_need < a.maxit ? k_need : a.maxit;
+    while (!done && !bad && it < a.maxit) {
+        const bool check = it + 1 >= chunk_end;
+        const int ki = it < ESDC_CHEB_TAB ? it : ESDC_CHEB_TAB - 1;
+        const double ca = c.ca[ki], cb = c.cb[ki];
+        double v[1] = {0.0};
+        for (int qi = tid; qi < nq; qi += stride) {
+            const Geo G = geo(m, qi);
+            const DiagIdx di = diag_idx<false>(G);
+            Q4<double> d, bd;
+            apply4<double, false>(m, t, dc, G, di, d, bd);
+            const Q4<double> r = ld4(a.r + G.p), x = ld4(a.x + G.p);
+            Q4<double> rn, xn, dnew;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                rn.v[j] = r.v[j] - bd.v[j];
+                xn.v[j] = x.v[j] + d.v[j];
+                dnew.v[j] = fma(ca, d.v[j], cb * rn.v[j]);
+                if (check) v[0] = fma(rn.v[j], rn.v[j], v[0]);
+            }
+            st4(a.r + G.p, rn);
+            st4(a.x + G.p, xn);
+            st4(dn + G.p, dnew);
+        }
+        double* sw = dc; dc = dn; dn = sw;
+        ++it;
+        if (check) {
+            block_sum<1>(v, bs);
+            if (threadIdx.x == 0) part[(2 + (it & 1)) * gridDim.x + blockIdx.x] = bs[0];
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        if (check) {
+            double rr[1];
+            grid_total<1>(part, 2 + (it & 1), rr);
+            if (!isfinite(rr[0])) { bad = true; break; }
+            if (rr[0] <= stop) { done = true; break; }
+            chunk_end = it + 2 < a.maxit ? it + 2 : a.maxit;     // rounding left it short: two more, then check
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = it;
+        if (a.iter_log) *a.iter_log = it;
+        if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+        else if (!done) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+    }
+}
+
 // ---------------------------------------------------------------- iterative refinement
 struct Cg4MixArgs {
     float *r, *p, *q, *z, *e;   // FP32 inner vectors
@@ -549,6 +673,61 @@ bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x)
     if ((reinterpret_cast<uintptr_t>(b) & 15u) || (reinterpret_cast<uintptr_t>(x) & 15u)) return false;
     if (m.lay && (m.nz > ESDC_CG4_MAX_LAYERS || !m.wdiag)) return false;
     return true;
+}
+
+bool esdc_cheb_eligible(const MeshDev& m, const void* b, const void* x)
+{
+    if (m.lay || m.sig || m.order != 2 || !esdc_cg4_eligible(m, b, x)) return false;
+    return m.nx > 1 || m.ny > 1 || m.nz > 1;                   // an interval of positive width
+}
+
+cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
+{
+    CgArgs a;
+    a.m = h.mesh;
+    a.g = h.g;
+    for (int c = 0; c < 7; ++c) a.dinv[c] = 0.0;
+    a.b = h.b;
+    a.x = h.x;
+    a.r = h.w.r; a.p = h.w.p; a.q = h.w.q; a.z = h.w.z;
+    a.part = h.w.part;
+    a.bar = h.w.bar;
+    a.status = h.w.status;
+    a.iter_log = h.iter_log;
+    a.flags = h.flags;
+    a.tol2 = h.tol * h.tol;
+    a.maxit = h.maxit;
+    a.precond = 0;
+    // spectrum of I - g L: [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))]
+    const int n[3] = {h.mesh.nx, h.mesh.ny, h.mesh.nz};
+    double w = 0.0;
+    for (int k = 0; k < 3; ++k)
+        if (n[k] > 1) {
+            const double sn = std::sin(M_PI * (n[k] - 1) / (2.0 * n[k]));
+            w += 4.0 * sn * sn;
+        }
+    const double lmin = 1.0, lmax = 1.0 + h.g * h.mesh.ih2 * w;
+    if (!(lmax > lmin)) return cudaErrorInvalidValue;
+    ChebArgs c;
+    c.theta = 0.5 * (lmax + lmin);
+    const double delta = 0.5 * (lmax - lmin), s1 = c.theta / delta;
+    const double kap = lmax / lmin;
+    c.q = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    double rho = 1.0 / s1;
+    for (int k = 0; k < ESDC_CHEB_TAB; ++k) {
+        const double rn = 1.0 / (2.0 * s1 - rho);
+        c.ca[k] = rn * rho;
+        c.cb[k] = 2.0 * rn / delta;
+        rho = rn;
+    }
+    const int ne = tab_entries(h.mesh);
+    const int nb = quad_blocks(h.mesh, h.w);
+    const size_t bytes = sizeof(double) * ne;
+    cudaError_t e = cudaMemsetAsync(h.w.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if ((e = prepare(k_cheb4, bytes)) != cudaSuccess) return e;
+    void* args[] = {&a, &c};
+    return cudaLaunchCooperativeKernel((const void*)k_cheb4, dim3(nb), dim3(h.w.threads), args, bytes, s);
 }
 
 cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s)

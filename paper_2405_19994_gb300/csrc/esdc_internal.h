@@ -113,10 +113,12 @@ int esdc_model_setup(int model, const double* params, int n_params, ModelDev* mp
 #define ESDC_FLAG_TIMEOUT    2
 #define ESDC_FLAG_NONFINITE  4
 
-// Enqueue one CG solve; iter_log (device, optional) receives the iteration count.
-// flags (device) accumulates ESDC_FLAG_* bits.  Returns a cudaError_t.
+// Enqueue one solve of (I - g A) x = b; iter_log (device, optional) receives the
+// iteration count, flags (device) accumulates ESDC_FLAG_* bits.  solver 0 takes
+// the Chebyshev semi-iteration where esdc_cheb_eligible holds and g > 0, the
+// (Jacobi-P)CG otherwise; solver 1 always the CG.  Returns a cudaError_t.
 cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
-                           double* x, double tol, int maxit, int precond, int* iter_log,
+                           double* x, double tol, int maxit, int precond, int solver, int* iter_log,
                            int* flags, cudaStream_t s);
 // Precision form: FP32 inner PCG with FP64 iterative refinement (same contract;
 // iter_log receives the number of inner iterations).
@@ -144,3 +146,7 @@ struct CgArgsHost {
 };
 bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x);
 cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s);
+// Chebyshev semi-iteration on the exactly known spectrum of the scalar-sigma
+// second-order operator (quad layout, no dot products inside the iteration).
+bool esdc_cheb_eligible(const MeshDev& m, const void* b, const void* x);
+cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s);

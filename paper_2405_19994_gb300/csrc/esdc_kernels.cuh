@@ -611,7 +611,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
                 e = MIXED ? esdc_cg_mixed_launch(h->mesh, h->cg, g, h->rhs, Vi, h->opt.tol_cg, h->opt.cg_maxit,
                                                  h->opt.precond, log, h->flags, s)
                           : esdc_cg_launch(h->mesh, h->cg, g, h->rhs, Vi, h->opt.tol_cg, h->opt.cg_maxit,
-                                           h->opt.precond, log, h->flags, s);
+                                           h->opt.precond, h->opt.solver, log, h->flags, s);
                 prof_end(h, s);
                 if (e != cudaSuccess) return e;
             }

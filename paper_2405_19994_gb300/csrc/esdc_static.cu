@@ -101,7 +101,7 @@ extern "C" int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, cons
     // The array keeps the previous call's contents: clear the words that must
     // start at zero (the CG vectors and partial sums are fully written first).
     if (cudaMemsetAsync(flags, 0, sizeof(int), s) != cudaSuccess) return ESDC_ERR_CUDA;
-    if (esdc_cg_launch(m, w, g, b, x, tol, maxit, precond != 0, nullptr, flags, s) != cudaSuccess)
+    if (esdc_cg_launch(m, w, g, b, x, tol, maxit, precond != 0, 1, nullptr, flags, s) != cudaSuccess)
         return ESDC_ERR_CUDA;
     int st[2] = {0, 0}, fl = 0;
     if (cudaMemcpyAsync(st, w.status, sizeof st, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

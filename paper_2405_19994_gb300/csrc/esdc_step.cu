@@ -216,6 +216,7 @@ void esdc_default_options(esdc_options* opt)
     opt->cg_maxit = 200;
     opt->precond = 1;
     opt->precision = 0;
+    opt->solver = 0;
 }
 
 int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int model,
@@ -248,6 +249,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     if (opt) o = *opt;
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
     if (o.precision != 0 && o.precision != 1) return ESDC_ERR_INVALID_ARG;
+    if (o.solver != 0 && o.solver != 1) return ESDC_ERR_INVALID_ARG;
 
     esdc_handle* h = new (std::nothrow) esdc_handle();
     if (!h) return ESDC_ERR_NO_MEMORY;
@@ -606,7 +608,7 @@ int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, i
                                          h->opt.precond, nullptr, h->flags, s));
     else
         CUDA_TRY(h, esdc_cg_launch(h->mesh, h->cg, g, b, x, h->opt.tol_cg, h->opt.cg_maxit, h->opt.precond,
-                                   nullptr, h->flags, s));
+                                   h->opt.solver, nullptr, h->flags, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     int st[2] = {0, 0}, flags = 0;
     CUDA_TRY(h, cudaMemcpy(st, h->cg.status, sizeof st, cudaMemcpyDeviceToHost));

@@ -34,7 +34,7 @@ class esdc_mesh(C.Structure):
 
 class esdc_options(C.Structure):
     _fields_ = [("M_max", C.c_int), ("tol_cg", C.c_double), ("cg_maxit", C.c_int), ("precond", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("solver", C.c_int)]
 
 
 _lib = None
@@ -145,7 +145,7 @@ class Solver:
 
     def __init__(self, dim: int, nx: int, ny: int, nz: int, h: float, sigma: float, chi: float,
                  Cm: float, model: int, params, M_max: int = 8, tol_cg: float = 1e-14,
-                 cg_maxit: int = 200, precond: bool = True, precision: str = "fp64"):
+                 cg_maxit: int = 200, precond: bool = True, precision: str = "fp64", solver: str = "auto"):
         self._h = None
         L = lib()
         mesh = esdc_mesh(dim, nx, ny, nz, h)
@@ -155,6 +155,9 @@ class Solver:
         if precision not in ("fp64", "mixed"):
             raise ValueError("precision must be 'fp64' or 'mixed'")
         opt.precision = 1 if precision == "mixed" else 0
+        if solver not in ("auto", "cg"):
+            raise ValueError("solver must be 'auto' or 'cg'")
+        opt.solver = 0 if solver == "auto" else 1
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_create(C.byref(mesh), sigma, chi, Cm, model, p.ctypes.data_as(C.POINTER(_D)), len(p),

@@ -135,6 +135,74 @@ def test_diffusion_solve_matches_dct(shape, g):
     assert it <= 2000
 
 
+# ---------------------------------------------------------------- Chebyshev semi-iteration
+
+def _spectrum_hi(wl, g):
+    return 1 + g / wl.h**2 * sum(4 * math.sin(math.pi * (n - 1) / (2 * n)) ** 2
+                                 for n in (wl.nx, wl.ny, wl.nz) if n > 1)
+
+
+@pytest.mark.parametrize("shape", [(4, 1, 1), (64, 1, 1), (32, 24, 1), (48, 40, 9), (8, 3, 17)])
+@pytest.mark.parametrize("g", [1e-3, 0.05, 2.0])
+def test_chebyshev_solve_matches_dct(shape, g):
+    """solver="auto" on scalar-sigma meshes with nx % 4 == 0 takes the
+    Chebyshev semi-iteration; both solvers against the exact DCT-II solve."""
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    m = O.Monodomain(wl)
+    rng = np.random.default_rng(17)
+    b = rng.normal(size=wl.n_nodes)
+    x0 = rng.normal(size=wl.n_nodes)
+    want = m.solve_shifted(g, b, method=O.SOLVE_DCT)
+    tol = 1e-14
+    kappa = _spectrum_hi(wl, g)
+    its = {}
+    for solver in ("auto", "cg"):
+        s = P.Solver.from_workload(wl, cg_maxit=4000, tol_cg=tol, solver=solver)
+        xd = torch.from_numpy(x0).cuda()
+        its[solver] = s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+        got = xd.cpu().numpy()
+        assert rel(got, want) < 50 * kappa * tol, (solver, rel(got, want), its[solver])
+    # The Chebyshev run stops at the first k with 2 q^k ||r_0|| <= tol ||b||,
+    # q = (sqrt(kappa) - 1)/(sqrt(kappa) + 1), then checks every two iterations
+    # if rounding left the residual short; a CG run would not follow this count.
+    r0 = b - (x0 - g * m.laplacian(x0))
+    q = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    k = max(1, math.ceil(math.log(0.5 * tol * np.linalg.norm(b) / np.linalg.norm(r0)) / math.log(q)))
+    assert k - 1 <= its["auto"] <= k + 6, (its, k)
+
+
+def test_chebyshev_zero_shift_and_ineligible_meshes():
+    # g = 0 is the identity (the interval has no width: the CG runs); nx not a
+    # multiple of 4 keeps the CG too; both give the exact result.
+    rng = np.random.default_rng(4)
+    for shape, g in (((16, 8, 1), 0.0), ((18, 7, 3), 0.3)):
+        wl = I.hh_sheet_32().with_mesh(*shape)
+        m = O.Monodomain(wl)
+        b = rng.normal(size=wl.n_nodes)
+        s = P.Solver.from_workload(wl, cg_maxit=2000)
+        xd = torch.zeros(wl.n_nodes, dtype=torch.float64, device="cuda")
+        s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+        want = m.solve_shifted(g, b, method=O.SOLVE_DCT)
+        assert rel(xd.cpu().numpy(), want) < 50 * _spectrum_hi(wl, g) * 1e-14
+
+
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_one_step_either_solver_matches_oracle(solver):
+    wl = I.syn19_slab().with_mesh(16, 12, 5)
+    M, K = 4, 6
+    s = P.Solver.from_workload(wl, M_max=M, solver=solver)
+    y0 = I.random_state(wl, seed=31)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.5, wl.dt, M, K)
+    assert s.residual()[0] == 0
+    got = from_dev(s, yd)
+    want, _, _, _ = O.Monodomain(wl).step(y0, 0.5, wl.dt, M, K)
+    for srow in range(wl.n_state):
+        scale = max(np.abs(want[srow]).max(), 1e-3)
+        assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (solver, srow)
+
+
 # ---------------------------------------------------------------- one HSDC step
 
 CASES = [

@@ -48,6 +48,21 @@ def test_laplacian_dense_properties(orc):
     assert abs(np.diag(L)).max() <= 6 / 0.25 + 1e-12
 
 
+@pytest.mark.parametrize("shape", [(8, 1, 1), (4, 6, 1), (8, 3, 5), (1, 1, 1)])
+def test_shifted_operator_spectrum_interval(orc, shape):
+    # The whole spectrum of I - g L lies in [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))]
+    # and reaches both ends: the interval a Chebyshev semi-iteration on this
+    # operator is built on.  Dense eigenvalues of the oracle's operator.
+    nx, ny, nz = shape
+    h, g = 0.3, 0.07
+    m = _mono(nx, ny, nz, h=h)
+    N = nx * ny * nz
+    B = np.stack([e - g * m.laplacian(e) for e in np.eye(N)], axis=1)
+    ev = np.linalg.eigvalsh(0.5 * (B + B.T))
+    hi = 1 + g / h**2 * sum(4 * np.sin(np.pi * (n - 1) / (2 * n)) ** 2 for n in shape)
+    assert abs(ev.min() - 1.0) < 1e-12 and abs(ev.max() - hi) < 1e-12 * hi
+
+
 @pytest.mark.parametrize("shape", [(12, 1, 1), (9, 7, 1), (6, 5, 4)])
 def test_solvers_agree_and_solve(orc, shape):
     nx, ny, nz = shape

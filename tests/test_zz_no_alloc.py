@@ -25,7 +25,8 @@ def test_static_scratch_solve_matches_handle_solve():
     L = P.lib()
     wl = I.hh_sheet_32().with_mesh(48, 40, 9)         # 17,280 nodes, ragged in every axis
     tol, maxit = 1e-14, 500
-    s = P.Solver.from_workload(wl, tol_cg=tol, cg_maxit=maxit)
+    # the static solve runs the Jacobi-PCG: compare with the handle's solve run the same way
+    s = P.Solver.from_workload(wl, tol_cg=tol, cg_maxit=maxit, solver="cg")
     mesh = E.esdc_mesh(wl.dim, wl.nx, wl.ny, wl.nz, wl.h)
     stream = torch.cuda.current_stream().cuda_stream
     rng = np.random.default_rng(12)
