@@ -504,7 +504,7 @@ def run_batch_form(args):
         return e0.elapsed_time(e1)
 
     # ---- batched
-    b = P.Batch.from_workloads(wls, M_max=M)
+    b = P.Batch.from_workloads(wls, M_max=M, solver=args.solver)
     scratch = b.new_state()
     b.tune(scratch, w0.V0, 0.0, dt, M, K, reps=2)
     shape = b.shape()
@@ -529,7 +529,7 @@ def run_batch_form(args):
     iters = b.stats(K, M)
 
     # ---- one tissue at a time, as batches of one (same kernels)
-    singles = [P.Batch.from_workloads([w], M_max=M) for w in wls]
+    singles = [P.Batch.from_workloads([w], M_max=M, solver=args.solver) for w in wls]
     for s1 in singles:
         s1.set_shape(*shape[:2], 1)
     ys = [s1.new_state() for s1 in singles]
@@ -553,7 +553,7 @@ def run_batch_form(args):
     del ys
 
     # ---- one tissue at a time through esdc_sweep
-    solvers = [P.Solver.from_workload(w, M_max=M) for w in wls]
+    solvers = [P.Solver.from_workload(w, M_max=M, solver=args.solver) for w in wls]
     yv = [s.new_state() for s in solvers]
     for s, y in zip(solvers, yv):
         s.init_state(y, w0.V0)
@@ -614,6 +614,7 @@ def run_batch_form(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "hh_batch_64 (64 2D HH tissues, sides U[64,512], sigma U[0.05,0.3], seed 4)",
                    "form": "batch", "tissues": len(wls), "nodes": nodes, "M": M, "K": K, "dt_ms": dt,
+                   "solver": args.solver,
                    "l2": "inputs larger than L2 (batch state and workspace ~3.7 GB)"},
         "s_per_sim_ms": ms_b / steps * 1e-3 / dt,
         "launch_shape": {"node_waves": shape[0], "cg_threads": shape[1], "cg_blocks": shape[2]},
@@ -646,7 +647,7 @@ def run_qpar_batch(args, P, I, torch, timed):
     w = I.hh_sheet_32().with_mesh(512, 512, 1, name="hh_sheet_512")
     Pn, M, iters, dt = 16, w.M, 4, w.dt
     reps = 5
-    b = P.Batch.from_workloads([w] * Pn, M_max=M)
+    b = P.Batch.from_workloads([w] * Pn, M_max=M, solver=args.solver)
     yin, yout = b.new_state(), b.new_state()
     y0 = b.new_state()
     b.init_state(y0, w.V0)
@@ -660,7 +661,7 @@ def run_qpar_batch(args, P, I, torch, timed):
     if b.residual()[0] != 0:
         raise RuntimeError("Q^par batch failed")
     graph = b.graph_active()
-    singles = [P.Batch.from_workloads([w], M_max=M) for _ in range(Pn)]
+    singles = [P.Batch.from_workloads([w], M_max=M, solver=args.solver) for _ in range(Pn)]
     yi = [s.new_state() for s in singles]
     yo = [s.new_state() for s in singles]
     y0s = b.tissue(y0, 0).clone()
@@ -810,7 +811,7 @@ def run_fas_form(args):
     iters = args.steps if args.steps is not None else 10
     stream = torch.cuda.current_stream()
     # state at t0 = 0.4 ms: inside the stimulus window, the upstroke under way
-    one = P.Batch.from_workloads([w], M_max=M1)
+    one = P.Batch.from_workloads([w], M_max=M1, solver=args.solver)
     y0 = one.new_state()
     one.init_state(y0, w.V0)
     t0 = 0.0
@@ -827,8 +828,8 @@ def run_fas_form(args):
         raise RuntimeError("reference run failed")
     ref = yref[0, :w.n_nodes].clone()
 
-    fine = P.Batch.from_workloads([w] * Pn, M_max=M1)
-    coarse = [P.Batch.from_workloads([w], M_max=M2) for _ in range(Pn)]
+    fine = P.Batch.from_workloads([w] * Pn, M_max=M1, solver=args.solver)
+    coarse = [P.Batch.from_workloads([w], M_max=M2, solver=args.solver) for _ in range(Pn)]
     yin, yout = fine.new_state(), fine.new_state()
     last = int(fine.offsets[Pn - 1])
 
@@ -879,7 +880,7 @@ def run_fas_form(args):
         "steps": Pn, "warmup": 0, "ms_per_step": (h["ms"] / Pn) if h else None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"hh_sheet_{n} (corner stimulus), P=16 slices from t0={t0:.2f} ms",
-                   "form": "fas", "levels": [M1, M2], "dt_ms": dt,
+                   "form": "fas", "levels": [M1, M2], "dt_ms": dt, "solver": args.solver,
                    "value_is": "node-updates/s of the two-level solve to 1e-8 relative error of the last slice"},
         "tolerance": tol,
         "hsdc2_to_tol": h, "qpar_to_tol": q,
@@ -972,8 +973,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
     ap.add_argument("--solver", choices=["auto", "cg"], default="auto",
-                    help="diffusion solves of the headline step: auto (Chebyshev semi-iteration on the "
-                         "exactly known spectrum of the scalar-sigma operator) or cg (Jacobi-PCG)")
+                    help="diffusion solves (headline, batch and fas forms): auto (Chebyshev semi-iteration on "
+                         "the exactly known spectrum of the scalar-sigma operator) or cg (Jacobi-PCG)")
     ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet"], default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
                          "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "

@@ -373,7 +373,10 @@ int esdc_adjoint_backward(esdc_handle* h, const double* ckpt, double t0, double 
  * occupies columns [offset_b, offset_b + N_b), offset_b a multiple of 512
  * (esdc_batch_layout); the padding columns are never read as mesh nodes.
  * Batches run the FP64 path (options.precision must be 0) with scalar
- * conductivities.
+ * conductivities.  All tissues' diffusion solves run in one cooperative
+ * launch: the Chebyshev semi-iteration, each tissue on its own exactly known
+ * spectrum, with options.solver = 0 (the default), the Jacobi-PCG with
+ * solver = 1.
  * ------------------------------------------------------------------------ */
 typedef struct esdc_batch esdc_batch;
 

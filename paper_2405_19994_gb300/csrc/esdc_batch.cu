@@ -441,6 +441,230 @@ __global__ void __launch_bounds__(512) k_cgb(BCgArgs a)
     }
 }
 
+// Chebyshev semi-iteration for all tissues at once (options.solver = 0).  The
+// spectrum of tissue b's operator I - g_b L_b is [1, 1 + g_b ih2_b wspec_b]
+// (cosine modes), so each tissue runs the three-term recurrence on its own
+// interval with no inner products: x += d, r -= B d, d = rho' rho d + (2 rho'/delta) r,
+// rho' = 1/(2 theta/delta - rho), d_0 = r_0/theta.  Its iteration count comes
+// from the bound 2 q^k ||r_0|| <= tol ||b||, q = (sqrt(kappa) - 1)/(sqrt(kappa) + 1);
+// the residual is reduced (tile, then tissue, as in k_cgb) only at that
+// iteration and every second one after it, and at the cap.  One grid barrier
+// per iteration.  The same bookkeeping as k_cgb: the block holding a tissue's
+// first tile records its outcome, and the loop ends after the barrier at which
+// every tissue has recorded one.  Results per tissue depend on nothing but the
+// tissue, so batching keeps them bit for bit.
+__global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
+{
+    constexpr int U = ESDC_TILE / 32;
+    __shared__ bool s_active[kMaxBlockTissues], s_chk[kMaxBlockTissues];
+    __shared__ double s_gih2[kMaxBlockTissues], s_diag[kMaxBlockTissues][8];
+    __shared__ double s_s1[kMaxBlockTissues], s_delta[kMaxBlockTissues], s_rho[kMaxBlockTissues];
+    __shared__ double s_ca[kMaxBlockTissues], s_cb[kMaxBlockTissues], s_stop[kMaxBlockTissues];
+    __shared__ int s_chunk[kMaxBlockTissues];
+    __shared__ double s_tot[kMaxBlockTissues * 2];
+    __shared__ int s_exit;
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const long long nwt = (long long)gridDim.x * nwb;
+    BlockTissues bt;
+    bt.t0 = (long long)blockIdx.x * nwb * a.ntiles / nwt;
+    bt.t1 = (long long)(blockIdx.x + 1) * nwb * a.ntiles / nwt;
+    const long long wt0 = ((long long)blockIdx.x * nwb + w) * a.ntiles / nwt;
+    const long long wt1 = ((long long)blockIdx.x * nwb + w + 1) * a.ntiles / nwt;
+    if (bt.t1 > bt.t0) {
+        bt.lo = a.tile_tissue[bt.t0];
+        bt.n = a.tile_tissue[bt.t1 - 1] - bt.lo + 1;
+    } else {
+        bt.lo = 0;
+        bt.n = 0;
+    }
+    if (bt.n > kMaxBlockTissues) {
+        // As in k_cgb: the host sizes the grid so that this cannot happen.
+        if (threadIdx.x == 0) atomicOr(a.flags, ESDC_FLAG_TIMEOUT);
+        return;
+    }
+    for (int k = threadIdx.x; k < bt.n; k += blockDim.x) {
+        const TissueDev* T = a.tis + bt.lo + k;
+        const double gih2 = a.gfac * T->D * T->ih2;
+        s_gih2[k] = gih2;
+        for (int c = 0; c < 8; ++c) s_diag[k][c] = 1.0 + gih2 * c;
+        const double delta = 0.5 * gih2 * T->wspec, theta = 1.0 + delta;
+        s_delta[k] = delta;
+        s_s1[k] = delta > 0.0 ? theta / delta : 0.0;
+        s_rho[k] = delta > 0.0 ? delta / theta : 0.0;        // rho_0
+        s_active[k] = true;
+        if (T->tile0 >= bt.t0 && T->tile0 < bt.t1) a.done_at[bt.lo + k] = INT_MAX;
+    }
+    __syncthreads();
+
+    auto op = [&](const double* v, int p, const TileGeo& G, int k) -> double {
+        const int q = p - G.off;
+        const int r = q / G.nx;
+        const int ix = q - r * G.nx;
+        const int iz = r / G.ny;
+        const int iy = r - iz * G.ny;
+        const int sxy = G.nx * G.ny;
+        const double vp = __ldcg(v + p);
+        double s = 0.0;
+        int c = 0;
+        if (ix > 0)        { s += __ldcg(v + p - 1); ++c; }
+        if (ix < G.nx - 1) { s += __ldcg(v + p + 1); ++c; }
+        if (iy > 0)        { s += __ldcg(v + p - G.nx); ++c; }
+        if (iy < G.ny - 1) { s += __ldcg(v + p + G.nx); ++c; }
+        if (iz > 0)        { s += __ldcg(v + p - sxy); ++c; }
+        if (iz < G.nz - 1) { s += __ldcg(v + p + sxy); ++c; }
+        return fma(s_diag[k][c], vp, -(s_gih2[k] * s));
+    };
+    auto tile_geo = [&](long long t, int& k) -> TileGeo {
+        const int b = a.tile_tissue[t];
+        k = b - bt.lo;
+        const TissueDev* T = a.tis + b;
+        TileGeo G;
+        G.base = (int)(t << ESDC_TILE_SHIFT);
+        G.nx = T->nx; G.ny = T->ny; G.nz = T->nz; G.N = T->N; G.off = T->off;
+        return G;
+    };
+    unsigned target = 0;
+    double* dc = a.p;                 // d_k
+    double* dn = a.q;                 // d_{k+1}
+
+    // [S] r = b - B x, d_0 = r / theta; tile partials r.r, b.b (slots 0-1)
+    for (long long t = wt0; t < wt1; ++t) {
+        int k;
+        const TileGeo G = tile_geo(t, k);
+        const double inv_theta = 1.0 / (1.0 + s_delta[k]);
+        double v0 = 0.0, v1 = 0.0;
+#pragma unroll 4
+        for (int u = 0; u < U; ++u) {
+            const int p = G.base + lane + 32 * u;
+            if (p - G.off >= G.N) continue;
+            const double bx = op(a.x, p, G, k);
+            const double bp = __ldcg(a.b + p);
+            const double rp = bp - bx;
+            a.r[p] = rp;
+            dc[p] = rp * inv_theta;
+            v0 = fma(rp, rp, v0);
+            v1 = fma(bp, bp, v1);
+        }
+        v0 = warp_tree(v0); v1 = warp_tree(v1);
+        if (lane == 0) {
+            a.part[t] = v0;
+            a.part[(size_t)a.ntiles + t] = v1;
+        }
+    }
+    if (!grid_barrier(a.bar, target, a.flags)) return;
+    tissue_totals(a, bt, s_active, 0, 2, s_tot);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < bt.n; ++k) {
+            const double rr = s_tot[2 * k], stop = a.tol2 * s_tot[2 * k + 1];
+            s_stop[k] = stop;
+            const bool bad = !isfinite(rr) || !isfinite(stop);
+            const bool conv = rr <= stop;
+            if (bad || conv) {
+                s_active[k] = false;
+                const TissueDev* T = a.tis + bt.lo + k;
+                if (T->tile0 >= bt.t0 && T->tile0 < bt.t1) {
+                    a.done_at[bt.lo + k] = -1;
+                    a.status[2 * (bt.lo + k)] = 0;
+                    a.status[2 * (bt.lo + k) + 1] = bad ? ESDC_FLAG_NONFINITE : 0;
+                    if (a.iter_log) a.iter_log[bt.lo + k] = 0;
+                    if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+                }
+                continue;
+            }
+            // iterations the bound asks for (tol 0: up to the cap)
+            int kn = 1;
+            const double kap = 1.0 + 2.0 * s_delta[k];
+            const double q = (sqrt(kap) - 1.0) / (sqrt(kap) + 1.0);
+            if (q > 0.0) {
+                const double kd = stop > 0.0 ? ceil(log(0.5 * sqrt(stop / rr)) / log(q)) : (double)a.maxit;
+                kn = kd < (double)a.maxit ? (int)kd : a.maxit;
+            }
+            s_chunk[k] = kn < 1 ? 1 : kn;
+        }
+    }
+    __syncthreads();
+
+    for (int it = 0;; ++it) {
+        if (it > a.maxit) {                   // cannot happen: every tissue stops by maxit
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+            break;
+        }
+        // this iteration's coefficients, and which tissues check their residual after it
+        for (int k = threadIdx.x; k < bt.n; k += blockDim.x) {
+            if (!s_active[k]) { s_chk[k] = false; continue; }
+            const double rho = s_rho[k];
+            const double rn = s_delta[k] > 0.0 ? 1.0 / (2.0 * s_s1[k] - rho) : 0.0;
+            s_ca[k] = rn * rho;
+            s_cb[k] = s_delta[k] > 0.0 ? 2.0 * rn / s_delta[k] : 0.0;
+            s_rho[k] = rn;
+            s_chk[k] = it + 1 >= s_chunk[k] || it + 1 >= a.maxit;
+        }
+        __syncthreads();
+        // [U] x += d, r -= B d, d' = ca d + cb r; tile partials r.r of the checking tissues (slot 2)
+        for (long long t = wt0; t < wt1; ++t) {
+            int k;
+            const TileGeo G = tile_geo(t, k);
+            if (!s_active[k]) continue;
+            const double ca = s_ca[k], cb = s_cb[k];
+            const bool chk = s_chk[k];
+            double v = 0.0;
+#pragma unroll 4
+            for (int u = 0; u < U; ++u) {
+                const int p = G.base + lane + 32 * u;
+                if (p - G.off >= G.N) continue;
+                const double bd = op(dc, p, G, k);
+                const double dp = __ldcg(dc + p);
+                const double rp = __ldcg(a.r + p) - bd;
+                a.x[p] = __ldcg(a.x + p) + dp;
+                a.r[p] = rp;
+                dn[p] = fma(ca, dp, cb * rp);
+                if (chk) v = fma(rp, rp, v);
+            }
+            if (chk) {
+                v = warp_tree(v);
+                if (lane == 0) a.part[2 * (size_t)a.ntiles + t] = v;
+            }
+        }
+        double* sw = dc; dc = dn; dn = sw;
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        // every tissue has stopped by the previous iteration: leave (the same decision in every block)
+        if (threadIdx.x < 32) {
+            bool all = true;
+            for (int b = threadIdx.x; b < a.ntis; b += 32) all &= __ldcg(a.done_at + b) <= it - 1;
+            all = __all_sync(0xffffffffu, all);
+            if (threadIdx.x == 0) s_exit = all;
+        }
+        __syncthreads();
+        if (s_exit) break;
+        tissue_totals(a, bt, s_chk, 2, 1, s_tot);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < bt.n; ++k) {
+                if (!s_chk[k]) continue;
+                const double rr = s_tot[k];
+                const bool bad = !isfinite(rr);
+                const bool conv = rr <= s_stop[k];
+                const bool maxed = it + 1 >= a.maxit;
+                if (bad || conv || maxed) {
+                    s_active[k] = false;
+                    const TissueDev* T = a.tis + bt.lo + k;
+                    if (T->tile0 >= bt.t0 && T->tile0 < bt.t1) {
+                        const int f = bad ? ESDC_FLAG_NONFINITE : (conv ? 0 : ESDC_FLAG_CG_MAXIT);
+                        a.done_at[bt.lo + k] = it;
+                        a.status[2 * (bt.lo + k)] = it + 1;
+                        a.status[2 * (bt.lo + k) + 1] = f;
+                        if (a.iter_log) a.iter_log[bt.lo + k] = it + 1;
+                        if (f) atomicOr(a.flags, f);
+                    }
+                } else {
+                    s_chunk[k] = it + 3;          // rounding left it short: two more, then check
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- host
 template <class F>
 int occupancy(F kernel, int threads)
@@ -547,7 +771,7 @@ int max_block_tissues(const esdc_batch* b, int nb, int threads)
 
 int cg_grid(const esdc_batch* b, int threads, int per_sm_wanted)
 {
-    const int occ = occupancy(k_cgb, threads);
+    const int occ = b->opt.solver == 0 ? occupancy(k_chebb, threads) : occupancy(k_cgb, threads);
     if (occ < 1) return 0;
     int per_sm = std::min(occ, per_sm_wanted);
     long long nb = (long long)b->sms * per_sm;
@@ -580,7 +804,8 @@ cudaError_t launch_cgb(esdc_batch* b, double gfac, const double* rhs, double* x,
     void* args[] = {&a};
     cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void*)k_cgb, dim3(b->cg_blocks), dim3(b->cg_threads), args, 0, s);
+    const void* k = b->opt.solver == 0 ? (const void*)k_chebb : (const void*)k_cgb;
+    return cudaLaunchCooperativeKernel(k, dim3(b->cg_blocks), dim3(b->cg_threads), args, 0, s);
 }
 
 // Occupancy of the step kernels (queried before any stream capture).
@@ -823,6 +1048,7 @@ int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, doubl
     if (opt) o = *opt;
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
     if (o.precision != 0) return ESDC_ERR_UNSUPPORTED;            // batches run the FP64 path
+    if (o.solver != 0 && o.solver != 1) return ESDC_ERR_INVALID_ARG;
 
     esdc_batch* b = new (std::nothrow) esdc_batch();
     if (!b) return ESDC_ERR_NO_MEMORY;
@@ -844,6 +1070,12 @@ int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, doubl
         T.ntile = (T.N + ESDC_TILE - 1) / ESDC_TILE;
         T.ih2 = 1.0 / (meshes[k].h * meshes[k].h);
         T.D = sigma[k] / (chi * Cm);
+        const int ext[3] = {T.nx, T.ny, T.nz};
+        for (int d = 0; d < 3; ++d)
+            if (ext[d] > 1) {
+                const double sn = std::sin(M_PI * (ext[d] - 1) / (2.0 * ext[d]));
+                T.wspec += 4.0 * sn * sn;
+            }
         tile += T.ntile;
     }
     b->ntiles = tile;

@@ -91,6 +91,8 @@ struct TissueDev {
     int off;                 // first node in the concatenated arrays (multiple of ESDC_TILE)
     int tile0, ntile;        // its tiles
     double ih2, D;           // 1/h^2, sigma / (chi C_m)
+    double wspec;            // sum over axes with n > 1 of 4 sin^2(pi (n-1)/(2n)): the spectrum
+                             // of I - g L is [1, 1 + g ih2 wspec]
     StimDev st;
 };
 

@@ -340,7 +340,7 @@ class Batch:
     offsets[b] .. offsets[b] + n_nodes[b]."""
 
     def __init__(self, meshes, sigmas, chi: float, Cm: float, model: int, params, M_max: int = 8,
-                 tol_cg: float = 1e-14, cg_maxit: int = 200, precond: bool = True):
+                 tol_cg: float = 1e-14, cg_maxit: int = 200, precond: bool = True, solver: str = "auto"):
         self._b = None
         L = lib()
         n = len(meshes)
@@ -349,6 +349,9 @@ class Batch:
         opt = esdc_options()
         L.esdc_default_options(C.byref(opt))
         opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond = M_max, tol_cg, cg_maxit, int(precond)
+        if solver not in ("auto", "cg"):
+            raise ValueError("solver must be 'auto' or 'cg'")
+        opt.solver = 0 if solver == "auto" else 1
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_batch_create(n, arr, sig.ctypes.data_as(C.POINTER(_D)), chi, Cm, model,

@@ -117,6 +117,9 @@ def test_batch_invalid_arguments_rejected_without_gpu(L):
     opt = E.esdc_options(); L.esdc_default_options(C.byref(opt))
     opt.precision = 1
     assert create(optp=C.byref(opt)) == -6                     # batches run the FP64 path
+    opt.precision = 0
+    opt.solver = 3
+    assert create(optp=C.byref(opt)) == -1
     assert L.esdc_batch_sweep(None, None, None, 0.1, 3, 4, None) == -1
     assert L.esdc_batch_residual(None, None, None) == -1
     assert L.esdc_batch_layout(None, None, None, None) == -1

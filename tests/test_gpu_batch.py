@@ -30,8 +30,8 @@ def small_batch():
     return wls
 
 
-def run_batch(wls, steps, shape=None, graph=True, t0=0.0):
-    b = P.Batch.from_workloads(wls, M_max=3)
+def run_batch(wls, steps, shape=None, graph=True, t0=0.0, solver="auto"):
+    b = P.Batch.from_workloads(wls, M_max=3, solver=solver)
     if shape:
         b.set_shape(*shape)
     b.set_graph(graph)
@@ -51,10 +51,11 @@ def run_batch(wls, steps, shape=None, graph=True, t0=0.0):
     return out, r, graph_used
 
 
-def test_batch_matches_oracle_per_tissue():
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_batch_matches_oracle_per_tissue(solver):
     wls = small_batch()
     steps = 8
-    got, res, _ = run_batch(wls, steps)
+    got, res, _ = run_batch(wls, steps, solver=solver)
     for k, w in enumerate(wls):
         m = O.Monodomain(w)
         y = m.init_state()
@@ -67,13 +68,31 @@ def test_batch_matches_oracle_per_tissue():
         assert np.abs(got[k][1:] - y[1:]).max() < 1e-12, (k, w.name)
 
 
-def test_batch_bitwise_equals_one_at_a_time():
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_batch_bitwise_equals_one_at_a_time(solver):
     wls = small_batch()
     steps = 6
-    batched, _, _ = run_batch(wls, steps)
+    batched, _, _ = run_batch(wls, steps, solver=solver)
     for k, w in enumerate(wls):
-        alone, _, _ = run_batch([w], steps)
+        alone, _, _ = run_batch([w], steps, solver=solver)
         assert np.array_equal(batched[k], alone[0]), (k, w.name)
+
+
+def test_batch_chebyshev_degenerate_tissues():
+    """A single node (the operator is the identity: an interval of no width), a
+    four-node strip and a thin slab in one batch, each against the oracle."""
+    base = I.hh_batch(n=1, seed=21, side=(12, 12))[0]
+    wls = [base.with_mesh(1, 1, 1), base.with_mesh(4, 1, 1), base.with_mesh(9, 5, 2), base]
+    steps = 6
+    got, _, _ = run_batch(wls, steps)
+    for k, w in enumerate(wls):
+        m = O.Monodomain(w)
+        y = m.init_state()
+        t = 0.0
+        for _ in range(steps):
+            y, _, _, _ = m.step(y, t, w.dt, w.M, w.K)
+            t += w.dt
+        assert np.abs(got[k] - y).max() < 1e-12 * max(1.0, np.abs(y).max()), (k, w.nx, w.ny, w.nz)
 
 
 @pytest.mark.parametrize("shape", [(1, 512, 1), (2, 256, 2), (4, 256, 1)])
@@ -158,9 +177,10 @@ def test_batch_tuner_keeps_results():
     b.close()
 
 
-def test_batch_cg_maxit_reported_per_batch():
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_batch_cg_maxit_reported_per_batch(solver):
     wls = small_batch()[:2]
-    b = P.Batch.from_workloads(wls, M_max=3, cg_maxit=1)
+    b = P.Batch.from_workloads(wls, M_max=3, cg_maxit=1, solver=solver)
     y = b.new_state()
     b.init_state(y, -75.0)
     w0 = wls[0]
