@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
     __shared__ double s_gih2[kMaxBlockTissues], s_diag[kMaxBlockTissues][8];
     __shared__ double s_s1[kMaxBlockTissues], s_delta[kMaxBlockTissues], s_rho[kMaxBlockTissues];
     __shared__ double s_ca[kMaxBlockTissues], s_cb[kMaxBlockTissues], s_stop[kMaxBlockTissues];
+    __shared__ double s_itheta[kMaxBlockTissues];
     __shared__ int s_chunk[kMaxBlockTissues];
     __shared__ double s_tot[kMaxBlockTissues * 2];
     __shared__ int s_exit;
@@ -490,6 +491,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
         for (int c = 0; c < 8; ++c) s_diag[k][c] = 1.0 + gih2 * c;
         const double delta = 0.5 * gih2 * T->wspec, theta = 1.0 + delta;
         s_delta[k] = delta;
+        s_itheta[k] = 1.0 / theta;
         s_s1[k] = delta > 0.0 ? theta / delta : 0.0;
         s_rho[k] = delta > 0.0 ? delta / theta : 0.0;        // rho_0
         s_active[k] = true;
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
     for (long long t = wt0; t < wt1; ++t) {
         int k;
         const TileGeo G = tile_geo(t, k);
-        const double inv_theta = 1.0 / (1.0 + s_delta[k]);
+        const double inv_theta = s_itheta[k];
         double v0 = 0.0, v1 = 0.0;
 #pragma unroll 4
         for (int u = 0; u < U; ++u) {

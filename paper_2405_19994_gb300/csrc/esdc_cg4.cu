@@ -368,32 +368,34 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg4(CgArgs a)
 // One grid barrier per iteration (CG needs two and three dot products), and
 // 11 FP64 operations per node: the stencil, r, x and d.
 #define ESDC_CHEB_TAB 64
+#define ESDC_CHEB_THREADS 1024   // one block per SM; the quads of a mesh are too few to fill more warps
 struct ChebArgs {
-    double theta, q;
+    double inv_theta, q, log_q;
     double ca[ESDC_CHEB_TAB];   // rho_{k+1} rho_k
     double cb[ESDC_CHEB_TAB];   // 2 rho_{k+1} / delta   (index k; the last entry is used beyond)
 };
 
-__global__ void __launch_bounds__(ESDC_CG_THREADS) k_cheb4(CgArgs a, ChebArgs c)
+__global__ void __launch_bounds__(ESDC_CHEB_THREADS, 1) k_cheb4(CgArgs a, ChebArgs c)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const MeshDev& m = a.m;
     Tab<double> t = carve<double>(reinterpret_cast<double*>(dsm), m);
     build_tab(m, a.g, false, t);
     const int nq = m.N >> 2;
-    const int stride = gridDim.x * blockDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    // a contiguous, balanced range of quads per block (one block per SM)
+    const int q0 = (int)((long long)blockIdx.x * nq / gridDim.x);
+    const int q1 = (int)((long long)(blockIdx.x + 1) * nq / gridDim.x);
     double* part = a.part;
     __shared__ double bs[3];
     unsigned target = 0;
     double* dc = a.p;            // d_k
     double* dn = a.q;            // d_{k+1}
-    const double inv_theta = 1.0 / c.theta;
+    const double inv_theta = c.inv_theta;
 
     // r = b - B x, d_0 = r / theta; partials r.r, b.b
     {
         double v[2] = {0.0, 0.0};
-        for (int qi = tid; qi < nq; qi += stride) {
+        for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
             const Geo G = geo(m, qi);
             const DiagIdx di = diag_idx<false>(G);
             Q4<double> xc, bx;
@@ -419,13 +421,19 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cheb4(CgArgs a, ChebArgs c)
     const double stop = a.tol2 * tot[1];
     bool done = tot[0] <= stop;
     bool bad = !isfinite(tot[0]) || !isfinite(stop);
-    // iterations the bound asks for: 2 q^k ||r_0|| <= tol ||b||  (the same value in every thread)
-    int k_need = 1;
-    if (!done && !bad && c.q > 0.0) {
-        const double kd = stop > 0.0 ? ceil(log(0.5 * sqrt(stop / tot[0])) / log(c.q)) : (double)a.maxit;
-        k_need = kd < (double)a.maxit ? (int)kd : a.maxit;     // tol 0: run to the cap
+    // iterations the bound asks for: 2 q^k ||r_0|| <= tol ||b||.  One thread per block
+    // evaluates it (a few dozen FP64 operations) and shares it; every block gets the same value.
+    __shared__ int s_kneed;
+    if (threadIdx.x == 0) {
+        int kn = 1;
+        if (!done && !bad && c.q > 0.0) {
+            const double kd = stop > 0.0 ? ceil(log(0.5 * sqrt(stop / tot[0])) / c.log_q) : (double)a.maxit;
+            kn = kd < (double)a.maxit ? (int)kd : a.maxit;     // tol 0: run to the cap
+        }
+        s_kneed = kn < 1 ? 1 : kn;
     }
-    if (k_need < 1) k_need = 1;
+    __syncthreads();
+    const int k_need = s_kneed;
     int it = 0;
     int chunk_end = k_need < a.maxit ? k_need : a.maxit;
     while (!done && !bad && it < a.maxit) {
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cheb4(CgArgs a, ChebArgs c)
         const int ki = it < ESDC_CHEB_TAB ? it : ESDC_CHEB_TAB - 1;
         const double ca = c.ca[ki], cb = c.cb[ki];
         double v[1] = {0.0};
-        for (int qi = tid; qi < nq; qi += stride) {
+        for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
             const Geo G = geo(m, qi);
             const DiagIdx di = diag_idx<false>(G);
             Q4<double> d, bd;
@@ -709,10 +717,12 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     const double lmin = 1.0, lmax = 1.0 + h.g * h.mesh.ih2 * w;
     if (!(lmax > lmin)) return cudaErrorInvalidValue;
     ChebArgs c;
-    c.theta = 0.5 * (lmax + lmin);
-    const double delta = 0.5 * (lmax - lmin), s1 = c.theta / delta;
+    const double theta = 0.5 * (lmax + lmin);
+    c.inv_theta = 1.0 / theta;
+    const double delta = 0.5 * (lmax - lmin), s1 = theta / delta;
     const double kap = lmax / lmin;
     c.q = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    c.log_q = c.q > 0.0 ? std::log(c.q) : -1.0;
     double rho = 1.0 / s1;
     for (int k = 0; k < ESDC_CHEB_TAB; ++k) {
         const double rn = 1.0 / (2.0 * s1 - rho);
@@ -721,13 +731,21 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
         rho = rn;
     }
     const int ne = tab_entries(h.mesh);
-    const int nb = quad_blocks(h.mesh, h.w);
     const size_t bytes = sizeof(double) * ne;
-    cudaError_t e = cudaMemsetAsync(h.w.bar, 0, sizeof(unsigned), s);
+    cudaError_t e = prepare(k_cheb4, bytes);
     if (e != cudaSuccess) return e;
-    if ((e = prepare(k_cheb4, bytes)) != cudaSuccess) return e;
+    // One block per SM, balanced ranges of quads (blocks of at least 128 quads on small meshes).
+    int threads = ESDC_CHEB_THREADS, per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb4, threads, bytes)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) threads = h.w.threads;              // fewer registers than expected: the CG block size
+    const long long nq = h.mesh.N / 4;
+    long long nb = (nq + 127) / 128;
+    if (nb > h.w.max_blocks) nb = h.w.max_blocks;
+    if (nb < 1) nb = 1;
+    if ((e = cudaMemsetAsync(h.w.bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     void* args[] = {&a, &c};
-    return cudaLaunchCooperativeKernel((const void*)k_cheb4, dim3(nb), dim3(h.w.threads), args, bytes, s);
+    return cudaLaunchCooperativeKernel((const void*)k_cheb4, dim3((unsigned)nb), dim3(threads), args, bytes, s);
 }
 
 cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s)
