@@ -972,9 +972,10 @@ def main():
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
-    ap.add_argument("--solver", choices=["auto", "cg"], default="auto",
+    ap.add_argument("--solver", choices=["auto", "cg", "dct"], default="auto",
                     help="diffusion solves (headline, batch and fas forms): auto (Chebyshev semi-iteration on "
-                         "the exactly known spectrum of the scalar-sigma operator) or cg (Jacobi-PCG)")
+                         "the exactly known spectrum of the scalar-sigma operator), cg (Jacobi-PCG) or dct "
+                         "(the DCT-II direct solve; headline form only)")
     ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet"], default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
                          "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "
@@ -984,6 +985,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.solver == "dct" and (args.form != "plain" or args.impl != "ours"):
+        ap.error("--solver dct applies to the headline form only")
     if args.steps is None and args.form == "plain":
         args.steps = 40
     if args.impl == "reference":

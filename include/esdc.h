@@ -91,7 +91,17 @@ typedef struct {
                           nx a multiple of 4: the interval [1, 1 + (g/h^2)
                           sum_axes 4 sin^2(pi (n-1)/(2n))], the cosine modes
                           being its eigenvectors), the Jacobi-PCG elsewhere;
-                          1 = the (Jacobi-P)CG always.
+                          1 = the (Jacobi-P)CG always;
+                          2 = the DCT-II direct solve, the paper's solver (Sec. 5):
+                          x = C^T diag(1/(1 - g mu)) C b with C the orthonormal
+                          3D DCT-II (one dense product per axis, cuBLAS DGEMM)
+                          and mu the eigenvalues of the second- or fourth-order
+                          stencil; exact, no iteration (iters reports 1).
+                          Scalar sigma and precision 0 only (esdc_create returns
+                          ESDC_ERR_UNSUPPORTED with precision 1; the conductivity
+                          setters return it for layers or a field); holds the
+                          axes' DCT matrices (nx^2 + ny^2 + nz^2 doubles).
+                          Batches take 0 or 1.
                           Both stop at the same ||r|| <= tol_cg ||b||.  The paper
                           leaves the inner solver open (it uses PCG).            */
 } esdc_options;

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libesdc.so")
-SOURCES = ["esdc_step.cu", "esdc_step_mixed.cu", "esdc_cg.cu", "esdc_cg4.cu", "esdc_batch.cu", "esdc_adjoint.cu", "esdc_static.cu", "esdc_colloc.cpp"]
+SOURCES = ["esdc_step.cu", "esdc_step_mixed.cu", "esdc_cg.cu", "esdc_cg4.cu", "esdc_batch.cu", "esdc_adjoint.cu",
+           "esdc_static.cu", "esdc_dct.cu", "esdc_colloc.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 
@@ -61,7 +62,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], check=True)
+    # cuBLAS (the DGEMMs of the DCT-II solve) from the toolkit that compiled the library
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-L" + cuda_lib, "-lcublas",
+                    "-Xlinker", "-rpath," + cuda_lib], check=True)
     os.replace(tmp, LIB)
     return LIB
 

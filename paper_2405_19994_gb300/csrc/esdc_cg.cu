@@ -498,6 +498,10 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
                            double* x, double tol, int maxit, int precond, int solver, int* iter_log,
                            int* flags, cudaStream_t s)
 {
+    if (solver == 2) {
+        if (!w.dct) return cudaErrorInvalidValue;
+        return esdc_dct_launch(mesh, w, g, b, x, iter_log, flags, s);
+    }
     if (esdc_cg4_eligible(mesh, b, x)) {
         CgArgsHost hq{mesh, w, g, b, x, tol, maxit, precond, iter_log, flags};
         if (solver == 0 && g > 0.0 && esdc_cheb_eligible(mesh, b, x)) return esdc_cheb_launch(hq, s);

@@ -58,6 +58,7 @@ struct esdc_handle {
     double *Y = nullptr, *G0 = nullptr, *G1 = nullptr, *FI = nullptr, *S = nullptr, *PHI = nullptr,
            *LAMN = nullptr, *rhs = nullptr, *R = nullptr, *ydev = nullptr, *Vprev = nullptr;
     CgWork cg{};
+    DctDev dct{};                         // options.solver = 2
     // adjoint recording (set only inside esdc_adjoint_backward): Y^{1..K},
     // G^{0..K}, FI^{0..K} of one step, each block [M][NS][ld] or [M][ld]
     double *tapeY = nullptr, *tapeG = nullptr, *tapeFI = nullptr;

@@ -96,6 +96,16 @@ struct TissueDev {
     StimDev st;
 };
 
+// Direct DCT-II solve (options.solver = 2): orthonormal DCT-II matrices of the
+// axes with more than one cell (column-major, [n][n]), eigenvalues of the 1D
+// difference operator per mode (1/h^2 included), and the cuBLAS handle of the
+// axis transforms.
+struct DctDev {
+    double *cx = nullptr, *cy = nullptr, *cz = nullptr;
+    double *ex = nullptr, *ey = nullptr, *ez = nullptr;
+    void* blas = nullptr;
+};
+
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
 struct CgWork {
     double *r, *p, *q, *z;          // [ld] each
@@ -105,7 +115,15 @@ struct CgWork {
     int* status;                    // [2]: iterations of the last solve, flag bits
     int max_blocks;
     int threads;
+    const DctDev* dct = nullptr;    // set when options.solver = 2
 };
+
+cudaError_t esdc_dct_create(const MeshDev& m, DctDev* d);
+cudaError_t esdc_dct_set_order(const MeshDev& m, DctDev* d);   // eigenvalues for m.order
+void esdc_dct_destroy(DctDev* d);
+// x = (I - g L)^{-1} b by the DCT-II (scalar sigma); uses w.r and w.p as work vectors.
+cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const double* b, double* x,
+                            int* iter_log, int* flags, cudaStream_t s);
 
 // Validates ionic-model parameters and fills the device parameter blocks;
 // returns ESDC_OK or ESDC_ERR_INVALID_ARG.
@@ -118,7 +136,8 @@ int esdc_model_setup(int model, const double* params, int n_params, ModelDev* mp
 // Enqueue one solve of (I - g A) x = b; iter_log (device, optional) receives the
 // iteration count, flags (device) accumulates ESDC_FLAG_* bits.  solver 0 takes
 // the Chebyshev semi-iteration where esdc_cheb_eligible holds and g > 0, the
-// (Jacobi-P)CG otherwise; solver 1 always the CG.  Returns a cudaError_t.
+// (Jacobi-P)CG otherwise; solver 1 always the CG; solver 2 the DCT-II direct
+// solve (w.dct must be set).  Returns a cudaError_t.
 cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
                            double* x, double tol, int maxit, int precond, int solver, int* iter_log,
                            int* flags, cudaStream_t s);

@@ -162,6 +162,7 @@ void free_all(esdc_handle* h)
 {
     for (auto& e : h->prof_ev)
         if (e) cudaEventDestroy(e);
+    esdc_dct_destroy(&h->dct);
     if (h->lay) cudaFree(h->lay);
     if (h->layf) cudaFree(h->layf);
     if (h->wdiag) cudaFree(h->wdiag);
@@ -249,7 +250,8 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     if (opt) o = *opt;
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
     if (o.precision != 0 && o.precision != 1) return ESDC_ERR_INVALID_ARG;
-    if (o.solver != 0 && o.solver != 1) return ESDC_ERR_INVALID_ARG;
+    if (o.solver < 0 || o.solver > 2) return ESDC_ERR_INVALID_ARG;
+    if (o.solver == 2 && o.precision != 0) return ESDC_ERR_UNSUPPORTED;     // the DCT solve is FP64
 
     esdc_handle* h = new (std::nothrow) esdc_handle();
     if (!h) return ESDC_ERR_NO_MEMORY;
@@ -311,6 +313,11 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     cudaMemset(h->cg.status, 0, sizeof(int) * 2);
     cudaMemset(h->flags, 0, sizeof(int));
     cudaMemset(h->cg_log, 0, sizeof(int) * h->cg_log_len);
+    if (o.solver == 2) {
+        const cudaError_t e = esdc_dct_create(h->mesh, &h->dct);
+        if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA);
+        h->cg.dct = &h->dct;
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(ESDC_ERR_CUDA);
     *out = h;
     return ESDC_OK;
@@ -363,6 +370,7 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
         return ESDC_OK;
     }
     if (!sxx || !syy || !sxy || !szz) return set_err(h, ESDC_ERR_INVALID_ARG, "all four layer arrays are needed");
+    if (h->opt.solver == 2) return set_err(h, ESDC_ERR_UNSUPPORTED, "the DCT solve needs the scalar sigma");
     if (h->mesh.order != 2)
         return set_err(h, ESDC_ERR_UNSUPPORTED, "layered conductivity needs the second-order stencil");
     if (h->sigf) {                                       // layers replace a conductivity field
@@ -409,6 +417,7 @@ int esdc_set_stencil_order(esdc_handle* h, int order)
     if (order == 2) {
         h->mesh.order = 2;
         if (h->wdiag && !h->lay && !h->sigf) { cudaFree(h->wdiag); h->wdiag = nullptr; h->mesh.wdiag = nullptr; }
+        if (h->cg.dct) CUDA_TRY(h, esdc_dct_set_order(h->mesh, &h->dct));
         return ESDC_OK;
     }
     if (h->lay || h->sigf) return set_err(h, ESDC_ERR_UNSUPPORTED, "the fourth-order stencil needs the scalar sigma");
@@ -418,6 +427,7 @@ int esdc_set_stencil_order(esdc_handle* h, int order)
     h->mesh.wdiag = h->wdiag;
     k_wdiag<<<grid_for(h, 256), 256>>>(h->mesh, h->wdiag);
     CUDA_TRY(h, cudaGetLastError());
+    if (h->cg.dct) CUDA_TRY(h, esdc_dct_set_order(h->mesh, &h->dct));
     CUDA_TRY(h, cudaDeviceSynchronize());
     return ESDC_OK;
 }
@@ -435,6 +445,7 @@ int esdc_set_conductivity_field(esdc_handle* h, const double* sigma)
     }
     if (h->opt.precision != 0)
         return set_err(h, ESDC_ERR_UNSUPPORTED, "a conductivity field runs on the FP64 path only");
+    if (h->opt.solver == 2) return set_err(h, ESDC_ERR_UNSUPPORTED, "the DCT solve needs the scalar sigma");
     if (h->mesh.order != 2)
         return set_err(h, ESDC_ERR_UNSUPPORTED, "a conductivity field needs the second-order stencil");
     const int64_t N = h->mesh.N;

@@ -155,9 +155,9 @@ class Solver:
         if precision not in ("fp64", "mixed"):
             raise ValueError("precision must be 'fp64' or 'mixed'")
         opt.precision = 1 if precision == "mixed" else 0
-        if solver not in ("auto", "cg"):
-            raise ValueError("solver must be 'auto' or 'cg'")
-        opt.solver = 0 if solver == "auto" else 1
+        if solver not in ("auto", "cg", "dct"):
+            raise ValueError("solver must be 'auto', 'cg' or 'dct'")
+        opt.solver = {"auto": 0, "cg": 1, "dct": 2}[solver]
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_create(C.byref(mesh), sigma, chi, Cm, model, p.ctypes.data_as(C.POINTER(_D)), len(p),

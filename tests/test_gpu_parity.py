@@ -203,6 +203,62 @@ def test_one_step_either_solver_matches_oracle(solver):
         assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (solver, srow)
 
 
+# ---------------------------------------------------------------- DCT-II direct solve (options.solver = 2)
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5), (2, 3, 2)])
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("g", [1e-3, 0.05, 2.0])
+def test_dct_solve_matches_oracle(shape, order, g):
+    """The GPU DCT-II solve (cuBLAS products per axis, own spectral division)
+    against the oracle's exact DCT-II solve of the same stencil."""
+    nx, ny, nz = shape
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.order = order
+    s = P.Solver.from_workload(wl, solver="dct")
+    m = O.Monodomain(wl)
+    rng = np.random.default_rng(23)
+    b = rng.normal(size=wl.n_nodes)
+    want = m.solve_shifted(g, b, method=O.SOLVE_DCT)
+    xd = torch.from_numpy(rng.normal(size=wl.n_nodes)).cuda()     # the initial guess plays no part
+    it = s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+    got = xd.cpu().numpy()
+    assert it == 1
+    # both are exact solves: rounding of a few dense products of length <= 64
+    assert rel(got, want) < 1e-13, rel(got, want)
+    # and the residual of the oracle's own operator is at rounding level
+    Bx = got - g * m.laplacian(got)
+    assert np.abs(Bx - b).max() < 1e-12 * (1 + 16 * 3 * g / wl.h**2) * np.abs(b).max()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_dct_one_step_matches_oracle(order):
+    wl = I.syn19_slab().with_mesh(12, 10, 4)
+    wl.order = order
+    M, K = 4, 6
+    s = P.Solver.from_workload(wl, M_max=M, solver="dct")
+    y0 = I.random_state(wl, seed=41)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.5, wl.dt, M, K)
+    assert s.residual()[0] == 0
+    assert (s.stats(K * M) == 1).all()
+    got = from_dev(s, yd)
+    want, _, _, _ = O.Monodomain(wl).step(y0, 0.5, wl.dt, M, K)
+    for srow in range(wl.n_state):
+        scale = max(np.abs(want[srow]).max(), 1e-3)
+        assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (order, srow)
+
+
+def test_dct_needs_scalar_sigma():
+    wl = I.hh_sheet_32().with_mesh(16, 12, 1)
+    s = P.Solver.from_workload(wl, solver="dct")
+    with pytest.raises(P.EsdcError) as e:
+        s.set_conductivity_field(I.lognormal_field(wl.nx, wl.ny, wl.nz, seed=3))
+    assert e.value.code == -6
+    with pytest.raises(P.EsdcError) as e:
+        s.set_conductivity_layers(I.fibre_layers(1))
+    assert e.value.code == -6
+
+
 # ---------------------------------------------------------------- one HSDC step
 
 CASES = [
