@@ -325,9 +325,9 @@ class Monodomain:
         """Algorithm HSDC (Sec. 3.2) with two levels, M = M1, M2 (M1 > M2 Radau
         nodes), over P consecutive steps from y0 at t0, without Burn-in (not
         specified: z^0 = 1 (x) y0 in every slice).  One iteration:
-          tau = S D_1(z) - D_2(S z), per slice S R_1(z_p) - R_2(S z_p), with R the
-                collocation residual vectors (the slice couplings cancel, and
-                row 0 of tau vanishes because c_M = 1 on both levels);
+          tau = D_2(S z) - S D_1(z), per slice S R_1(z_p) - R_2(S z_p), with
+                R = b - D the collocation residual vectors (the slice couplings
+                cancel, and row 0 of tau vanishes because c_M = 1 on both levels);
           coarse: one Q^seq sweep from S z with tau: slice p starts from the
                 new end value of slice p-1;
           fine:   one Q^par sweep from z + T(z_2 - S z): slice p starts from the
@@ -362,6 +362,83 @@ class Monodomain:
                 _, _, Znew[p], _ = self.step(Y0[p], t0 + p * dt, dt, M1, 1, want_colloc=True, colloc_in=W[p])
             Z = Znew
         return Z
+
+    def hsdc(self, y0: np.ndarray, t0: float, dt: float, P: int, Ms, iters: int,
+             Z0: np.ndarray | None = None):
+        """Algorithm HSDC (Sec. 3.2) with L = len(Ms) >= 2 levels of M_1 > ... > M_L
+        Radau nodes over P consecutive steps from y0 at t0, without Burn-in
+        (z^0 = 1 (x) y0 in every slice).  S_l restricts level l to level l+1 and
+        T_l prolongs back: Lagrange interpolation through the nodes c_1..c_M of
+        the source level (row 0, the slice's initial value, is kept).  With
+        R_l(z; tau) = b + tau - D_l(z) the residual vectors, one iteration is
+          level 1:      z_1^{k+1/2} = z_1^k, tau_1 = 0;
+          l = 2..L:     tau_l = S R_{l-1}(z_{l-1}^{k+1/2}; tau_{l-1}) - R_l(S z_{l-1}^{k+1/2}; 0)
+                        (that is D_l(S z) - S D_{l-1}(z) + S tau_{l-1});
+                        for l < L one Q^par sweep from S z_{l-1}^{k+1/2} with tau_l gives z_l^{k+1/2};
+          level L:      one Q^seq sweep from S z_{L-1}^{k+1/2} with tau_L gives z_L^{k+1};
+          l = L-1..1:   one Q^par sweep from z_l^{k+1/2} + T (z_{l+1}^{k+1} - S z_l^{k+1/2})
+                        with tau_l gives z_l^{k+1}.
+        A Q^par sweep starts slice p from the end value of slice p-1 of the
+        iterate it sweeps (y0 for slice 0), the Q^seq sweep from the new end
+        value of slice p-1; a residual of slice p uses the initial value its
+        iterate was swept with.  Z0 [P, M_1, ns, N] (optional) replaces z^0.
+        Returns the level-1 iterates [P, M_1, ns, N].  With two levels this is
+        hsdc2."""
+        Ms = [int(M) for M in Ms]
+        L = len(Ms)
+        if L < 2 or any(Ms[l + 1] >= Ms[l] for l in range(L - 1)):
+            raise ValueError("need L >= 2 levels with M_1 > M_2 > ... > M_L")
+        y0 = np.asarray(y0, np.float64).reshape(self.ns, self.N)
+        nodes = [radau_nodes(M)[1:] for M in Ms]
+        Smat = [lagrange_matrix(nodes[l], nodes[l + 1]) for l in range(L - 1)]    # [M_{l+1}, M_l]
+        Tmat = [lagrange_matrix(nodes[l + 1], nodes[l]) for l in range(L - 1)]    # [M_l, M_{l+1}]
+
+        def restrict(l, X):                      # level l -> l + 1 (0-based levels)
+            return np.einsum("ij,pjsn->pisn", Smat[l], X)
+
+        def prolong(l, X):                       # level l + 1 -> l
+            return np.einsum("ij,pjsn->pisn", Tmat[l], X)
+
+        def residuals(l, Z, Y0, tau):
+            out = np.empty_like(Z)
+            for p in range(P):
+                _, _, _, out[p] = self.step(Y0[p], t0 + p * dt, dt, Ms[l], 0, want_resid=True, colloc_in=Z[p],
+                                            tau=None if tau is None else tau[p])
+            return out
+
+        def sweep_par(l, Zs, tau):
+            Zn = np.empty_like(Zs)
+            Y0 = np.empty((P, self.ns, self.N))
+            for p in range(P):
+                Y0[p] = y0 if p == 0 else Zs[p - 1, Ms[l] - 1]
+                _, _, Zn[p], _ = self.step(Y0[p], t0 + p * dt, dt, Ms[l], 1, want_colloc=True, colloc_in=Zs[p],
+                                           tau=None if tau is None else tau[p])
+            return Zn, Y0
+
+        Z1 = np.broadcast_to(y0, (P, Ms[0], self.ns, self.N)).copy() if Z0 is None else np.array(Z0, np.float64)
+        Y01 = np.broadcast_to(y0, (P, self.ns, self.N)).copy()
+        if Z0 is not None:
+            Y01[1:] = Z1[:-1, Ms[0] - 1]
+        for _ in range(iters):
+            Zh, Y0h, SZ, tau = [Z1], [Y01], [None], [None]
+            for l in range(1, L):                                           # down to the coarsest level
+                SZ.append(restrict(l - 1, Zh[l - 1]))
+                tau.append(restrict(l - 1, residuals(l - 1, Zh[l - 1], Y0h[l - 1], tau[l - 1]))
+                           - residuals(l, SZ[l], Y0h[l - 1], None))
+                if l < L - 1:
+                    zl, yl = sweep_par(l, SZ[l], tau[l])
+                    Zh.append(zl)
+                    Y0h.append(yl)
+            Zc = np.empty_like(SZ[L - 1])                                   # Q^seq on the coarsest level
+            for p in range(P):
+                yi = y0 if p == 0 else Zc[p - 1, Ms[L - 1] - 1]
+                _, _, Zc[p], _ = self.step(yi, t0 + p * dt, dt, Ms[L - 1], 1, want_colloc=True,
+                                           colloc_in=SZ[L - 1][p], tau=tau[L - 1][p])
+            Znew = Zc
+            for l in range(L - 2, -1, -1):                                  # back up, correcting each level
+                Znew, Y0new = sweep_par(l, Zh[l] + prolong(l, Znew - SZ[l + 1]), tau[l])
+            Z1, Y01 = Znew, Y0new
+        return Z1
 
     def run(self, y0: np.ndarray, t0: float, dt: float, nsteps: int, M: int, K: int):
         y = np.array(y0, np.float64)

@@ -402,3 +402,37 @@ def test_step_tau_shifts_the_collocation_solution(orc):
     # with tau = -r(Yp) the collocation system C(y) = 1 (x) y_n + tau is solved by Yp
     _, _, Z, rz = m.step(y0, 0.0, wl.dt, M, 60, want_colloc=True, want_resid=True, colloc_in=Yp, tau=-r)
     assert np.abs(Z - Yp).max() < 1e-11 * np.abs(Yp).max()
+
+
+def test_hsdc_two_levels_is_hsdc2(orc):
+    # the L-level driver with L = 2 takes exactly the two-level algorithm's steps
+    wl, m, y0 = _hsdc_case()
+    P, M1, M2 = 3, 3, 2
+    a = m.hsdc(y0, 0.0, wl.dt, P, (M1, M2), 2)
+    b = m.hsdc2(y0, 0.0, wl.dt, P, M1, M2, 2)
+    assert np.array_equal(a, b)
+
+
+def test_hsdc_three_levels_fixed_point_is_sequential_collocation(orc):
+    wl, m, y0 = _hsdc_case()
+    P, Ms = 3, (4, 3, 1)
+    Z = m.hsdc(y0, 0.0, wl.dt, P, Ms, 16)
+    ref = _sequential_collocation(m, y0, wl.dt, P, Ms[0])
+    assert np.abs(Z - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_hsdc_three_levels_converged_solution_is_left_unchanged(orc):
+    # FAS consistency on every level: at the fine solution each tau-corrected
+    # coarser problem is solved by the restricted solution, so nothing moves
+    wl, m, y0 = _hsdc_case()
+    P, Ms = 3, (4, 3, 2)
+    ref = _sequential_collocation(m, y0, wl.dt, P, Ms[0])
+    Z = m.hsdc(y0, 0.0, wl.dt, P, Ms, 1, Z0=ref)
+    assert np.abs(Z - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_hsdc_rejects_bad_levels(orc):
+    wl, m, y0 = _hsdc_case()
+    for Ms in ((3,), (2, 3), (3, 3)):
+        with pytest.raises(ValueError):
+            m.hsdc(y0, 0.0, wl.dt, 2, Ms, 1)
