@@ -850,11 +850,19 @@ def run_fas_form(args):
         yin.zero_()
         fine.tissue(yin, 0).copy_(y0[:, :w.n_nodes])
 
-    out = {"hsdc2": [], "qpar": []}
+    # three levels, M = 3, 2, 1: a second Q^par level of the same slices, Q^seq at M = 1
+    M3 = 1
+    mid = P.Batch.from_workloads([w] * Pn, M_max=M2, solver=args.solver)
+    coarse3 = [P.Batch.from_workloads([w], M_max=M3, solver=args.solver) for _ in range(Pn)]
+
+    out = {"hsdc2": [], "hsdc3": [], "qpar": []}
     for k in range(1, iters + 1):
         load()
         ms = timed(lambda: P.esdc.hsdc2(fine, coarse, yin, yout, t0, dt, M1, M2, k))
         out["hsdc2"].append({"iters": k, "ms": ms, "err": err()})
+        load()
+        ms = timed(lambda: P.esdc.hsdc([fine, mid], coarse3, yin, yout, t0, dt, (M1, M2, M3), k))
+        out["hsdc3"].append({"iters": k, "ms": ms, "err": err()})
         load()
         ms = timed(lambda: fine.qpar(yin, yout, t0, dt, M1, k))
         if fine.residual()[0] != 0:
@@ -874,6 +882,7 @@ def run_fas_form(args):
     tol = 1e-8
     h, q = first_below(out["hsdc2"], tol), first_below(out["qpar"], tol)
     h6, q6 = first_below(out["hsdc2"], 1e-6), first_below(out["qpar"], 1e-6)
+    h3, h36 = first_below(out["hsdc3"], tol), first_below(out["hsdc3"], 1e-6)
     nodes = Pn * w.n_nodes
     line = {
         "metric": METRIC, "value": (nodes / (h["ms"] * 1e-3)) if h else None, "unit": UNIT, "n_gpus": 1,
@@ -887,10 +896,12 @@ def run_fas_form(args):
         "speedup_hsdc2_vs_qpar_to_tol": (q["ms"] / h["ms"]) if (h and q) else None,
         "hsdc2_to_1e-6": h6, "qpar_to_1e-6": q6,
         "speedup_hsdc2_vs_qpar_to_1e-6": (q6["ms"] / h6["ms"]) if (h6 and q6) else None,
+        "hsdc3_levels": [M1, M2, M3], "hsdc3_to_tol": h3, "hsdc3_to_1e-6": h36,
         "history": out,
     }
-    for c in coarse:
+    for c in coarse + coarse3:
         c.close()
+    mid.close()
     fine.close()
     print(json.dumps(line), flush=True)
 

@@ -479,6 +479,28 @@ int esdc_interp(const double* src, int Ms, int64_t src_ld, double* dst, int Md, 
 int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double* y_out, double t0, double dt, int M1,
                int M2, int iters, void* stream);
 
+/* Algorithm HSDC (Sec. 3.2) with L >= 2 levels, M[0] > M[1] > ... > M[L-1]
+ * Radau nodes (host array), over the P tissues of levels[0] as consecutive
+ * time slices, without Burn-in.  levels[0..L-2] are P-tissue batches of the
+ * same slices (same meshes, so the same layout; M_max >= M[l]) swept by Q^par;
+ * coarse[p] (p < P) are single-tissue batches of the slice mesh with
+ * M_max >= M[L-1], swept one slice after another by Q^seq.  Restriction and
+ * prolongation between consecutive levels are the Lagrange interpolators
+ * through the source level's nodes c_1..c_M.  One iteration: going down,
+ * tau_l = S R_{l-1}(z_{l-1}; tau_{l-1}) - R_l(S z_{l-1}) (the paper's
+ * D_l(S z) - S D_{l-1}(z) + S tau_{l-1}) and, above the coarsest level, one
+ * Q^par sweep from S z_{l-1} with tau_l; one Q^seq sweep with tau on the
+ * coarsest level; going up, the coarse-grid correction z_l += T (z_{l+1} -
+ * S z_l) and one Q^par sweep with tau_l on each level.  A Q^par sweep starts
+ * slice p from the end value of slice p-1 of the iterate it sweeps.  y_in
+ * slice 0 holds y0 at t0 on entry; on return the finest iterate is in
+ * esdc_batch_iterate(levels[0]) and y_out slice p holds y_{p,M[0]}.  With
+ * L = 2 this is esdc_hsdc2.  Allocates its scratch (per level above the
+ * coarsest: 2 M_l + 1 state arrays).  Synchronises.  Errors: INVALID_ARG,
+ * NO_MEMORY, CUDA and those of the sweeps. */
+int esdc_hsdc(esdc_batch* const* levels, esdc_batch* const* coarse, const int* M, int L, double* y_in,
+              double* y_out, double t0, double dt, int iters, void* stream);
+
 /* Per tissue (host [n], optional): max |r| of the collocation residual and
  * max |y| of the last step.  Synchronises that step's stream.  Returns
  * NONFINITE, CG_NOT_CONVERGED or DEVICE_TIMEOUT if any tissue raised it. */

@@ -1409,16 +1409,38 @@ int esdc_interp(const double* src, int Ms, int64_t src_ld, double* dst, int Md, 
     return cudaGetLastError() == cudaSuccess ? ESDC_OK : ESDC_ERR_CUDA;
 }
 
-int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double* y_out, double t0, double dt, int M1,
-               int M2, int iters, void* stream)
+int esdc_hsdc(esdc_batch* const* levels, esdc_batch* const* coarse, const int* M, int L, double* y_in,
+              double* y_out, double t0, double dt, int iters, void* stream)
 {
-    if (!fine || !coarse || !y_in || !y_out || y_in == y_out || iters < 1 || M2 < 1 || M2 >= M1 ||
-        M1 > fine->opt.M_max)
-        return fine ? set_berr(fine, ESDC_ERR_INVALID_ARG, "bad two-level arguments") : ESDC_ERR_INVALID_ARG;
-    // Lagrange matrices between the Radau nodes c_1..c_M of the two levels
-    // (Sec. 3.2: I_l(y, s) = sum_j l_j(s) y_j): restriction S [M2][M1], prolongation T [M1][M2]
-    const double* cf = fine->col[M1 - 1].c + 1;
-    const double* cc = fine->col[M2 - 1].c + 1;
+    if (!levels || !levels[0]) return ESDC_ERR_INVALID_ARG;
+    esdc_batch* fine = levels[0];
+    if (!coarse || !M || !y_in || !y_out || y_in == y_out || iters < 1 || L < 2 || L > ESDC_MMAX)
+        return set_berr(fine, ESDC_ERR_INVALID_ARG, "bad multilevel arguments");
+    for (int l = 0; l < L; ++l)
+        if (M[l] < 1 || (l > 0 && M[l] >= M[l - 1]) || (l < L - 1 && (!levels[l] || M[l] > levels[l]->opt.M_max)))
+            return set_berr(fine, ESDC_ERR_INVALID_ARG, "levels need M_1 > M_2 > ... > M_L and M_l <= M_max");
+    const int P = fine->ntis, NSt = fine->NS;
+    const TissueDev& T0 = fine->tis_h[0];
+    for (const TissueDev& T : fine->tis_h)
+        if (T.nx != T0.nx || T.ny != T0.ny || T.nz != T0.nz || T.D != T0.D || T.ih2 != T0.ih2)
+            return set_berr(fine, ESDC_ERR_INVALID_ARG, "slices must share mesh and conductivity");
+    const int64_t slice = (int64_t)T0.ntile * ESDC_TILE, ldf = fine->ld;
+    for (int l = 1; l < L - 1; ++l) {                 // the Q^par levels share the fine level's layout
+        const esdc_batch* b = levels[l];
+        if (b->ntis != P || b->ld != ldf || b->NS != NSt || b->tis_h[0].N != T0.N || b->tis_h[0].D != T0.D ||
+            b->tis_h[0].ih2 != T0.ih2 || b->tis_h[0].ntile != T0.ntile)
+            return set_berr(fine, ESDC_ERR_INVALID_ARG, "every Q^par level: the same slices as the finest");
+    }
+    const int Mc = M[L - 1];
+    for (int p = 0; p < P; ++p) {
+        const esdc_batch* c = coarse[p];
+        if (!c || c->ntis != 1 || c->ld != slice || c->NS != NSt || c->opt.M_max < Mc || c->tis_h[0].N != T0.N ||
+            c->tis_h[0].D != T0.D || c->tis_h[0].ih2 != T0.ih2)
+            return set_berr(fine, ESDC_ERR_INVALID_ARG, "coarsest level: one single-slice batch per slice, same mesh");
+    }
+    // Lagrange matrices between the Radau nodes c_1..c_M of consecutive levels
+    // (Sec. 3.2: I_l(y, s) = sum_j l_j(s) y_j): restriction S_l [M_{l+1}][M_l],
+    // prolongation T_l [M_l][M_{l+1}]
     auto lagrange = [](const double* nodes, int n, const double* pts, int m, double* W) {
         for (int i = 0; i < m; ++i)
             for (int j = 0; j < n; ++j) {
@@ -1428,27 +1450,18 @@ int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double
                 W[i * n + j] = l;
             }
     };
-    std::vector<double> Rv((size_t)M2 * M1), Tv((size_t)M1 * M2);
-    lagrange(cf, M1, cc, M2, Rv.data());
-    lagrange(cc, M2, cf, M1, Tv.data());
-    const double* Rmat = Rv.data();
-    const double* Tmat = Tv.data();
-    const int P = fine->ntis, NSt = fine->NS;
-    const TissueDev& T0 = fine->tis_h[0];
-    for (const TissueDev& T : fine->tis_h)
-        if (T.nx != T0.nx || T.ny != T0.ny || T.nz != T0.nz || T.D != T0.D || T.ih2 != T0.ih2)
-            return set_berr(fine, ESDC_ERR_INVALID_ARG, "slices must share mesh and conductivity");
-    const int64_t slice = (int64_t)T0.ntile * ESDC_TILE, ldf = fine->ld;
-    for (int p = 0; p < P; ++p) {
-        const esdc_batch* c = coarse[p];
-        if (!c || c->ntis != 1 || c->ld != slice || c->NS != NSt || c->opt.M_max < M2 || c->tis_h[0].N != T0.N ||
-            c->tis_h[0].D != T0.D || c->tis_h[0].ih2 != T0.ih2)
-            return set_berr(fine, ESDC_ERR_INVALID_ARG, "coarse level: one single-slice batch per slice, same mesh");
+    std::vector<std::vector<double>> Sm(L - 1), Tm(L - 1);
+    for (int l = 0; l < L - 1; ++l) {
+        const double* ca = fine->col[M[l] - 1].c + 1;
+        const double* cb = fine->col[M[l + 1] - 1].c + 1;
+        Sm[l].resize((size_t)M[l + 1] * M[l]);
+        Tm[l].resize((size_t)M[l] * M[l + 1]);
+        lagrange(ca, M[l], cb, M[l + 1], Sm[l].data());
+        lagrange(cb, M[l + 1], ca, M[l], Tm[l].data());
     }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t pitchf = sizeof(double) * ldf, pitchc = sizeof(double) * slice;
     const int64_t rowsf = (int64_t)NSt * ldf, rowsc = (int64_t)NSt * slice;
-    // scratch: per slice SZ, tau, y_in, y_out of the coarse level; a time per slice
     struct Scratch {
         std::vector<void*> p;
         ~Scratch() { for (void* q : p) cudaFree(q); }
@@ -1458,108 +1471,174 @@ int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double
         sc.p.push_back(*q);
         return true;
     };
+    // per Q^par level l >= 1: S z_{l-1} [M_l][NS][ld], tau_l (same), its slices' initial values [NS][ld];
+    // coarsest level, per slice: S z, tau, y_{p,0} and the new end values
+    std::vector<double*> SZl(L, nullptr), TAUl(L, nullptr), Y0l(L, nullptr);
     double *SZ = nullptr, *TAU = nullptr, *YIC = nullptr, *YOC = nullptr, *ytmp = nullptr;
-    if (!alloc(&SZ, (int64_t)P * M2 * rowsc) || !alloc(&TAU, (int64_t)P * M2 * rowsc) || !alloc(&YIC, rowsc) ||
+    for (int l = 1; l < L - 1; ++l)
+        if (!alloc(&SZl[l], (int64_t)M[l] * rowsf) || !alloc(&TAUl[l], (int64_t)M[l] * rowsf) ||
+            !alloc(&Y0l[l], rowsf))
+            return set_berr(fine, ESDC_ERR_NO_MEMORY, "multilevel scratch");
+    if (!alloc(&SZ, (int64_t)P * Mc * rowsc) || !alloc(&TAU, (int64_t)P * Mc * rowsc) || !alloc(&YIC, rowsc) ||
         !alloc(&YOC, (int64_t)P * rowsc) || !alloc(&ytmp, rowsf))
-        return set_berr(fine, ESDC_ERR_NO_MEMORY, "two-level scratch");
+        return set_berr(fine, ESDC_ERR_NO_MEMORY, "multilevel scratch");
+    Y0l[0] = y_in;
     std::vector<double> tf(P);
     for (int p = 0; p < P; ++p) tf[p] = t0 + p * dt;
-    std::vector<double> I2(M2 * M2, 0.0), Ip(M2 * M2, 0.0);     // -I and +I
-    for (int i = 0; i < M2; ++i) { I2[i * M2 + i] = -1.0; Ip[i * M2 + i] = 1.0; }
+    std::vector<double> Im(Mc * Mc, 0.0), Ip(Mc * Mc, 0.0);     // -I and +I of the coarsest level
+    for (int i = 0; i < Mc; ++i) { Im[i * Mc + i] = -1.0; Ip[i * Mc + i] = 1.0; }
     // the calls below alternate between kinds of step: record no graphs
     struct GraphsOff {
-        esdc_batch* const* c;
-        esdc_batch* f;
-        int P;
-        bool fg;
-        std::vector<char> cg;
-        GraphsOff(esdc_batch* f_, esdc_batch* const* c_, int P_) : c(c_), f(f_), P(P_), fg(f_->use_graph), cg(P_)
-        {
-            f->use_graph = false;
-            for (int p = 0; p < P; ++p) { cg[p] = c[p]->use_graph; c[p]->use_graph = false; }
-        }
-        ~GraphsOff()
-        {
-            f->use_graph = fg;
-            for (int p = 0; p < P; ++p) c[p]->use_graph = cg[p] != 0;
-        }
-    } graphs_off(fine, coarse, P);
-    double *Yf = nullptr, *Rf = nullptr;
+        std::vector<esdc_batch*> b;
+        std::vector<char> was;
+        ~GraphsOff() { for (size_t i = 0; i < b.size(); ++i) b[i]->use_graph = was[i] != 0; }
+        void add(esdc_batch* x) { b.push_back(x); was.push_back(x->use_graph); x->use_graph = false; }
+    } graphs_off;
+    for (int l = 0; l < L - 1; ++l) graphs_off.add(levels[l]);
+    for (int p = 0; p < P; ++p) graphs_off.add(coarse[p]);
+    auto fail_cuda = [&](const char* what) { return set_berr(fine, ESDC_ERR_CUDA, what); };
+    // y_{p,0} of slice p >= 1 := row M-1 of slice p-1 of the iterate Z (the Q^par coupling)
+    auto shift_ends = [&](double* y0dst, const double* Z, int Ml) {
+        return P > 1 && cudaMemcpy2DAsync(y0dst + slice, pitchf, Z + (int64_t)(Ml - 1) * rowsf, pitchf,
+                                          sizeof(double) * slice * (P - 1), NSt, cudaMemcpyDeviceToDevice,
+                                          s) != cudaSuccess;
+    };
+    std::vector<double*> Yl(L - 1, nullptr), Rl(L - 1, nullptr);
     int rc;
     // z^0 = 1 (x) y0 in every slice: y_in[p] = y0, Y_j = y0
     for (int p = 1; p < P; ++p)
         if (cudaMemcpy2DAsync(y_in + p * slice, pitchf, y_in, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) !=
             cudaSuccess)
-            return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
-    // a K = 0 call allocates the residual buffer and gives the iterate pointers
-    if ((rc = esdc_batch_sweep_ex(fine, y_in, ytmp, nullptr, tf.data(), dt, M1, 0, 1, 1, stream)) != ESDC_OK) return rc;
-    esdc_batch_iterate(fine, &Yf, &Rf);
-    for (int j = 0; j < M1; ++j)
-        if (cudaMemcpyAsync(Yf + (int64_t)j * rowsf, y_in, sizeof(double) * rowsf, cudaMemcpyDeviceToDevice, s) !=
-            cudaSuccess)
-            return set_berr(fine, ESDC_ERR_CUDA, "spread failed");
-    for (int k = 0; k < iters; ++k) {
-        // fine residual vectors at the iterate
-        if ((rc = esdc_batch_sweep_ex(fine, y_in, ytmp, nullptr, tf.data(), dt, M1, 0, 1, 1, stream)) != ESDC_OK)
+            return fail_cuda("slice copy failed");
+    // K = 0 calls allocate the residual buffers and give the iterate pointers
+    for (int l = 0; l < L - 1; ++l) {
+        if ((rc = esdc_batch_sweep_ex(levels[l], y_in, ytmp, nullptr, tf.data(), dt, M[l], 0, 1, 1, stream)) !=
+            ESDC_OK)
             return rc;
+        esdc_batch_iterate(levels[l], &Yl[l], &Rl[l]);
+    }
+    for (int j = 0; j < M[0]; ++j)
+        if (cudaMemcpyAsync(Yl[0] + (int64_t)j * rowsf, y_in, sizeof(double) * rowsf, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+            return fail_cuda("spread failed");
+    for (int k = 0; k < iters; ++k) {
+        // finest level: its residual vectors at the iterate (tau_1 = 0)
+        if ((rc = esdc_batch_sweep_ex(fine, y_in, ytmp, nullptr, tf.data(), dt, M[0], 0, 1, 1, stream)) != ESDC_OK)
+            return rc;
+        // down: tau_l = S R_{l-1}(z_{l-1}; tau_{l-1}) - R_l(S z_{l-1}); one Q^par sweep from S z_{l-1} with tau_l
+        for (int l = 1; l < L - 1; ++l) {
+            esdc_batch* b = levels[l];
+            if ((rc = esdc_interp(Yl[l - 1], M[l - 1], ldf, SZl[l], M[l], ldf, NSt, ldf, Sm[l - 1].data(), 0.0,
+                                  stream)) != ESDC_OK)
+                return set_berr(fine, rc, "restriction failed");
+            if (cudaMemcpyAsync(Yl[l], SZl[l], sizeof(double) * M[l] * rowsf, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+                return fail_cuda("iterate copy failed");
+            if ((rc = esdc_batch_sweep_ex(b, Y0l[l - 1], ytmp, nullptr, tf.data(), dt, M[l], 0, 1, 1, stream)) !=
+                ESDC_OK)
+                return rc;
+            if ((rc = esdc_interp(Rl[l - 1], M[l - 1], ldf, TAUl[l], M[l], ldf, NSt, ldf, Sm[l - 1].data(), 0.0,
+                                  stream)) != ESDC_OK)
+                return set_berr(fine, rc, "tau failed");
+            {
+                std::vector<double> Iml(M[l] * M[l], 0.0);
+                for (int i = 0; i < M[l]; ++i) Iml[i * M[l] + i] = -1.0;
+                if ((rc = esdc_interp(Rl[l], M[l], ldf, TAUl[l], M[l], ldf, NSt, ldf, Iml.data(), 1.0, stream)) !=
+                    ESDC_OK)
+                    return set_berr(fine, rc, "tau failed");
+            }
+            // the sweep: slice p starts from the end of slice p-1 of S z_{l-1}; it keeps R_l(z_l; tau_l)
+            if (cudaMemcpy2DAsync(Y0l[l], pitchf, y_in, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) !=
+                    cudaSuccess ||
+                shift_ends(Y0l[l], SZl[l], M[l]))
+                return fail_cuda("slice shift failed");
+            if ((rc = esdc_batch_sweep_ex(b, Y0l[l], ytmp, TAUl[l], tf.data(), dt, M[l], 1, 1, 1, stream)) != ESDC_OK)
+                return rc;
+        }
+        // coarsest level, per slice: S z, tau = S R_{L-1} - R_L(S z)
+        const int lp = L - 2;                                      // the level above the coarsest
         for (int p = 0; p < P; ++p) {
             esdc_batch* c = coarse[p];
             double *Yc = nullptr, *Rc = nullptr;
-            double* SZp = SZ + (int64_t)p * M2 * rowsc;
-            double* TAUp = TAU + (int64_t)p * M2 * rowsc;
+            double* SZp = SZ + (int64_t)p * Mc * rowsc;
+            double* TAUp = TAU + (int64_t)p * Mc * rowsc;
             const double tp = tf[p];
-            // S z: restriction of the fine iterate, into the coarse iterate and a copy
-            if ((rc = esdc_interp(Yf + p * slice, M1, ldf, SZp, M2, slice, NSt, slice, Rmat, 0.0, stream)) != ESDC_OK)
+            if ((rc = esdc_interp(Yl[lp] + p * slice, M[lp], ldf, SZp, Mc, slice, NSt, slice, Sm[lp].data(), 0.0,
+                                  stream)) != ESDC_OK)
                 return set_berr(fine, rc, "restriction failed");
-            // y_{p,0} of the slice in the coarse layout
-            if (cudaMemcpy2DAsync(YIC, pitchc, y_in + p * slice, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess)
-                return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
+            if (cudaMemcpy2DAsync(YIC, pitchc, Y0l[lp] + p * slice, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice,
+                                  s) != cudaSuccess)
+                return fail_cuda("slice copy failed");
             esdc_batch_iterate(c, &Yc, nullptr);
-            if (cudaMemcpyAsync(Yc, SZp, sizeof(double) * M2 * rowsc, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return set_berr(fine, ESDC_ERR_CUDA, "iterate copy failed");
-            // coarse residual at S z, then tau = S R_1 - R_2
-            if ((rc = esdc_batch_sweep_ex(c, YIC, YOC + p * rowsc, nullptr, &tp, dt, M2, 0, 1, 1, stream)) != ESDC_OK)
+            if (cudaMemcpyAsync(Yc, SZp, sizeof(double) * Mc * rowsc, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return fail_cuda("iterate copy failed");
+            if ((rc = esdc_batch_sweep_ex(c, YIC, YOC + p * rowsc, nullptr, &tp, dt, Mc, 0, 1, 1, stream)) != ESDC_OK)
                 return rc;
             esdc_batch_iterate(c, nullptr, &Rc);
-            if ((rc = esdc_interp(Rf + p * slice, M1, ldf, TAUp, M2, slice, NSt, slice, Rmat, 0.0, stream)) != ESDC_OK ||
-                (rc = esdc_interp(Rc, M2, slice, TAUp, M2, slice, NSt, slice, I2.data(), 1.0, stream)) != ESDC_OK)
+            if ((rc = esdc_interp(Rl[lp] + p * slice, M[lp], ldf, TAUp, Mc, slice, NSt, slice, Sm[lp].data(), 0.0,
+                                  stream)) != ESDC_OK ||
+                (rc = esdc_interp(Rc, Mc, slice, TAUp, Mc, slice, NSt, slice, Im.data(), 1.0, stream)) != ESDC_OK)
                 return set_berr(fine, rc, "tau failed");
         }
-        // coarse Q^seq sweep: slice p starts from the new end value of slice p-1
+        // coarsest Q^seq sweep (slice p starts from the new end value of slice p-1), then the
+        // coarse-grid correction of level L-1: z += T (z_L - S z)
         for (int p = 0; p < P; ++p) {
             esdc_batch* c = coarse[p];
             double *Yc = nullptr, *Rc = nullptr;
             esdc_batch_iterate(c, &Yc, &Rc);
-            const double* src = p == 0 ? y_in : nullptr;
             if (p == 0) {
-                if (cudaMemcpy2DAsync(YIC, pitchc, src, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                    return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
-            } else if (cudaMemcpyAsync(YIC, YOC + (p - 1) * rowsc, sizeof(double) * rowsc, cudaMemcpyDeviceToDevice, s) !=
-                       cudaSuccess) {
-                return set_berr(fine, ESDC_ERR_CUDA, "slice copy failed");
+                if (cudaMemcpy2DAsync(YIC, pitchc, y_in, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    return fail_cuda("slice copy failed");
+            } else if (cudaMemcpyAsync(YIC, YOC + (p - 1) * rowsc, sizeof(double) * rowsc, cudaMemcpyDeviceToDevice,
+                                       s) != cudaSuccess) {
+                return fail_cuda("slice copy failed");
             }
-            if (cudaMemcpyAsync(Yc, SZ + (int64_t)p * M2 * rowsc, sizeof(double) * M2 * rowsc, cudaMemcpyDeviceToDevice,
-                                s) != cudaSuccess)
-                return set_berr(fine, ESDC_ERR_CUDA, "iterate copy failed");
+            if (cudaMemcpyAsync(Yc, SZ + (int64_t)p * Mc * rowsc, sizeof(double) * Mc * rowsc,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return fail_cuda("iterate copy failed");
             const double tp = tf[p];
-            if ((rc = esdc_batch_sweep_ex(c, YIC, YOC + p * rowsc, TAU + (int64_t)p * M2 * rowsc, &tp, dt, M2, 1, 1, 0,
+            if ((rc = esdc_batch_sweep_ex(c, YIC, YOC + p * rowsc, TAU + (int64_t)p * Mc * rowsc, &tp, dt, Mc, 1, 1, 0,
                                           stream)) != ESDC_OK)
                 return rc;
-            // coarse-grid correction of the fine iterate: z += T (z_2 - S z)
-            double* SZp = SZ + (int64_t)p * M2 * rowsc;
-            if ((rc = esdc_interp(Yc, M2, slice, SZp, M2, slice, NSt, slice, Ip.data(), -1.0, stream)) != ESDC_OK ||
-                (rc = esdc_interp(SZp, M2, slice, Yf + p * slice, M1, ldf, NSt, slice, Tmat, 1.0, stream)) != ESDC_OK)
+            double* SZp = SZ + (int64_t)p * Mc * rowsc;
+            if ((rc = esdc_interp(Yc, Mc, slice, SZp, Mc, slice, NSt, slice, Ip.data(), -1.0, stream)) != ESDC_OK ||
+                (rc = esdc_interp(SZp, Mc, slice, Yl[lp] + p * slice, M[lp], ldf, NSt, slice, Tm[lp].data(), 1.0,
+                                  stream)) != ESDC_OK)
                 return set_berr(fine, rc, "correction failed");
         }
-        // fine Q^par sweep from the corrected iterate: y_{p,0} = its end value in slice p-1
-        if (P > 1 && cudaMemcpy2DAsync(y_in + slice, pitchf, Yf + (int64_t)(M1 - 1) * rowsf, pitchf,
-                                       sizeof(double) * slice * (P - 1), NSt, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return set_berr(fine, ESDC_ERR_CUDA, "slice shift failed");
-        if ((rc = esdc_batch_sweep_ex(fine, y_in, y_out, nullptr, tf.data(), dt, M1, 1, 1, 0, stream)) != ESDC_OK)
-            return rc;
+        // up: one Q^par sweep of level l from its corrected iterate (slice p starts from
+        // that iterate's end of slice p-1), then the correction of level l-1
+        for (int l = L - 2; l >= 0; --l) {
+            esdc_batch* b = levels[l];
+            if (l > 0 && cudaMemcpy2DAsync(Y0l[l], pitchf, y_in, pitchf, pitchc, NSt, cudaMemcpyDeviceToDevice, s) !=
+                             cudaSuccess)
+                return fail_cuda("slice copy failed");
+            if (shift_ends(Y0l[l], Yl[l], M[l])) return fail_cuda("slice shift failed");
+            if ((rc = esdc_batch_sweep_ex(b, Y0l[l], l == 0 ? y_out : ytmp, l == 0 ? nullptr : TAUl[l], tf.data(), dt,
+                                          M[l], 1, 1, 0, stream)) != ESDC_OK)
+                return rc;
+            if (l > 0) {
+                // z_{l-1} += T (z_l - S z_{l-1}): the difference in place of S z_{l-1}
+                std::vector<double> Ipl(M[l] * M[l], 0.0);
+                for (int i = 0; i < M[l]; ++i) Ipl[i * M[l] + i] = 1.0;
+                if ((rc = esdc_interp(Yl[l], M[l], ldf, SZl[l], M[l], ldf, NSt, ldf, Ipl.data(), -1.0, stream)) !=
+                        ESDC_OK ||
+                    (rc = esdc_interp(SZl[l], M[l], ldf, Yl[l - 1], M[l - 1], ldf, NSt, ldf, Tm[l - 1].data(), 1.0,
+                                      stream)) != ESDC_OK)
+                    return set_berr(fine, rc, "correction failed");
+            }
+        }
     }
-    return cudaStreamSynchronize(s) == cudaSuccess ? ESDC_OK : set_berr(fine, ESDC_ERR_CUDA, "two-level run failed");
+    return cudaStreamSynchronize(s) == cudaSuccess ? ESDC_OK : set_berr(fine, ESDC_ERR_CUDA, "multilevel run failed");
+}
+
+int esdc_hsdc2(esdc_batch* fine, esdc_batch* const* coarse, double* y_in, double* y_out, double t0, double dt, int M1,
+               int M2, int iters, void* stream)
+{
+    if (!fine) return ESDC_ERR_INVALID_ARG;
+    esdc_batch* levels[1] = {fine};
+    const int M[2] = {M1, M2};
+    return esdc_hsdc(levels, coarse, M, 2, y_in, y_out, t0, dt, iters, stream);
 }
 
 }  // extern "C"

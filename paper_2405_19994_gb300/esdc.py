@@ -99,6 +99,8 @@ def lib() -> C.CDLL:
             "esdc_batch_iterate": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP)]),
             "esdc_interp": (C.c_int, [_VP, C.c_int, _I64, _VP, C.c_int, _I64, C.c_int, _I64, C.POINTER(_D), _D, _VP]),
             "esdc_hsdc2": (C.c_int, [_VP, C.POINTER(_VP), _VP, _VP, _D, _D, C.c_int, C.c_int, C.c_int, _VP]),
+            "esdc_hsdc": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(C.c_int), C.c_int, _VP, _VP, _D, _D,
+                                    C.c_int, _VP]),
             "esdc_batch_stats": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
             "esdc_batch_set_graph": (C.c_int, [_VP, C.c_int]),
             "esdc_batch_graph_active": (C.c_int, [_VP]),
@@ -485,6 +487,17 @@ def hsdc2(fine: "Batch", coarse, y_in, y_out, t0: float, dt: float, M1: int, M2:
     arr = (_VP * len(coarse))(*[c._b for c in coarse])
     rc = lib().esdc_hsdc2(fine._b, arr, _ptr(y_in), _ptr(y_out), t0, dt, M1, M2, iters, _stream(stream))
     fine._check(rc)
+
+
+def hsdc(levels, coarse, y_in, y_out, t0: float, dt: float, Ms, iters: int, stream=None):
+    """Algorithm HSDC with L = len(Ms) levels (esdc_hsdc): levels is a list of
+    L - 1 batches of the same P slices (the Q^par levels, finest first), coarse
+    a list of P single-tissue batches (the Q^seq level)."""
+    lv = (_VP * len(levels))(*[b._b for b in levels])
+    arr = (_VP * len(coarse))(*[c._b for c in coarse])
+    m = (C.c_int * len(Ms))(*[int(x) for x in Ms])
+    rc = lib().esdc_hsdc(lv, arr, m, len(Ms), _ptr(y_in), _ptr(y_out), t0, dt, iters, _stream(stream))
+    levels[0]._check(rc)
 
 
 def sensor_traces(solver: "Solver", sigma, g_na, g_k, y0, t0: float, dt: float, M: int, K: int, nsteps: int, sens):

@@ -145,6 +145,10 @@ def test_later_entry_points_reject_invalid_arguments_without_gpu(L):
     assert L.esdc_batch_qpar(None, None, None, 0.0, 0.1, 3, 2, None) == -1
     assert L.esdc_batch_iterate(None, None, None) == -1
     assert L.esdc_hsdc2(None, None, None, None, 0.0, 0.1, 3, 2, 1, None) == -1
+    nolev = (C.c_void_p * 1)(None)
+    ms = (C.c_int * 2)(3, 2)
+    assert L.esdc_hsdc(None, None, ms, 2, None, None, 0.0, 0.1, 1, None) == -1
+    assert L.esdc_hsdc(nolev, None, ms, 2, None, None, 0.0, 0.1, 1, None) == -1
     assert L.esdc_batch_set_shape(None, 1, 512, 1) == -1
     assert L.esdc_batch_tune(None, None, -75.0, 0.0, 0.1, 3, 4, 1, None) == -1
     assert L.esdc_batch_graph_active(None) == 0

@@ -332,3 +332,59 @@ def test_hsdc2_converges_to_sequential_collocation():
     for c in coarse:
         c.close()
     fine.close()
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+def test_hsdc_three_levels_matches_oracle(iters):
+    P_, Ms = 4, (3, 2, 1)
+    w, m, y0, t0 = qpar_setup(P_)
+    levels = [P.Batch.from_workloads([w] * P_, M_max=Ms[0]), P.Batch.from_workloads([w] * P_, M_max=Ms[1])]
+    coarse = [P.Batch.from_workloads([w], M_max=Ms[2]) for _ in range(P_)]
+    fine = levels[0]
+    yin, yout = fine.new_state(), fine.new_state()
+    fine.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    P.esdc.hsdc(levels, coarse, yin, yout, t0, w.dt, Ms, iters)
+    assert fine.residual()[0] == 0
+    Z = m.hsdc(y0, t0, w.dt, P_, Ms, iters)
+    Y = fine.iterate(Ms[0])
+    for p in range(P_):
+        o = int(fine.offsets[p])
+        got = Y[:, :, o:o + w.n_nodes].cpu().numpy()
+        assert np.abs(got - Z[p]).max() < 1e-12 * np.abs(Z[p]).max(), p
+        assert np.array_equal(fine.tissue(yout, p).cpu().numpy(), got[Ms[0] - 1]), p
+    for b in coarse + levels:
+        b.close()
+
+
+def test_hsdc_three_levels_converges_to_sequential_collocation():
+    P_, Ms = 4, (3, 2, 1)
+    w, m, y0, t0 = qpar_setup(P_)
+    levels = [P.Batch.from_workloads([w] * P_, M_max=Ms[0]), P.Batch.from_workloads([w] * P_, M_max=Ms[1])]
+    coarse = [P.Batch.from_workloads([w], M_max=Ms[2]) for _ in range(P_)]
+    fine = levels[0]
+    yin, yout = fine.new_state(), fine.new_state()
+    fine.tissue(yin, 0).copy_(torch.from_numpy(y0))
+    P.esdc.hsdc(levels, coarse, yin, yout, t0, w.dt, Ms, 16)
+    y, t = y0, t0
+    for p in range(P_):
+        yn, _, _, _ = m.step(y, t, w.dt, Ms[0], 60)
+        got = fine.tissue(yout, p).cpu().numpy()
+        assert np.abs(got - yn).max() < 1e-11 * np.abs(yn).max(), p
+        y, t = yn, t + w.dt
+    for b in coarse + levels:
+        b.close()
+
+
+def test_hsdc_rejects_bad_levels():
+    P_ = 2
+    w, m, y0, t0 = qpar_setup(P_)
+    fine = P.Batch.from_workloads([w] * P_, M_max=3)
+    mid = P.Batch.from_workloads([w] * P_, M_max=1)                 # M_max below its level's M
+    coarse = [P.Batch.from_workloads([w], M_max=1) for _ in range(P_)]
+    yin, yout = fine.new_state(), fine.new_state()
+    for Ms, levels in (((3, 3, 1), [fine, mid]), ((3, 2, 1), [fine, mid]), ((3,), [fine])):
+        with pytest.raises(P.EsdcError) as e:
+            P.esdc.hsdc(levels, coarse, yin, yout, t0, w.dt, Ms, 1)
+        assert e.value.code == -1
+    for b in coarse + [fine, mid]:
+        b.close()
