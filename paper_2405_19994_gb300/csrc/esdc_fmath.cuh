@@ -16,11 +16,14 @@
 // above 709.78 return +inf, NaN returns NaN.  Cost: 9 FP64 operations and one
 // table load (2 KB table, L1-resident).
 //
-// esdc_rcp: 1/d by two Newton steps r <- r + r (1 - d r) from the hardware
-// reciprocal approximation rcp.approx.ftz.f64 (relative error e -> e^2 -> e^4,
-// then rounding), about 1 ulp, for 2^-99 <= |d| < 2^100 (an integer test on
-// the exponent field); other values (0, tiny, huge, inf, NaN) use the IEEE
-// division.  Cost: 4 FP64 operations.
+// esdc_rcp: 1/d from the hardware reciprocal approximation r =
+// rcp.approx.ftz.f64(d) by one third-order step: with e = 1 - d r (one FMA,
+// exact to first order), 1/d = r/(1 - e) = r (1 + e + e^2 + ...), so
+// r + r (e + e^2) has relative error e^3 plus the final rounding (the
+// truncated geometric series, the third-order member of the Newton-type
+// reciprocal iterations).  About 1 ulp for 2^-99 <= |d| < 2^100 (an integer
+// test on the exponent field); other values (0, tiny, huge, inf, NaN) use the
+// IEEE division.  Cost: 3 FP64 operations.
 #pragma once
 #include <cstdint>
 
@@ -130,10 +133,8 @@ __device__ __forceinline__ double esdc_rcp(double d)
     if (ex - 924u > 198u) return 1.0 / d;
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 }  // namespace esdc

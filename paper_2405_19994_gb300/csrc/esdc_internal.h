@@ -8,7 +8,7 @@
 #define ESDC_MMAX 8        // collocation nodes
 #define ESDC_NSMAX 19      // states per mesh node
 #define ESDC_NGMAX 12      // gating variables per mesh node
-#define ESDC_NPMAX 128     // ionic-model parameters (+ derived reciprocals)
+#define ESDC_NPMAX 160     // ionic-model parameters (+ derived constants)
 #define ESDC_MAXBOX 16     // stimulus boxes
 #define ESDC_NSER 48       // reciprocal table length for the phi_k series
 #define ESDC_PROF_CLASSES 4  // esdc_profile kernel classes

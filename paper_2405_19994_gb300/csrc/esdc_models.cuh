@@ -161,8 +161,10 @@ struct HH1952 {
 //   a4' = (g4 g5 - a4)/tau4, a5' = (a4-a5)/tau5, a6' = (a5-a6)/tau6
 struct SYN19 {
     static constexpr int NS = 19, NA = 6, NG = 12;
-    // mp[88 + q] = 1/k_q, mp[100 + q] = 1/sr_q, mp[112 + l] = 1/tau_l (set on the host)
-    static constexpr int NPARAM = 88, NDERIVED = 30;
+    // mp[88 + q] = 1/k_q, mp[100 + q] = 1/sr_q, mp[112 + l] = 1/tau_l,
+    // mp[118 + q] = Vh_q/k_q, mp[130 + q] = Vr_q/sr_q, mp[142 + q] = ln r_lo,q (set on the host):
+    // (Vh - V)/k = Vh/k - V/k and r_lo exp(a) = exp(a + ln r_lo) each save an FP64 operation
+    static constexpr int NPARAM = 88, NDERIVED = 66;
     __device__ static void eval(const double* __restrict__ mp, const double* u, double& mI,
                                 double* ha, double* lam, double* yinf)
     {
@@ -171,13 +173,7 @@ struct SYN19 {
         const double* g = u + 7;
         const double* inv = mp + 88;
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            const double* p = mp + 6 * q;
-            const double w = esdc_rcp(1.0 + esdc_exp((p[0] - V) * inv[q]));
-            const double s = esdc_rcp(1.0 + esdc_exp((p[4] - V) * inv[12 + q]));
-            lam[q] = -p[2] * esdc_exp(p[3] * s);
-            yinf[q] = w;
-        }
+        for (int q = 0; q < 12; ++q) gate(mp, q, V, lam[q], yinf[q]);
         const double* c = mp + 72;
         const double If = c[0] * g[0] * g[1] * g[2] * a[0] * (V - c[1]);
         const double Is = c[2] * g[3] * g[4] * a[2] * (V - c[3]);
@@ -219,9 +215,10 @@ struct SYN19 {
     {
         const double* p = mp + 6 * q;
         const double* inv = mp + 88;
-        yinf = esdc_rcp(1.0 + esdc_exp((p[0] - V) * inv[q]));
-        const double s = esdc_rcp(1.0 + esdc_exp((p[4] - V) * inv[12 + q]));
-        lam = -p[2] * esdc_exp(p[3] * s);
+        const double* dv = mp + 118;
+        yinf = esdc_rcp(1.0 + esdc_exp(fma(-V, inv[q], dv[q])));
+        const double s = esdc_rcp(1.0 + esdc_exp(fma(-V, inv[12 + q], dv[12 + q])));
+        lam = -esdc_exp(fma(p[3], s, dv[24 + q]));
     }
     __device__ static void currents_f(const float* __restrict__ mp, const float* u, float& mI, float* ha)
     {

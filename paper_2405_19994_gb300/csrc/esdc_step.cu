@@ -198,6 +198,9 @@ int esdc_model_setup(int model, const double* params, int n_params, ModelDev* mp
         for (int q = 0; q < 12; ++q) {
             mp->p[88 + q] = 1.0 / params[6 * q + 1];
             mp->p[100 + q] = 1.0 / params[6 * q + 5];
+            mp->p[118 + q] = params[6 * q] / params[6 * q + 1];
+            mp->p[130 + q] = params[6 * q + 4] / params[6 * q + 5];
+            mp->p[142 + q] = std::log(params[6 * q + 2]);
         }
         for (int l = 0; l < 6; ++l) mp->p[112 + l] = 1.0 / params[82 + l];
     }

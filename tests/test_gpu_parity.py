@@ -74,7 +74,10 @@ def test_library_exp_and_reciprocal_error_bounds():
     e2 = e2.cpu().numpy()
     assert e2[0] == 0.0 and np.isinf(e2[1]) and np.isnan(e2[2]) and np.isinf(e2[3]) and e2[4] == 0.0
     d = np.concatenate([np.geomspace(1e-30, 1e290, 100001), -np.geomspace(1e-30, 1e290, 1001),
-                        1 + rng.uniform(0, 1e12, 100000)])
+                        1 + rng.uniform(0, 1e12, 100000),
+                        # every region of the mantissa, at many binades and both signs
+                        np.ldexp(1 + rng.uniform(0, 1, 1000000), rng.integers(-95, 95, 1000000))
+                        * rng.choice([-1.0, 1.0], 1000000)])
     dd = torch.from_numpy(d).cuda()
     _, rc = E.math_check(dd)
     ref = 1.0 / dd
