@@ -293,8 +293,11 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, 
     }
 }
 
+#ifndef ESDC_SETUP_MINBLOCKS
+#define ESDC_SETUP_MINBLOCKS 1     // blocks of 128 threads per SM the register budget must allow
+#endif
 template <class Model, int M, bool MIXED, bool BATCH>
-__global__ void __launch_bounds__(128) k_setup(StepArgs a)
+__global__ void __launch_bounds__(128, ESDC_SETUP_MINBLOCKS) k_setup(StepArgs a)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
         if (!BATCH) {
