@@ -715,7 +715,7 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
             w += 4.0 * sn * sn;
         }
     const double lmin = 1.0, lmax = 1.0 + h.g * h.mesh.ih2 * w;
-    if (!(lmax > lmin)) return cudaErrorInvalidValue;
+    if (!(lmax > lmin)) return esdc_cg4_launch(h, false, s);    // g below rounding: no interval to work on
     ChebArgs c;
     const double theta = 0.5 * (lmax + lmin);
     c.inv_theta = 1.0 / theta;

@@ -176,10 +176,11 @@ def test_chebyshev_solve_matches_dct(shape, g):
 
 
 def test_chebyshev_zero_shift_and_ineligible_meshes():
-    # g = 0 is the identity (the interval has no width: the CG runs); nx not a
-    # multiple of 4 keeps the CG too; both give the exact result.
+    # g = 0 is the identity, and a g whose interval 1 + g w/h^2 rounds to 1 has
+    # no width either (the CG runs); nx not a multiple of 4 keeps the CG too;
+    # all give the exact result.
     rng = np.random.default_rng(4)
-    for shape, g in (((16, 8, 1), 0.0), ((18, 7, 3), 0.3)):
+    for shape, g in (((16, 8, 1), 0.0), ((16, 8, 1), 1e-19), ((18, 7, 3), 0.3)):
         wl = I.hh_sheet_32().with_mesh(*shape)
         m = O.Monodomain(wl)
         b = rng.normal(size=wl.n_nodes)
