@@ -85,12 +85,15 @@ typedef struct {
                           same tol_cg; state, coefficient tables, quadrature and
                           residual stay FP64                                       */
     int    solver;     /* FP64 diffusion solves of the sweep and esdc_diffusion_solve:
-                          0 = automatic: the Chebyshev semi-iteration where the
-                          spectrum of the operator I - g L of esdc_diffusion_solve
-                          is known exactly (scalar sigma, second-order stencil,
-                          nx a multiple of 4: the interval [1, 1 + (g/h^2)
-                          sum_axes 4 sin^2(pi (n-1)/(2n))], the cosine modes
-                          being its eigenvectors), the Jacobi-PCG elsewhere;
+                          0 = automatic: the Chebyshev semi-iteration where an
+                          interval holding the spectrum of the operator of
+                          esdc_diffusion_solve is known (nx a multiple of 4,
+                          second-order stencil; scalar sigma: exactly [1, 1 +
+                          (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))], the cosine
+                          modes being its eigenvectors; layered conductivity:
+                          [1, 1 + g G] with G the Gershgorin bound of -A), the
+                          Jacobi-PCG elsewhere (a conductivity field, the
+                          fourth-order stencil, other nx);
                           1 = the (Jacobi-P)CG always;
                           2 = the DCT-II direct solve, the paper's solver (Sec. 5):
                           x = C^T diag(1/(1 - g mu)) C b with C the orthonormal

@@ -355,7 +355,9 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg4(CgArgs a)
 // ---------------------------------------------------------------- Chebyshev semi-iteration
 // For the scalar-sigma second-order stencil the spectrum of B = I - g L is
 // known exactly: the cosine modes are its eigenvectors, so it lies in
-// [lmin, lmax] = [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))].  The
+// [lmin, lmax] = [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))].  For the
+// layered operator lmin = 1 still holds (constants are the null space of A)
+// and lmax = 1 + g lam_bound with the host's Gershgorin bound.  The
 // Chebyshev semi-iteration on that interval needs no dot products:
 //   x_{k+1} = x_k + d_k,  r_{k+1} = r_k - B d_k,
 //   d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1}/delta) r_{k+1},
@@ -375,7 +377,12 @@ struct ChebArgs {
     double cb[ESDC_CHEB_TAB];   // 2 rho_{k+1} / delta   (index k; the last entry is used beyond)
 };
 
-__global__ void __launch_bounds__(ESDC_CHEB_THREADS, 1) k_cheb4(CgArgs a, ChebArgs c)
+// 1024 threads for the scalar stencil (64 registers suffice); the layered
+// stencil's extra neighbours and coefficients need more registers: 512.
+template <bool LAY> constexpr int cheb_threads() { return LAY ? 512 : ESDC_CHEB_THREADS; }
+
+template <bool LAY>
+__global__ void __launch_bounds__(cheb_threads<LAY>(), 1) k_cheb4(CgArgs a, ChebArgs c)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const MeshDev& m = a.m;
@@ -397,9 +404,9 @@ __global__ void __launch_bounds__(ESDC_CHEB_THREADS, 1) k_cheb4(CgArgs a, ChebAr
         double v[2] = {0.0, 0.0};
         for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
             const Geo G = geo(m, qi);
-            const DiagIdx di = diag_idx<false>(G);
+            const DiagIdx di = diag_idx<LAY>(G);
             Q4<double> xc, bx;
-            apply4<double, false>(m, t, a.x, G, di, xc, bx);
+            apply4<double, LAY>(m, t, a.x, G, di, xc, bx);
             const Q4<double> b = ld4(a.b + G.p);
             Q4<double> r, d;
 #pragma unroll
@@ -443,9 +450,9 @@ __global__ void __launch_bounds__(ESDC_CHEB_THREADS, 1) k_cheb4(CgArgs a, ChebAr
         double v[1] = {0.0};
         for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
             const Geo G = geo(m, qi);
-            const DiagIdx di = diag_idx<false>(G);
+            const DiagIdx di = diag_idx<LAY>(G);
             Q4<double> d, bd;
-            apply4<double, false>(m, t, dc, G, di, d, bd);
+            apply4<double, LAY>(m, t, dc, G, di, d, bd);
             const Q4<double> r = ld4(a.r + G.p), x = ld4(a.x + G.p);
             Q4<double> rn, xn, dnew;
 #pragma unroll
@@ -685,7 +692,8 @@ bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x)
 
 bool esdc_cheb_eligible(const MeshDev& m, const void* b, const void* x)
 {
-    if (m.lay || m.sig || m.order != 2 || !esdc_cg4_eligible(m, b, x)) return false;
+    if (m.sig || m.order != 2 || !esdc_cg4_eligible(m, b, x)) return false;
+    if (m.lay) return m.lam_bound > 0.0;                       // the Gershgorin interval
     return m.nx > 1 || m.ny > 1 || m.nz > 1;                   // an interval of positive width
 }
 
@@ -706,15 +714,21 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     a.tol2 = h.tol * h.tol;
     a.maxit = h.maxit;
     a.precond = 0;
-    // spectrum of I - g L: [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))]
-    const int n[3] = {h.mesh.nx, h.mesh.ny, h.mesh.nz};
+    // spectrum of I - g L: exactly [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))] for
+    // the scalar sigma; inside [1, 1 + g lam_bound] for the layered operator
     double w = 0.0;
-    for (int k = 0; k < 3; ++k)
-        if (n[k] > 1) {
-            const double sn = std::sin(M_PI * (n[k] - 1) / (2.0 * n[k]));
-            w += 4.0 * sn * sn;
-        }
-    const double lmin = 1.0, lmax = 1.0 + h.g * h.mesh.ih2 * w;
+    if (h.mesh.lay) {
+        w = h.mesh.lam_bound;
+    } else {
+        const int n[3] = {h.mesh.nx, h.mesh.ny, h.mesh.nz};
+        for (int k = 0; k < 3; ++k)
+            if (n[k] > 1) {
+                const double sn = std::sin(M_PI * (n[k] - 1) / (2.0 * n[k]));
+                w += 4.0 * sn * sn;
+            }
+        w *= h.mesh.ih2;
+    }
+    const double lmin = 1.0, lmax = 1.0 + h.g * w;
     if (!(lmax > lmin)) return esdc_cg4_launch(h, false, s);    // g below rounding: no interval to work on
     ChebArgs c;
     const double theta = 0.5 * (lmax + lmin);
@@ -732,11 +746,14 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     }
     const int ne = tab_entries(h.mesh);
     const size_t bytes = sizeof(double) * ne;
-    cudaError_t e = prepare(k_cheb4, bytes);
+    const bool lay = h.mesh.lay != nullptr;
+    cudaError_t e = lay ? prepare(k_cheb4<true>, bytes) : prepare(k_cheb4<false>, bytes);
     if (e != cudaSuccess) return e;
     // One block per SM, balanced ranges of quads (blocks of at least 128 quads on small meshes).
-    int threads = ESDC_CHEB_THREADS, per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb4, threads, bytes)) != cudaSuccess)
+    int threads = lay ? cheb_threads<true>() : cheb_threads<false>(), per_sm = 0;
+    if ((e = lay ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb4<true>, threads, bytes)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb4<false>, threads, bytes)) !=
+        cudaSuccess)
         return e;
     if (per_sm < 1) threads = h.w.threads;              // fewer registers than expected: the CG block size
     const long long nq = h.mesh.N / 4;
@@ -745,7 +762,8 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     if (nb < 1) nb = 1;
     if ((e = cudaMemsetAsync(h.w.bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     void* args[] = {&a, &c};
-    return cudaLaunchCooperativeKernel((const void*)k_cheb4, dim3((unsigned)nb), dim3(threads), args, bytes, s);
+    const void* k = lay ? (const void*)k_cheb4<true> : (const void*)k_cheb4<false>;
+    return cudaLaunchCooperativeKernel(k, dim3((unsigned)nb), dim3(threads), args, bytes, s);
 }
 
 cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s)

@@ -57,6 +57,11 @@ struct MeshDev {
     // Order of the Laplacian (scalar sigma only): 2 (3/5/7-point) or 4 (the
     // fourth-order five-point difference per axis with mirrored ghost cells).
     int order = 2;
+    // Layered operator: an upper bound of the spectrum of -A (Gershgorin, set
+    // on the host with the layers; 0 otherwise).  The spectrum of I - g A is
+    // then inside [1, 1 + g lam_bound] (A is symmetric negative semi-definite
+    // with the constants as null space).
+    double lam_bound = 0.0;
 };
 
 // Mirror image of index j on an axis of n cells (reflection about the outer

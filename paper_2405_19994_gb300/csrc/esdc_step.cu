@@ -364,6 +364,7 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
         h->lay = nullptr;
         h->layf = nullptr;
         h->mesh.lay = nullptr; h->mesh.layf = nullptr;
+        h->mesh.lam_bound = 0.0;
         if (!h->sigf) {
             if (h->wdiag) cudaFree(h->wdiag);
             h->wdiag = nullptr;
@@ -394,6 +395,13 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
         c[2 * nz + k] = 0.5 * d * ih2;
         c[3 * nz + k] = (k + 1 < nz) ? 0.5 * (e + szz[k + 1]) * ih2 : 0.0;
     }
+    // Gershgorin bound of the spectrum of -A: an interior row has diagonal
+    // 2 cx + 2 cy + faces and off-diagonal magnitudes 2 cx + 2 cy + 4 |cd| + faces
+    double gb = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        const double faces = (k > 0 ? c[3 * nz + k - 1] : 0.0) + c[3 * nz + k];
+        gb = std::max(gb, 4.0 * c[k] + 4.0 * c[nz + k] + 4.0 * std::fabs(c[2 * nz + k]) + 2.0 * faces);
+    }
     std::vector<float> cf(c.begin(), c.end());
     if (!h->lay) {
         CUDA_TRY(h, cudaMalloc((void**)&h->lay, sizeof(double) * 4 * nz));
@@ -403,6 +411,7 @@ int esdc_set_conductivity_layers(esdc_handle* h, const double* sxx, const double
     CUDA_TRY(h, cudaMemcpy(h->lay, c.data(), sizeof(double) * 4 * nz, cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->layf, cf.data(), sizeof(float) * 4 * nz, cudaMemcpyHostToDevice));
     h->mesh.lay = h->lay;
+    h->mesh.lam_bound = gb;
     h->mesh.layf = h->layf;
     h->mesh.wdiag = h->wdiag;
     k_wdiag<<<grid_for(h, 256), 256>>>(h->mesh, h->wdiag);

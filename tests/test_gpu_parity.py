@@ -408,13 +408,15 @@ def test_precision_form_hh_sheet_run():
 
 # ---------------------------------------------------------------- layered anisotropic conductivity
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("shape", [(13, 11, 5), (40, 33, 3), (9, 9, 1)])
-def test_layered_solve_matches_oracle(precision, shape):
+@pytest.mark.parametrize("precision,solver", [("fp64", "auto"), ("fp64", "cg"), ("mixed", "auto")])
+@pytest.mark.parametrize("shape", [(13, 11, 5), (40, 33, 3), (9, 9, 1), (16, 12, 6)])
+def test_layered_solve_matches_oracle(precision, solver, shape):
+    # fp64 with solver "auto" and nx % 4 == 0: the Chebyshev semi-iteration on
+    # the Gershgorin interval of the layered operator
     nx, ny, nz = shape
     wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
     wl.layers = I.fibre_layers(nz)
-    s = P.Solver.from_workload(wl, cg_maxit=2000, precision=precision)
+    s = P.Solver.from_workload(wl, cg_maxit=2000, precision=precision, solver=solver)
     m = O.Monodomain(wl, solver=O.SOLVE_CG, cg_tol=1e-15)
     rng = np.random.default_rng(8)
     b = rng.normal(size=wl.n_nodes)
