@@ -531,10 +531,12 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
 }
 
 cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b, double* x,
-                                 double tol, int maxit, int precond, int* iter_log, int* flags, cudaStream_t s)
+                                 double tol, int maxit, int precond, int solver, int* iter_log, int* flags,
+                                 cudaStream_t s)
 {
     if (esdc_cg4_eligible(mesh, b, x)) {
         CgArgsHost hq{mesh, w, g, b, x, tol, maxit, precond, iter_log, flags};
+        if (solver == 0 && g > 0.0 && esdc_cheb_eligible(mesh, b, x)) return esdc_cheb_mixed_launch(hq, s);
         return esdc_cg4_launch(hq, true, s);
     }
     CgArgs a;

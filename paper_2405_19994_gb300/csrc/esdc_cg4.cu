@@ -665,6 +665,135 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg4_mixed(CgArgs a, Cg4MixA
     }
 }
 
+// ---------------------------------------------------------------- refinement, Chebyshev inner solves
+// The precision form's refinement (FP64 residual r = b - A x, FP32 inner solve
+// of A e = r from e = 0, x += e in FP64) with each inner solve done by kin
+// Chebyshev iterations on the operator's interval.  kin comes from the bound
+// 2 q^kin <= 1e-5, the same reduction the CG's inner stop asks for, so the
+// inner iterations need no reductions: one grid barrier each.  The outer stop
+// is the FP64 test ||b - A x|| <= tol ||b|| of every other solve.
+template <bool LAY>
+__global__ void __launch_bounds__(ESDC_CG_THREADS) k_cheb4_mixed(CgArgs a, Cg4MixArgs f, ChebArgs c, int kin)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const MeshDev& m = a.m;
+    const int ne = tab_entries(m);
+    Tab<double> t = carve<double>(reinterpret_cast<double*>(dsm), m);
+    Tab<float> tf = carve<float>(reinterpret_cast<float*>(dsm + sizeof(double) * ne), m);
+    build_tab(m, a.g, false, t);
+    build_tab(m, a.g, false, tf);
+    const int nq = m.N >> 2;
+    const int q0 = (int)((long long)blockIdx.x * nq / gridDim.x);
+    const int q1 = (int)((long long)(blockIdx.x + 1) * nq / gridDim.x);
+    double* part = a.part;
+    __shared__ double bs[3];
+    unsigned target = 0;
+    const float inv_theta = (float)c.inv_theta;
+
+    // b.b (slot 7), once
+    {
+        double v[1] = {0.0};
+        for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
+            const Q4<double> b = ld4(a.b + 4 * qi);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[0] = fma(b.v[j], b.v[j], v[0]);
+        }
+        block_sum<1>(v, bs);
+        if (threadIdx.x == 0) part[7 * gridDim.x + blockIdx.x] = bs[0];
+    }
+    double stop = 0.0;
+    bool first_outer = true, done = false, bad = false;
+    int outer = 0, inner_total = 0;
+    for (;;) {
+        // [R] r = b - A x (FP64), r.r (slot 0); the inner start r32 = r, d32 = r32/theta
+        {
+            double v[1] = {0.0};
+            for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
+                const Geo G = geo(m, qi);
+                const DiagIdx di = diag_idx<LAY>(G);
+                Q4<double> xc, ax;
+                apply4<double, LAY>(m, t, a.x, G, di, xc, ax);
+                const Q4<double> b = ld4(a.b + G.p);
+                Q4<float> r32, d32;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const double r = b.v[j] - ax.v[j];
+                    v[0] = fma(r, r, v[0]);
+                    r32.v[j] = (float)r;
+                    d32.v[j] = r32.v[j] * inv_theta;
+                }
+                st4(f.r + G.p, r32);
+                st4(f.p + G.p, d32);
+            }
+            block_sum<1>(v, bs);
+            if (threadIdx.x == 0) part[blockIdx.x] = bs[0];
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        double tr[1];
+        grid_total<1>(part, 0, tr);
+        if (first_outer) {
+            double bb[1];
+            grid_total<1>(part, 7, bb);
+            stop = a.tol2 * bb[0];
+            first_outer = false;
+            if (!isfinite(stop)) { bad = true; break; }
+        }
+        if (!isfinite(tr[0])) { bad = true; break; }
+        if (tr[0] <= stop) { done = true; break; }
+        if (outer >= f.maxout) break;
+        // inner: kin iterations e += d, r -= B d, d = ca d + cb r (FP32), from e = 0
+        float* dc = f.p;
+        float* dn = f.q;
+        for (int it = 0; it < kin; ++it) {
+            const int ki = it < ESDC_CHEB_TAB ? it : ESDC_CHEB_TAB - 1;
+            const float ca = (float)c.ca[ki], cb = (float)c.cb[ki];
+            const bool last = it + 1 == kin;
+            for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
+                const Geo G = geo(m, qi);
+                const DiagIdx di = diag_idx<LAY>(G);
+                Q4<float> d, bd;
+                apply4<float, LAY>(m, tf, dc, G, di, d, bd);
+                Q4<float> ev = {{0.0f, 0.0f, 0.0f, 0.0f}};
+                if (it > 0) ev = ld4(f.e + G.p);
+                const Q4<float> rv = ld4(f.r + G.p);
+                Q4<float> en, rn, dnew;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    en.v[j] = ev.v[j] + d.v[j];
+                    rn.v[j] = rv.v[j] - bd.v[j];
+                    dnew.v[j] = fmaf(ca, d.v[j], cb * rn.v[j]);
+                }
+                st4(f.e + G.p, en);
+                if (!last) {
+                    st4(f.r + G.p, rn);
+                    st4(dn + G.p, dnew);
+                }
+            }
+            float* sw = dc; dc = dn; dn = sw;
+            if (!grid_barrier(a.bar, target, a.flags)) return;
+        }
+        inner_total += kin;
+        // [X] x += e (FP64)
+        for (int qi = q0 + (int)threadIdx.x; qi < q1; qi += blockDim.x) {
+            const int p = 4 * qi;
+            const Q4<float> e = ld4(f.e + p);
+            Q4<double> x = ld4(a.x + p);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x.v[j] += (double)e.v[j];
+            st4(a.x + p, x);
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        ++outer;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = inner_total;
+        a.status[1] = outer;
+        if (a.iter_log) *a.iter_log = inner_total;
+        if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+        else if (!done) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+    }
+}
+
 // Dynamic shared memory of a launch, and the one-time opt-in above 48 KB.
 template <typename K>
 cudaError_t prepare(K kernel, size_t bytes)
@@ -678,6 +807,42 @@ int quad_blocks(const MeshDev& m, const CgWork& w)
     long long want = (nq + w.threads - 1) / w.threads;
     if (want < 1) want = 1;
     return (int)(want < w.max_blocks ? want : w.max_blocks);
+}
+
+// The Chebyshev interval of I - g A and the recurrence coefficients: the
+// spectrum is exactly [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))] for the
+// scalar sigma and inside [1, 1 + g lam_bound] for the layered operator.
+// False when the interval has no width in FP64 (g below rounding).
+bool cheb_interval(const CgArgsHost& h, ChebArgs& c)
+{
+    double w = 0.0;
+    if (h.mesh.lay) {
+        w = h.mesh.lam_bound;
+    } else {
+        const int n[3] = {h.mesh.nx, h.mesh.ny, h.mesh.nz};
+        for (int k = 0; k < 3; ++k)
+            if (n[k] > 1) {
+                const double sn = std::sin(M_PI * (n[k] - 1) / (2.0 * n[k]));
+                w += 4.0 * sn * sn;
+            }
+        w *= h.mesh.ih2;
+    }
+    const double lmin = 1.0, lmax = 1.0 + h.g * w;
+    if (!(lmax > lmin)) return false;
+    const double theta = 0.5 * (lmax + lmin);
+    c.inv_theta = 1.0 / theta;
+    const double delta = 0.5 * (lmax - lmin), s1 = theta / delta;
+    const double kap = lmax / lmin;
+    c.q = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    c.log_q = c.q > 0.0 ? std::log(c.q) : -1.0;
+    double rho = 1.0 / s1;
+    for (int k = 0; k < ESDC_CHEB_TAB; ++k) {
+        const double rn = 1.0 / (2.0 * s1 - rho);
+        c.ca[k] = rn * rho;
+        c.cb[k] = 2.0 * rn / delta;
+        rho = rn;
+    }
+    return true;
 }
 
 }  // namespace
@@ -714,36 +879,8 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     a.tol2 = h.tol * h.tol;
     a.maxit = h.maxit;
     a.precond = 0;
-    // spectrum of I - g L: exactly [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))] for
-    // the scalar sigma; inside [1, 1 + g lam_bound] for the layered operator
-    double w = 0.0;
-    if (h.mesh.lay) {
-        w = h.mesh.lam_bound;
-    } else {
-        const int n[3] = {h.mesh.nx, h.mesh.ny, h.mesh.nz};
-        for (int k = 0; k < 3; ++k)
-            if (n[k] > 1) {
-                const double sn = std::sin(M_PI * (n[k] - 1) / (2.0 * n[k]));
-                w += 4.0 * sn * sn;
-            }
-        w *= h.mesh.ih2;
-    }
-    const double lmin = 1.0, lmax = 1.0 + h.g * w;
-    if (!(lmax > lmin)) return esdc_cg4_launch(h, false, s);    // g below rounding: no interval to work on
     ChebArgs c;
-    const double theta = 0.5 * (lmax + lmin);
-    c.inv_theta = 1.0 / theta;
-    const double delta = 0.5 * (lmax - lmin), s1 = theta / delta;
-    const double kap = lmax / lmin;
-    c.q = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
-    c.log_q = c.q > 0.0 ? std::log(c.q) : -1.0;
-    double rho = 1.0 / s1;
-    for (int k = 0; k < ESDC_CHEB_TAB; ++k) {
-        const double rn = 1.0 / (2.0 * s1 - rho);
-        c.ca[k] = rn * rho;
-        c.cb[k] = 2.0 * rn / delta;
-        rho = rn;
-    }
+    if (!cheb_interval(h, c)) return esdc_cg4_launch(h, false, s);    // g below rounding: no interval
     const int ne = tab_entries(h.mesh);
     const size_t bytes = sizeof(double) * ne;
     const bool lay = h.mesh.lay != nullptr;
@@ -764,6 +901,52 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     void* args[] = {&a, &c};
     const void* k = lay ? (const void*)k_cheb4<true> : (const void*)k_cheb4<false>;
     return cudaLaunchCooperativeKernel(k, dim3((unsigned)nb), dim3(threads), args, bytes, s);
+}
+
+cudaError_t esdc_cheb_mixed_launch(const CgArgsHost& h, cudaStream_t s)
+{
+    if (!h.w.r32) return cudaErrorInvalidValue;
+    ChebArgs c;
+    if (!cheb_interval(h, c)) return esdc_cg4_launch(h, true, s);     // g below rounding: no interval
+    CgArgs a;
+    a.m = h.mesh;
+    a.g = h.g;
+    for (int k = 0; k < 7; ++k) a.dinv[k] = 0.0;
+    a.b = h.b;
+    a.x = h.x;
+    a.r = h.w.r; a.p = h.w.p; a.q = h.w.q; a.z = h.w.z;
+    a.part = h.w.part;
+    a.bar = h.w.bar;
+    a.status = h.w.status;
+    a.iter_log = h.iter_log;
+    a.flags = h.flags;
+    a.tol2 = h.tol * h.tol;
+    a.maxit = h.maxit;
+    a.precond = 0;
+    Cg4MixArgs f;
+    f.r = h.w.r32; f.p = h.w.p32; f.q = h.w.q32; f.z = h.w.z32; f.e = h.w.e32;
+    f.eta2 = 1e-10;
+    f.maxin = h.maxit < 60 ? h.maxit : 60;
+    f.maxout = 8;
+    // inner iterations: 2 q^k <= 1e-5 (q > 0 whenever the interval has width)
+    int kin = f.maxin;
+    if (c.q > 0.0) {
+        const double kd = std::ceil(std::log(0.5e-5) / c.log_q);
+        if (kd < kin) kin = kd < 1.0 ? 1 : (int)kd;
+    }
+    const int ne = tab_entries(h.mesh);
+    const size_t bytes = (sizeof(double) + sizeof(float)) * ne + 16;
+    const bool lay = h.mesh.lay != nullptr;
+    cudaError_t e = lay ? prepare(k_cheb4_mixed<true>, bytes) : prepare(k_cheb4_mixed<false>, bytes);
+    if (e != cudaSuccess) return e;
+    const long long nq = h.mesh.N / 4;
+    long long nb = (nq + 127) / 128;
+    if (nb > h.w.max_blocks) nb = h.w.max_blocks;
+    if (nb < 1) nb = 1;
+    if ((e = cudaMemsetAsync(h.w.bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    void* args[] = {&a, &f, &c, &kin};
+    const void* k = lay ? (const void*)k_cheb4_mixed<true> : (const void*)k_cheb4_mixed<false>;
+    return cudaLaunchCooperativeKernel(k, dim3((unsigned)nb), dim3(h.w.threads), args, bytes, s);
 }
 
 cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s)

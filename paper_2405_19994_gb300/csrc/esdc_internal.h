@@ -149,7 +149,7 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
 // Precision form: FP32 inner PCG with FP64 iterative refinement (same contract;
 // iter_log receives the number of inner iterations).
 cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g, const double* b,
-                                 double* x, double tol, int maxit, int precond, int* iter_log,
+                                 double* x, double tol, int maxit, int precond, int solver, int* iter_log,
                                  int* flags, cudaStream_t s);
 // Blocks to use for a cooperative CG launch on this device.
 int esdc_cg_blocks(const MeshDev& mesh, int threads);
@@ -176,3 +176,5 @@ cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s);
 // second-order operator (quad layout, no dot products inside the iteration).
 bool esdc_cheb_eligible(const MeshDev& m, const void* b, const void* x);
 cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s);
+// The precision form's refinement with Chebyshev inner solves (same eligibility).
+cudaError_t esdc_cheb_mixed_launch(const CgArgsHost& h, cudaStream_t s);

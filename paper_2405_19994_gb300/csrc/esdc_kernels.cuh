@@ -612,7 +612,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
                 int* log = (k * M + (i - 1) < h->cg_log_len) ? h->cg_log + k * M + (i - 1) : nullptr;
                 prof_begin(h, 2, s);
                 e = MIXED ? esdc_cg_mixed_launch(h->mesh, h->cg, g, h->rhs, Vi, h->opt.tol_cg, h->opt.cg_maxit,
-                                                 h->opt.precond, log, h->flags, s)
+                                                 h->opt.precond, h->opt.solver, log, h->flags, s)
                           : esdc_cg_launch(h->mesh, h->cg, g, h->rhs, Vi, h->opt.tol_cg, h->opt.cg_maxit,
                                            h->opt.precond, h->opt.solver, log, h->flags, s);
                 prof_end(h, s);

@@ -628,7 +628,7 @@ int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, i
     CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, sizeof(int), s));
     if (h->opt.precision == 1)
         CUDA_TRY(h, esdc_cg_mixed_launch(h->mesh, h->cg, g, b, x, h->opt.tol_cg, h->opt.cg_maxit,
-                                         h->opt.precond, nullptr, h->flags, s));
+                                         h->opt.precond, h->opt.solver, nullptr, h->flags, s));
     else
         CUDA_TRY(h, esdc_cg_launch(h->mesh, h->cg, g, b, x, h->opt.tol_cg, h->opt.cg_maxit, h->opt.precond,
                                    h->opt.solver, nullptr, h->flags, s));

@@ -350,14 +350,16 @@ def test_errors_reported():
 
 # ---------------------------------------------------------------- precision form (FP32 ionic model)
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5), (16, 12, 3)])
 @pytest.mark.parametrize("g", [1e-3, 0.05, 2.0])
-def test_refinement_solve_matches_dct(shape, g):
-    """Precision-form solve (FP32 inner PCG, FP64 residuals): reaches the same
-    FP64 tolerance as the FP64 CG, so it meets the same bound against the DCT."""
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_refinement_solve_matches_dct(shape, g, solver):
+    """Precision-form solve (FP32 inner solves, FP64 residuals): reaches the same
+    FP64 tolerance as the FP64 CG, so it meets the same bound against the DCT.
+    With solver "auto" and nx % 4 == 0 the inner solves are Chebyshev iterations."""
     nx, ny, nz = shape
     wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
-    s = P.Solver.from_workload(wl, cg_maxit=2000, precision="mixed")
+    s = P.Solver.from_workload(wl, cg_maxit=2000, precision="mixed", solver=solver)
     m = O.Monodomain(wl)
     rng = np.random.default_rng(6)
     b = rng.normal(size=wl.n_nodes)
