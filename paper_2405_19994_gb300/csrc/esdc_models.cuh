@@ -18,7 +18,7 @@ namespace esdc {
 __device__ __forceinline__ double x_over_expm1(double x)
 {
     if (fabs(x) < 1e-6) return 1.0 - x * (0.5 - x * (1.0 / 12.0));
-    return x / expm1(x);
+    return x * esdc_rcp(expm1(x));
 }
 
 // FP32 versions (the precision form): x/(e^x - 1) with a Taylor branch.
@@ -37,19 +37,9 @@ struct HH1952 {
     {
         (void)ha;
         const double V = u[0], m = u[1], h = u[2], n = u[3];
-        const double v = V - mp[6];
-        const double am = x_over_expm1((25.0 - v) * 0.1);
-        const double bm = 4.0 * exp(v * (-1.0 / 18.0));
-        const double ah = 0.07 * exp(v * (-0.05));
-        const double bh = 1.0 / (exp((30.0 - v) * 0.1) + 1.0);
-        const double an = 0.1 * x_over_expm1((10.0 - v) * 0.1);
-        const double bn = 0.125 * exp(v * (-0.0125));
         const double m3h = m * m * m * h, n2 = n * n;
         mI = -(mp[0] * m3h * (V - mp[3]) + mp[1] * n2 * n2 * (V - mp[4]) + mp[2] * (V - mp[5]));
-        double sm = am + bm, sh = ah + bh, sn = an + bn;
-        lam[0] = -sm; yinf[0] = am / sm;
-        lam[1] = -sh; yinf[1] = ah / sh;
-        lam[2] = -sn; yinf[2] = an / sn;
+        for (int q = 0; q < 3; ++q) gate(mp, q, V, lam[q], yinf[q]);
     }
     // -I_ion only (the currents need the gate values, not their rates).
     __device__ static void currents(const double* __restrict__ mp, const double* u, double& mI, double* ha)
@@ -59,17 +49,23 @@ struct HH1952 {
         const double m3h = m * m * m * h, n2 = n * n;
         mI = -(mp[0] * m3h * (V - mp[3]) + mp[1] * n2 * n2 * (V - mp[4]) + mp[2] * (V - mp[5]));
     }
+    // Rates alpha, beta of gate q (0 = m, 1 = h, 2 = n) at v = V - Vrest, with the
+    // library's exponential and reciprocal (about 1 ulp each); the x/(e^x - 1)
+    // terms keep CUDA's expm1, which has no cancellation near 0.
+    __device__ static void rates(int q, double v, double& al, double& be)
+    {
+        if (q == 0) { al = x_over_expm1((25.0 - v) * 0.1); be = 4.0 * esdc_exp(v * (-1.0 / 18.0)); }
+        else if (q == 1) { al = 0.07 * esdc_exp(v * (-0.05)); be = esdc_rcp(esdc_exp((30.0 - v) * 0.1) + 1.0); }
+        else { al = 0.1 * x_over_expm1((10.0 - v) * 0.1); be = 0.125 * esdc_exp(v * (-0.0125)); }
+    }
     // Lambda_g and w_g,inf of gate q (0 = m, 1 = h, 2 = n) at potential V.
     __device__ static void gate(const double* __restrict__ mp, int q, double V, double& lam, double& yinf)
     {
-        const double v = V - mp[6];
         double al, be;
-        if (q == 0) { al = x_over_expm1((25.0 - v) * 0.1); be = 4.0 * exp(v * (-1.0 / 18.0)); }
-        else if (q == 1) { al = 0.07 * exp(v * (-0.05)); be = 1.0 / (exp((30.0 - v) * 0.1) + 1.0); }
-        else { al = 0.1 * x_over_expm1((10.0 - v) * 0.1); be = 0.125 * exp(v * (-0.0125)); }
+        rates(q, V - mp[6], al, be);
         const double sum = al + be;
         lam = -sum;
-        yinf = al / sum;
+        yinf = al * esdc_rcp(sum);
     }
     // FP32 counterparts of currents() and gate() (parameters as floats).
     __device__ static void currents_f(const float* __restrict__ mp, const float* u, float& mI, float* ha)
@@ -113,28 +109,21 @@ struct HH1952 {
             return fabs(x) < 1e-3 ? -0.5 + x * (1.0 / 6.0 - x * x * (1.0 / 180.0)) : f * (1.0 - f - x) / x;
         };
         double al, be, dal, dbe;
+        rates(q, v, al, be);                       // the forward rates, bit for bit
         if (q == 0) {
-            const double x = (25.0 - v) * 0.1;
-            al = x_over_expm1(x);
-            dal = -0.1 * fprime(x, al);
-            be = 4.0 * exp(v * (-1.0 / 18.0));
+            dal = -0.1 * fprime((25.0 - v) * 0.1, al);
             dbe = be * (-1.0 / 18.0);
         } else if (q == 1) {
-            al = 0.07 * exp(v * (-0.05));
             dal = -0.05 * al;
-            be = 1.0 / (exp((30.0 - v) * 0.1) + 1.0);
             dbe = 0.1 * be * (1.0 - be);
         } else {
             const double x = (10.0 - v) * 0.1;
-            const double f = x_over_expm1(x);
-            al = 0.1 * f;
-            dal = 0.1 * (-0.1) * fprime(x, f);
-            be = 0.125 * exp(v * (-0.0125));
+            dal = 0.1 * (-0.1) * fprime(x, x_over_expm1(x));
             dbe = be * (-0.0125);
         }
         const double sum = al + be;
         lam = -sum;
-        yinf = al / sum;
+        yinf = al * esdc_rcp(sum);
         dlam = -(dal + dbe);
         dyinf = (dal * be - al * dbe) / (sum * sum);
     }
