@@ -116,6 +116,26 @@ def test_aniso_operator_symmetric_nsd_constant_nullspace(orc):
     np.testing.assert_allclose(A @ np.ones(N), 0.0, atol=1e-13)
 
 
+@pytest.mark.parametrize("sl,st", [(0.17, 0.02), (0.3, 0.01)])
+def test_aniso_spectrum_inside_gershgorin_interval(orc, sl, st):
+    # The interval a Chebyshev semi-iteration on I - g A is built on for the
+    # layered operator: the smallest eigenvalue of I - g A is 1 (constants), the
+    # largest at most 1 + g G with G = max over layers of
+    # (4 sxx + 4 syy + 2|sxy| + 2 (faces' szz means))/h^2 (Gershgorin).
+    nx, ny, nz, h, g = 6, 5, 4, 0.4, 0.3
+    wl, m = _aniso(nx, ny, nz, h, sl=sl, st=st)
+    N = nx * ny * nz
+    B = np.stack([e - g * m.conductivity(e) for e in np.eye(N)], axis=1)
+    ev = np.linalg.eigvalsh(0.5 * (B + B.T))
+    L = wl.layers
+    face = np.append(0.5 * (L["szz"][:-1] + L["szz"][1:]), 0.0)            # face k | k+1
+    below = np.insert(face[:-1], 0, 0.0)
+    G = np.max(4 * L["sxx"] + 4 * L["syy"] + 2 * np.abs(L["sxy"]) + 2 * (face + below)) / h**2
+    assert abs(ev.min() - 1.0) < 1e-12
+    assert ev.max() <= 1 + g * G + 1e-12
+    assert ev.max() >= 1 + 0.6 * g * G                                      # and the bound is not loose
+
+
 def test_aniso_reduces_to_isotropic(orc):
     nx, ny, nz = 7, 6, 3
     wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
