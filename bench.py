@@ -36,16 +36,16 @@ UNIT = "node-updates/s"
 #  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
 #  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu
 #  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep:
-#  191.0 + 3 x 1152.7 + 940.7 = 4589.8 flops per node per sweep
+#  191.0 + 3 x 1080.7 + 868.7 = 4301.8 flops per node per sweep
 #  (profiles/k_node_syn19_slab_128x128x16.md).
 #  Algorithmic bytes per node: node 1 reads 158 / writes 20 doubles, nodes 2..M
 #  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep, 1493 B per launch
-#  on average; DRAM traffic measured by ncu: 7042 B per sweep (1408 B per launch).
+#  on average; DRAM traffic measured by ncu: 7048 B per sweep (1410 B per launch).
 #  cg (per mesh node and iteration): [A] z (stencil), p, q -> p, q;
 #  [B] q, r, x, p -> x, r, z: 12 doubles = 96 B, plus 8 doubles per solve.
-NODE_FLOPS_PER_SWEEP = {4: 4589.8}
+NODE_FLOPS_PER_SWEEP = {4: 4301.8}
 NODE_BYTES_PER_LAUNCH = {4: 1493}
-NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {4: 1408}
+NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {4: 1410}
 CG_BYTES_PER_NODE_ITER = 96
 CG_BYTES_PER_NODE_SETUP = 64
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.

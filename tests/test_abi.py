@@ -1,6 +1,7 @@
 """The C-ABI library loads without a GPU, exports every entry point that
 include/esdc.h declares, and rejects invalid arguments before touching CUDA."""
 import ctypes as C
+import math
 import os
 import re
 
@@ -163,3 +164,18 @@ def test_later_entry_points_reject_invalid_arguments_without_gpu(L):
     bad = np.array([[1.0, np.nan], [0.0, 1.0]])
     assert L.esdc_interp(src, 2, 4, dst, 2, 4, 1, 4, bad.ctypes.data_as(D), 0.0, None) == -1
     assert L.esdc_interp(src, 2, 4, dst, 2, 4, 1, 0, Wp, 0.0, None) == 0      # nothing to do
+
+
+def test_exp_table_entries_are_correctly_rounded():
+    # esdc_exp's table: 2^(j/2048) for j = 0..2047, each within half an ulp of
+    # the exact value (here computed as a decimal power at 40 digits)
+    import decimal
+    import re
+    src = open(os.path.join(ROOT, "paper_2405_19994_gb300", "csrc", "esdc_exp_table.h")).read()
+    vals = [float.fromhex(v) for v in re.findall(r"0x[0-9a-f.]+p[+-]\d+", src[src.index("{"):])]
+    assert len(vals) == 2048
+    decimal.getcontext().prec = 40
+    for j, v in enumerate(vals):
+        exact = decimal.Decimal(2) ** (decimal.Decimal(j) / 2048)
+        ulp = math.ulp(v)
+        assert abs(decimal.Decimal(v) - exact) <= decimal.Decimal(ulp) / 2, j
