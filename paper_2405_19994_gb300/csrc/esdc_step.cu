@@ -511,8 +511,7 @@ int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, voi
     CUDA_TRY(h, cudaMemsetAsync(h->rmax, 0, sizeof(unsigned long long) * 2 * ESDC_NSMAX, s));
     CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, sizeof(int), s));
     CUDA_TRY(h, cudaMemsetAsync(h->cg_log, 0, sizeof(int) * h->cg_log_len, s));
-    StepArgs a{};
-    std::memset(&a, 0, sizeof a);
+    StepArgs a{};                        // value-initialised: every pointer null, every count 0
     a.m = h->mesh; a.st = h->stim; a.mp = h->mp; a.mpf = h->mpf;
     a.dt = dt; a.t_n = t; a.D = h->D; a.inv_Cm = 1.0 / h->Cm;
     a.yn = y; a.Y = h->Y; a.FI = h->FI; a.S = h->S; a.PHI = h->PHI; a.LAMN = h->LAMN; a.rhs = h->rhs;
