@@ -109,13 +109,14 @@ __device__ __forceinline__ double stim_at(const StimDev& st, unsigned on, int ix
 //             Horner form with host coefficients; the number of terms steps
 //             down with |x|), then phi_k = x phi_{k+1} + 1/k!.
 // X1 balances the rounding growth of the two recurrences (set on the host).
-// M = 1: phi_1 = expm1(x)/x.
+// M = 1: phi_1 as in phi1().
 template <int M>
 __device__ __forceinline__ void phi_all(double x, double (&ph)[M])
 {
     const ColloData& C = c_col[M - 1];
     if (M == 1) {
-        ph[0] = (x == 0.0) ? 1.0 : expm1(x) / x;
+        ph[0] = x < -0.5 ? (esdc::esdc_exp(x) - 1.0) * esdc::esdc_rcp(x)           // as phi1() below
+                         : (x == 0.0 ? 1.0 : esdc::esdc_rcp(esdc::x_over_expm1(x)));
     } else if (-x > C.X1) {
         const double rx = esdc::esdc_rcp(x);
         ph[0] = (esdc::esdc_exp(x) - 1.0) * rx;
@@ -133,11 +134,13 @@ __device__ __forceinline__ void phi_all(double x, double (&ph)[M])
     }
 }
 
-// phi_1(y) = (e^y - 1)/y for y <= 0.
+// phi_1(y) = (e^y - 1)/y for y <= 0: below -1/2 directly (e^y - 1 keeps at least
+// 1 - e^{-1/2} of its magnitude, so about 3 ulp); above, the reciprocal of
+// x/(e^x - 1) from its Bernoulli series.
 __device__ __forceinline__ double phi1(double y)
 {
-    if (y < -1.0) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);
-    return (y == 0.0) ? 1.0 : expm1(y) / y;
+    if (y < -0.5) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);
+    return (y == 0.0) ? 1.0 : esdc::esdc_rcp(esdc::x_over_expm1(y));
 }
 
 // ------------------------------------------------------------------ set-up
