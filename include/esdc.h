@@ -81,10 +81,10 @@ typedef struct {
     int    precision;  /* 0 = FP64 throughout; 1 = precision form: the ionic model
                           (f_E, Lambda, y_inf) evaluated in FP32, and each diffusion
                           solve done by iterative refinement (FP64 residuals
-                          r = b - A x, FP32 inner PCG on A e = r, x += e) to the
+                          r = b - A x, FP32 inner solve of A e = r, x += e) to the
                           same tol_cg; state, coefficient tables, quadrature and
                           residual stay FP64                                       */
-    int    solver;     /* FP64 diffusion solves of the sweep and esdc_diffusion_solve:
+    int    solver;     /* diffusion solves of the sweep and esdc_diffusion_solve:
                           0 = automatic: the Chebyshev semi-iteration where an
                           interval holding the spectrum of the operator of
                           esdc_diffusion_solve is known (nx a multiple of 4,
@@ -93,7 +93,9 @@ typedef struct {
                           modes being its eigenvectors; layered conductivity:
                           [1, 1 + g G] with G the Gershgorin bound of -A), the
                           Jacobi-PCG elsewhere (a conductivity field, the
-                          fourth-order stencil, other nx);
+                          fourth-order stencil, other nx); with precision 1 the
+                          refinement's FP32 inner solves are then a fixed number
+                          of Chebyshev iterations (2 q^k <= 1e-5), else PCG;
                           1 = the (Jacobi-P)CG always;
                           2 = the DCT-II direct solve, the paper's solver (Sec. 5):
                           x = C^T diag(1/(1 - g mu)) C b with C the orthonormal
@@ -105,8 +107,8 @@ typedef struct {
                           setters return it for layers or a field); holds the
                           axes' DCT matrices (nx^2 + ny^2 + nz^2 doubles).
                           Batches take 0 or 1.
-                          Both stop at the same ||r|| <= tol_cg ||b||.  The paper
-                          leaves the inner solver open (it uses PCG).            */
+                          0 and 1 stop at the same ||r|| <= tol_cg ||b||.  The
+                          paper solves these systems with the DCT-II.            */
 } esdc_options;
 
 /* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1,
