@@ -406,7 +406,7 @@ def run_precision_form(args):
     clocks = ClockSampler(local)
     clocks.start()
     for prec in ("fp64", "mixed"):
-        s = P.Solver.from_workload(wl, M_max=wl.M, precision=prec)
+        s = P.Solver.from_workload(wl, M_max=wl.M, precision=prec, solver=args.solver)
         _simulate(s, wl, args.warmup, record=False)                 # warm-up (clocks, caches, first launches)
         s.profile(True)
         v, act, ms = _simulate(s, wl, n_steps)
@@ -453,6 +453,7 @@ def run_precision_form(args):
         "steps": n_steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": wl.name, "form": "precision", "nodes": N, "M": wl.M, "K": wl.K, "dt_ms": wl.dt,
+                   "solver": args.solver,
                    "T_ms": n_steps * wl.dt, "model": "hh1952", "conductivity": "layered, fibres -60..60 deg",
                    "l2": "inputs larger than L2 (state + workspace ~1.5 GB)"},
         "s_per_sim_ms": ms_step * 1e-3 / wl.dt,
@@ -984,7 +985,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
     ap.add_argument("--solver", choices=["auto", "cg", "dct"], default="auto",
-                    help="diffusion solves (headline, batch and fas forms): auto (Chebyshev semi-iteration on "
+                    help="diffusion solves (headline, precision, batch and fas forms): auto (Chebyshev semi-iteration on "
                          "the exactly known spectrum of the scalar-sigma operator), cg (Jacobi-PCG) or dct "
                          "(the DCT-II direct solve; headline form only)")
     ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet"], default="plain",
@@ -996,7 +997,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.solver == "dct" and (args.form != "plain" or args.impl != "ours"):
+    if args.solver == "dct" and (args.form != "plain" or args.impl != "ours"):     # DCT: scalar sigma, FP64
         ap.error("--solver dct applies to the headline form only")
     if args.steps is None and args.form == "plain":
         args.steps = 40
