@@ -453,6 +453,15 @@ __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
 // One state s of one node: the residual recursion over the M nodes, the
 // largest |r_i| and |y| (y_n included), and y_{n+1} = y_{n,M} (c_M = 1).
 // Returns false if a residual or iterate is not finite.
+// The maxima are taken on the bit patterns of |r| and |y| with integer
+// operations: for non-negative doubles the patterns order like the values, and
+// Inf and NaN have the largest patterns (>= 0x7ff0...), so one test at the end
+// finds them.  This keeps the comparisons off the FP64 pipe, the scarce unit.
+__device__ __forceinline__ unsigned long long abs_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
 template <class Model, int M, bool TAU = false>
 __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, double& rmax, double& ymax)
 {
@@ -460,9 +469,7 @@ __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, 
     const int64_t ld = a.m.ld;
     const int g = s - 1 - NA;
     const double yns = a.yn[s * ld + p];
-    bool ok = true;
-    ymax = fabs(yns);
-    rmax = 0.0;
+    unsigned long long rb = 0ULL, yb = abs_bits(yns);
     // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
     double r = 0.0, yprev = yns;
 #pragma unroll
@@ -479,13 +486,14 @@ __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, 
             r += a.tau[((int64_t)i * NS + s) * ld + p] - (i > 0 ? a.tau[((int64_t)(i - 1) * NS + s) * ld + p] : 0.0);
         yprev = yi;
         if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
-        ok &= isfinite(r) && isfinite(yi);
-        rmax = fmax(rmax, fabs(r));
-        ymax = fmax(ymax, fabs(yi));
+        rb = max(rb, abs_bits(r));
+        yb = max(yb, abs_bits(yi));
     }
     // y_n was read above by this thread only, so y may alias y_{n+1}.
     a.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
-    return ok;
+    rmax = __longlong_as_double((long long)rb);
+    ymax = __longlong_as_double((long long)yb);
+    return rb < 0x7ff0000000000000ULL && yb < 0x7ff0000000000000ULL;
 }
 
 template <class Model, int M>
