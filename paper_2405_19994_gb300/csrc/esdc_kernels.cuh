@@ -102,6 +102,20 @@ __device__ __forceinline__ double stim_at(const StimDev& st, unsigned on, int ix
     return s;
 }
 
+// Order tests of non-negative doubles on their bit patterns: for a, b >= 0 (or
+// -0), a <= b exactly when the patterns compare so as signed 64-bit integers.
+// Integer compares run on the ALU pipe; the FP64 pipe is the scarce unit.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+
+// phi_1(y) = (e^y - 1)/y for y <= 0: below -1/2 directly (e^y - 1 keeps at least
+// 1 - e^{-1/2} of its magnitude, so about 3 ulp); above, the reciprocal of
+// x/(e^x - 1) from its Bernoulli series.
+__device__ __forceinline__ double phi1(double y)
+{
+    if (dbits(-y) > dbits(0.5)) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);   // y < -1/2
+    return (dbits(y) << 1) == 0 ? 1.0 : esdc::esdc_rcp(esdc::x_over_expm1(y));          // y = +-0
+}
+
 // phi_1..phi_M at x <= 0 (App. A eq. def_phik).  Two regimes:
 //  |x| >  X1: phi_1 = (e^x - 1)/x (no cancellation there: X1 > 1.4 for M >= 2),
 //             then phi_{k+1} = (phi_k - 1/k!)/x;
@@ -114,18 +128,18 @@ template <int M>
 __device__ __forceinline__ void phi_all(double x, double (&ph)[M])
 {
     const ColloData& C = c_col[M - 1];
+    const double nx = -x;
+    const long long nbits = dbits(nx);
     if (M == 1) {
-        ph[0] = x < -0.5 ? (esdc::esdc_exp(x) - 1.0) * esdc::esdc_rcp(x)           // as phi1() below
-                         : (x == 0.0 ? 1.0 : esdc::esdc_rcp(esdc::x_over_expm1(x)));
-    } else if (-x > C.X1) {
+        ph[0] = phi1(x);
+    } else if (nbits > dbits(C.X1)) {                     // -x > X1
         const double rx = esdc::esdc_rcp(x);
         ph[0] = (esdc::esdc_exp(x) - 1.0) * rx;
 #pragma unroll
         for (int k = 1; k < M; ++k) ph[k] = (ph[k - 1] - c_invfact[k]) * rx;
     } else {
-        const double nx = -x;
-        const int n = nx <= C.xb[0] ? C.nb[0] : nx <= C.xb[1] ? C.nb[1] : nx <= C.xb[2] ? C.nb[2]
-                    : nx <= C.xb[3] ? C.nb[3] : C.nb[4];
+        const int n = nbits <= dbits(C.xb[0]) ? C.nb[0] : nbits <= dbits(C.xb[1]) ? C.nb[1]
+                    : nbits <= dbits(C.xb[2]) ? C.nb[2] : nbits <= dbits(C.xb[3]) ? C.nb[3] : C.nb[4];
         double acc = C.ser[n];
         for (int m = n - 1; m >= 0; --m) acc = fma(acc, nx, C.ser[m]);
         ph[M - 1] = esdc::esdc_exp(x) * acc;
@@ -134,14 +148,6 @@ __device__ __forceinline__ void phi_all(double x, double (&ph)[M])
     }
 }
 
-// phi_1(y) = (e^y - 1)/y for y <= 0: below -1/2 directly (e^y - 1 keeps at least
-// 1 - e^{-1/2} of its magnitude, so about 3 ulp); above, the reciprocal of
-// x/(e^x - 1) from its Bernoulli series.
-__device__ __forceinline__ double phi1(double y)
-{
-    if (y < -0.5) return (esdc::esdc_exp(y) - 1.0) * esdc::esdc_rcp(y);
-    return (y == 0.0) ? 1.0 : esdc::esdc_rcp(esdc::x_over_expm1(y));
-}
 
 // ------------------------------------------------------------------ set-up
 // Lambda_n, dt S_ij(dt Lambda_n), dt d_i phi_1(d_i dt Lambda_n) (tables carry the

@@ -21,7 +21,8 @@ namespace esdc {
 // |x| >= 1/2, about 3 ulp in all.  About 12 FP64 operations either way.
 __device__ __forceinline__ double x_over_expm1(double x)
 {
-    if (fabs(x) < 0.5) {
+    // |x| < 1/2, tested on the bit pattern (an integer compare, off the FP64 pipe)
+    if ((__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x3fe0000000000000LL) {
         const double x2 = x * x;
         double p = -3617.0 / 10670622842880000.0;                 // B_16/16!
         p = fma(p, x2, 1.0 / 74724249600.0);                       // B_14/14!
