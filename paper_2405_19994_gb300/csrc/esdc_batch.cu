@@ -83,20 +83,21 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
     const int lane = threadIdx.x & 31;
     const long long ng = (long long)a.m.N >> 5;
     const long long g0 = gw * ng / nw, g1 = (gw + 1) * ng / nw;
-    double rm[NS], ym[NS];
+    // maxima kept as the bit patterns of non-negative doubles (integer max, as in residual_state)
+    unsigned long long rm[NS], ym[NS];
     int cur = -1;
     bool bad = false;
     auto flush = [&](int b) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            double r = rm[s], y = ym[s];
+            unsigned long long r = rm[s], y = ym[s];
             for (int o = 16; o > 0; o >>= 1) {
-                r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-                y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
+                r = max(r, __shfl_xor_sync(0xffffffffu, r, o));
+                y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
             }
             if (lane == 0) {
-                atomicMax(rmax + (size_t)b * 2 * NS + s, (unsigned long long)__double_as_longlong(r));
-                atomicMax(rmax + (size_t)b * 2 * NS + NS + s, (unsigned long long)__double_as_longlong(y));
+                atomicMax(rmax + (size_t)b * 2 * NS + s, r);
+                atomicMax(rmax + (size_t)b * 2 * NS + NS + s, y);
             }
         }
     };
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
             if (cur >= 0) flush(cur);
             cur = b;
 #pragma unroll
-            for (int s = 0; s < NS; ++s) { rm[s] = 0.0; ym[s] = 0.0; }
+            for (int s = 0; s < NS; ++s) { rm[s] = 0ULL; ym[s] = 0ULL; }
         }
         const TissueDev* T = a.tis + b;
         if (p - T->off < T->N) {
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
             for (int s = 0; s < NS; ++s) {
                 double r, y;
                 bad |= !residual_state<Model, M, true>(a, p, s, r, y);
-                rm[s] = fmax(rm[s], r);
-                ym[s] = fmax(ym[s], y);
+                rm[s] = max(rm[s], (unsigned long long)__double_as_longlong(r));
+                ym[s] = max(ym[s], (unsigned long long)__double_as_longlong(y));
             }
         }
     }
