@@ -286,6 +286,99 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg(CgArgs a)
 }
 
 
+// Chebyshev semi-iteration, one node per thread: the meshes the quad form does
+// not take (a conductivity field, the fourth-order stencil, nx not a multiple
+// of 4, unaligned vectors).  The recurrence, the bound-derived iteration count
+// and the stop checks are those of the quad form (x += d, r -= B d,
+// d = ca d + cb r); the interval comes from esdc_cheb_interval.  One grid
+// barrier per iteration; the residual is reduced only at the checks.
+__global__ void __launch_bounds__(ESDC_CG_THREADS) k_cheb(CgArgs a, ChebArgs c)
+{
+    const MeshDev& m = a.m;
+    const int N = m.N;
+    const int stride = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double* part = a.part;
+    const double gih2 = (m.lay || m.sig) ? a.g : a.g * m.ih2;     // layered / field coefficients carry 1/h^2
+    __shared__ double bs[3];
+    unsigned target = 0;
+    double* dc = a.p;            // d_k
+    double* dn = a.q;            // d_{k+1}
+    const double inv_theta = c.inv_theta;
+
+    // r = b - B x, d_0 = r / theta; partials r.r, b.b
+    {
+        double v[2] = {0.0, 0.0};
+        for (int p = tid; p < N; p += stride) {
+            int nnb;
+            const double bx = apply_op(m, a.x, p, node_idx(m, p), gih2, &nnb);
+            const double bp = a.b[p];
+            const double rp = bp - bx;
+            a.r[p] = rp;
+            dc[p] = rp * inv_theta;
+            v[0] = fma(rp, rp, v[0]);
+            v[1] = fma(bp, bp, v[1]);
+        }
+        block_sum<2>(v, bs);
+        if (threadIdx.x == 0) for (int k = 0; k < 2; ++k) part[k * gridDim.x + blockIdx.x] = bs[k];
+    }
+    if (!grid_barrier(a.bar, target, a.flags)) return;
+    double tot[2];
+    grid_total<2>(part, 0, tot);
+    const double stop = a.tol2 * tot[1];
+    bool done = tot[0] <= stop;
+    bool bad = !isfinite(tot[0]) || !isfinite(stop);
+    // iterations the bound asks for (one thread per block evaluates it)
+    __shared__ int s_kneed;
+    if (threadIdx.x == 0) {
+        int kn = 1;
+        if (!done && !bad && c.q > 0.0) {
+            const double kd = stop > 0.0 ? ceil(log(0.5 * sqrt(stop / tot[0])) / c.log_q) : (double)a.maxit;
+            kn = kd < (double)a.maxit ? (int)kd : a.maxit;
+        }
+        s_kneed = kn < 1 ? 1 : kn;
+    }
+    __syncthreads();
+    int it = 0;
+    int chunk_end = s_kneed < a.maxit ? s_kneed : a.maxit;
+    while (!done && !bad && it < a.maxit) {
+        const bool check = it + 1 >= chunk_end;
+        const int ki = it < ESDC_CHEB_TAB ? it : ESDC_CHEB_TAB - 1;
+        const double ca = c.ca[ki], cb = c.cb[ki];
+        double v[1] = {0.0};
+        for (int p = tid; p < N; p += stride) {
+            int nnb;
+            const double bd = apply_op(m, dc, p, node_idx(m, p), gih2, &nnb);
+            const double dp = __ldcg(dc + p);
+            const double rn = __ldcg(a.r + p) - bd;
+            a.x[p] = __ldcg(a.x + p) + dp;
+            a.r[p] = rn;
+            dn[p] = fma(ca, dp, cb * rn);
+            if (check) v[0] = fma(rn, rn, v[0]);
+        }
+        double* sw = dc; dc = dn; dn = sw;
+        ++it;
+        if (check) {
+            block_sum<1>(v, bs);
+            if (threadIdx.x == 0) part[(2 + (it & 1)) * gridDim.x + blockIdx.x] = bs[0];
+        }
+        if (!grid_barrier(a.bar, target, a.flags)) return;
+        if (check) {
+            double rr[1];
+            grid_total<1>(part, 2 + (it & 1), rr);
+            if (!isfinite(rr[0])) { bad = true; break; }
+            if (rr[0] <= stop) { done = true; break; }
+            chunk_end = it + 2 < a.maxit ? it + 2 : a.maxit;     // rounding left it short: two more, then check
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = it;
+        if (a.iter_log) *a.iter_log = it;
+        if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+        else if (!done) atomicOr(a.flags, ESDC_FLAG_CG_MAXIT);
+    }
+}
+
 // Precision form of the solve: iterative refinement with FP64 residuals and
 // FP32 inner Jacobi-PCG (the matrix-vector products of the inner solve are FP32):
 //   r = b - A x (FP64); until ||r|| <= tol ||b||:
@@ -507,6 +600,8 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
         if (solver == 0 && g > 0.0 && esdc_cheb_eligible(mesh, b, x)) return esdc_cheb_launch(hq, s);
         return esdc_cg4_launch(hq, false, s);
     }
+    ChebArgs cheb;
+    const bool use_cheb = solver == 0 && g > 0.0 && esdc_cheb_interval(mesh, g, cheb);
     CgArgs a;
     a.m = mesh;
     a.g = g;
@@ -523,10 +618,14 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
     a.maxit = maxit;
     a.precond = precond;
     int nb = w.max_blocks;
-    void* args[] = {&a};
     // The arrival counter starts from zero in every solve.
     cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    if (use_cheb) {
+        void* args[] = {&a, &cheb};
+        return cudaLaunchCooperativeKernel((const void*)k_cheb, dim3(nb), dim3(w.threads), args, 0, s);
+    }
+    void* args[] = {&a};
     return cudaLaunchCooperativeKernel((const void*)k_cg, dim3(nb), dim3(w.threads), args, 0, s);
 }
 

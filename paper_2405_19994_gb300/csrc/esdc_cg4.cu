@@ -369,13 +369,7 @@ __global__ void __launch_bounds__(ESDC_CG_THREADS) k_cg4(CgArgs a)
 // checked, and a short extension runs if rounding left it above the tolerance.
 // One grid barrier per iteration (CG needs two and three dot products), and
 // 11 FP64 operations per node: the stencil, r, x and d.
-#define ESDC_CHEB_TAB 64
 #define ESDC_CHEB_THREADS 1024   // one block per SM; the quads of a mesh are too few to fill more warps
-struct ChebArgs {
-    double inv_theta, q, log_q;
-    double ca[ESDC_CHEB_TAB];   // rho_{k+1} rho_k
-    double cb[ESDC_CHEB_TAB];   // 2 rho_{k+1} / delta   (index k; the last entry is used beyond)
-};
 
 // 1024 threads for the scalar stencil (64 registers suffice); the layered
 // stencil's extra neighbours and coefficients need more registers: 512.
@@ -809,26 +803,39 @@ int quad_blocks(const MeshDev& m, const CgWork& w)
     return (int)(want < w.max_blocks ? want : w.max_blocks);
 }
 
-// The Chebyshev interval of I - g A and the recurrence coefficients: the
-// spectrum is exactly [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))] for the
-// scalar sigma and inside [1, 1 + g lam_bound] for the layered operator.
-// False when the interval has no width in FP64 (g below rounding).
-bool cheb_interval(const CgArgsHost& h, ChebArgs& c)
+}  // namespace
+
+bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x)
+{
+    if (m.nx % 4 != 0 || m.N < 4 || m.sig || m.order != 2) return false;   // field and fourth order: scalar path
+    if ((reinterpret_cast<uintptr_t>(b) & 15u) || (reinterpret_cast<uintptr_t>(x) & 15u)) return false;
+    if (m.lay && (m.nz > ESDC_CG4_MAX_LAYERS || !m.wdiag)) return false;
+    return true;
+}
+
+bool esdc_cheb_interval(const MeshDev& m, double g, ChebArgs& c)
 {
     double w = 0.0;
-    if (h.mesh.lay) {
-        w = h.mesh.lam_bound;
+    const int n[3] = {m.nx, m.ny, m.nz};
+    if (m.lay || m.sig) {
+        w = m.lam_bound;
+    } else if (m.order == 4) {
+        for (int k = 0; k < 3; ++k)
+            if (n[k] > 1) {
+                const double t = M_PI * (n[k] - 1) / n[k];
+                w += 30.0 + 2.0 * std::cos(2.0 * t) - 32.0 * std::cos(t);
+            }
+        w *= m.ih2 / 12.0;
     } else {
-        const int n[3] = {h.mesh.nx, h.mesh.ny, h.mesh.nz};
         for (int k = 0; k < 3; ++k)
             if (n[k] > 1) {
                 const double sn = std::sin(M_PI * (n[k] - 1) / (2.0 * n[k]));
                 w += 4.0 * sn * sn;
             }
-        w *= h.mesh.ih2;
+        w *= m.ih2;
     }
-    const double lmin = 1.0, lmax = 1.0 + h.g * w;
-    if (!(lmax > lmin)) return false;
+    const double lmin = 1.0, lmax = 1.0 + g * w;
+    if (!(lmax > lmin) || !std::isfinite(lmax)) return false;
     const double theta = 0.5 * (lmax + lmin);
     c.inv_theta = 1.0 / theta;
     const double delta = 0.5 * (lmax - lmin), s1 = theta / delta;
@@ -842,16 +849,6 @@ bool cheb_interval(const CgArgsHost& h, ChebArgs& c)
         c.cb[k] = 2.0 * rn / delta;
         rho = rn;
     }
-    return true;
-}
-
-}  // namespace
-
-bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x)
-{
-    if (m.nx % 4 != 0 || m.N < 4 || m.sig || m.order != 2) return false;   // field and fourth order: scalar path
-    if ((reinterpret_cast<uintptr_t>(b) & 15u) || (reinterpret_cast<uintptr_t>(x) & 15u)) return false;
-    if (m.lay && (m.nz > ESDC_CG4_MAX_LAYERS || !m.wdiag)) return false;
     return true;
 }
 
@@ -880,7 +877,7 @@ cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s)
     a.maxit = h.maxit;
     a.precond = 0;
     ChebArgs c;
-    if (!cheb_interval(h, c)) return esdc_cg4_launch(h, false, s);    // g below rounding: no interval
+    if (!esdc_cheb_interval(h.mesh, h.g, c)) return esdc_cg4_launch(h, false, s);    // no interval
     const int ne = tab_entries(h.mesh);
     const size_t bytes = sizeof(double) * ne;
     const bool lay = h.mesh.lay != nullptr;
@@ -907,7 +904,7 @@ cudaError_t esdc_cheb_mixed_launch(const CgArgsHost& h, cudaStream_t s)
 {
     if (!h.w.r32) return cudaErrorInvalidValue;
     ChebArgs c;
-    if (!cheb_interval(h, c)) return esdc_cg4_launch(h, true, s);     // g below rounding: no interval
+    if (!esdc_cheb_interval(h.mesh, h.g, c)) return esdc_cg4_launch(h, true, s);     // no interval
     CgArgs a;
     a.m = h.mesh;
     a.g = h.g;

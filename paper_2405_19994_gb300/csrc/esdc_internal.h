@@ -172,8 +172,24 @@ struct CgArgsHost {
 };
 bool esdc_cg4_eligible(const MeshDev& m, const void* b, const void* x);
 cudaError_t esdc_cg4_launch(const CgArgsHost& h, bool mixed, cudaStream_t s);
-// Chebyshev semi-iteration on the exactly known spectrum of the scalar-sigma
-// second-order operator (quad layout, no dot products inside the iteration).
+// Chebyshev semi-iteration: 1/theta, q = (sqrt(kappa) - 1)/(sqrt(kappa) + 1),
+// log q, and the recurrence coefficients ca[k] = rho_{k+1} rho_k and
+// cb[k] = 2 rho_{k+1}/delta (the last entry serves beyond the table).
+#define ESDC_CHEB_TAB 64
+struct ChebArgs {
+    double inv_theta, q, log_q;
+    double ca[ESDC_CHEB_TAB];
+    double cb[ESDC_CHEB_TAB];
+};
+// The interval [1, 1 + g w] holding the spectrum of I - g A (or I - g L) of the
+// mesh's operator, and the coefficients on it.  w: exactly
+// (1/h^2) sum_axes 4 sin^2(pi (n-1)/(2n)) for the scalar second-order stencil,
+// exactly (1/(12 h^2)) sum_axes (30 + 2 cos 2t - 32 cos t), t = pi (n-1)/n, for
+// the fourth-order one, and the host's Gershgorin bound lam_bound for the
+// layered operator and the conductivity field.  False when the interval has no
+// width in FP64 (g below rounding) or no bound is known.
+bool esdc_cheb_interval(const MeshDev& m, double g, ChebArgs& c);
+// Chebyshev semi-iteration, quad layout (no dot products inside the iteration).
 bool esdc_cheb_eligible(const MeshDev& m, const void* b, const void* x);
 cudaError_t esdc_cheb_launch(const CgArgsHost& h, cudaStream_t s);
 // The precision form's refinement with Chebyshev inner solves (same eligibility).

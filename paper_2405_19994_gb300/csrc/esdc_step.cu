@@ -452,7 +452,10 @@ int esdc_set_conductivity_field(esdc_handle* h, const double* sigma)
         if (h->wdiag && !h->lay) { cudaFree(h->wdiag); h->wdiag = nullptr; h->mesh.wdiag = nullptr; }
         h->sigf = nullptr;
         h->mesh.sig = nullptr;
-        if (!h->lay) h->D = h->sigma / (h->chi * h->Cm);
+        if (!h->lay) {
+            h->D = h->sigma / (h->chi * h->Cm);
+            h->mesh.lam_bound = 0.0;
+        }
         return ESDC_OK;
     }
     if (h->opt.precision != 0)
@@ -473,6 +476,28 @@ int esdc_set_conductivity_field(esdc_handle* h, const double* sigma)
     CUDA_TRY(h, cudaMemcpy(h->sigf, sigma, sizeof(double) * N, cudaMemcpyHostToDevice));
     h->mesh.sig = h->sigf;
     h->mesh.wdiag = h->wdiag;
+    // Gershgorin bound of the spectrum of -A: the off-diagonals (face means over
+    // h^2) are positive and sum to the diagonal, so the bound is twice the
+    // largest diagonal, max_p sum_faces (sigma_p + sigma_q)/h^2
+    {
+        const int nx = h->mesh.nx, ny = h->mesh.ny, nz = h->mesh.nz;
+        const int64_t sxy = (int64_t)nx * ny;
+        double gb = 0.0;
+        for (int iz = 0; iz < nz; ++iz)
+            for (int iy = 0; iy < ny; ++iy)
+                for (int ix = 0; ix < nx; ++ix) {
+                    const int64_t p = ix + nx * (int64_t)iy + sxy * iz;
+                    double s = 0.0;
+                    if (ix > 0) s += sigma[p] + sigma[p - 1];
+                    if (ix < nx - 1) s += sigma[p] + sigma[p + 1];
+                    if (iy > 0) s += sigma[p] + sigma[p - nx];
+                    if (iy < ny - 1) s += sigma[p] + sigma[p + nx];
+                    if (iz > 0) s += sigma[p] + sigma[p - sxy];
+                    if (iz < nz - 1) s += sigma[p] + sigma[p + sxy];
+                    gb = std::max(gb, s);
+                }
+        h->mesh.lam_bound = gb * h->mesh.ih2;
+    }
     k_wdiag<<<grid_for(h, 256), 256>>>(h->mesh, h->wdiag);
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaDeviceSynchronize());

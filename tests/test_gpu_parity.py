@@ -177,8 +177,8 @@ def test_chebyshev_solve_matches_dct(shape, g):
 
 def test_chebyshev_zero_shift_and_ineligible_meshes():
     # g = 0 is the identity, and a g whose interval 1 + g w/h^2 rounds to 1 has
-    # no width either (the CG runs); nx not a multiple of 4 keeps the CG too;
-    # all give the exact result.
+    # no width either (the CG runs); nx not a multiple of 4 takes the
+    # one-node-per-thread Chebyshev kernel; all give the exact result.
     rng = np.random.default_rng(4)
     for shape, g in (((16, 8, 1), 0.0), ((16, 8, 1), 1e-19), ((18, 7, 3), 0.3)):
         wl = I.hh_sheet_32().with_mesh(*shape)
@@ -500,11 +500,13 @@ def test_syn19_slab_full_size_one_step():
 # ---------------------------------------------------------------- heterogeneous conductivity field
 
 @pytest.mark.parametrize("shape", [(13, 11, 1), (32, 24, 1), (9, 8, 5)])
-def test_field_solve_matches_oracle(shape):
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_field_solve_matches_oracle(shape, solver):
+    # "auto": the Chebyshev semi-iteration on the Gershgorin interval of the field operator
     nx, ny, nz = shape
     wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
     wl.sigma_field = I.lognormal_field(nx, ny, nz, seed=7, corr=3.0)
-    s = P.Solver.from_workload(wl, cg_maxit=2000)
+    s = P.Solver.from_workload(wl, cg_maxit=2000, solver=solver)
     m = O.Monodomain(wl, solver=O.SOLVE_CG, cg_tol=1e-15)
     b = np.random.default_rng(9).normal(size=wl.n_nodes)
     g = 0.3
@@ -546,11 +548,13 @@ def test_field_rejected_in_precision_form():
 # ---------------------------------------------------------------- fourth-order Laplacian
 
 @pytest.mark.parametrize("shape", [(13, 11, 1), (32, 24, 1), (9, 8, 5), (2, 3, 2)])
-def test_order4_solve_matches_oracle(shape):
+@pytest.mark.parametrize("solver", ["auto", "cg"])
+def test_order4_solve_matches_oracle(shape, solver):
+    # "auto": the Chebyshev semi-iteration on the exact fourth-order spectrum
     nx, ny, nz = shape
     wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
     wl.order = 4
-    s = P.Solver.from_workload(wl, cg_maxit=2000)
+    s = P.Solver.from_workload(wl, cg_maxit=2000, solver=solver)
     m = O.Monodomain(wl)                                   # the exact DCT-II solve
     b = np.random.default_rng(12).normal(size=wl.n_nodes)
     g = 0.3 * 0.17

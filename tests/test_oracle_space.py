@@ -308,3 +308,51 @@ def test_laplacian4_solvers_agree_and_solve(orc, shape):
         assert np.abs(x - g * m.laplacian(x) - b).max() < 1e-13 * np.abs(b).max()
     np.testing.assert_allclose(xs[0], xs[2], atol=1e-13)
     np.testing.assert_allclose(xs[1], xs[2], atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 1), (5, 4, 3)])
+def test_field_spectrum_inside_gershgorin_interval(orc, shape):
+    # The interval of the Chebyshev solves for a conductivity field: 1 is the
+    # smallest eigenvalue of I - g A (constants), and twice the largest
+    # diagonal of -A, max_p sum_faces (sigma_p + sigma_q)/h^2, bounds the rest.
+    nx, ny, nz = shape
+    h, g = 0.3, 0.2
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.h = h
+    wl.sigma_field = I.lognormal_field(nx, ny, nz, seed=11, corr=2.0)
+    m = O.Monodomain(wl, solver=O.SOLVE_CG)
+    N = nx * ny * nz
+    B = np.stack([e - g * m.conductivity(e) for e in np.eye(N)], axis=1)
+    ev = np.linalg.eigvalsh(0.5 * (B + B.T))
+    sg = wl.sigma_field.reshape(nz, ny, nx)
+    G = 0.0
+    for iz in range(nz):
+        for iy in range(ny):
+            for ix in range(nx):
+                s = 0.0
+                for dz, dy, dx in ((0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)):
+                    jz, jy, jx = iz + dz, iy + dy, ix + dx
+                    if 0 <= jz < nz and 0 <= jy < ny and 0 <= jx < nx:
+                        s += sg[iz, iy, ix] + sg[jz, jy, jx]
+                G = max(G, s / h**2)
+    assert abs(ev.min() - 1.0) < 1e-12
+    assert ev.max() <= 1 + g * G + 1e-12
+    assert ev.max() >= 1 + 0.5 * g * G
+
+
+@pytest.mark.parametrize("shape", [(7, 1, 1), (6, 5, 1), (5, 4, 3), (2, 3, 2)])
+def test_laplacian4_spectrum_interval(orc, shape):
+    # The fourth-order operator's spectrum: I - g L4 fills exactly
+    # [1, 1 + (g/(12 h^2)) sum_axes (30 + 2 cos 2t - 32 cos t)], t = pi (n-1)/n.
+    nx, ny, nz = shape
+    h, g = 0.3, 0.05
+    wl = I.hh_sheet_32().with_mesh(nx, ny, nz)
+    wl.h = h
+    wl.order = 4
+    m = O.Monodomain(wl)
+    N = nx * ny * nz
+    B = np.stack([e - g * m.laplacian(e) for e in np.eye(N)], axis=1)
+    ev = np.linalg.eigvalsh(0.5 * (B + B.T))
+    hi = 1 + g / (12 * h**2) * sum(30 + 2 * np.cos(2 * np.pi * (n - 1) / n) - 32 * np.cos(np.pi * (n - 1) / n)
+                                   for n in shape if n > 1)
+    assert abs(ev.min() - 1.0) < 1e-12 and abs(ev.max() - hi) < 1e-12 * hi
