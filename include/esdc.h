@@ -85,17 +85,19 @@ typedef struct {
                           same tol_cg; state, coefficient tables, quadrature and
                           residual stay FP64                                       */
     int    solver;     /* diffusion solves of the sweep and esdc_diffusion_solve:
-                          0 = automatic: the Chebyshev semi-iteration where an
+                          0 = automatic: the Chebyshev semi-iteration on an
                           interval holding the spectrum of the operator of
-                          esdc_diffusion_solve is known (nx a multiple of 4,
-                          second-order stencil; scalar sigma: exactly [1, 1 +
-                          (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))], the cosine
-                          modes being its eigenvectors; layered conductivity:
-                          [1, 1 + g G] with G the Gershgorin bound of -A), the
-                          Jacobi-PCG elsewhere (a conductivity field, the
-                          fourth-order stencil, other nx); with precision 1 the
-                          refinement's FP32 inner solves are then a fixed number
-                          of Chebyshev iterations (2 q^k <= 1e-5), else PCG;
+                          esdc_diffusion_solve: for the scalar sigma exactly
+                          [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))] (the
+                          cosine modes are its eigenvectors) or the fourth-order
+                          stencil's [1, 1 + (g/(12 h^2)) sum_axes (30 + 2 cos 2t
+                          - 32 cos t)], t = pi (n-1)/n; for layers and a field
+                          [1, 1 + g G] with G the Gershgorin bound of -A.  The
+                          Jacobi-PCG runs only when g is too small for the
+                          interval to have width in FP64.  With precision 1 and
+                          nx a multiple of 4 the refinement's FP32 inner solves
+                          are a fixed number of Chebyshev iterations
+                          (2 q^k <= 1e-5), else PCG;
                           1 = the (Jacobi-P)CG always;
                           2 = the DCT-II direct solve, the paper's solver (Sec. 5):
                           x = C^T diag(1/(1 - g mu)) C b with C the orthonormal
