@@ -323,9 +323,11 @@ def test_sweep_host_matches_device():
     np.testing.assert_array_equal(yh, dev)
 
 
-def test_errors_reported():
-    wl = I.hh_sheet_32().with_mesh(16, 16, 1)
-    s = P.Solver.from_workload(wl, M_max=3, cg_maxit=1, tol_cg=1e-15)
+@pytest.mark.parametrize("nx,solver", [(16, "auto"), (15, "auto"), (16, "cg"), (15, "cg")])
+def test_errors_reported(nx, solver):
+    # nx = 16 takes the quad-form kernels, nx = 15 the one-node-per-thread ones
+    wl = I.hh_sheet_32().with_mesh(nx, 16, 1)
+    s = P.Solver.from_workload(wl, M_max=3, cg_maxit=1, tol_cg=1e-15, solver=solver)
     y = to_dev(s, I.random_state(wl, seed=1))
     with pytest.raises(P.EsdcError) as e:
         s.sweep(y, 0.0, wl.dt, 4, 2)                          # M > M_max
@@ -333,14 +335,14 @@ def test_errors_reported():
     s.sweep(y, 0.0, wl.dt, 3, 2)
     rc, *_ = s.residual()
     assert rc == -3                                           # CG_NOT_CONVERGED
-    s2 = P.Solver.from_workload(wl, M_max=3)
+    s2 = P.Solver.from_workload(wl, M_max=3, solver=solver)
     y2 = I.random_state(wl, seed=2)
     y2[0, 17] = np.nan
     yd = to_dev(s2, y2)
     s2.sweep(yd, 0.0, wl.dt, 3, 2)
     rc, *_ = s2.residual()
     assert rc == -4                                           # NONFINITE
-    s3 = P.Solver.from_workload(wl, M_max=3)
+    s3 = P.Solver.from_workload(wl, M_max=3, solver=solver)
     yd = to_dev(s3, I.random_state(wl, seed=2))
     s3.sweep(yd, 0.0, wl.dt, 3, 2)
     assert s3.residual()[0] == 0                              # a fresh handle is clean
