@@ -258,8 +258,8 @@ def run_ours(args):
         ach = flops / (per_launch_ms["node"] * 1e-3) / 1e12
         roof.update({"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                      "frac": ach / FP64_PEAK_TFLOPS,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
-                                    "(an FMA-chain probe measured 1.20 TFLOP/s)",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; the "
+                                    "library's FMA probe (bench.py --form peaks) measures 1.256 TFLOP/s",
                      "traffic": NODE_DRAM_BYTES_PER_LAUNCH_MEASURED[M] * N,
                      "algorithmic_bytes": NODE_BYTES_PER_LAUNCH[M] * N,
                      "hbm_gbs": NODE_BYTES_PER_LAUNCH[M] * N / (per_launch_ms["node"] * 1e-3) / 1e9,
@@ -907,6 +907,39 @@ def run_fas_form(args):
     print(json.dumps(line), flush=True)
 
 
+def run_peaks_form(args):
+    """The FMA throughput ceilings the FP64 kernels are compared with: the
+    library's probe (independent FMA chains on every SM) in FP64 and FP32,
+    best of a few launches after a warm-up, with the SM clocks sampled."""
+    import torch
+    import paper_2405_19994_gb300 as P
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1 and rank != 0:
+        return
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    out = {}
+    for name, fp32, n in (("fp64", False, 40000), ("fp32", True, 2000000)):
+        P.esdc.fma_probe(fp32, n // 10, stream)                       # warm-up
+        best = None
+        for _ in range(max(args.warmup, 3)):
+            ms, flops = P.esdc.fma_probe(fp32, n, stream)
+            tf = flops / (ms * 1e-3) / 1e12
+            best = tf if best is None else max(best, tf)
+        out[name] = best
+    clk = clocks.stop()
+    sm = clk.get("sm_mhz") or 2070.0
+    line = {"metric": "FMA throughput ceiling", "value": out["fp64"], "unit": "TFLOP/s", "n_gpus": 1,
+            "fp64_tflops": out["fp64"], "fp32_tflops": out["fp32"],
+            "fp64_fma_per_sm_per_clk": out["fp64"] * 1e12 / 2 / (152 * sm * 1e6),
+            "fp64_derived_peak_tflops": FP64_PEAK_TFLOPS, "clocks": clk,
+            "config": {"form": "peaks", "probe": "esdc_fma_probe: 4 x 256 threads per SM, 8 FMA chains each"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_sheet_form(args):
     """Config 1: the 32x32 HH parity sheet (corner stimulus, M = 3, K = 4,
     dt = 0.025 ms, T = 4 ms, 160 steps) on the GPU, its V error at T against
@@ -988,12 +1021,14 @@ def main():
                     help="diffusion solves (headline, precision, batch and fas forms): auto (Chebyshev semi-iteration on "
                          "the exactly known spectrum of the scalar-sigma operator), cg (Jacobi-PCG) or dct "
                          "(the DCT-II direct solve; headline form only)")
-    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet"], default="plain",
+    ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet", "peaks"],
+                    default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
                          "batch: the 64-tissue ragged HH batch against looped single-tissue steps; "
                          "adjoint: forward + discrete adjoint on the 256x256 HH conductivity-field sheet; "
                          "fas: two-level Algorithm HSDC against Q^par on 16 slices of the 512x512 HH sheet; "
-                         "sheet: the 32x32 HH parity sheet's full run against the oracle")
+                         "sheet: the 32x32 HH parity sheet's full run against the oracle; "
+                         "peaks: the FP64/FP32 FMA throughput ceilings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -1013,6 +1048,8 @@ def main():
         run_fas_form(args)
     elif args.form == "sheet":
         run_sheet_form(args)
+    elif args.form == "peaks":
+        run_peaks_form(args)
     else:
         run_ours(args)
 

@@ -301,6 +301,16 @@ int esdc_ionic(esdc_handle* h, const double* y, double* fE, double* lam, double*
 int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* stream);
 
 /*
+ * FMA throughput probe (not part of the method; it measures the ceiling the
+ * FP64 kernels are compared with): 4 blocks of 256 threads per SM, each thread
+ * running 8 independent chains of n dependent FMAs in FP64 (fp32 = 0) or FP32
+ * (fp32 = 1).  *ms (host) receives the CUDA-event time of the launch on
+ * `stream`, *flops (host) the flop count (an FMA counts 2).  Synchronises.
+ * Errors: INVALID_ARG (n < 1, null outputs), NO_MEMORY, CUDA.
+ */
+int esdc_fma_probe(int fp32, int64_t n, double* ms, double* flops, void* stream);
+
+/*
  * Allocation-free diffusion solve (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, e.g. code that
  * runs inside a memory-pool or allocator callback, in a process whose device

@@ -67,6 +67,26 @@ __global__ void k_ionic(MeshDev m, ModelDev mp, const double* y, double* fE, dou
     }
 }
 
+// FMA throughput probe: ESDC_FMA_CHAINS independent dependent-FMA chains per
+// thread, n FMAs each; the result is stored only if it hits an impossible
+// value, so the chains stay live without memory traffic.
+#define ESDC_FMA_CHAINS 8
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(double* sink, int64_t n, T a, T b)
+{
+    T x[ESDC_FMA_CHAINS];
+#pragma unroll
+    for (int c = 0; c < ESDC_FMA_CHAINS; ++c) x[c] = (T)(threadIdx.x + 1) * (T)(c + 1) * (T)1e-3;
+    for (int64_t k = 0; k < n; ++k) {
+#pragma unroll
+        for (int c = 0; c < ESDC_FMA_CHAINS; ++c) x[c] = fma(x[c], a, b);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int c = 0; c < ESDC_FMA_CHAINS; ++c) sum += x[c];
+    if (sum == (T)-1.0) *sink = (double)sum;
+}
+
 __global__ void k_math(const double* x, int64_t n, double* ex, double* rc)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -687,6 +707,38 @@ int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* st
     if (nb > 4096) nb = 4096;
     k_math<<<(int)nb, 256, 0, (cudaStream_t)stream>>>(x, n, ex, rc);
     return cudaGetLastError() == cudaSuccess ? ESDC_OK : ESDC_ERR_CUDA;
+}
+
+int esdc_fma_probe(int fp32, int64_t n, double* ms, double* flops, void* stream)
+{
+    if (!ms || !flops || n < 1 || (fp32 != 0 && fp32 != 1)) return ESDC_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ESDC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = 256, per_sm = 4, blocks = sms * per_sm;
+    double* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(double)) != cudaSuccess) return ESDC_ERR_NO_MEMORY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = ESDC_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = ESDC_ERR_CUDA;
+    if (rc == ESDC_OK) {
+        cudaEventRecord(e0, s);
+        if (fp32) k_fma_probe<float><<<blocks, threads, 0, s>>>(sink, n, 0.999999f, 1e-6f);
+        else k_fma_probe<double><<<blocks, threads, 0, s>>>(sink, n, 0.999999, 1e-6);
+        cudaEventRecord(e1, s);
+        float t = 0.0f;
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            rc = ESDC_ERR_CUDA;
+        *ms = t;
+        *flops = 2.0 * ESDC_FMA_CHAINS * (double)n * (double)blocks * threads;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    return rc;
 }
 
 int esdc_profile(esdc_handle* h, int enable)

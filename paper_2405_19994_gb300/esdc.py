@@ -75,6 +75,7 @@ def lib() -> C.CDLL:
             "esdc_diffusion_solve": (C.c_int, [_VP, _D, _VP, _VP, C.POINTER(C.c_int), _VP]),
             "esdc_ionic": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
             "esdc_math_check": (C.c_int, [_VP, _I64, _VP, _VP, _VP]),
+            "esdc_fma_probe": (C.c_int, [C.c_int, _I64, C.POINTER(_D), C.POINTER(_D), _VP]),
             "esdc_diffusion_solve_static": (C.c_int, [C.POINTER(esdc_mesh), _D, _VP, _VP, _D, C.c_int, C.c_int,
                                                       C.POINTER(C.c_int), _VP]),
             "esdc_set_params": (C.c_int, [_VP, C.POINTER(_D), C.c_int]),
@@ -127,6 +128,15 @@ def _ptr(t) -> int:
     import torch
     assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
     return t.data_ptr()
+
+
+def fma_probe(fp32: bool, n: int, stream=None):
+    """FMA throughput of the device (esdc_fma_probe): returns (ms, flops)."""
+    ms, fl = C.c_double(), C.c_double()
+    rc = lib().esdc_fma_probe(int(fp32), n, C.byref(ms), C.byref(fl), _stream(stream))
+    if rc != ESDC_OK:
+        raise EsdcError(rc, "esdc_fma_probe failed")
+    return ms.value, fl.value
 
 
 def math_check(x, stream=None):

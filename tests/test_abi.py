@@ -150,6 +150,10 @@ def test_later_entry_points_reject_invalid_arguments_without_gpu(L):
     ms = (C.c_int * 2)(3, 2)
     assert L.esdc_hsdc(None, None, ms, 2, None, None, 0.0, 0.1, 1, None) == -1
     assert L.esdc_hsdc(nolev, None, ms, 2, None, None, 0.0, 0.1, 1, None) == -1
+    d1, d2 = C.c_double(), C.c_double()
+    assert L.esdc_fma_probe(2, 10, C.byref(d1), C.byref(d2), None) == -1
+    assert L.esdc_fma_probe(0, 0, C.byref(d1), C.byref(d2), None) == -1
+    assert L.esdc_fma_probe(0, 10, None, C.byref(d2), None) == -1
     assert L.esdc_batch_set_shape(None, 1, 512, 1) == -1
     assert L.esdc_batch_tune(None, None, -75.0, 0.0, 0.1, 3, 4, 1, None) == -1
     assert L.esdc_batch_graph_active(None) == 0
