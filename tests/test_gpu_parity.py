@@ -603,3 +603,13 @@ def test_order4_combinations_rejected():
     with pytest.raises(P.EsdcError) as e:
         s3.set_conductivity_field(np.full(wl.n_nodes, 0.2))
     assert e.value.code == -6
+
+
+def test_fma_probe_counts_and_rates():
+    from paper_2405_19994_gb300 import esdc as E
+    ms64, fl64 = E.fma_probe(False, 2000)
+    ms32, fl32 = E.fma_probe(True, 2000)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert fl64 == fl32 == 2 * 8 * 2000 * sms * 4 * 256
+    assert ms64 > 0 and ms32 > 0
+    assert fl32 / ms32 > 8 * fl64 / ms64          # FP32 issues many times faster than FP64 on this part
