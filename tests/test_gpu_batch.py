@@ -388,3 +388,36 @@ def test_hsdc_rejects_bad_levels():
         assert e.value.code == -1
     for b in coarse + [fine, mid]:
         b.close()
+
+
+@pytest.mark.slow
+def test_full_batch_in_bench_configuration_matches_oracle():
+    """The 64-tissue batch of the batching form at full size (5.1M nodes), in the
+    launch configuration the bench ends up with (recorded graph, 4 node waves,
+    256-thread solve blocks, 2 per SM): after 3 steps from rest, the three
+    smallest tissues against the oracle run on each alone, element by element."""
+    wls = I.hh_batch()
+    w0 = wls[0]
+    b = P.Batch.from_workloads(wls, M_max=w0.M)
+    b.set_shape(4, 256, 2)
+    b.set_graph(True)
+    y = b.new_state()
+    b.init_state(y, w0.V0)
+    t = 0.0
+    for _ in range(3):
+        b.sweep(y, t, w0.dt, w0.M, w0.K)
+        t += w0.dt
+    assert b.residual()[0] == 0
+    assert b.graph_active()
+    torch.cuda.synchronize()
+    for k in sorted(range(len(wls)), key=lambda j: wls[j].n_nodes)[:3]:
+        w = wls[k]
+        m = O.Monodomain(w)
+        yo = m.init_state()
+        to = 0.0
+        for _ in range(3):
+            yo, _, _, _ = m.step(yo, to, w.dt, w.M, w.K)
+            to += w.dt
+        got = b.tissue(y, k).cpu().numpy()
+        assert np.abs(got - yo).max() < 1e-12 * max(1.0, np.abs(yo).max()), (k, w.name)
+    b.close()
