@@ -456,6 +456,34 @@ def test_layered_one_step_matches_oracle(precision, tol):
     assert np.abs(got[1:] - want[1:]).max() <= tol
 
 
+@pytest.fixture(scope="module")
+def aniso_full_step():
+    """The oracle's step of the full precision-form workload (256x256x64, 4.2M
+    nodes) from rest at t = 0, with the planar stimulus on (computed once)."""
+    wl = I.hh_aniso_slab()
+    m = O.Monodomain(wl, cg_tol=1e-15)
+    y0 = m.init_state()
+    want, _, _, _ = m.step(y0, 0.0, wl.dt, wl.M, wl.K)
+    return wl, y0, want
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+def test_precision_workload_full_size_one_step(aniso_full_step, precision, tol):
+    """The precision-form workload at full size in the configuration the bench
+    times (default solver: the layered Chebyshev solve, or the Chebyshev
+    refinement), one step, every element against the oracle."""
+    wl, y0, want = aniso_full_step
+    s = P.Solver.from_workload(wl, M_max=wl.M, precision=precision)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.0, wl.dt, wl.M, wl.K)
+    assert s.residual()[0] == 0
+    got = from_dev(s, yd)
+    assert np.abs(got[0] - want[0]).max() <= tol * np.abs(want[0]).max()
+    assert np.abs(got[1:] - want[1:]).max() <= tol
+    s.close()
+
+
 # ---------------------------------------------------------------- full workloads
 
 def test_hh_sheet_full_run_matches_oracle():
