@@ -484,6 +484,27 @@ def test_precision_workload_full_size_one_step(aniso_full_step, precision, tol):
     s.close()
 
 
+@pytest.mark.slow
+def test_field_sheet_full_size_steps():
+    """The differentiation form's tissue at full size (256x256, log-normal field,
+    the default solver: the field Chebyshev solve), 4 steps from rest with the
+    corner stimulus on, every element against the oracle."""
+    wl = I.hh_field_sheet()
+    m = O.Monodomain(wl, cg_tol=1e-15)
+    y = m.init_state()
+    s = P.Solver.from_workload(wl, M_max=wl.M)
+    yd = to_dev(s, y)
+    t = 0.0
+    for _ in range(4):
+        s.sweep(yd, t, wl.dt, wl.M, wl.K)
+        y, _, _, _ = m.step(y, t, wl.dt, wl.M, wl.K)
+        t += wl.dt
+    assert s.residual()[0] == 0
+    got = from_dev(s, yd)
+    assert np.abs(got[0] - y[0]).max() <= 1e-11 * np.abs(y[0]).max()
+    assert np.abs(got[1:] - y[1:]).max() <= 1e-11
+
+
 # ---------------------------------------------------------------- full workloads
 
 def test_hh_sheet_full_run_matches_oracle():
