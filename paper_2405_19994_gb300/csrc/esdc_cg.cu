@@ -1,8 +1,11 @@
-// Matrix-free Jacobi-preconditioned conjugate gradients for the implicit
-// diffusion rows of the HSDC preconditioner (eq. def_P: the f_I(y_{n,i}) term
-// is taken implicitly, so each node solves (I - g L) V_i = rhs with
-// g = dt d_i sigma/(chi C_m)).  The paper solves these systems with DCT-II
-// (Sec. 5); this library uses CG on the 3/5/7-point Neumann stencil.
+// Matrix-free iterative solves of the implicit diffusion rows of the HSDC
+// preconditioner (eq. def_P: the f_I(y_{n,i}) term is taken implicitly, so each
+// node solves (I - g L) V_i = rhs with g = dt d_i sigma/(chi C_m)), one node per
+// thread: Jacobi-preconditioned conjugate gradients (k_cg), the Chebyshev
+// semi-iteration on a known spectrum interval (k_cheb), and the precision
+// form's refinement (k_cg_mixed); esdc_cg_launch also dispatches to the quad
+// form (esdc_cg4.cu) and the DCT-II solve (esdc_dct.cu).  The paper solves these
+// systems with DCT-II (Sec. 5).
 //
 // One cooperative launch runs the whole solve: the blocks stay resident and
 // meet at a grid barrier (bounded spin; on timeout a flag is raised and every

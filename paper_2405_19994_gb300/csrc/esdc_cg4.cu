@@ -1,5 +1,8 @@
-// Quad form of the persistent CG solves of the implicit diffusion rows
-// (eq. def_P: (I - g A) V_i = rhs at every collocation node).
+// Quad form of the persistent solves of the implicit diffusion rows
+// (eq. def_P: (I - g A) V_i = rhs at every collocation node): the Jacobi-PCG
+// (k_cg4), the Chebyshev semi-iteration (k_cheb4, the default), and the
+// precision form's refinement with CG or Chebyshev inner solves (k_cg4_mixed,
+// k_cheb4_mixed).
 //
 // Each thread owns runs of four x-consecutive nodes ("quads"), so every vector
 // access is a 16-byte (FP32) or 2 x 16-byte (FP64) load or store and a thread
