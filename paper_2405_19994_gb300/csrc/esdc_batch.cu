@@ -7,7 +7,7 @@
 // tile of 512 nodes belongs to exactly one tissue.  Node kernels find a node's
 // tissue from its tile and skip the padding at the end of each tissue.
 //
-// Determinism.  Every dot product of the CG is reduced first over one tile, in
+// Determinism.  Every dot product of the solves is reduced first over one tile, in
 // an order fixed by the tile alone (lane l of a warp adds nodes l, l+32, ...,
 // then a fixed shuffle tree), then over the tiles of the tissue in tile order.
 // The result of every tissue is therefore independent of which other tissues
@@ -16,9 +16,11 @@
 // bit for bit the results of the same tissues stepped one at a time, and the
 // launch-shape autotuner may choose any configuration without changing a bit.
 //
-// CG.  One cooperative launch solves all tissues' systems (I - dt d_i D_b L_b) x = b
-// together: the grid meets at the same barriers, each tissue has its own alpha,
-// beta and stop test, and a tissue that has converged drops out of the work.
+// Solves.  One cooperative launch solves all tissues' systems (I - dt d_i D_b L_b) x = b
+// together: the Chebyshev semi-iteration (k_chebb, the default), each tissue on
+// its own exactly known spectrum, or the CG (k_cgb).  The grid meets at the same
+// barriers, each tissue has its own coefficients and stop test, and a tissue
+// that has converged drops out of the work.
 // Each block owns a contiguous range of tiles, hence few tissues; it reduces
 // only their totals.  The block holding a tissue's first tile records its
 // outcome, and the loop ends after the barrier at which every tissue has
