@@ -783,7 +783,9 @@ def run_adjoint_form(args):
         "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
         "forward_node_updates_per_s": nodes * nsteps / (ms_f * 1e-3),
         "loss": loss, "dL_dgNa": float(gpar[0]), "dL_dgK": float(gpar[1]),
-        "grad_check_field": {"adjoint": ad, "central_difference": fd, "rel_err": abs(ad - fd) / abs(fd), "eps": eps},
+        "grad_check_field": {"adjoint": ad, "central_difference": fd,
+                             "rel_err": abs(ad - fd) / abs(fd) if fd != 0.0 else None,
+                             "abs_err": abs(ad - fd), "eps": eps},
         "checkpoint_bytes": int(ck.numel() * 8),
         "cpu_baseline": cpu,
         "clocks": clk,
