@@ -584,7 +584,7 @@ int esdc_cg_blocks(const MeshDev& mesh, int threads)
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg, threads, 0) != cudaSuccess) return 0;
-    long long want = ((long long)mesh.N + (long long)threads * 2 - 1) / ((long long)threads * 2);
+    long long want = ((long long)mesh.N + threads - 1) / threads;     // a node per thread: every SM busy sooner
     long long cap = (long long)sms * (per_sm < 1 ? per_sm : 1);   // one block per SM
     if (want < 1) want = 1;
     return (int)(want < cap ? want : cap);
