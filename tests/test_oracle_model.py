@@ -57,8 +57,8 @@ def test_hh_removable_singularities(orc):
 
 def test_gating_form_alpha_beta(orc):
     # eq. monodomain_g_lambda: Lambda_g = -(alpha+beta), w_inf = alpha/(alpha+beta);
-    # hence Lambda_g (w - w_inf) = alpha (1 - w) - beta w for any w (eq. monodomain_g).
-    # Check the identity by recovering alpha = -Lambda w_inf, beta = -Lambda (1 - w_inf).
+    # hence Lambda_g (w - w_inf) = alpha (1 - w) - beta w for any w (eq. monodomain_g),
+    # with alpha = -Lambda w_inf > 0 and beta = -Lambda (1 - w_inf) > 0.
     p = I.hh1952_params()
     for V in np.linspace(-100, 60, 17):
         u = np.array([V, 0.2, 0.7, 0.4])
@@ -66,10 +66,49 @@ def test_gating_form_alpha_beta(orc):
         alpha = -lam[1:] * yinf[1:]
         beta = -lam[1:] * (1 - yinf[1:])
         assert np.all(alpha > 0) and np.all(beta > 0)
-        v = V + 75.0
-        np.testing.assert_allclose(beta[0], 4.0 * np.exp(-v / 18.0), rtol=1e-10)   # recovery through 1 - w_inf cancels digits
-        np.testing.assert_allclose(alpha[1], 0.07 * np.exp(-v / 20.0), rtol=1e-10)   # recovery through 1 - w_inf cancels digits
-        np.testing.assert_allclose(beta[2], 0.125 * np.exp(-v / 80.0), rtol=1e-10)   # recovery through 1 - w_inf cancels digits
+        w = u[1:]
+        np.testing.assert_allclose(lam[1:] * (w - yinf[1:]), alpha * (1 - w) - beta * w, rtol=1e-12, atol=1e-15)
+
+
+def _hh_rate_table():
+    rows = []
+    for line in open(os.path.join(GOLD, "hh1952_rates.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append([float(x) for x in line.split()])
+    return np.array(rows)
+
+
+def test_hh_rates_match_published_equations(orc):
+    # All six rate constants of Hodgkin & Huxley (1952), eqs. (12), (13), (20),
+    # (21), (23), (24), at nine depolarisations from -30 to +100 mV (golden
+    # table, evaluated in the 1952 paper's own sign convention).  They are
+    # recovered from the oracle's model output: alpha = -Lambda w_inf,
+    # beta = -Lambda (1 - w_inf), for m, h, n in that order.  A slip in the
+    # sign or offset of any rate's voltage argument changes every row but one.
+    tab = _hh_rate_table()
+    assert tab.shape == (9, 7)
+    p = I.hh1952_params()
+    for v, am, bm, ah, bh, an, bn in tab:
+        u = np.array([-75.0 + v, 0.3, 0.4, 0.5])
+        _, lam, yinf = O.ionic_point(I.MODEL_HH1952, p, u)
+        alpha = -lam[1:] * yinf[1:]
+        beta = -lam[1:] * (1 - yinf[1:])
+        np.testing.assert_allclose(alpha, [am, ah, an], rtol=1e-10, err_msg=f"alpha at v={v}")
+        np.testing.assert_allclose(beta, [bm, bh, bn], rtol=1e-10, err_msg=f"beta at v={v}")
+
+
+def test_hh_steady_states_and_time_constants(orc):
+    # w_inf = alpha/(alpha + beta) and -1/Lambda = 1/(alpha + beta) (the 1952
+    # paper's n_inf, tau_n and their m, h analogues, eqs. (8)-(9) and their
+    # sodium counterparts) at the tabulated depolarisations.
+    tab = _hh_rate_table()
+    p = I.hh1952_params()
+    for v, am, bm, ah, bh, an, bn in tab:
+        _, lam, yinf = O.ionic_point(I.MODEL_HH1952, p, np.array([-75.0 + v, 0.3, 0.4, 0.5]))
+        a = np.array([am, ah, an])
+        b = np.array([bm, bh, bn])
+        np.testing.assert_allclose(yinf[1:], a / (a + b), rtol=1e-12)
+        np.testing.assert_allclose(-lam[1:], a + b, rtol=1e-12)
 
 
 def test_syn19_shape_and_ranges(orc):
