@@ -85,7 +85,10 @@ typedef struct {
                           same tol_cg; state, coefficient tables, quadrature and
                           residual stay FP64                                       */
     int    solver;     /* diffusion solves of the sweep and esdc_diffusion_solve:
-                          0 = automatic: the Chebyshev semi-iteration on an
+                          0 = automatic: with precision 0 and the scalar sigma
+                          the DCT-II direct solve of 2 (exact; the handle holds
+                          its tables from esdc_create on), otherwise as 3;
+                          3 = the Chebyshev semi-iteration on an
                           interval holding the spectrum of the operator of
                           esdc_diffusion_solve: for the scalar sigma exactly
                           [1, 1 + (g/h^2) sum_axes 4 sin^2(pi (n-1)/(2n))] (the
@@ -101,15 +104,21 @@ typedef struct {
                           1 = the (Jacobi-P)CG always;
                           2 = the DCT-II direct solve, the paper's solver (Sec. 5):
                           x = C^T diag(1/(1 - g mu)) C b with C the orthonormal
-                          3D DCT-II (one dense product per axis, cuBLAS DGEMM)
-                          and mu the eigenvalues of the second- or fourth-order
-                          stencil; exact, no iteration (iters reports 1).
+                          3D DCT-II and mu the eigenvalues of the second- or
+                          fourth-order stencil, computed by this library's own
+                          kernels: a fast transform (FFT of pairs of lines,
+                          O(n log n)) along axes of power-of-two length, a dense
+                          product along other axes, and for the second-order
+                          stencil a direct tridiagonal solve along z instead of
+                          the z transform; exact, no iteration (iters reports 1).
                           Scalar sigma and precision 0 only (esdc_create returns
                           ESDC_ERR_UNSUPPORTED with precision 1; the conductivity
                           setters return it for layers or a field); holds the
-                          axes' DCT matrices (nx^2 + ny^2 + nz^2 doubles).
-                          Batches take 0 or 1.
-                          0 and 1 stop at the same ||r|| <= tol_cg ||b||.  The
+                          axes' tables (dense axes: 2 n^2 doubles) and the
+                          z-solve factors of up to M_max values of g (16 bytes
+                          per node each).
+                          Batches take 0, 1 or 3 (0 and 3 alike: Chebyshev).
+                          1 and 3 stop at the same ||r|| <= tol_cg ||b||.  The
                           paper solves these systems with the DCT-II.            */
 } esdc_options;
 

@@ -62,10 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = LIB + f".tmp{os.getpid()}"
-    # cuBLAS (the DGEMMs of the DCT-II solve) from the toolkit that compiled the library
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-L" + cuda_lib, "-lcublas",
-                    "-Xlinker", "-rpath," + cuda_lib], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
     return LIB
 

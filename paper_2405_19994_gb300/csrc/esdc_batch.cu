@@ -1053,6 +1053,7 @@ int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, doubl
     if (opt) o = *opt;
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
     if (o.precision != 0) return ESDC_ERR_UNSUPPORTED;            // batches run the FP64 path
+    if (o.solver == 3) o.solver = 0;                               // batches: Chebyshev where exact
     if (o.solver != 0 && o.solver != 1) return ESDC_ERR_INVALID_ARG;
 
     esdc_batch* b = new (std::nothrow) esdc_batch();

@@ -594,10 +594,13 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
                            double* x, double tol, int maxit, int precond, int solver, int* iter_log,
                            int* flags, cudaStream_t s)
 {
-    if (solver == 2) {
+    // the DCT-II solve: requested (2), or automatic (0) on the scalar sigma
+    // where the handle holds its tables
+    if (solver == 2 || (solver == 0 && w.dct && !mesh.lay && !mesh.sig)) {
         if (!w.dct) return cudaErrorInvalidValue;
         return esdc_dct_launch(mesh, w, g, b, x, iter_log, flags, s);
     }
+    if (solver == 3) solver = 0;                 // the iterative choice of the automatic mode
     if (esdc_cg4_eligible(mesh, b, x)) {
         CgArgsHost hq{mesh, w, g, b, x, tol, maxit, precond, iter_log, flags};
         if (solver == 0 && g > 0.0 && esdc_cheb_eligible(mesh, b, x)) return esdc_cheb_launch(hq, s);
@@ -636,6 +639,7 @@ cudaError_t esdc_cg_mixed_launch(const MeshDev& mesh, const CgWork& w, double g,
                                  double tol, int maxit, int precond, int solver, int* iter_log, int* flags,
                                  cudaStream_t s)
 {
+    if (solver == 3) solver = 0;
     if (esdc_cg4_eligible(mesh, b, x)) {
         CgArgsHost hq{mesh, w, g, b, x, tol, maxit, precond, iter_log, flags};
         if (solver == 0 && g > 0.0 && esdc_cheb_eligible(mesh, b, x)) return esdc_cheb_mixed_launch(hq, s);

@@ -101,14 +101,30 @@ struct TissueDev {
     StimDev st;
 };
 
-// Direct DCT-II solve (options.solver = 2): orthonormal DCT-II matrices of the
-// axes with more than one cell (column-major, [n][n]), eigenvalues of the 1D
-// difference operator per mode (1/h^2 included), and the cuBLAS handle of the
-// axis transforms.
+// Direct DCT-II solve (options.solver = 2), per axis: the FFT tables (powers
+// of two: twiddles e^{-2 pi i k/n}, and (cos, sin)(pi k/(2n)) whole and halved
+// for the inverse and forward post-processing) or the two dense cosine
+// matrices (other lengths).
+struct DctAxisDev {
+    int n = 1, logn = -1;
+    const double2* tw = nullptr;
+    const double2* cs = nullptr;
+    const double2* csh = nullptr;
+    const double* fwd = nullptr;
+    const double* inv = nullptr;
+};
+#define ESDC_DCT_SLOTS ESDC_MMAX
+// The axes' tables, the eigenvalues of the 1D difference operators per mode
+// (1/h^2 included), and the factor tables of the z-direction tridiagonal
+// solves of the second-order stencil: per slot [2][N] (A then C) for the
+// value gkey of g (a slot is refilled, round robin, when a new g comes).
 struct DctDev {
-    double *cx = nullptr, *cy = nullptr, *cz = nullptr;
+    DctAxisDev ax, ay, az;
     double *ex = nullptr, *ey = nullptr, *ez = nullptr;
-    void* blas = nullptr;
+    double* ztab = nullptr;
+    int nslot = 0, next_slot = 0;
+    double gkey[ESDC_DCT_SLOTS] = {};
+    bool used[ESDC_DCT_SLOTS] = {};
 };
 
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
@@ -120,13 +136,18 @@ struct CgWork {
     int* status;                    // [2]: iterations of the last solve, flag bits
     int max_blocks;
     int threads;
-    const DctDev* dct = nullptr;    // set when options.solver = 2
+    DctDev* dct = nullptr;          // set when options.solver = 2
 };
 
-cudaError_t esdc_dct_create(const MeshDev& m, DctDev* d);
+// Whether the DCT solve takes this mesh (every axis length does, up to the
+// shared-memory size of a dense tile).
+bool esdc_dct_supported(const MeshDev& m);
+// Tables for the mesh, with nslot (1..ESDC_DCT_SLOTS) cached values of g.
+cudaError_t esdc_dct_create(const MeshDev& m, int nslot, DctDev* d);
 cudaError_t esdc_dct_set_order(const MeshDev& m, DctDev* d);   // eigenvalues for m.order
 void esdc_dct_destroy(DctDev* d);
-// x = (I - g L)^{-1} b by the DCT-II (scalar sigma); uses w.r and w.p as work vectors.
+// x = (I - g L)^{-1} b by the DCT-II (scalar sigma); uses w.r and w.p as work vectors
+// (b may alias x, not w.r or w.p).
 cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const double* b, double* x,
                             int* iter_log, int* flags, cudaStream_t s);
 

@@ -273,7 +273,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     if (opt) o = *opt;
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
     if (o.precision != 0 && o.precision != 1) return ESDC_ERR_INVALID_ARG;
-    if (o.solver < 0 || o.solver > 2) return ESDC_ERR_INVALID_ARG;
+    if (o.solver < 0 || o.solver > 3) return ESDC_ERR_INVALID_ARG;
     if (o.solver == 2 && o.precision != 0) return ESDC_ERR_UNSUPPORTED;     // the DCT solve is FP64
 
     esdc_handle* h = new (std::nothrow) esdc_handle();
@@ -336,8 +336,12 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     cudaMemset(h->cg.status, 0, sizeof(int) * 2);
     cudaMemset(h->flags, 0, sizeof(int));
     cudaMemset(h->cg_log, 0, sizeof(int) * h->cg_log_len);
-    if (o.solver == 2) {
-        const cudaError_t e = esdc_dct_create(h->mesh, &h->dct);
+    // the DCT-II tables: for the DCT solve itself (2) and for the automatic
+    // choice on the FP64 path (0), which takes it while sigma is scalar
+    const bool dct_auto = o.solver == 0 && o.precision == 0 && esdc_dct_supported(h->mesh);
+    if (o.solver == 2 || dct_auto) {
+        if (!esdc_dct_supported(h->mesh)) return fail(ESDC_ERR_UNSUPPORTED);
+        const cudaError_t e = esdc_dct_create(h->mesh, o.M_max, &h->dct);
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? ESDC_ERR_NO_MEMORY : ESDC_ERR_CUDA);
         h->cg.dct = &h->dct;
     }

@@ -167,9 +167,9 @@ class Solver:
         if precision not in ("fp64", "mixed"):
             raise ValueError("precision must be 'fp64' or 'mixed'")
         opt.precision = 1 if precision == "mixed" else 0
-        if solver not in ("auto", "cg", "dct"):
-            raise ValueError("solver must be 'auto', 'cg' or 'dct'")
-        opt.solver = {"auto": 0, "cg": 1, "dct": 2}[solver]
+        if solver not in ("auto", "cg", "dct", "cheb"):
+            raise ValueError("solver must be 'auto', 'cg', 'dct' or 'cheb'")
+        opt.solver = {"auto": 0, "cg": 1, "dct": 2, "cheb": 3}[solver]
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_create(C.byref(mesh), sigma, chi, Cm, model, p.ctypes.data_as(C.POINTER(_D)), len(p),
@@ -361,9 +361,9 @@ class Batch:
         opt = esdc_options()
         L.esdc_default_options(C.byref(opt))
         opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond = M_max, tol_cg, cg_maxit, int(precond)
-        if solver not in ("auto", "cg"):
-            raise ValueError("solver must be 'auto' or 'cg'")
-        opt.solver = 0 if solver == "auto" else 1
+        if solver not in ("auto", "cg", "cheb"):
+            raise ValueError("solver must be 'auto', 'cg' or 'cheb'")
+        opt.solver = 1 if solver == "cg" else 0
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_batch_create(n, arr, sig.ctypes.data_as(C.POINTER(_D)), chi, Cm, model,

@@ -67,7 +67,7 @@ def test_invalid_arguments_rejected_without_gpu(L):
     opt.precision = 2
     assert create(ok, optp=C.byref(opt)) == -1
     opt.precision = 0
-    opt.solver = 3
+    opt.solver = 4
     assert create(ok, optp=C.byref(opt)) == -1
     opt.solver = 2; opt.precision = 1                           # the DCT solve is FP64
     assert create(ok, optp=C.byref(opt)) == -6
@@ -121,7 +121,7 @@ def test_batch_invalid_arguments_rejected_without_gpu(L):
     opt.precision = 1
     assert create(optp=C.byref(opt)) == -6                     # batches run the FP64 path
     opt.precision = 0
-    for bad_solver in (2, 3):                                  # batches: automatic or CG
+    for bad_solver in (2, 4):                                  # batches: automatic (0, 3) or CG
         opt.solver = bad_solver
         assert create(optp=C.byref(opt)) == -1
     assert L.esdc_batch_sweep(None, None, None, 0.1, 3, 4, None) == -1
