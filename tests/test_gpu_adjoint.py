@@ -156,3 +156,71 @@ def test_autograd_function_matches_adjoint(case):
     np.testing.assert_allclose(sig.grad.numpy(), gsig, rtol=1e-12, atol=1e-18)
     assert abs(gna.grad.item() - gpar[0]) <= 1e-12 * abs(gpar[0])
     assert abs(gk.grad.item() - gpar[1]) <= 1e-12 * abs(gpar[1])
+
+
+# ---------------------------------------------------------------- against the oracle's discrete adjoint
+
+def _gpu_and_oracle_gradients(n, nsteps, nsens, seed):
+    from oracle.adjoint import HHFieldAdjoint
+    wl = I.hh_field_sheet(n)
+    rng = np.random.default_rng(seed)
+    sens = np.sort(rng.choice(wl.n_nodes, size=nsens, replace=False)).astype(np.int32)
+    s = P.Solver.from_workload(wl, M_max=wl.M)
+    y0 = s.new_state()
+    s.init_state(y0, wl.V0)
+    sd = torch.from_numpy(sens).cuda()
+
+    def forward(sig, params, want_ckpt):
+        s.set_params(params)
+        s.set_conductivity_field(sig)
+        y = y0.clone()
+        tr = torch.empty((nsteps, nsens), dtype=torch.float64, device="cuda")
+        ck = torch.empty((nsteps, s.n_state, s.ld), dtype=torch.float64, device="cuda")
+        s.adjoint_forward(y, 0.0, wl.dt, wl.M, wl.K, nsteps, sd, tr, ck)
+        assert s.residual()[0] == 0
+        torch.cuda.synchronize()
+        return tr.cpu().numpy(), ck
+
+    p = wl.params.copy()
+    p[0] *= 1.05
+    p[1] *= 0.95
+    target, _ = forward(I.lognormal_field(n, n, 1, seed=seed + 1), p, False)
+    tr, ck = forward(wl.sigma_field, wl.params, True)
+    dtr = tr - target
+    gsig, gpar, gy0 = s.adjoint_backward(ck, 0.0, wl.dt, wl.M, wl.K, nsteps, sd, torch.from_numpy(dtr).cuda(),
+                                         want_y0=True)
+    torch.cuda.synchronize()
+    gpu = (gsig.cpu().numpy(), float(gpar[0]), float(gpar[1]), gy0[:, :wl.n_nodes].cpu().numpy())
+    adj = HHFieldAdjoint(O.Monodomain(wl, cg_tol=1e-15))
+    y0c = y0[:, :wl.n_nodes].cpu().numpy()
+    tr_o, _ = adj.traces(y0c, 0.0, wl.dt, wl.M, wl.K, nsteps, sens)
+    assert np.abs(tr - tr_o).max() < 1e-10 * np.abs(tr_o).max()
+    orc = adj.sensor_gradients(y0c, 0.0, wl.dt, wl.M, wl.K, nsteps, sens, dtr)
+    return gpu, orc
+
+
+def _compare(gpu, orc, tol):
+    (gs, gna, gk, gy), (os_, ona, ok, oy) = gpu, orc
+    assert np.abs(os_).max() > 0 and ona != 0 and ok != 0
+    # the conductivity field, node by node (max-norm relative)
+    assert np.abs(gs - os_).max() <= tol * np.abs(os_).max(), np.abs(gs - os_).max() / np.abs(os_).max()
+    assert abs(gna - ona) <= tol * abs(ona), (gna, ona)
+    assert abs(gk - ok) <= tol * abs(ok), (gk, ok)
+    for s in range(oy.shape[0]):                 # every state of every node
+        assert np.abs(gy[s] - oy[s]).max() <= tol * np.abs(oy[s]).max(), (s, np.abs(gy[s] - oy[s]).max())
+
+
+def test_adjoint_matches_oracle_adjoint_16x16():
+    """The GPU adjoint (esdc_adjoint_backward) against the oracle's discrete
+    adjoint on the 16x16 field sheet over 30 steps: every component of
+    dL/dsigma and dL/dy0, and dL/dg_Na, dL/dg_K, within 1e-9 (max-norm
+    relative).  Both differentiate the same step map; their forward solves stop
+    at relative residuals of 1e-14 (GPU) and 1e-15 (oracle)."""
+    gpu, orc = _gpu_and_oracle_gradients(16, 30, 8, seed=41)
+    _compare(gpu, orc, 1e-9)
+
+
+@pytest.mark.slow
+def test_adjoint_matches_oracle_adjoint_32x32_100_steps():
+    gpu, orc = _gpu_and_oracle_gradients(32, 100, 16, seed=43)
+    _compare(gpu, orc, 1e-9)
