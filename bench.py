@@ -10,9 +10,11 @@ ionic/quadrature kernel + CG diffusion solve each) and the collocation residual.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line.  ``value`` is node-updates/s (one mesh node advanced by
-one dt), device-timed with CUDA events over K steps after W warm-up steps from
-rest (t = 0 is the stimulus onset, so the timed window follows the stimulus).
-``--impl reference`` times the FP64 CPU oracle on this host instead.
+one dt), device-timed with CUDA events over K steps.  Before them the run goes,
+untimed, from rest through the stimulus (t < 1 ms) and --pre-steps (100) steps
+after it, then W warm-up steps, so the timed window sees a propagating wave
+(config.window_ms).  ``--impl reference`` times the FP64 CPU oracle on this
+host instead.
 """
 from __future__ import annotations
 
@@ -50,6 +52,40 @@ CG_BYTES_PER_NODE_ITER = 96
 CG_BYTES_PER_NODE_SETUP = 64
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 issue peak: 152 SMs x 2 FP64 instructions (thread level) per clock x 2.07 GHz.
+FP64_ISSUE_PEAK = 152 * 2 * 2.07e9
+
+# Work per mesh node of each kernel class of one step (M = 4, SYN19): FP64
+# instructions (thread-level DFMA + DADD + DMUL, counted by ncu on the
+# 128x128x16 slab, profiles/classes_syn19_slab_128x128x16.md) and the bytes the
+# method streams.  Set-up: the coefficient tables and one ionic evaluation per
+# step; node: per sweep (M + 1 launches); DCT solve: four transform passes
+# and the tridiagonal z solve; Chebyshev and CG: per iteration; residual: per
+# step.
+CLASS_FP64_OPS = {"setup": 3187.2, "node_sweep": 2542.8, "dct_solve": 56.3, "cheb_iter": 12.2, "cg_iter": 15.0,
+                  "residual": 703.0}
+CLASS_BYTES = {"setup": 3256.0, "node_sweep": 7464.0, "dct_solve": 120.0, "cheb_iter": 48.0, "cg_iter": 96.0,
+               "residual": 2904.0}
+
+
+def class_work(solver_kind: str, K: int, it_mean: float, M: int = 4) -> dict:
+    """(FP64 instructions, bytes) per node and step of each kernel class."""
+    solves = M * K
+    if solver_kind == "dct":
+        sv = (CLASS_FP64_OPS["dct_solve"] * solves, CLASS_BYTES["dct_solve"] * solves)
+    else:
+        sv = (CLASS_FP64_OPS["cheb_iter"] * it_mean * solves, CLASS_BYTES["cheb_iter"] * it_mean * solves)
+    return {"setup": (CLASS_FP64_OPS["setup"], CLASS_BYTES["setup"]),
+            "node": (CLASS_FP64_OPS["node_sweep"] * K, CLASS_BYTES["node_sweep"] * K),
+            "cg": sv,
+            "residual": (CLASS_FP64_OPS["residual"], CLASS_BYTES["residual"])}
+
+
+def DCT_KERNELS_PER_SOLVE(wl) -> int:
+    """Kernel launches of one DCT-II solve of the second-order stencil: the
+    forward and inverse transform of every axis of x, y longer than one cell,
+    and the z solve."""
+    return 2 * ((wl.nx > 1) + (wl.ny > 1)) + 1
 
 
 def _peaks():
@@ -175,6 +211,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _strip_dt8_error(wl, t_w, n_window, dt):
+    """Time-discretisation error of the window [t_w, t_w + n_window dt] from the
+    oracle on the 128x1x1 strip: the headline slab's planar wave (stimulus on
+    the whole x = 0 face, uniform initial state, zero-flux faces) does not vary
+    in y or z, so the strip carries the slab's solution.  The strip runs at dt
+    from rest to t_w, then over the window once at dt and once at dt/8 from that
+    state.  Returns (V(dt), V(dt/8)) at the window end and the oracle seconds."""
+    import oracle
+    strip = wl.with_mesh(wl.nx, 1, 1)
+    m = oracle.Monodomain(strip)
+    y = m.init_state()
+    c0 = time.perf_counter()
+    n_pre = int(round(t_w / dt))
+    t = 0.0
+    for _ in range(n_pre):
+        y, _, _, _ = m.step(y, t, dt, wl.M, wl.K)
+        t += dt
+    ya, yb = y.copy(), y.copy()
+    ta = tb = t
+    for _ in range(n_window):
+        ya, _, _, _ = m.step(ya, ta, dt, wl.M, wl.K)
+        ta += dt
+    for _ in range(8 * n_window):
+        yb, _, _, _ = m.step(yb, tb, dt / 8, wl.M, wl.K)
+        tb += dt / 8
+    return ya[0], yb[0], time.perf_counter() - c0
+
+
+def _rel(a, b):
+    import numpy as np
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _rel2(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -197,13 +271,19 @@ def run_ours(args):
     y = solver.new_state()
     solver.init_state(y, wl.V0)
     stream = torch.cuda.current_stream()
+    # untimed: through the stimulus and args.pre_steps steps after it, so that
+    # the timed window sees a propagating wave; then the warm-up steps
+    n_stim = int(np.ceil(float(np.max(wl.t_off)) / dt - 1e-9))
+    n_pre = n_stim + args.pre_steps
     t = 0.0
-    for _ in range(args.warmup):
+    for _ in range(n_pre + args.warmup):
         solver.sweep(y, t, dt, M, K)
         t += dt
     rc = solver.residual()[0]
     if rc != 0:
         raise RuntimeError(f"warm-up step failed with code {rc}")
+    t_w = t
+    y_w = y.clone()                           # state at the window start
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -232,6 +312,8 @@ def run_ours(args):
     ms = max_over_ranks(ms, pg)
     value = aggregate_value(N * args.steps, ws, ms)
     ms_step = ms / args.steps
+    t_end = t
+    V_end = y[0, :N].cpu().numpy().copy()     # V at the window end
 
     # ---- end to end: the same steps through the host-buffer entry point (H2D + step + D2H)
     ns, ld = solver.n_state, solver.ld
@@ -247,11 +329,12 @@ def run_ours(args):
     e2e_value = N * n_e2e * ws / e2e_s
     y.copy_(y_host.cuda())
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant kernel class, and the FP64-issue fraction of every class
     peaks = _peaks()
     dom = max(prof, key=lambda k: prof[k][0])
     per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
     it_mean = sum(cg_iters) / max(len(cg_iters), 1)
+    solver_kind = "dct" if (args.solver == "dct" or (args.solver == "auto" and args.precision == "fp64")) else "iter"
     roof = {"kernel": dom}
     if dom == "node" and M in NODE_FLOPS_PER_SWEEP and args.precision == "fp64":
         flops = NODE_FLOPS_PER_SWEEP[M] * N / (M + 1)           # per launch, average over a sweep
@@ -274,10 +357,28 @@ def run_ours(args):
         roof.update({"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
                      "frac": ach / peaks["hbm_gbs"] if ach else None, "peak_source": peaks["source"],
                      "traffic": None})
+    if args.precision == "fp64" and M == 4:
+        classes = {}
+        for cls, (ops, byts) in class_work(solver_kind, K, it_mean).items():
+            sec = prof[cls][0] * 1e-3 / args.steps
+            if sec <= 0:
+                continue
+            rate = ops * N / sec
+            classes[cls] = {"ms_per_step": sec * 1e3, "fp64_ops_per_node_step": ops,
+                            "fp64_issue_frac": rate / FP64_ISSUE_PEAK,
+                            "bytes_per_node_step": byts, "gbs": byts * N / sec / 1e9,
+                            "hbm_frac": byts * N / sec / 1e9 / peaks["hbm_gbs"]}
+        roof["classes"] = classes
+        roof["classes_note"] = (
+            "fp64_issue_frac: FP64 instructions (DFMA, DADD, DMUL; counted by ncu per node, profiles/) per second "
+            "over the FP64 issue peak, 152 SMs x 2 per clock x 2.07 GHz.  On this GPU every class, the diffusion "
+            "solve included, is bound by FP64 issue, not HBM: the solve's vectors stay in L2, so its GB/s is "
+            "reported against HBM for reference only (the 70%-of-HBM target assumes an HBM-bound stencil).")
 
     # ---- CPU oracle baseline on one full-size step from the live state (rank 0, N = 1)
     cpu = None
     verr = None
+    nxt = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         yh = y[:, :N].cpu().numpy().copy()
@@ -292,6 +393,22 @@ def run_ours(args):
                "sample": f"one HSDC step of the full {wl.nx}x{wl.ny}x{wl.nz} slab at t={t:.2f} ms"}
         verr = {"V_max_rel_vs_oracle_one_step": float(np.abs(g1[0] - want[0]).max() / np.abs(want[0]).max()),
                 "state_max_abs_vs_oracle_one_step": float(np.abs(g1 - want).max())}
+        # time-discretisation error over the timed window (oracle, planar strip)
+        Va, Vb, osec = _strip_dt8_error(wl, t_w, args.steps, dt)
+        Vx = V_end.reshape(wl.nz, wl.ny, wl.nx)
+        verr.update({
+            "window_ms": [t_w, t_end],
+            "discretisation_vs_dt8": _rel(Va, Vb),
+            "discretisation_vs_dt8_l2": _rel2(Va, Vb),
+            "gpu_slab_vs_oracle_strip_at_window_end": max(_rel(Vx[k, j], Va) for k in (0, wl.nz - 1)
+                                                          for j in (0, wl.ny - 1)),
+            "gpu_slab_vs_dt8_at_window_end": _rel(Vx[0, 0], Vb),
+            "slab_yz_spread": float(np.abs(Vx - Vx[:1, :1, :]).max() / np.abs(Vx).max()),
+            "reference": "oracle on the 128x1x1 strip (the slab's planar solution), the window run at dt and "
+                         "at dt/8 from the dt run's state at the window start",
+            "oracle_seconds": osec})
+        if args.precision == "fp64" and not args.no_next_forms:
+            nxt = _next_forms(args, wl, y_w, t_w, V_end, Vb, ms_step, solver_kind)
         if args.precision != "fp64":
             ref64 = P.Solver.from_workload(wl, M_max=M)
             y64 = y.clone()
@@ -302,6 +419,8 @@ def run_ours(args):
             ref64.close()
 
     launches = int(sum(v[1] for v in prof.values()))
+    if solver_kind == "dct":                 # one profiled "launch" per solve: its kernel passes
+        launches += int(prof["cg"][1]) * (DCT_KERNELS_PER_SOLVE(wl) - 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -309,9 +428,12 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "nodes": N, "n_state": wl.n_state, "M": M, "K": K, "dt_ms": dt,
                    "precision": args.precision, "solver": args.solver,
+                   "solve": "DCT-II direct" if solver_kind == "dct" else "iterative",
                    "model": "syn19 (seed 20240530)", "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (state + workspace ~2 GB per GPU)",
-                   "window_ms": [args.warmup * dt, (args.warmup + args.steps) * dt]},
+                   "window_ms": [t_w, t_end],
+                   "untimed_before_window": f"{n_stim} stimulus steps + {args.pre_steps} steps + "
+                                            f"{args.warmup} warm-up steps"},
         "s_per_sim_ms": ms_step * 1e-3 / dt,
         "v_error": verr,
         "residual": {"res_inf": res_inf, "y_inf": y_inf},
@@ -324,11 +446,110 @@ def run_ours(args):
                 "h2d_bytes_per_step": ns * N * 8, "d2h_bytes_per_step": ns * N * 8},
         "gpu_launches": launches,
         "clocks": clk,
+        "next_forms": nxt,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def _next_forms(args, wl, y_w, t_w, V64, Vdt8, ms64, solver_kind):
+    """The precision and batching forms beside the headline, on the same box:
+    (1) the precision form (FP32 ionic model, FP64 elsewhere) over the same
+    window of the same slab from the same state: speedup, its V against the
+    FP64 path and both against the dt/8 reference (equal V-error); (2) a small
+    ragged batch of HH tissues, batched against one at a time (batches of one,
+    identical results)."""
+    import numpy as np
+    import torch
+    import paper_2405_19994_gb300 as P
+    from paper_2405_19994_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
+    M, K, dt, N = wl.M, wl.K, wl.dt, wl.n_nodes
+    out = {}
+    c0 = time.perf_counter()
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(n):
+            fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # (1) precision form
+    sm = P.Solver.from_workload(wl, M_max=M, precision="mixed", solver=args.solver)
+    ym = y_w.clone()
+    for k in range(2):                               # warm-up on a copy
+        sm.sweep(ym, t_w + k * dt, dt, M, K)
+    ym.copy_(y_w)
+    tt = [t_w]
+
+    def step_m(k):
+        sm.sweep(ym, tt[0], dt, M, K)
+        tt[0] += dt
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms_m = timed(step_m, args.steps) / args.steps
+    clk = clocks.stop()
+    if sm.residual()[0] != 0:
+        raise RuntimeError("precision-form step failed")
+    Vm = ym[0, :N].cpu().numpy()
+    sm.close()
+    Vmx = Vm.reshape(wl.nz, wl.ny, wl.nx)
+    V64x = V64.reshape(wl.nz, wl.ny, wl.nx)
+    out["precision"] = {
+        "what": "FP32 ionic model, FP64 state/tables/quadrature/residual, FP64-refined solves",
+        "window_ms": [t_w, t_w + args.steps * dt],
+        "ms_per_step": ms_m, "fp64_ms_per_step": ms64, "speedup_vs_fp64": ms64 / ms_m,
+        "V_max_rel_vs_fp64": _rel(Vm, V64), "V_l2_rel_vs_fp64": _rel2(Vm, V64),
+        "V_max_rel_vs_dt8": _rel(Vmx[0, 0], Vdt8), "fp64_V_max_rel_vs_dt8": _rel(V64x[0, 0], Vdt8),
+        "clocks": clk}
+    # (2) small ragged batch: the first 8 tissues of the 64-tissue batch workload
+    wls = I.hh_batch()[:8]
+    Mb, Kb, dtb = wls[0].M, wls[0].K, wls[0].dt
+    nb_steps = 10
+    b = P.Batch.from_workloads(wls, M_max=Mb)
+    yb = b.new_state()
+    b.init_state(yb, wls[0].V0)
+    tb = [0.0]
+
+    def step_b(k):
+        b.sweep(yb, tb[0], dtb, Mb, Kb)
+        tb[0] += dtb
+    for k in range(3):
+        step_b(k)
+    ms_b = timed(step_b, nb_steps) / nb_steps
+    singles = [P.Batch.from_workloads([w], M_max=Mb) for w in wls]
+    for s1 in singles:
+        s1.set_shape(*b.shape()[:2], 1)
+    ys = [s1.new_state() for s1 in singles]
+    for s1, y1 in zip(singles, ys):
+        s1.init_state(y1, wls[0].V0)
+    t1 = [0.0]
+
+    def step_1(k):
+        for s1, y1 in zip(singles, ys):
+            s1.sweep(y1, t1[0], dtb, Mb, Kb)
+        t1[0] += dtb
+    for k in range(3):
+        step_1(k)
+    ms_1 = timed(step_1, nb_steps) / nb_steps
+    ok = b.residual()[0] == 0 and all(s1.residual()[0] == 0 for s1 in singles)
+    same = all(torch.equal(b.tissue(yb, k), singles[k].tissue(ys[k], 0)) for k in range(len(wls)))
+    nodes = int(sum(w.n_nodes for w in wls))
+    out["batch"] = {"tissues": len(wls), "nodes": nodes, "steps": nb_steps,
+                    "batched_ms_per_step": ms_b, "looped_ms_per_step": ms_1, "speedup": ms_1 / ms_b,
+                    "identical_bit_for_bit": bool(same), "ok": bool(ok),
+                    "batched_node_updates_per_s": nodes / (ms_b * 1e-3), "graph": bool(b.graph_active())}
+    for s1 in singles:
+        s1.close()
+    b.close()
+    out["seconds"] = time.perf_counter() - c0
+    return out
 
 
 def _activation_update(act, v_old, v_new, t_old, dt, level=-40.0):
@@ -859,6 +1080,8 @@ def run_fas_form(args):
     coarse3 = [P.Batch.from_workloads([w], M_max=M3, solver=args.solver) for _ in range(Pn)]
 
     out = {"hsdc2": [], "hsdc3": [], "qpar": []}
+    clocks = ClockSampler(local)
+    clocks.start()
     for k in range(1, iters + 1):
         load()
         ms = timed(lambda: P.esdc.hsdc2(fine, coarse, yin, yout, t0, dt, M1, M2, k))
@@ -876,6 +1099,8 @@ def run_fas_form(args):
         load()
         ms = timed(lambda: fine.qpar(yin, yout, t0, dt, M1, k))
         out["qpar"].append({"iters": k, "ms": ms, "err": err()})
+
+    clk = clocks.stop()
 
     def first_below(rows, tol):
         for r in rows:
@@ -901,6 +1126,7 @@ def run_fas_form(args):
         "speedup_hsdc2_vs_qpar_to_1e-6": (q6["ms"] / h6["ms"]) if (h6 and q6) else None,
         "hsdc3_levels": [M1, M2, M3], "hsdc3_to_tol": h3, "hsdc3_to_1e-6": h36,
         "history": out,
+        "clocks": clk,
     }
     for c in coarse + coarse3:
         c.close()
@@ -1016,13 +1242,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-next-forms", action="store_true",
+                    help="headline: skip the precision-form and batch comparisons beside the timed window")
+    ap.add_argument("--pre-steps", type=int, default=100,
+                    help="headline: untimed steps after the stimulus before the warm-up and the timed window")
     ap.add_argument("--nz", type=int, default=None, help="slab depth (default: the workload's own)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
-    ap.add_argument("--solver", choices=["auto", "cg", "dct"], default="auto",
-                    help="diffusion solves (headline, precision, batch and fas forms): auto (Chebyshev semi-iteration on "
-                         "the exactly known spectrum of the scalar-sigma operator), cg (Jacobi-PCG) or dct "
-                         "(the DCT-II direct solve; headline form only)")
+    ap.add_argument("--solver", choices=["auto", "cg", "dct", "cheb"], default="auto",
+                    help="diffusion solves (headline, precision, batch and fas forms): auto (the DCT-II direct solve "
+                         "for the scalar sigma on the FP64 path, else as cheb), cheb (Chebyshev semi-iteration on a "
+                         "known spectral interval, else CG), cg (Jacobi-PCG) or dct (the DCT-II direct solve; "
+                         "headline form only)")
     ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet", "peaks"],
                     default="plain",
                     help="precision: FP64 vs mixed on the anisotropic HH slab (256x256x64, T = 10 ms); "
