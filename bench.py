@@ -37,15 +37,16 @@ UNIT = "node-updates/s"
 #  node kernel (SYN19, M = 4), per mesh node and sweep: the M + 1 launches of a
 #  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
 #  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu
-#  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep:
-#  191.0 + 3 x 1080.7 + 868.7 = 4301.8 flops per node per sweep
+#  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep, with the gate
+#  functions evaluated from their V table:
+#  191.0 + 3 x 723.7 + 511.7 = 2873.8 flops per node per sweep
 #  (profiles/k_node_syn19_slab_128x128x16.md).
 #  Algorithmic bytes per node: node 1 reads 158 / writes 20 doubles, nodes 2..M
 #  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep, 1493 B per launch
 #  on average; DRAM traffic measured by ncu: 7048 B per sweep (1410 B per launch).
 #  cg (per mesh node and iteration): [A] z (stencil), p, q -> p, q;
 #  [B] q, r, x, p -> x, r, z: 12 doubles = 96 B, plus 8 doubles per solve.
-NODE_FLOPS_PER_SWEEP = {4: 4301.8}
+NODE_FLOPS_PER_SWEEP = {4: 2873.8}
 NODE_BYTES_PER_LAUNCH = {4: 1493}
 NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {4: 1410}
 CG_BYTES_PER_NODE_ITER = 96
@@ -62,7 +63,7 @@ FP64_ISSUE_PEAK = 152 * 2 * 2.07e9
 # step; node: per sweep (M + 1 launches); DCT solve: four transform passes
 # and the tridiagonal z solve; Chebyshev and CG: per iteration; residual: per
 # step.
-CLASS_FP64_OPS = {"setup": 3187.2, "node_sweep": 2542.8, "dct_solve": 56.3, "cheb_iter": 12.2, "cg_iter": 15.0,
+CLASS_FP64_OPS = {"setup": 2949.1, "node_sweep": 1642.8, "dct_solve": 56.3, "cheb_iter": 12.2, "cg_iter": 15.0,
                   "residual": 703.0}
 CLASS_BYTES = {"setup": 3256.0, "node_sweep": 7464.0, "dct_solve": 120.0, "cheb_iter": 48.0, "cg_iter": 96.0,
                "residual": 2904.0}

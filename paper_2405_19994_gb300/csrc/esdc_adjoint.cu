@@ -542,6 +542,7 @@ int esdc_set_params(esdc_handle* h, const double* params, int n_params)
     if (rc != ESDC_OK) return set_err(h, rc, "invalid model parameters");
     h->mp = mp;
     h->mpf = mpf;
+    if (esdc_vtab_upload(h) != cudaSuccess) return set_err(h, ESDC_ERR_CUDA, "gate table upload failed");
     return ESDC_OK;
 }
 

@@ -691,6 +691,7 @@ struct esdc_batch {
     ColloData col[ESDC_MMAX];
     ModelDev mp{};
     ModelDevF mpf{};
+    double* vtab = nullptr;                // the gate table of the model (see ModelDev)
     std::vector<TissueDev> tis_h;
     std::vector<unsigned> on_h;            // [ntis][ESDC_MMAX + 1]
     TissueDev* tis = nullptr;
@@ -741,7 +742,7 @@ void free_batch(esdc_batch* b)
     for (auto& g : b->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    void* ptrs[] = {b->R, b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
+    void* ptrs[] = {b->vtab, b->R, b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
                     b->rhs, b->Vprev, b->r, b->p, b->q, b->z, b->part, b->bar, b->done_at, b->status,
                     b->cg_log, b->flags, b->rmax};
     for (void* p : ptrs)
@@ -1063,6 +1064,16 @@ int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, doubl
     b->model = model; b->NS = NS; b->NG = NG; b->NA = NS - 1 - NG;
     b->chi = chi; b->Cm = Cm;
     b->mp = mp; b->mpf = mpf;
+    {
+        std::vector<double> rows;
+        double err[2];
+        if (esdc_vtab_build(model, mp.p, rows, &err[0], &err[1]) == 0) {
+            if (cudaMalloc((void**)&b->vtab, sizeof(double) * rows.size()) != cudaSuccess ||
+                cudaMemcpy(b->vtab, rows.data(), sizeof(double) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(ESDC_ERR_NO_MEMORY);
+            b->mp.vtab = b->vtab;
+        }
+    }
     b->ntis = n;
     b->tis_h.resize(n);
     int tile = 0;

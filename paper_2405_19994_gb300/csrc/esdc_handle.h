@@ -50,6 +50,8 @@ struct esdc_handle {
     ModelDev mp{};
     ModelDevF mpf{};
     double sigma = 0, chi = 0, Cm = 0, D = 0;
+    double* vtab = nullptr;                    // the gate table of the model (SYN19), see ModelDev
+    double vtab_err[2] = {0, 0};               // its build-time errors (w_inf absolute, Lambda relative)
     double *lay = nullptr, *wdiag = nullptr;   // layered conductivity (see MeshDev)
     double* sigf = nullptr;                    // conductivity field (see MeshDev)
     float* layf = nullptr;
@@ -80,6 +82,9 @@ struct esdc_handle {
     long long prof_cnt[ESDC_PROF_CLASSES] = {};
     char err[256] = {0};
 };
+// (Re)builds the handle's gate table for its current parameters (esdc_step.cu).
+cudaError_t esdc_vtab_upload(esdc_handle* h);
+
 
 
 // Records a formatted message on the handle and returns code.

@@ -1,6 +1,7 @@
 // Internal declarations of the HSDC library (not part of the C ABI).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/esdc.h"
@@ -78,8 +79,19 @@ struct StimDev {
     double amp[ESDC_MAXBOX], t_on[ESDC_MAXBOX], t_off[ESDC_MAXBOX];
 };
 
+// The gate functions tabulated in V (esdc_vtab.cpp; SYN19 and HH1952): ESDC_VTAB_N
+// intervals of ESDC_VTAB_W mV from ESDC_VTAB_VLO, a polynomial of degree
+// ESDC_VTAB_NC - 1 in t = V - V_mid per function and interval; a row holds
+// V_mid, then per gate the coefficients of w_inf and of Lambda.
+#define ESDC_VTAB_VLO (-140.0)
+#define ESDC_VTAB_W 1.0
+#define ESDC_VTAB_N 240
+#define ESDC_VTAB_NC 9
+#define ESDC_VTAB_ROW (1 + 2 * ESDC_NGMAX * ESDC_VTAB_NC)
+#define ESDC_VTAB_TOL 4e-15        // refuse a table whose FP64 evaluation misses by more
 struct ModelDev {
     double p[ESDC_NPMAX];
+    const double* vtab = nullptr;  // the gate table, or nullptr: direct evaluation
 };
 
 struct ModelDevF {            // FP32 copy of the parameters (precision form)
@@ -150,6 +162,12 @@ void esdc_dct_destroy(DctDev* d);
 // (b may alias x, not w.r or w.p).
 cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const double* b, double* x,
                             int* iter_log, int* flags, cudaStream_t s);
+
+// The gate table of a model (SYN19, HH1952): rows [ESDC_VTAB_N][ESDC_VTAB_ROW] and
+// the largest errors of its FP64 evaluation against the direct functions
+// (absolute for w_inf, relative for Lambda).  0: built; -1: no table for this
+// model; -2: an error above ESDC_VTAB_TOL (rows cleared).
+int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, double* err_winf, double* err_lam);
 
 // Validates ionic-model parameters and fills the device parameter blocks;
 // returns ESDC_OK or ESDC_ERR_INVALID_ARG.

@@ -217,10 +217,11 @@ __device__ __forceinline__ void setup_iter_body(const StepArgs& a, const MeshDev
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
     const int64_t ld = a.m.ld;
     const double vn = a.yn[p];
+    const typename Model::VCtx vcn = Model::vctx(a.mp, vn);
 #pragma unroll 1
     for (int g = 0; g < NG; ++g) {
         double lam, yinf;
-        Model::gate(a.mp.p, g, vn, lam, yinf);
+        Model::gate(a.mp.p, vcn, g, vn, lam, yinf);
         gate_tables<M>(a, g, NG, lam, p);
     }
 #pragma unroll 1
@@ -237,11 +238,12 @@ __device__ __forceinline__ void setup_iter_body(const StepArgs& a, const MeshDev
 #pragma unroll
         for (int s = 1; s <= NA; ++s) Gj[s * ld + p] = ha[s - 1];
         a.FI[(int64_t)j * ld + p] = fi;
+        const typename Model::VCtx vc = Model::vctx(a.mp, u[0]);
 #pragma unroll 1
         for (int g = 0; g < NG; ++g) {
             const int s = 1 + NA + g;
             double lam, yinf;
-            Model::gate(a.mp.p, g, u[0], lam, yinf);
+            Model::gate(a.mp.p, vc, g, u[0], lam, yinf);
             Gj[s * ld + p] = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
         }
     }
@@ -280,6 +282,7 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, 
         for (int s = 1; s <= NA; ++s) { Gj[s * ld + p] = ha[s - 1]; Yj[s * ld + p] = u[s]; }
         a.FI[(int64_t)j * ld + p] = fi;
     }
+    const typename Model::VCtx vc = Model::vctx(a.mp, u[0]);
 #pragma unroll 1
     for (int g = 0; g < NG; ++g) {
         const int s = 1 + NA + g;
@@ -289,7 +292,7 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, 
             Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
             lam = lf; yinf = yf;
         } else {
-            Model::gate(a.mp.p, g, u[0], lam, yinf);
+            Model::gate(a.mp.p, vc, g, u[0], lam, yinf);
         }
         const double us = a.yn[s * ld + p];
         const double g0 = lam * (us - yinf);
@@ -406,6 +409,8 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
         }
     }
     // ---- gates, one at a time
+    typename Model::VCtx vc{};
+    if (eval && !MIXED) vc = Model::vctx(a.mp, u[0]);
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
         const int s = 1 + NA + g;
@@ -417,7 +422,7 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
                 Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
                 lam = lf; yinf = yf;
             } else {
-                Model::gate(a.mp.p, g, u[0], lam, yinf);
+                Model::gate(a.mp.p, vc, g, u[0], lam, yinf);
             }
             const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
             Gq[s * ld + p] = gn;

@@ -10,8 +10,19 @@
 // State order in u: V, the NA auxiliaries, the NG gates.
 #pragma once
 #include "esdc_fmath.cuh"
+#include "esdc_internal.h"
 
 namespace esdc {
+
+// A polynomial of the gate table (esdc_vtab.cpp) at t = V - V_mid: Horner's
+// rule, ESDC_VTAB_NC - 1 FMAs.
+__device__ __forceinline__ double vt_poly(const double* __restrict__ c, double t)
+{
+    double r = __ldg(c + ESDC_VTAB_NC - 1);
+#pragma unroll
+    for (int k = ESDC_VTAB_NC - 2; k >= 0; --k) r = fma(r, t, __ldg(c + k));
+    return r;
+}
 
 // x/(e^x - 1), removable singularity at x = 0.  |x| < 1/2: its Taylor series
 // 1 - x/2 + sum_k B_2k x^2k/(2k)! (B_2k the Bernoulli numbers), truncated after
@@ -81,6 +92,44 @@ struct HH1952 {
         const double sum = al + be;
         lam = -sum;
         yinf = al * esdc_rcp(sum);
+    }
+    // The gate table (esdc_vtab.cpp), as for SYN19: the node's interval row
+    // and t = V - V_mid once per node; row = nullptr: the direct rates.
+    struct VCtx {
+        const double* row;
+        double t;
+    };
+    __device__ static VCtx vctx(const ModelDev& md, double V)
+    {
+        VCtx c{nullptr, 0.0};
+        if (md.vtab) {
+            const int i = __double2int_rd((V - ESDC_VTAB_VLO) * (1.0 / ESDC_VTAB_W));
+            if (i >= 0 && i < ESDC_VTAB_N) {
+                c.row = md.vtab + (size_t)i * ESDC_VTAB_ROW;
+                c.t = V - __ldg(c.row);
+            }
+        }
+        return c;
+    }
+    __device__ static void gate(const double* __restrict__ mp, const VCtx& c, int q, double V, double& lam,
+                                double& yinf)
+    {
+        if (c.row) {
+            const double* cw = c.row + 1 + q * (2 * ESDC_VTAB_NC);
+            yinf = vt_poly(cw, c.t);
+            lam = vt_poly(cw + ESDC_VTAB_NC, c.t);
+            return;
+        }
+        gate(mp, q, V, lam, yinf);
+    }
+    __device__ static void eval(const ModelDev& md, const double* u, double& mI, double* ha, double* lam,
+                                double* yinf)
+    {
+        (void)ha;
+        const VCtx c = vctx(md, u[0]);
+        for (int q = 0; q < 3; ++q) gate(md.p, c, q, u[0], lam[q], yinf[q]);
+        double hl[1];
+        currents(md.p, u, mI, hl);
     }
     // FP32 counterparts of currents() and gate() (parameters as floats).
     __device__ static void currents_f(const float* __restrict__ mp, const float* u, float& mI, float* ha)
@@ -223,6 +272,48 @@ struct SYN19 {
         yinf = esdc_rcp(1.0 + esdc_exp(fma(-V, inv[q], dv[q])));
         const double s = esdc_rcp(1.0 + esdc_exp(fma(-V, inv[12 + q], dv[12 + q])));
         lam = -esdc_exp(fma(p[3], s, dv[24 + q]));
+    }
+    // The gate table (esdc_vtab.cpp): a node's interval row and t = V - V_mid,
+    // computed once per node for all twelve gates; row = nullptr (no table, or
+    // V outside [ESDC_VTAB_VLO, ESDC_VTAB_VLO + ESDC_VTAB_N ESDC_VTAB_W)) selects
+    // the direct evaluation.  A NaN V stays NaN either way.
+    struct VCtx {
+        const double* row;
+        double t;
+    };
+    __device__ static VCtx vctx(const ModelDev& md, double V)
+    {
+        VCtx c{nullptr, 0.0};
+        if (md.vtab) {
+            const int i = __double2int_rd((V - ESDC_VTAB_VLO) * (1.0 / ESDC_VTAB_W));
+            if (i >= 0 && i < ESDC_VTAB_N) {
+                c.row = md.vtab + (size_t)i * ESDC_VTAB_ROW;
+                c.t = V - __ldg(c.row);
+            }
+        }
+        return c;
+    }
+    // w_inf and Lambda of gate q: two degree-8 polynomials (16 FMAs) on the
+    // table, else the direct formulas (about 35 FP64 operations).
+    __device__ static void gate(const double* __restrict__ mp, const VCtx& c, int q, double V, double& lam,
+                                double& yinf)
+    {
+        if (c.row) {
+            const double* cw = c.row + 1 + q * (2 * ESDC_VTAB_NC);
+            yinf = vt_poly(cw, c.t);
+            lam = vt_poly(cw + ESDC_VTAB_NC, c.t);
+            return;
+        }
+        gate(mp, q, V, lam, yinf);
+    }
+    __device__ static void eval(const ModelDev& md, const double* u, double& mI, double* ha, double* lam,
+                                double* yinf)
+    {
+        const VCtx c = vctx(md, u[0]);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) gate(md.p, c, q, u[0], lam[q], yinf[q]);
+        double hl[NA];
+        currents(md.p, u, mI, ha ? ha : hl);
     }
     __device__ static void currents_f(const float* __restrict__ mp, const float* u, float& mI, float* ha)
     {

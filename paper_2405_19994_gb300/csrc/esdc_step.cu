@@ -57,7 +57,7 @@ __global__ void k_ionic(MeshDev m, ModelDev mp, const double* y, double* fE, dou
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.N; p += gridDim.x * blockDim.x) {
         double u[NS], mI, ha[NA > 0 ? NA : 1], l[NG], yi[NG];
         for (int s = 0; s < NS; ++s) u[s] = y[s * m.ld + p];
-        Model::eval(mp.p, u, mI, NA > 0 ? ha : nullptr, l, yi);
+        Model::eval(mp, u, mI, NA > 0 ? ha : nullptr, l, yi);
         fE[p] = mI; lam[p] = 0.0; yinf[p] = 0.0;
         for (int s = 1; s <= NA; ++s) { fE[s * m.ld + p] = ha[s - 1]; lam[s * m.ld + p] = 0.0; yinf[s * m.ld + p] = 0.0; }
         for (int g = 0; g < NG; ++g) {
@@ -187,6 +187,7 @@ void free_all(esdc_handle* h)
     if (h->layf) cudaFree(h->layf);
     if (h->wdiag) cudaFree(h->wdiag);
     if (h->sigf) cudaFree(h->sigf);
+    if (h->vtab) cudaFree(h->vtab);
     void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev, h->Vprev,
                     h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.r32, h->cg.p32, h->cg.q32, h->cg.z32,
                     h->cg.e32, h->cg.part, h->cg.bar, h->cg.status,
@@ -196,6 +197,24 @@ void free_all(esdc_handle* h)
 }
 
 }  // namespace
+
+// The gate table of the handle's model for the parameters in h->mp (built on
+// the host, copied into h->vtab, allocated on first use); h->mp.vtab points
+// to it, or stays nullptr (direct evaluation) for models without a table or a
+// table that missed its accuracy check.  Synchronises the device before it
+// overwrites a table that kernels in flight may read.
+cudaError_t esdc_vtab_upload(esdc_handle* h)
+{
+    std::vector<double> rows;
+    h->mp.vtab = nullptr;
+    if (esdc_vtab_build(h->model, h->mp.p, rows, &h->vtab_err[0], &h->vtab_err[1]) != 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!h->vtab) e = cudaMalloc((void**)&h->vtab, sizeof(double) * rows.size());
+    else e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h->vtab, rows.data(), sizeof(double) * rows.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) h->mp.vtab = h->vtab;
+    return e;
+}
 
 // Validates the ionic-model parameters and fills the device parameter blocks
 // (FP64, with host reciprocals of the constant divisors of SYN19, and FP32).
@@ -296,6 +315,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     for (int M = 1; M <= ESDC_MMAX; ++M)
         if (esdc_colloc_build(M, &h->col[M - 1])) return fail(ESDC_ERR_CUDA);
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(ESDC_ERR_CUDA);
+    if (esdc_vtab_upload(h) != cudaSuccess) return fail(ESDC_ERR_CUDA);
     if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
         return fail(ESDC_ERR_CUDA);
     {
