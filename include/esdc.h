@@ -345,8 +345,25 @@ int esdc_fma_probe(int fp32, int64_t n, double* ms, double* flops, void* stream)
  * Returns ESDC_OK, ESDC_ERR_INVALID_ARG, ESDC_ERR_TOO_LARGE, ESDC_ERR_CUDA,
  * ESDC_ERR_CG_NOT_CONVERGED, ESDC_ERR_NONFINITE or ESDC_ERR_DEVICE_TIMEOUT.
  */
+/*
+ * Failure-path check: makes the grid-barrier waits of the handle's iterative
+ * solves run out on purpose, so that the error path (ESDC_ERR_DEVICE_TIMEOUT)
+ * can be exercised without a hang or a GPU fault.  With skip_block >= 0, block
+ * `skip_block` of each cooperative solve kernel does not arrive at the
+ * kernel's first grid barrier; every block then waits there until limit_us
+ * microseconds (0: the normal 1 s) have passed, raises the TIMEOUT flag and
+ * returns.  The solve's result, and the state of a sweep that ran such solves,
+ * are then undefined, and esdc_diffusion_solve / esdc_residual return
+ * ESDC_ERR_DEVICE_TIMEOUT.  skip_block < 0 restores normal operation.  Only the
+ * Chebyshev and CG solves have grid barriers (options.solver 1 and 3, and 0
+ * where it does not take the DCT).  Synchronises the device.  Returns
+ * ESDC_OK, ESDC_ERR_INVALID_ARG (null handle, limit_us above 1e6) or
+ * ESDC_ERR_CUDA.
+ */
+int esdc_debug_barrier(esdc_handle* h, int skip_block, unsigned limit_us);
+
 #define ESDC_STATIC_MAX_NODES 262144
-#define ESDC_STATIC_SCRATCH_BYTES ((4LL * ESDC_STATIC_MAX_NODES + 6 * 1024 + 32) * 8)
+#define ESDC_STATIC_SCRATCH_BYTES ((4LL * ESDC_STATIC_MAX_NODES + 8 * 1024 + 32) * 8)
 int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, const double* b, double* x,
                                 double tol, int maxit, int precond, int* iters, void* stream);
 

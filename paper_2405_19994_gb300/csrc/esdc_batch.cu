@@ -1121,7 +1121,7 @@ int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, doubl
     if (cudaMalloc((void**)&b->tis, sizeof(TissueDev) * n) != cudaSuccess ||
         cudaMalloc((void**)&b->tile_tissue, sizeof(int) * tile) != cudaSuccess ||
         cudaMalloc((void**)&b->tis_on, sizeof(unsigned) * b->on_h.size()) != cudaSuccess ||
-        cudaMalloc((void**)&b->bar, sizeof(unsigned) * 2) != cudaSuccess ||
+        cudaMalloc((void**)&b->bar, sizeof(unsigned) * 4) != cudaSuccess ||
         cudaMalloc((void**)&b->done_at, sizeof(int) * n) != cudaSuccess ||
         cudaMalloc((void**)&b->status, sizeof(int) * 2 * n) != cudaSuccess ||
         cudaMalloc((void**)&b->cg_log, sizeof(int) * b->cg_log_len) != cudaSuccess ||
@@ -1135,7 +1135,7 @@ int esdc_batch_create(int n, const esdc_mesh* meshes, const double* sigma, doubl
         cudaMemcpy(b->tile_tissue, tt.data(), sizeof(int) * tile, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(ESDC_ERR_CUDA);
     cudaMemset(b->tis_on, 0, sizeof(unsigned) * b->on_h.size());
-    cudaMemset(b->bar, 0, sizeof(unsigned) * 2);
+    cudaMemset(b->bar, 0, sizeof(unsigned) * 4);
     cudaMemset(b->status, 0, sizeof(int) * 2 * n);
     cudaMemset(b->cg_log, 0, sizeof(int) * b->cg_log_len);
     cudaMemset(b->flags, 0, sizeof(int));

@@ -40,29 +40,42 @@ struct CgArgs {
     int precond;
 };
 
-// Grid barrier on one monotonic arrival counter (zeroed before the launch):
-// barrier number b is passed once the counter reaches b * gridDim.x.  Thread 0
-// of each block adds its arrival and polls with acquire loads, tightly at
-// first, then with short sleeps; after 1 s of waiting it raises TIMEOUT and
-// returns false, and the caller must return from the kernel.
+// Grid barrier on one monotonic arrival counter bar[0] (zeroed before the
+// launch): barrier number b is passed once the counter reaches b * gridDim.x.
+// Thread 0 of each block adds its arrival and polls with acquire loads,
+// tightly at first, then with short sleeps; after 1 s of waiting it raises
+// TIMEOUT and returns false, and the caller must return from the kernel.
+// bar[2] and bar[3] are zero in use.  esdc_debug_barrier sets them to make the
+// waits of a solve run out on purpose (the failure path, tested on the host's
+// side): bar[2] = 1 + the index of a block that does not arrive at the
+// kernel's first barrier, bar[3] = the wait limit in microseconds (0: 1 s).
+// bar[2] is read at the first barrier only and bar[3] only once a wait is long.
 __device__ bool grid_barrier(unsigned* bar, unsigned& target, int* flags)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
+        const bool skip = target == gridDim.x && __ldcg(bar + 2) == blockIdx.x + 1;
         __threadfence();
-        atomicAdd(bar, 1u);
+        if (!skip) atomicAdd(bar, 1u);
         int ok = 1;
         if (load_acquire(bar) < target) {
             const unsigned long long t0 = global_ns();
+            unsigned long long limit = 0;
             unsigned spins = 0;
             while (load_acquire(bar) < target) {
                 if (++spins > 32) __nanosleep(32);
-                if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
-                    ok = 0;
-                    atomicOr(flags, ESDC_FLAG_TIMEOUT);
-                    break;
+                if ((spins & 255u) == 0) {
+                    if (!limit) {
+                        const unsigned us = __ldcg(bar + 3);
+                        limit = us ? 1000ull * us : kWaitLimitNs;
+                    }
+                    if (global_ns() - t0 > limit) {
+                        ok = 0;
+                        atomicOr(flags, ESDC_FLAG_TIMEOUT);
+                        break;
+                    }
                 }
             }
         }

@@ -144,7 +144,7 @@ struct CgWork {
     double *r, *p, *q, *z;          // [ld] each
     float *r32, *p32, *q32, *z32, *e32;   // [ld] each, precision form only (else null)
     double* part;                   // [8 * max_blocks] block partial sums
-    unsigned* bar;                  // [2] grid barrier: arrival count, generation
+    unsigned* bar;                  // [4] grid barrier: arrival count, spare, and two test words (grid_barrier)
     int* status;                    // [2]: iterations of the last solve, flag bits
     int max_blocks;
     int threads;

@@ -29,11 +29,14 @@ namespace {
 
 // Layout of the scratch array (in doubles):
 //   r, p, q, z        4 x ESDC_STATIC_MAX_NODES
-//   partial sums      6 x kMaxBlocks
-//   control words     32 doubles' worth (barrier counter, status, flags)
+//   partial sums      8 x kMaxBlocks (the slots CgWork::part provides; the FP64
+//                     CG kernels this entry point runs use the first six)
+//   control words     32 doubles' worth: the grid barrier's four words (two
+//                     doubles), the status words, the flags
 constexpr int kMaxBlocks = 1024;
 constexpr long long kVec = ESDC_STATIC_MAX_NODES;
-constexpr long long kDoubles = 4 * kVec + 6LL * kMaxBlocks + 32;
+constexpr long long kDoubles = 4 * kVec + 8LL * kMaxBlocks + 32;
+static_assert(kDoubles * 8 == ESDC_STATIC_SCRATCH_BYTES, "ESDC_STATIC_SCRATCH_BYTES (esdc.h) states the array's size");
 
 static __device__ __align__(256) double g_static_scratch[kDoubles];
 
@@ -88,19 +91,21 @@ extern "C" int esdc_diffusion_solve_static(const esdc_mesh* mesh, double g, cons
     w.q = base + 2 * kVec;
     w.z = base + 3 * kVec;
     w.part = base + 4 * kVec;
-    double* ctl = base + 4 * kVec + 6LL * kMaxBlocks;
-    w.bar = reinterpret_cast<unsigned*>(ctl);              // barrier counter (zeroed per solve by the launch)
-    w.status = reinterpret_cast<int*>(ctl + 1);            // [0] iterations, [1] spare
-    int* flags = reinterpret_cast<int*>(ctl + 2);          // error flags, cleared below
+    double* ctl = base + 4 * kVec + 8LL * kMaxBlocks;
+    w.bar = reinterpret_cast<unsigned*>(ctl);              // [4]: barrier counter, spare, test words (zero)
+    w.status = reinterpret_cast<int*>(ctl + 2);            // [0] iterations, [1] spare
+    int* flags = reinterpret_cast<int*>(ctl + 3);          // error flags
     w.threads = ESDC_CG_THREADS;
     w.max_blocks = esdc_cg_blocks(m, w.threads);
     if (w.max_blocks < 1) return ESDC_ERR_CUDA;
     if (w.max_blocks > kMaxBlocks) w.max_blocks = kMaxBlocks;
 
     cudaStream_t s = (cudaStream_t)stream;
-    // The array keeps the previous call's contents: clear the words that must
-    // start at zero (the CG vectors and partial sums are fully written first).
-    if (cudaMemsetAsync(flags, 0, sizeof(int), s) != cudaSuccess) return ESDC_ERR_CUDA;
+    // The array keeps the previous call's contents: clear the control words
+    // (barrier, status, flags), so that a solve that stops early reports no
+    // stale iteration count.  The CG vectors and partial sums are fully written
+    // before they are read.
+    if (cudaMemsetAsync(ctl, 0, 4 * sizeof(double), s) != cudaSuccess) return ESDC_ERR_CUDA;
     if (esdc_cg_launch(m, w, g, b, x, tol, maxit, precond != 0, 1, nullptr, flags, s) != cudaSuccess)
         return ESDC_ERR_CUDA;
     int st[2] = {0, 0}, fl = 0;

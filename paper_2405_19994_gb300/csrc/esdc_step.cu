@@ -338,7 +338,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     h->cg.max_blocks = esdc_cg_blocks(h->mesh, h->cg.threads);
     if (h->cg.max_blocks < 1) return fail(ESDC_ERR_CUDA);
     if (cudaMalloc((void**)&h->cg.part, sizeof(double) * 8 * h->cg.max_blocks) != cudaSuccess ||
-        cudaMalloc((void**)&h->cg.bar, sizeof(unsigned) * 2) != cudaSuccess ||
+        cudaMalloc((void**)&h->cg.bar, sizeof(unsigned) * 4) != cudaSuccess ||
         cudaMalloc((void**)&h->cg.status, sizeof(int) * 2) != cudaSuccess ||
         cudaMalloc((void**)&h->rmax, sizeof(unsigned long long) * 2 * ESDC_NSMAX) != cudaSuccess ||
         cudaMalloc((void**)&h->flags, sizeof(int)) != cudaSuccess ||
@@ -352,7 +352,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
             cudaMemset(*f, 0, sizeof(float) * ld);
         }
     }
-    cudaMemset(h->cg.bar, 0, sizeof(unsigned) * 2);
+    cudaMemset(h->cg.bar, 0, sizeof(unsigned) * 4);
     cudaMemset(h->cg.status, 0, sizeof(int) * 2);
     cudaMemset(h->flags, 0, sizeof(int));
     cudaMemset(h->cg_log, 0, sizeof(int) * h->cg_log_len);
@@ -708,6 +708,17 @@ int esdc_diffusion_solve(esdc_handle* h, double g, const double* b, double* x, i
     if (flags & ESDC_FLAG_TIMEOUT) return set_err(h, ESDC_ERR_DEVICE_TIMEOUT, "CG grid barrier timed out");
     if (flags & ESDC_FLAG_NONFINITE) return set_err(h, ESDC_ERR_NONFINITE, "non-finite CG residual");
     if (flags & ESDC_FLAG_CG_MAXIT) return set_err(h, ESDC_ERR_CG_NOT_CONVERGED, "CG hit cg_maxit");
+    return ESDC_OK;
+}
+
+int esdc_debug_barrier(esdc_handle* h, int skip_block, unsigned limit_us)
+{
+    if (!h) return ESDC_ERR_INVALID_ARG;
+    if (limit_us > 1000000u) return set_err(h, ESDC_ERR_INVALID_ARG, "limit_us above 1 s");
+    // grid_barrier reads bar[2] (1 + the block that skips its first arrival) and bar[3] (the wait limit)
+    const unsigned w[2] = {skip_block >= 0 ? (unsigned)skip_block + 1u : 0u, limit_us};
+    CUDA_TRY(h, cudaDeviceSynchronize());
+    CUDA_TRY(h, cudaMemcpy(h->cg.bar + 2, w, sizeof w, cudaMemcpyHostToDevice));
     return ESDC_OK;
 }
 

@@ -79,6 +79,7 @@ def lib() -> C.CDLL:
             "esdc_diffusion_solve_static": (C.c_int, [C.POINTER(esdc_mesh), _D, _VP, _VP, _D, C.c_int, C.c_int,
                                                       C.POINTER(C.c_int), _VP]),
             "esdc_set_params": (C.c_int, [_VP, C.POINTER(_D), C.c_int]),
+            "esdc_debug_barrier": (C.c_int, [_VP, C.c_int, C.c_uint]),
             "esdc_adjoint_forward": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP,
                                                _VP]),
             "esdc_adjoint_backward": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP,
@@ -330,6 +331,11 @@ class Solver:
         a = torch.empty((M, M, n), dtype=torch.float64, device="cuda")
         self._check(lib().esdc_coefficients(self._h, _ptr(z), n, M, _ptr(a), _stream(stream)))
         return a
+
+    def debug_barrier(self, skip_block: int, limit_us: int = 0):
+        """esdc_debug_barrier: make the iterative solves' grid-barrier waits run
+        out (skip_block >= 0, waits limited to limit_us), or restore them (-1)."""
+        self._check(lib().esdc_debug_barrier(self._h, int(skip_block), int(limit_us)))
 
     def diffusion_solve(self, g: float, b, x, stream=None) -> int:
         it = C.c_int()

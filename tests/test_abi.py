@@ -145,6 +145,7 @@ def test_later_entry_points_reject_invalid_arguments_without_gpu(L):
     assert L.esdc_batch_sweep_from(None, None, None, None, 0.1, 3, 1, 0, None) == -1
     assert L.esdc_batch_qpar(None, None, None, 0.0, 0.1, 3, 2, None) == -1
     assert L.esdc_batch_iterate(None, None, None) == -1
+    assert L.esdc_debug_barrier(None, 0, 1000) == -1
     assert L.esdc_hsdc2(None, None, None, None, 0.0, 0.1, 3, 2, 1, None) == -1
     nolev = (C.c_void_p * 1)(None)
     ms = (C.c_int * 2)(3, 2)
