@@ -731,6 +731,7 @@ def run_batch_form(args):
     scratch = b.new_state()
     b.tune(scratch, w0.V0, 0.0, dt, M, K, reps=2)
     shape = b.shape()
+    pers = b.persistent()
     del scratch
     yb = b.new_state()
     b.init_state(yb, w0.V0)
@@ -755,6 +756,8 @@ def run_batch_form(args):
     singles = [P.Batch.from_workloads([w], M_max=M, solver=args.solver) for w in wls]
     for s1 in singles:
         s1.set_shape(*shape[:2], 1)
+        if pers[0]:
+            s1.set_persistent(True, pers[1], pers[2])
     ys = [s1.new_state() for s1 in singles]
     for s1, y1 in zip(singles, ys):
         s1.init_state(y1, w0.V0)
@@ -774,6 +777,33 @@ def run_batch_form(args):
     for s1 in singles:
         s1.close()
     del ys
+
+    # ---- the other launch mode on the same batch: one persistent launch per step, or the
+    # sequence, whichever the tuner did not pick; the same steps from rest, the same bits
+    persist_rows = None
+    if args.solver in ("auto", "cheb"):
+        persist_rows = []
+        modes = [(False, pers[1], pers[2])] if pers[0] else [(True, 512, 128), (True, 512, 512), (True, 256, 128)]
+        for mode in modes:
+            b.set_persistent(*mode)
+            y2 = b.new_state()
+            b.init_state(y2, w0.V0)
+            t2 = [0.0]
+
+            def step_p(k):
+                b.sweep(y2, t2[0], dt, M, K)
+                t2[0] += dt
+            for k in range(args.warmup):
+                step_p(k)
+            ms_p = timed(step_p, steps)
+            if b.residual()[0] != 0:
+                raise RuntimeError("persistent-mode step failed")
+            same = all(torch.equal(b.tissue(y2, k), b.tissue(yb, k)) for k in range(len(wls)))
+            persist_rows.append({"persistent": mode[0], "threads": mode[1], "node_tile": mode[2],
+                                 "ms_per_step": ms_p / steps, "identical_to_tuned": bool(same),
+                                 "graph": b.graph_active()})
+            del y2
+        b.set_persistent(*pers)
 
     # ---- one tissue at a time through esdc_sweep
     solvers = [P.Solver.from_workload(w, M_max=M, solver=args.solver) for w in wls]
@@ -840,7 +870,9 @@ def run_batch_form(args):
                    "solver": args.solver,
                    "l2": "inputs larger than L2 (batch state and workspace ~3.7 GB)"},
         "s_per_sim_ms": ms_b / steps * 1e-3 / dt,
-        "launch_shape": {"node_waves": shape[0], "cg_threads": shape[1], "cg_blocks": shape[2]},
+        "launch_shape": {"node_waves": shape[0], "cg_threads": shape[1], "cg_blocks": shape[2],
+                         "persistent": pers[0], "persistent_threads": pers[1], "node_tile": pers[2]},
+        "other_launch_modes": persist_rows,
         "graph": graph,
         "graph_error": b.graph_error() or None,
         "looped_batches_of_one": {"value": nodes * steps / (ms_1 * 1e-3), "ms_per_step": ms_1 / steps,

@@ -565,9 +565,24 @@ const char* esdc_batch_graph_error(const esdc_batch* b);
 int esdc_batch_set_shape(esdc_batch* b, int node_waves, int cg_threads, int cg_blocks_per_sm);
 int esdc_batch_get_shape(const esdc_batch* b, int* node_waves, int* cg_threads, int* cg_blocks);
 
+/* One persistent launch per step (on = 1; batches with options.solver 0 or 3,
+ * the Chebyshev solves): the set-up, the K (M+1) node phases, the K M solves
+ * of all tissues and the residual run in one cooperative kernel whose phases
+ * meet at the bounded grid barrier (the step is still recorded in a CUDA graph
+ * when graphs are on).  threads: block size (256 or 512); tile: the consecutive
+ * nodes a warp takes at a time in the node phases (a multiple of 32, at most
+ * 2048).  on = 0 returns to the launch sequence.  Results are bit for bit those
+ * of the launch sequence.  Synchronises.  Errors: INVALID_ARG, UNSUPPORTED
+ * (the CG solver), CUDA. */
+int esdc_batch_set_persistent(esdc_batch* b, int on, int threads, int tile);
+int esdc_batch_get_persistent(const esdc_batch* b, int* on, int* threads, int* tile);
+
 /* Autotuner: times `reps` steps of the batch itself (from rest at V0, time t,
  * on the caller's scratch state y_scratch of the batch's layout) for each
- * candidate launch shape and keeps the fastest.  Synchronises. */
+ * candidate and keeps the fastest: the launch sequence with each launch shape
+ * (node waves, solve block size, solve blocks per SM), and with the Chebyshev
+ * solves the persistent launch with block sizes 256 and 512 and node tiles of
+ * 32 to 512 nodes.  Synchronises. */
 int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, double dt, int M, int K, int reps,
                     void* stream);
 

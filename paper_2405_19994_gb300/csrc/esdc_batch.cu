@@ -30,6 +30,12 @@
 // residual) are captured once per (state buffer, M, K, dt) in a CUDA graph and
 // replayed; the only per-step data, the stimulus windows at the collocation
 // times, are copied to the device before each replay.
+//
+// Persistent step.  With the Chebyshev solves the whole step can instead run
+// as one cooperative kernel (k_bstep, esdc_batch_set_persistent): the same
+// phases, separated by the bounded grid barrier, with the same arithmetic, so
+// the same bits.  The autotuner times both launch modes, with their block
+// sizes and node tiles, and keeps the faster.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(128) k_setup_iter(StepArgs a)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
         BatchNode n;
         if (!batch_node(a, p, n)) continue;
-        setup_iter_body<Model, M>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+        setup_iter_body<Model, M>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
     }
 }
 
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(128) k_setup_iter(StepArgs a)
 // groups (a group never spans two tiles); running maxima are flushed to the
 // tissue's slots when the tissue changes.
 template <class Model, int M>
-__global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long long* rmax)
+__device__ __forceinline__ void residual_tissues(const StepArgs& a, const PhaseArgs& ph, unsigned long long* rmax)
 {
     constexpr int NS = Model::NS;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
 #pragma unroll 1
             for (int s = 0; s < NS; ++s) {
                 double r, y;
-                bad |= !residual_state<Model, M, true>(a, p, s, r, y);
+                bad |= !residual_state<Model, M, true>(a, ph, p, s, r, y);
                 rm[s] = max(rm[s], (unsigned long long)__double_as_longlong(r));
                 ym[s] = max(ym[s], (unsigned long long)__double_as_longlong(y));
             }
@@ -125,6 +131,12 @@ __global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long lo
     }
     if (cur >= 0) flush(cur);
     if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+}
+
+template <class Model, int M>
+__global__ void __launch_bounds__(128) k_residual_b(StepArgs a, unsigned long long* rmax)
+{
+    residual_tissues<Model, M>(a, phase_of(a), rmax);
 }
 
 // dst_i = beta dst_i + sum_j W_ij src_j for collocation rows i < Md, j < Ms,
@@ -455,8 +467,11 @@ __global__ void __launch_bounds__(512) k_cgb(BCgArgs a)
 // per iteration.  The same bookkeeping as k_cgb: the block holding a tissue's
 // first tile records its outcome, and the loop ends after the barrier at which
 // every tissue has recorded one.  Results per tissue depend on nothing but the
-// tissue, so batching keeps them bit for bit.
-__global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
+// tissue, so batching keeps them bit for bit.  cheb_all is the solve as a
+// device function: `target` carries the grid barrier's count across the
+// phases of a persistent kernel; false means a barrier wait gave up (the
+// caller must return).
+__device__ bool cheb_all(const BCgArgs& a, unsigned& target)
 {
     constexpr int U = ESDC_TILE / 32;
     __shared__ bool s_active[kMaxBlockTissues], s_chk[kMaxBlockTissues];
@@ -485,7 +500,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
     if (bt.n > kMaxBlockTissues) {
         // As in k_cgb: the host sizes the grid so that this cannot happen.
         if (threadIdx.x == 0) atomicOr(a.flags, ESDC_FLAG_TIMEOUT);
-        return;
+        return false;
     }
     for (int k = threadIdx.x; k < bt.n; k += blockDim.x) {
         const TissueDev* T = a.tis + bt.lo + k;
@@ -529,7 +544,6 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
         G.nx = T->nx; G.ny = T->ny; G.nz = T->nz; G.N = T->N; G.off = T->off;
         return G;
     };
-    unsigned target = 0;
     double* dc = a.p;                 // d_k
     double* dn = a.q;                 // d_{k+1}
 
@@ -557,7 +571,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
             a.part[(size_t)a.ntiles + t] = v1;
         }
     }
-    if (!grid_barrier(a.bar, target, a.flags)) return;
+    if (!grid_barrier(a.bar, target, a.flags)) return false;
     tissue_totals(a, bt, s_active, 0, 2, s_tot);
     if (threadIdx.x == 0) {
         for (int k = 0; k < bt.n; ++k) {
@@ -632,7 +646,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
             }
         }
         double* sw = dc; dc = dn; dn = sw;
-        if (!grid_barrier(a.bar, target, a.flags)) return;
+        if (!grid_barrier(a.bar, target, a.flags)) return false;
         // every tissue has stopped by the previous iteration: leave (the same decision in every block)
         if (threadIdx.x < 32) {
             bool all = true;
@@ -668,6 +682,97 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
         }
         __syncthreads();
     }
+    return true;
+}
+
+__global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
+{
+    unsigned target = 0;
+    cheb_all(a, target);
+}
+
+// ---------------------------------------------------------------- one persistent launch per step
+// The whole step of every tissue in one cooperative kernel: the set-up, then
+// for each sweep k and node i the node phase (ionic evaluation, quadrature,
+// right-hand side) and, for i <= M, the Chebyshev solve of all tissues
+// (cheb_all), then the residual.  Phases are separated by the bounded grid
+// barrier.  Each phase does exactly the arithmetic of the corresponding kernel
+// of the launch sequence (the node bodies are per node; the solve's
+// reductions are fixed by the 512-node tiles), so the results are bit for bit
+// those of the sequence whatever the grid, block size or node tile.
+struct BStepArgs {
+    int K;
+    int from_iter;
+    int tile;                       // node tile: consecutive nodes a warp takes in a node phase (a multiple of 32)
+    double gfac[ESDC_MMAX + 1];     // dt d_i, the solves' shifts
+    double rho0[ESDC_MMAX + 1];     // warm-start weights c_i / c_{i-1} of sweep 0 from y^0
+    double* G0;
+    double* G1;
+    double* yout;
+    double* Y;
+    int64_t row;                    // doubles per collocation row of Y (NS * ld)
+    unsigned long long* rmax;
+    int* cg_log;
+    int cg_log_len;
+};
+
+// Nodes of a node phase: warp w takes tiles of s.tile consecutive nodes,
+// w, w + #warps, ... (lane l of the warp the nodes l, l + 32, ... of a tile).
+template <class F>
+__device__ __forceinline__ void node_phase(int n, int tile, F body)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = gw * tile; base < n; base += nw * tile)
+        for (int o = lane; o < tile; o += 32) {
+            const long long p = base + o;
+            if (p < n) body((int)p);
+        }
+}
+
+template <class Model, int M>
+__global__ void __launch_bounds__(512, 1) k_bstep(StepArgs a, BCgArgs c, BStepArgs s)
+{
+    unsigned target = 0;
+    const int n = a.m.N;
+    PhaseArgs ph{0, 0.0, s.G0, s.G0, nullptr};
+    node_phase(n, s.tile, [&](int p) {
+        BatchNode nd;
+        if (!batch_node(a, p, nd)) return;
+        if (s.from_iter) setup_iter_body<Model, M>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
+        else setup_body<Model, M, false>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
+    });
+    if (!grid_barrier(c.bar, target, c.flags)) return;
+    double* Gold = s.G0;
+    double* Gnew = s.G1;
+    for (int k = 0; k < s.K; ++k) {
+        for (int i = 1; i <= M + 1; ++i) {
+            ph.i = i;
+            ph.Gold = Gold;
+            ph.Gnew = Gnew;
+            ph.rho = (i >= 2 && i <= M) ? (k == 0 && !s.from_iter ? s.rho0[i] : 1.0) : 0.0;
+            node_phase(n, s.tile, [&](int p) {
+                BatchNode nd;
+                if (!batch_node(a, p, nd)) return;
+                node_body<Model, M, false, true>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
+            });
+            if (!grid_barrier(c.bar, target, c.flags)) return;
+            if (i <= M) {
+                BCgArgs ci = c;
+                ci.gfac = s.gfac[i];
+                ci.x = s.Y + (int64_t)(i - 1) * s.row;
+                const int slot = k * M + (i - 1);
+                ci.iter_log = (slot + 1) * c.ntis <= s.cg_log_len ? s.cg_log + (size_t)slot * c.ntis : nullptr;
+                if (!cheb_all(ci, target)) return;
+                if (!grid_barrier(c.bar, target, c.flags)) return;
+            }
+        }
+        double* t = Gold; Gold = Gnew; Gnew = t;
+    }
+    ph.Gold = Gold;
+    ph.yout = s.yout;
+    residual_tissues<Model, M>(a, ph, s.rmax);
 }
 
 // ---------------------------------------------------------------- host
@@ -709,6 +814,10 @@ struct esdc_batch {
     int node_waves = 1, cg_threads = 512, cg_blocks = 0;
     int occ_node[ESDC_MMAX + 1] = {0}, occ_setup[ESDC_MMAX + 1] = {0}, occ_res[ESDC_MMAX + 1] = {0},
         occ_iter[ESDC_MMAX + 1] = {0};
+    // one persistent launch per step (k_bstep; Chebyshev solves only): on/off,
+    // block size, node tile, and the occupancy of k_bstep per M and block size
+    int persist = 0, p_threads = 512, p_tile = 128;
+    int occ_bstep[ESDC_MMAX + 1][2] = {};
     // graph of one step
     bool use_graph = true, graph_failed = false;
     cudaStream_t cap_stream = nullptr;     // private stream the step is recorded on
@@ -787,53 +896,10 @@ int cg_grid(const esdc_batch* b, int threads, int per_sm_wanted)
     return (int)nb;
 }
 
-cudaError_t launch_cgb(esdc_batch* b, double gfac, const double* rhs, double* x, int* log, cudaStream_t s)
+// The step's kernel arguments for M collocation nodes and step dt (the
+// launch-sequence and the persistent path build them alike).
+StepArgs step_args(esdc_batch* b, const double* yin, const double* tau, bool keepR, double dt, int M)
 {
-    BCgArgs a;
-    a.tis = b->tis;
-    a.tile_tissue = b->tile_tissue;
-    a.ntis = b->ntis;
-    a.ntiles = b->ntiles;
-    a.gfac = gfac;
-    a.b = rhs;
-    a.x = x;
-    a.r = b->r; a.p = b->p; a.q = b->q; a.z = b->z;
-    a.part = b->part;
-    a.bar = b->bar;
-    a.flags = b->flags;
-    a.done_at = b->done_at;
-    a.status = b->status;
-    a.iter_log = log;
-    a.tol2 = b->opt.tol_cg * b->opt.tol_cg;
-    a.maxit = b->opt.cg_maxit;
-    a.precond = b->opt.precond;
-    void* args[] = {&a};
-    cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    const void* k = b->opt.solver == 0 ? (const void*)k_chebb : (const void*)k_cgb;
-    return cudaLaunchCooperativeKernel(k, dim3(b->cg_blocks), dim3(b->cg_threads), args, 0, s);
-}
-
-// Occupancy of the step kernels (queried before any stream capture).
-template <class Model, int M>
-void batch_prime(esdc_batch* b)
-{
-    if (b->occ_node[M]) return;
-    b->occ_node[M] = occupancy(k_node<Model, M, false, true>, 128);
-    b->occ_setup[M] = occupancy(k_setup<Model, M, false, true>, 128);
-    b->occ_res[M] = occupancy(k_residual_b<Model, M>, 128);
-    b->occ_iter[M] = occupancy(k_setup_iter<Model, M>, 128);
-}
-
-// One step of every tissue: y_{n+1} of tissue b to yout (may alias yin).
-// from_iter: start from the iterate left in Y by the previous step with the new
-// y_n in yin (a Q^par iteration); otherwise from y^0 = 1 (x) y_n.
-template <class Model, int M>
-cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from_iter, const double* tau, bool keepR,
-                       double dt, int K, cudaStream_t s)
-{
-    const int T = 128;
-    batch_prime<Model, M>(b);
     const ColloData* C = &b->col[M - 1];
     StepArgs a{};
     a.m.nx = 1; a.m.ny = 1; a.m.nz = 1;
@@ -857,6 +923,81 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
     a.tis = b->tis;
     a.tile_tissue = b->tile_tissue;
     a.tis_on = b->tis_on;
+    return a;
+}
+
+// The batched solve's arguments, for the shift gfac, right-hand side rhs and solution x.
+BCgArgs cg_args(esdc_batch* b, double gfac, const double* rhs, double* x, int* log)
+{
+    BCgArgs a;
+    a.tis = b->tis;
+    a.tile_tissue = b->tile_tissue;
+    a.ntis = b->ntis;
+    a.ntiles = b->ntiles;
+    a.gfac = gfac;
+    a.b = rhs;
+    a.x = x;
+    a.r = b->r; a.p = b->p; a.q = b->q; a.z = b->z;
+    a.part = b->part;
+    a.bar = b->bar;
+    a.flags = b->flags;
+    a.done_at = b->done_at;
+    a.status = b->status;
+    a.iter_log = log;
+    a.tol2 = b->opt.tol_cg * b->opt.tol_cg;
+    a.maxit = b->opt.cg_maxit;
+    a.precond = b->opt.precond;
+    return a;
+}
+
+// Grid of the persistent step kernel: one or two blocks per SM (within its
+// occupancy), fewer if a block's tile range would touch more than
+// kMaxBlockTissues tissues.  0 if the kernel cannot run.
+int bstep_grid(const esdc_batch* b, int M)
+{
+    const int occ = b->occ_bstep[M][b->p_threads == 256 ? 0 : 1];
+    if (occ < 1) return 0;
+    long long nb = (long long)b->sms * std::min(occ, b->p_threads == 256 ? 2 : 1);
+    const long long need = ((long long)b->ntiles + b->p_threads / 32 - 1) / (b->p_threads / 32);
+    nb = std::max(1LL, std::min(nb, need));
+    while (nb > 1 && max_block_tissues(b, (int)nb, b->p_threads) > kMaxBlockTissues) --nb;
+    return (int)nb;
+}
+
+cudaError_t launch_cgb(esdc_batch* b, double gfac, const double* rhs, double* x, int* log, cudaStream_t s)
+{
+    BCgArgs a = cg_args(b, gfac, rhs, x, log);
+    void* args[] = {&a};
+    cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const void* k = b->opt.solver == 0 ? (const void*)k_chebb : (const void*)k_cgb;
+    return cudaLaunchCooperativeKernel(k, dim3(b->cg_blocks), dim3(b->cg_threads), args, 0, s);
+}
+
+// Occupancy of the step kernels (queried before any stream capture).
+template <class Model, int M>
+void batch_prime(esdc_batch* b)
+{
+    if (b->occ_node[M]) return;
+    b->occ_node[M] = occupancy(k_node<Model, M, false, true>, 128);
+    b->occ_setup[M] = occupancy(k_setup<Model, M, false, true>, 128);
+    b->occ_res[M] = occupancy(k_residual_b<Model, M>, 128);
+    b->occ_iter[M] = occupancy(k_setup_iter<Model, M>, 128);
+    b->occ_bstep[M][0] = occupancy(k_bstep<Model, M>, 256);
+    b->occ_bstep[M][1] = occupancy(k_bstep<Model, M>, 512);
+}
+
+// One step of every tissue: y_{n+1} of tissue b to yout (may alias yin).
+// from_iter: start from the iterate left in Y by the previous step with the new
+// y_n in yin (a Q^par iteration); otherwise from y^0 = 1 (x) y_n.
+template <class Model, int M>
+cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from_iter, const double* tau, bool keepR,
+                       double dt, int K, cudaStream_t s)
+{
+    const int T = 128;
+    batch_prime<Model, M>(b);
+    const ColloData* C = &b->col[M - 1];
+    StepArgs a = step_args(b, yin, tau, keepR, dt, M);
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(b->flags, 0, sizeof(int), s)) != cudaSuccess) return e;
@@ -892,6 +1033,59 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
     a.yout = yout;
     k_residual_b<Model, M><<<grid_nodes(b, b->occ_res[M], b->node_waves), T, 0, s>>>(a, b->rmax);
     return cudaGetLastError();
+}
+
+// The same step as one persistent cooperative launch (k_bstep).
+template <class Model, int M>
+cudaError_t batch_step_persist(esdc_batch* b, const double* yin, double* yout, bool from_iter, const double* tau,
+                               bool keepR, double dt, int K, cudaStream_t s)
+{
+    batch_prime<Model, M>(b);
+    const ColloData* C = &b->col[M - 1];
+    const int nb = bstep_grid(b, M);
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    StepArgs a = step_args(b, yin, tau, keepR, dt, M);
+    BCgArgs c = cg_args(b, 0.0, b->rhs, nullptr, nullptr);
+    BStepArgs st{};
+    st.K = K;
+    st.from_iter = from_iter ? 1 : 0;
+    st.tile = b->p_tile;
+    for (int i = 0; i <= M; ++i) {
+        st.gfac[i] = dt * C->d[i];
+        st.rho0[i] = i >= 2 ? C->c[i] / C->c[i - 1] : 0.0;
+    }
+    st.G0 = b->G0;
+    st.G1 = b->G1;
+    st.yout = yout;
+    st.Y = b->Y;
+    st.row = (int64_t)b->NS * b->ld;
+    st.rmax = b->rmax;
+    st.cg_log = b->cg_log;
+    st.cg_log_len = b->cg_log_len;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->flags, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->rmax, 0, sizeof(unsigned long long) * 2 * b->NS * b->ntis, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    void* args[] = {&a, &c, &st};
+    return cudaLaunchCooperativeKernel((const void*)k_bstep<Model, M>, dim3(nb), dim3(b->p_threads), args, 0, s);
+}
+
+template <class Model>
+cudaError_t batch_persist_M(esdc_batch* b, const double* yin, double* yout, bool fi, const double* tau, bool keepR,
+                            double dt, int M, int K, cudaStream_t s)
+{
+    switch (M) {
+        case 1: return batch_step_persist<Model, 1>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 2: return batch_step_persist<Model, 2>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 3: return batch_step_persist<Model, 3>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 4: return batch_step_persist<Model, 4>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 5: return batch_step_persist<Model, 5>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 6: return batch_step_persist<Model, 6>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 7: return batch_step_persist<Model, 7>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        case 8: return batch_step_persist<Model, 8>(b, yin, yout, fi, tau, keepR, dt, K, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <class Model>
@@ -930,6 +1124,9 @@ void batch_prime_M(esdc_batch* b, int M)
 cudaError_t batch_launch(esdc_batch* b, const double* yin, double* yout, bool fi, const double* tau, bool keepR,
                          double dt, int M, int K, cudaStream_t s)
 {
+    if (b->persist && b->opt.solver == 0)
+        return b->model == ESDC_MODEL_HH1952 ? batch_persist_M<esdc::HH1952>(b, yin, yout, fi, tau, keepR, dt, M, K, s)
+                                             : batch_persist_M<esdc::SYN19>(b, yin, yout, fi, tau, keepR, dt, M, K, s);
     return b->model == ESDC_MODEL_HH1952 ? batch_step_M<esdc::HH1952>(b, yin, yout, fi, tau, keepR, dt, M, K, s)
                                          : batch_step_M<esdc::SYN19>(b, yin, yout, fi, tau, keepR, dt, M, K, s);
 }
@@ -1333,6 +1530,29 @@ const char* esdc_batch_graph_error(const esdc_batch* b)
     return b ? b->graph_err : "null batch";
 }
 
+int esdc_batch_set_persistent(esdc_batch* b, int on, int threads, int tile)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if ((on != 0 && on != 1) || (threads != 256 && threads != 512) || tile < 32 || tile > 2048 || (tile & 31))
+        return set_berr(b, ESDC_ERR_INVALID_ARG, "persistent launch: on 0/1, threads 256/512, tile a multiple of 32");
+    if (on && b->opt.solver != 0) return set_berr(b, ESDC_ERR_UNSUPPORTED, "the persistent step runs the Chebyshev solves");
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_berr(b, ESDC_ERR_CUDA, "synchronise");
+    drop_graph(b);
+    b->persist = on;
+    b->p_threads = threads;
+    b->p_tile = tile;
+    return ESDC_OK;
+}
+
+int esdc_batch_get_persistent(const esdc_batch* b, int* on, int* threads, int* tile)
+{
+    if (!b) return ESDC_ERR_INVALID_ARG;
+    if (on) *on = b->persist;
+    if (threads) *threads = b->p_threads;
+    if (tile) *tile = b->p_tile;
+    return ESDC_OK;
+}
+
 int esdc_batch_get_shape(const esdc_batch* b, int* node_waves, int* cg_threads, int* cg_blocks)
 {
     if (!b) return ESDC_ERR_INVALID_ARG;
@@ -1367,8 +1587,15 @@ int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, doubl
     if (!y_scratch || reps < 1 || reps > 100 || !std::isfinite(V0))
         return set_berr(b, ESDC_ERR_INVALID_ARG, "bad tuning arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    struct Shape { int waves, threads, per_sm; };
-    const Shape cand[] = {{1, 512, 1}, {2, 512, 1}, {4, 512, 1}, {1, 256, 1}, {1, 256, 2}, {2, 256, 2}, {4, 256, 2}};
+    // Candidates: the launch sequence with its launch shapes (node-kernel waves,
+    // solve block size and blocks per SM), and, with the Chebyshev solves, the
+    // persistent step kernel with its block size and node tile.  None changes
+    // a bit of the results.
+    struct Shape { int persist, waves, threads, per_sm, tile; };
+    const Shape cand[] = {{0, 1, 512, 1, 0}, {0, 2, 512, 1, 0}, {0, 4, 512, 1, 0}, {0, 1, 256, 1, 0},
+                          {0, 1, 256, 2, 0}, {0, 2, 256, 2, 0}, {0, 4, 256, 2, 0},
+                          {1, 0, 512, 0, 32}, {1, 0, 512, 0, 128}, {1, 0, 512, 0, 512},
+                          {1, 0, 256, 0, 32}, {1, 0, 256, 0, 64}, {1, 0, 256, 0, 128}};
     std::vector<double> tv(b->ntis, t);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1376,11 +1603,18 @@ int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, doubl
         return set_berr(b, ESDC_ERR_CUDA, "event creation failed");
     }
     float best = 1e30f;
-    Shape pick = {b->node_waves, b->cg_threads, 0};
-    int pick_blocks = b->cg_blocks;
+    Shape pick = {b->persist, b->node_waves, b->cg_threads, 0, b->p_tile};
+    int pick_blocks = b->cg_blocks, pick_pthreads = b->p_threads;
+    const Shape seq0 = {0, b->node_waves, b->cg_threads, 0, 0};
     int rc = ESDC_OK;
     for (const Shape& c : cand) {
-        if (esdc_batch_set_shape(b, c.waves, c.threads, c.per_sm) != ESDC_OK) continue;
+        if (c.persist) {
+            if (b->opt.solver != 0) continue;
+            if (esdc_batch_set_persistent(b, 1, c.threads, c.tile) != ESDC_OK) continue;
+        } else {
+            if (esdc_batch_set_persistent(b, 0, b->p_threads, b->p_tile) != ESDC_OK) continue;
+            if (esdc_batch_set_shape(b, c.waves, c.threads, c.per_sm) != ESDC_OK) continue;
+        }
         rc = esdc_batch_init_state(b, y_scratch, V0, stream);
         if (rc == ESDC_OK) rc = esdc_batch_sweep(b, y_scratch, tv.data(), dt, M, K, stream);   // capture, warm-up
         if (rc == ESDC_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = ESDC_ERR_CUDA;
@@ -1390,16 +1624,28 @@ int esdc_batch_tune(esdc_batch* b, double* y_scratch, double V0, double t, doubl
         if (rc != ESDC_OK) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; pick = c; pick_blocks = b->cg_blocks; }
+        if (ms < best) {
+            best = ms;
+            pick = c;
+            if (!c.persist) pick_blocks = b->cg_blocks;
+            else pick_pthreads = c.threads;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != ESDC_OK) return rc;
     cudaDeviceSynchronize();
     drop_graph(b);
-    b->node_waves = pick.waves;
-    b->cg_threads = pick.threads;
-    b->cg_blocks = pick_blocks;
+    if (pick.persist) {
+        b->persist = 1;
+        b->p_threads = pick_pthreads;
+        b->p_tile = pick.tile;
+    } else {
+        b->persist = 0;
+        b->node_waves = pick.waves ? pick.waves : seq0.waves;
+        b->cg_threads = pick.threads;
+        b->cg_blocks = pick_blocks;
+    }
     return ESDC_OK;
 }
 

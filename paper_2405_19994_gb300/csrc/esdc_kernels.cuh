@@ -176,6 +176,20 @@ __device__ __forceinline__ bool batch_node(const StepArgs& a, int p, BatchNode& 
     return true;
 }
 
+// The values that change from one launch of a step's sequence to the next:
+// the collocation node i of a node launch, its warm-start weight, the sweep's
+// G buffers (G^k read, G^{k+1} written) and the residual's output.  The
+// launch-sequence kernels take them from their StepArgs; the persistent step
+// kernel of the batches passes its own for each phase.
+struct PhaseArgs {
+    int i;
+    double rho;
+    const double* Gold;
+    double* Gnew;
+    double* yout;
+};
+__device__ __forceinline__ PhaseArgs phase_of(const StepArgs& a) { return PhaseArgs{a.i, a.rho, a.Gold, a.Gnew, a.yout}; }
+
 // Per-step tables of gate g at node p: Lambda_n, dt d_i phi_1(d_i dt Lambda_n)
 // and dt S_ij(dt Lambda_n) (App. A).
 template <int M>
@@ -211,8 +225,9 @@ __device__ __forceinline__ void gate_tables(const StepArgs& a, int g, int NG, do
 // tables as in the plain set-up; G_j = g_n(t_{n,j}, y_j) and FI_j = f_I(y_j) on
 // the iterate (the plain set-up's G^0 with y_j in place of y_n).
 template <class Model, int M>
-__device__ __forceinline__ void setup_iter_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
-                                                const unsigned* on, double D, int p, int ix, int iy, int iz)
+__device__ __forceinline__ void setup_iter_body(const StepArgs& a, const PhaseArgs& ph, const MeshDev& m,
+                                                const StimDev& st, const unsigned* on, double D, int p, int ix,
+                                                int iy, int iz)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
     const int64_t ld = a.m.ld;
@@ -227,7 +242,7 @@ __device__ __forceinline__ void setup_iter_body(const StepArgs& a, const MeshDev
 #pragma unroll 1
     for (int j = 0; j < M; ++j) {
         const double* Yj = a.Y + (int64_t)j * NS * ld;
-        double* Gj = a.Gnew + (int64_t)j * NS * ld;
+        double* Gj = ph.Gnew + (int64_t)j * NS * ld;
         double u[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) u[s] = Yj[s * ld + p];
@@ -250,8 +265,9 @@ __device__ __forceinline__ void setup_iter_body(const StepArgs& a, const MeshDev
 }
 
 template <class Model, int M, bool MIXED>
-__device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
-                                           const unsigned* on, double D, int p, int ix, int iy, int iz)
+__device__ __forceinline__ void setup_body(const StepArgs& a, const PhaseArgs& ph, const MeshDev& m,
+                                           const StimDev& st, const unsigned* on, double D, int p, int ix, int iy,
+                                           int iz)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
     const int64_t ld = a.m.ld;
@@ -275,7 +291,7 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, 
 #pragma unroll
     for (int j = 0; j < M; ++j) {
         double* Yj = a.Y + (int64_t)j * NS * ld;
-        double* Gj = a.Gnew + (int64_t)j * NS * ld;
+        double* Gj = ph.Gnew + (int64_t)j * NS * ld;
         Gj[p] = fi + (stim_at(st, on[j + 1], ix, iy, iz) + mI) * a.inv_Cm;
         Yj[p] = u[0];
 #pragma unroll
@@ -298,7 +314,7 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const MeshDev& m, 
         const double g0 = lam * (us - yinf);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            a.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
+            ph.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
             a.Y[((int64_t)j * NS + s) * ld + p] = us;
         }
         gate_tables<M>(a, g, NG, lam, p);
@@ -315,11 +331,11 @@ __global__ void __launch_bounds__(128, ESDC_SETUP_MINBLOCKS) k_setup(StepArgs a)
         if (!BATCH) {
             int ix, iy, iz;
             node_xyz(a.m, p, ix, iy, iz);
-            setup_body<Model, M, MIXED>(a, a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+            setup_body<Model, M, MIXED>(a, phase_of(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
         } else {
             BatchNode n;
             if (!batch_node(a, p, n)) continue;
-            setup_body<Model, M, MIXED>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+            setup_body<Model, M, MIXED>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
         }
     }
 }
@@ -335,12 +351,13 @@ __global__ void __launch_bounds__(128, ESDC_SETUP_MINBLOCKS) k_setup(StepArgs a)
 // TAU: batched kernels may add the FAS correction tau (a.tau, rows 1..M; the
 // recursive form adds tau_i - tau_{i-1}, tau_0 = 0, to every row of node i).
 template <class Model, int M, bool MIXED, bool TAU = false>
-__device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, const StimDev& st,
-                                          const unsigned* on, double D, int p, int ix, int iy, int iz)
+__device__ __forceinline__ void node_body(const StepArgs& a, const PhaseArgs& ph, const MeshDev& m,
+                                          const StimDev& st, const unsigned* on, double D, int p, int ix, int iy,
+                                          int iz)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
     const int64_t ld = a.m.ld;
-    const int i = a.i;
+    const int i = ph.i;
     const bool eval = i >= 2;                 // G at y_{i-1}^{k+1}
     const bool quad = i <= M;                 // explicit rows of y_i^{k+1}
     const int jm = i - 2;                     // 0-based index of node i-1
@@ -354,8 +371,8 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
     double u[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) u[s] = src[s * ld + p];
-    const double* Gp = a.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
-    double* Gq = a.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
+    const double* Gp = ph.Gold + (int64_t)jm * NS * ld;               // G_{i-1}^k
+    double* Gq = ph.Gnew + (int64_t)jm * NS * ld;                     // G_{i-1}^{k+1}
     double* Yi = a.Y + (int64_t)ii * NS * ld;
     const double dtd = quad ? a.dtd[i] : 0.0;
 
@@ -389,11 +406,11 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
         // node just received, V_i^k + rho (V_{i-1}^{k+1} - V_{i-1}^k).  Only the
         // starting point of CG changes; the solution is the same.
         const double vik = Yi[p];
-        if (eval) Yi[p] = fma(a.rho, u[0] - a.Vprev[p], vik);
+        if (eval) Yi[p] = fma(ph.rho, u[0] - a.Vprev[p], vik);
         a.Vprev[p] = vik;
         double q = u[0];
 #pragma unroll
-        for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], a.Gold[(int64_t)j * NS * ld + p], q);
+        for (int j = 0; j < M; ++j) q = fma(a.dS0[ii][j], ph.Gold[(int64_t)j * NS * ld + p], q);
         double rv = fma(dtd, dlt0 - a.FI[(int64_t)ii * ld + p], q);
         if (TAU) rv += dtau(0);                // (x + 0.0 is not x in IEEE arithmetic: no add without TAU)
         a.rhs[p] = rv;
@@ -402,7 +419,7 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
             const double dl = eval ? ha[s - 1] - Gp[s * ld + p] : 0.0;
             double qa = u[s];
 #pragma unroll
-            for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], a.Gold[((int64_t)j * NS + s) * ld + p], qa);
+            for (int j = 0; j < M; ++j) qa = fma(a.dS0[ii][j], ph.Gold[((int64_t)j * NS + s) * ld + p], qa);
             double ya = fma(dtd, dl, qa);
             if (TAU) ya += dtau(s);
             Yi[s * ld + p] = ya;
@@ -433,7 +450,7 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const MeshDev& m, c
 #pragma unroll
             for (int j = 0; j < M; ++j)
                 qg = fma(a.S[(((int64_t)ii * M + j) * NG + g) * ld + p],
-                         a.Gold[((int64_t)j * NS + s) * ld + p], qg);
+                         ph.Gold[((int64_t)j * NS + s) * ld + p], qg);
             double yg = fma(a.PHI[((int64_t)ii * NG + g) * ld + p], dl, qg);
             if (TAU) yg += dtau(s);
             Yi[s * ld + p] = yg;
@@ -448,11 +465,11 @@ __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
         if (!BATCH) {
             int ix, iy, iz;
             node_xyz(a.m, p, ix, iy, iz);
-            node_body<Model, M, MIXED>(a, a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+            node_body<Model, M, MIXED>(a, phase_of(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
         } else {
             BatchNode n;
             if (!batch_node(a, p, n)) continue;
-            node_body<Model, M, MIXED, true>(a, n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+            node_body<Model, M, MIXED, true>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
         }
     }
 }
@@ -474,7 +491,8 @@ __device__ __forceinline__ unsigned long long abs_bits(double v)
 }
 
 template <class Model, int M, bool TAU = false>
-__device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, double& rmax, double& ymax)
+__device__ __forceinline__ bool residual_state(const StepArgs& a, const PhaseArgs& ph, int p, int s, double& rmax,
+                                               double& ymax)
 {
     constexpr int NS = Model::NS, NA = Model::NA, NG = Model::NG;
     const int64_t ld = a.m.ld;
@@ -489,7 +507,7 @@ __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, 
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
-            q = fma(sij, a.Gold[((int64_t)j * NS + s) * ld + p], q);
+            q = fma(sij, ph.Gold[((int64_t)j * NS + s) * ld + p], q);
         }
         const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
         r += q - (yi - yprev);
@@ -501,7 +519,7 @@ __device__ __forceinline__ bool residual_state(const StepArgs& a, int p, int s, 
         yb = max(yb, abs_bits(yi));
     }
     // y_n was read above by this thread only, so y may alias y_{n+1}.
-    a.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
+    ph.yout[s * ld + p] = a.Y[((int64_t)(M - 1) * NS + s) * ld + p];
     rmax = __longlong_as_double((long long)rb);
     ymax = __longlong_as_double((long long)yb);
     return rb < 0x7ff0000000000000ULL && yb < 0x7ff0000000000000ULL;
@@ -519,7 +537,7 @@ __global__ void __launch_bounds__(128) k_residual(StepArgs a)
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
             double rmax, ymax;
-            bad |= !residual_state<Model, M>(a, p, s, rmax, ymax);
+            bad |= !residual_state<Model, M>(a, phase_of(a), p, s, rmax, ymax);
             // shared-memory max of non-negative doubles through their bit patterns
             atomicMax((unsigned long long*)&smax[s], (unsigned long long)__double_as_longlong(rmax));
             atomicMax((unsigned long long*)&smax[NS + s], (unsigned long long)__double_as_longlong(ymax));

@@ -108,6 +108,8 @@ def lib() -> C.CDLL:
             "esdc_batch_graph_active": (C.c_int, [_VP]),
             "esdc_batch_graph_error": (C.c_char_p, [_VP]),
             "esdc_batch_set_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+            "esdc_batch_set_persistent": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+            "esdc_batch_get_persistent": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "esdc_batch_get_shape": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "esdc_batch_tune": (C.c_int, [_VP, _VP, _D, _D, _D, C.c_int, C.c_int, C.c_int, _VP]),
         }
@@ -474,6 +476,16 @@ class Batch:
         w, t, b = C.c_int(), C.c_int(), C.c_int()
         self._check(lib().esdc_batch_get_shape(self._b, C.byref(w), C.byref(t), C.byref(b)))
         return w.value, t.value, b.value
+
+    def set_persistent(self, on: bool, threads: int = 512, tile: int = 128):
+        """esdc_batch_set_persistent: one persistent launch per step (on) or the launch sequence."""
+        self._check(lib().esdc_batch_set_persistent(self._b, int(on), int(threads), int(tile)))
+
+    def persistent(self):
+        """(on, threads, tile) of the persistent launch."""
+        o, t, n = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().esdc_batch_get_persistent(self._b, C.byref(o), C.byref(t), C.byref(n)))
+        return bool(o.value), t.value, n.value
 
     def tune(self, y_scratch, V0: float, t: float, dt: float, M: int, K: int, reps: int = 3, stream=None):
         self._check(lib().esdc_batch_tune(self._b, _ptr(y_scratch), V0, t, dt, M, K, reps, _stream(stream)))

@@ -30,10 +30,12 @@ def small_batch():
     return wls
 
 
-def run_batch(wls, steps, shape=None, graph=True, t0=0.0, solver="auto"):
+def run_batch(wls, steps, shape=None, graph=True, t0=0.0, solver="auto", persistent=None, want_iters=False):
     b = P.Batch.from_workloads(wls, M_max=3, solver=solver)
     if shape:
         b.set_shape(*shape)
+    if persistent:
+        b.set_persistent(True, *persistent)
     b.set_graph(graph)
     y = b.new_state()
     b.init_state(y, -75.0)
@@ -47,7 +49,10 @@ def run_batch(wls, steps, shape=None, graph=True, t0=0.0, solver="auto"):
     torch.cuda.synchronize()
     out = [b.tissue(y, k).cpu().numpy().copy() for k in range(len(wls))]
     graph_used = (b.graph_active(), b.graph_error())
+    iters = b.stats(wls[0].K, wls[0].M).copy() if want_iters else None
     b.close()
+    if want_iters:
+        return out, r, graph_used, iters
     return out, r, graph_used
 
 
@@ -107,6 +112,52 @@ def test_batch_results_independent_of_launch_shape_and_graph(shape, graph):
         assert not used[0]
     else:
         assert used[0], "the step was not recorded in a CUDA graph: " + used[1]
+
+
+# ---------------------------------------------------------------- one persistent launch per step
+
+@pytest.mark.parametrize("threads,tile,graph", [(512, 32, True), (512, 128, False), (256, 512, True),
+                                                (512, 2048, True), (256, 64, False)])
+def test_persistent_step_bitwise_equals_launch_sequence(threads, tile, graph):
+    """The whole step in one cooperative kernel (set-up, node phases, the
+    Chebyshev solves of all tissues, residual) against the launch sequence:
+    identical bit for bit, solve iteration counts included, whatever the block
+    size, node tile or graph."""
+    wls = small_batch()
+    ref, rr, _, it_ref = run_batch(wls, 5, want_iters=True)
+    got, rg, used, it = run_batch(wls, 5, graph=graph, persistent=(threads, tile), want_iters=True)
+    for k in range(len(wls)):
+        assert np.array_equal(ref[k], got[k]), (threads, tile, graph, k)
+    assert np.array_equal(rr, rg)
+    assert np.array_equal(it_ref, it)
+    assert used[0] == graph, used[1]
+
+
+def test_persistent_qpar_and_tau_bitwise_equal_launch_sequence():
+    """Q^par (set-up from the iterate) and the FAS sweep with tau run through the
+    persistent kernel exactly as through the launch sequence."""
+    P_, iters = 4, 3
+    w, m, y0, t0 = qpar_setup(P_)
+    outs = []
+    for persist in (False, True):
+        b = P.Batch.from_workloads([w] * P_, M_max=w.M)
+        if persist:
+            b.set_persistent(True, 512, 128)
+        yin, yout = b.new_state(), b.new_state()
+        b.tissue(yin, 0).copy_(torch.from_numpy(y0))
+        b.qpar(yin, yout, t0, w.dt, w.M, iters)
+        assert b.residual()[0] == 0
+        outs.append(yout.clone())
+        b.close()
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_persistent_rejected_with_cg():
+    b = P.Batch.from_workloads(small_batch()[:2], M_max=3, solver="cg")
+    with pytest.raises(P.EsdcError) as e:
+        b.set_persistent(True)
+    assert e.value.code == -6
+    b.close()
 
 
 def test_batch_matches_single_tissue_solver():
@@ -391,6 +442,37 @@ def test_hsdc_rejects_bad_levels():
 
 
 @pytest.mark.slow
+@pytest.mark.slow
+def test_full_batch_persistent_matches_oracle():
+    """The full 64-tissue batch (5.1M nodes) with one persistent launch per step
+    (recorded graph): after 3 steps from rest, the three smallest tissues
+    against the oracle, element by element."""
+    wls = I.hh_batch()
+    w0 = wls[0]
+    b = P.Batch.from_workloads(wls, M_max=w0.M)
+    b.set_persistent(True, 512, 128)
+    y = b.new_state()
+    b.init_state(y, w0.V0)
+    t = 0.0
+    for _ in range(3):
+        b.sweep(y, t, w0.dt, w0.M, w0.K)
+        t += w0.dt
+    assert b.residual()[0] == 0
+    assert b.graph_active()
+    torch.cuda.synchronize()
+    for k in sorted(range(len(wls)), key=lambda j: wls[j].n_nodes)[:3]:
+        w = wls[k]
+        m = O.Monodomain(w)
+        yo = m.init_state()
+        to = 0.0
+        for _ in range(3):
+            yo, _, _, _ = m.step(yo, to, w.dt, w.M, w.K)
+            to += w.dt
+        got = b.tissue(y, k).cpu().numpy()
+        assert np.abs(got - yo).max() < 1e-12 * max(1.0, np.abs(yo).max()), (k, w.name)
+    b.close()
+
+
 def test_full_batch_in_bench_configuration_matches_oracle():
     """The 64-tissue batch of the batching form at full size (5.1M nodes), in the
     launch configuration the bench ends up with (recorded graph, 4 node waves,
