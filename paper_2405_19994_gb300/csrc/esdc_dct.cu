@@ -56,7 +56,7 @@ struct AxisArgs {
     int inner;              // element stride of the axis (1 for x)
     int lpt, loglpt;        // lines per tile (a power of two, at least 2)
     int G;                  // threads per line pair (FFT path)
-    const double2* tw;      // [n/2] e^{-2 pi i k/n}
+    const double2* tw;      // [n] e^{-2 pi i k/n}
     const double2* csh;     // [n/2 + 1] (cos, sin)(pi k/(2n)) / 2 (forward)
     const double2* cs;      // [n/2 + 1] (cos, sin)(pi k/(2n))     (inverse)
     const double* dmat;     // dense path: [n][n], row = output index
@@ -103,31 +103,69 @@ __device__ __forceinline__ void pair_sync(int G)
     else __syncwarp();
 }
 
-// Radix-2 Stockham FFT (decimation in time) of n = 2^logn points held by the
-// G threads g = 0..G-1 of a line pair; x -> y ping-pong, returns the buffer
-// that holds the result.  Stage s combines sub-transforms of length Ns = 2^s:
-//   a = x[j], b = x[j + n/2], w = e^{-2 pi i (j mod Ns)/(2 Ns)},
-//   y[2(j - k) + k] = a + w b, y[2(j - k) + k + Ns] = a - w b, k = j mod Ns,
-// the second output as 2a - (a + w b) (six FMAs per butterfly; the first
-// stage, where w = 1 for every j, takes four additions).  Threads with
-// active = false run the same loop without butterflies, so that every thread
+// Stockham FFT (decimation in time) of n = 2^logn points held by the G
+// threads g = 0..G-1 of a line pair; x -> y ping-pong, returns the buffer that
+// holds the result.  Radix-4 stages while they fit, then one radix-2 stage if
+// logn is odd.  A radix-4 stage combines sub-transforms of length Ns:
+//   v_r = x[j + r n/4], w_r = e^{-2 pi i r k/(4 Ns)}, k = j mod Ns,
+//   t0 = v0 + w2 v2, t1 = 2 v0 - t0, t2 = w1 v1 + w3 v3, t3 = 2 w1 v1 - t2,
+//   y[4(j - k) + k + q Ns] = t0 + t2, t1 - i t3, t0 - t2, t1 + i t3  (q = 0..3),
+// 24 FP64 operations per four points (the twiddle products fused into the
+// sums); the first stage (w = 1) takes 16 additions.  The radix-2 stage is
+//   y[2(j - k) + k] = a + w b, y[2(j - k) + k + Ns] = 2a - (a + w b).
+// tw: e^{-2 pi i m/n}, m = 0..n-1, in shared memory.  Threads with
+// active = false run the same loops without butterflies, so that every thread
 // meets the same barriers.
 __device__ __forceinline__ double2* fft_pow2(double2* x, double2* y, int n, int logn, int g, int G, bool active,
-                                             const double2* __restrict__ tw)
+                                             const double2* tw)
 {
-    const int h = n >> 1;
-    for (int s = 0; s < logn; ++s) {
-        const int Ns = 1 << s;
+    const int q4 = n >> 2;
+    int Ns = 1;
+    for (int s = 0; s + 2 <= logn; s += 2) {
+        const int stride = n >> (s + 2);                 // n / (4 Ns)
+        for (int j = active ? g : q4; j < q4; j += G) {
+            const int k = j & (Ns - 1);
+            const double2 v0 = x[j], v1 = x[j + q4], v2 = x[j + 2 * q4], v3 = x[j + 3 * q4];
+            double t0r, t0i, t1r, t1i, t2r, t2i, t3r, t3i;
+            if (s == 0) {
+                t0r = v0.x + v2.x; t0i = v0.y + v2.y;
+                t1r = v0.x - v2.x; t1i = v0.y - v2.y;
+                t2r = v1.x + v3.x; t2i = v1.y + v3.y;
+                t3r = v1.x - v3.x; t3i = v1.y - v3.y;
+            } else {
+                const double2 w1 = tw[k * stride], w2 = tw[2 * k * stride], w3 = tw[3 * k * stride];
+                const double b1r = fma(w1.x, v1.x, -w1.y * v1.y), b1i = fma(w1.x, v1.y, w1.y * v1.x);
+                t0r = fma(w2.x, v2.x, fma(-w2.y, v2.y, v0.x));
+                t0i = fma(w2.x, v2.y, fma(w2.y, v2.x, v0.y));
+                t1r = fma(2.0, v0.x, -t0r);
+                t1i = fma(2.0, v0.y, -t0i);
+                t2r = fma(w3.x, v3.x, fma(-w3.y, v3.y, b1r));
+                t2i = fma(w3.x, v3.y, fma(w3.y, v3.x, b1i));
+                t3r = fma(2.0, b1r, -t2r);
+                t3i = fma(2.0, b1i, -t2i);
+            }
+            const int idx = ((j - k) << 2) + k;
+            y[idx] = make_double2(t0r + t2r, t0i + t2i);
+            y[idx + Ns] = make_double2(t1r + t3i, t1i - t3r);
+            y[idx + 2 * Ns] = make_double2(t0r - t2r, t0i - t2i);
+            y[idx + 3 * Ns] = make_double2(t1r - t3i, t1i + t3r);
+        }
+        pair_sync(G);
+        double2* t = x; x = y; y = t;
+        Ns <<= 2;
+    }
+    if (logn & 1) {                                      // the last stage: radix 2, Ns = n/2
+        const int h = n >> 1;
         for (int j = active ? g : h; j < h; j += G) {
             const int k = j & (Ns - 1);
             const double2 a = x[j], b = x[j + h];
             const int idx = ((j - k) << 1) + k;
             double cr, ci, dr, di;
-            if (s == 0) {
+            if (Ns == 1) {
                 cr = a.x + b.x; ci = a.y + b.y;
                 dr = a.x - b.x; di = a.y - b.y;
             } else {
-                const double2 w = __ldg(tw + (k << (logn - 1 - s)));
+                const double2 w = tw[k];                 // e^{-2 pi i k/(2 Ns)} = e^{-2 pi i k/n}
                 cr = fma(w.x, b.x, fma(-w.y, b.y, a.x));
                 ci = fma(w.x, b.y, fma(w.y, b.x, a.y));
                 dr = fma(2.0, a.x, -cr);
@@ -152,11 +190,14 @@ __device__ __forceinline__ int makhoul_pos(int i, int n) { return (i & 1) ? n - 
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_dct_fft(AxisArgs a)
 {
-    extern __shared__ double2 sm[];
+    extern __shared__ double2 smem_all[];
     const int n = a.n, pitch = n + 1, P = a.lpt >> 1;
+    double2* stw = smem_all;                            // the twiddles e^{-2 pi i m/n}, m < n
+    double2* sm = smem_all + n;                         // then the two tile buffers
     const size_t bstride = (size_t)P * pitch;           // buffer c starts at sm + c * bstride
     __shared__ int base[32];
     tile_bases(a, blockIdx.x * a.lpt, base);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) stw[m] = __ldg(a.tw + m);
     __syncthreads();
     const int tile_elems = a.lpt * n;
 
@@ -196,8 +237,8 @@ __global__ void __launch_bounds__(256) k_dct_fft(AxisArgs a)
         cur = 1;
     }
     double2* z = fft_pow2(sm + cur * bstride + (size_t)p * pitch, sm + (cur ^ 1) * bstride + (size_t)p * pitch, n,
-                          a.logn, g, a.G, active, a.tw);
-    cur = (cur + a.logn) & 1;                             // the FFT ends in this buffer
+                          a.logn, g, a.G, active, stw);
+    cur = (cur + (a.logn >> 1) + (a.logn & 1)) & 1;     // the FFT ends in this buffer (one swap per stage)
     // the other buffer takes the real output rows: row l at pitch n + 1 doubles
     double* out = reinterpret_cast<double*>(sm + (cur ^ 1) * bstride);
     if (active) {
@@ -426,8 +467,8 @@ cudaError_t axis_tables(DctAxisDev& ax, int n)
     ax.logn = log2_exact(n);
     if (n == 1) return cudaSuccess;
     if (ax.logn >= 0) {
-        std::vector<double2> tw(n / 2), csh(n / 2 + 1), cs(n / 2 + 1);
-        for (int k = 0; k < n / 2; ++k)
+        std::vector<double2> tw(n), csh(n / 2 + 1), cs(n / 2 + 1);
+        for (int k = 0; k < n; ++k)
             tw[k] = make_double2(std::cos(2.0 * M_PI * k / n), -std::sin(2.0 * M_PI * k / n));
         for (int k = 0; k <= n / 2; ++k) {
             const double c = std::cos(M_PI * k / (2.0 * n)), s = std::sin(M_PI * k / (2.0 * n));
@@ -464,27 +505,28 @@ void axis_free(DctAxisDev& ax)
 
 int g_sms = 0;
 
-// Launch shape of one axis pass.  FFT path: n/2 threads per line pair (one
-// butterfly per thread and stage; at most 256), as many pairs per block as fit
-// in 256 threads, at most 16 (32 lines).  FP64 latency, not the FP64 pipe,
-// bounds a pass when fewer threads run, so the pass keeps N/4 threads in
-// flight.  Dense path: 128 threads per block of up to 32 lines.  Both keep
-// the tile's shared memory below kDctSmemLimit.
+// Launch shape of one axis pass.  FFT path: n/4 threads per line pair (one
+// radix-4 butterfly per thread and stage; at most 256), as many pairs per
+// block as fit in 256 threads, at most 16 (32 lines); a 128-point line pair is
+// one warp, so its stages meet at warp barriers.  Dense path: 128 threads per
+// block of up to 32 lines.  Both keep the tile's shared memory below
+// kDctSmemLimit.
 void axis_shape(const DctAxisDev& ax, int lines, AxisArgs& a, int& threads, size_t& smem, int& tiles)
 {
     const int n = ax.n;
     int lpt;
     if (ax.logn >= 0) {
-        int G = n / 2;
+        int G = n / 4;
+        if (G < 1) G = 1;
         if (G > 256) G = 256;
         int P = 256 / G;
         if (P > 16) P = 16;
         lpt = 2 * P;
-        while (lpt > 2 && (size_t)lpt * (n + 1) * 16 > (size_t)kDctSmemLimit) lpt >>= 1;
+        while (lpt > 2 && (size_t)(lpt * (n + 1) + n) * 16 > (size_t)kDctSmemLimit) lpt >>= 1;
         a.G = G;
         threads = (lpt / 2) * G;
         threads = (threads + 31) / 32 * 32;
-        smem = (size_t)lpt * (n + 1) * sizeof(double2);        // 2 buffers x lpt/2 pairs x (n+1) complex
+        smem = (size_t)(lpt * (n + 1) + n) * sizeof(double2);   // twiddles + 2 buffers x lpt/2 pairs x (n+1)
     } else {
         lpt = 32;
         while (lpt > 2 && (size_t)lpt * (n + 1) * 16 > (size_t)kDctSmemLimit) lpt >>= 1;
