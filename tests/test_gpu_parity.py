@@ -105,6 +105,29 @@ def test_ionic_pointwise(model):
 
 
 @pytest.mark.parametrize("model", [I.MODEL_HH1952, I.MODEL_SYN19])
+def test_gate_table_range_and_edges(model):
+    """The gate functions come from the handle's V table on [-140, 100) mV and
+    from the direct formulas outside it: both against the oracle from -300 to
+    +200 mV, at the table's edges and at points 1e-9 mV either side of them,
+    and a NaN potential stays NaN."""
+    wl = I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()
+    edges = [-140.0, -140.0 + 1e-9, -140.0 - 1e-9, -139.5, -0.5, 0.0, 99.5, 100.0 - 1e-9, 100.0, 100.0 + 1e-9]
+    V = np.concatenate([np.linspace(-300.0, 200.0, 1001), edges, [np.nan]])
+    wl = wl.with_mesh(len(V), 1, 1)
+    s = P.Solver.from_workload(wl)
+    y = I.random_state(wl, seed=13)
+    y[0] = V
+    fE, lam, yinf = (from_dev(s, t) for t in s.ionic(to_dev(s, y)))
+    for p in range(wl.n_nodes - 1):
+        f0, l0, i0 = O.ionic_point(model, wl.params, y[:, p])
+        np.testing.assert_allclose(lam[:, p], l0, rtol=4e-14, atol=0, err_msg=f"V={V[p]}")
+        np.testing.assert_allclose(yinf[:, p], i0, rtol=4e-14, atol=1e-300, err_msg=f"V={V[p]}")
+        np.testing.assert_allclose(fE[:, p], f0, rtol=4e-14, atol=1e-15, err_msg=f"V={V[p]}")
+    gates = slice(1 + (0 if model == I.MODEL_HH1952 else 6), None)
+    assert np.all(np.isnan(lam[gates, -1])) and np.all(np.isnan(yinf[gates, -1]))
+
+
+@pytest.mark.parametrize("model", [I.MODEL_HH1952, I.MODEL_SYN19])
 def test_init_state(model):
     wl = (I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()).with_mesh(7, 3, 2)
     s = P.Solver.from_workload(wl)
