@@ -63,7 +63,7 @@ FP64_ISSUE_PEAK = 152 * 2 * 2.07e9
 # step; node: per sweep (M + 1 launches); DCT solve: four transform passes
 # and the tridiagonal z solve; Chebyshev and CG: per iteration; residual: per
 # step.
-CLASS_FP64_OPS = {"setup": 2949.1, "node_sweep": 1642.8, "dct_solve": 56.3, "cheb_iter": 12.2, "cg_iter": 15.0,
+CLASS_FP64_OPS = {"setup": 2949.1, "node_sweep": 1642.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
                   "residual": 703.0}
 CLASS_BYTES = {"setup": 3256.0, "node_sweep": 7464.0, "dct_solve": 120.0, "cheb_iter": 48.0, "cg_iter": 96.0,
                "residual": 2904.0}
@@ -335,7 +335,7 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k][0])
     per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
     it_mean = sum(cg_iters) / max(len(cg_iters), 1)
-    solver_kind = "dct" if (args.solver == "dct" or (args.solver == "auto" and args.precision == "fp64")) else "iter"
+    solver_kind = "dct" if solver.solver_in_use() == "dct" else "iter"
     roof = {"kernel": dom}
     if dom == "node" and M in NODE_FLOPS_PER_SWEEP and args.precision == "fp64":
         flops = NODE_FLOPS_PER_SWEEP[M] * N / (M + 1)           # per launch, average over a sweep
@@ -1284,7 +1284,7 @@ def main():
                     help="mixed: the precision form (FP32 ionic model, FP64 elsewhere)")
     ap.add_argument("--solver", choices=["auto", "cg", "dct", "cheb"], default="auto",
                     help="diffusion solves (headline, precision, batch and fas forms): auto (the DCT-II direct solve "
-                         "for the scalar sigma on the FP64 path, else as cheb), cheb (Chebyshev semi-iteration on a "
+                         "for the scalar sigma on the FP64 path where its transforms are cheap, else as cheb), cheb (Chebyshev semi-iteration on a "
                          "known spectral interval, else CG), cg (Jacobi-PCG) or dct (the DCT-II direct solve; "
                          "headline form only)")
     ap.add_argument("--form", choices=["plain", "precision", "batch", "adjoint", "fas", "sheet", "peaks"],

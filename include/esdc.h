@@ -85,9 +85,10 @@ typedef struct {
                           same tol_cg; state, coefficient tables, quadrature and
                           residual stay FP64                                       */
     int    solver;     /* diffusion solves of the sweep and esdc_diffusion_solve:
-                          0 = automatic: with precision 0 and the scalar sigma
-                          the DCT-II direct solve of 2 (exact; the handle holds
-                          its tables from esdc_create on), otherwise as 3;
+                          0 = automatic: with precision 0, the scalar sigma and
+                          cheap transforms (esdc_get_solver) the DCT-II direct
+                          solve of 2 (exact; the handle holds its tables from
+                          esdc_create on), otherwise as 3;
                           3 = the Chebyshev semi-iteration on an
                           interval holding the spectrum of the operator of
                           esdc_diffusion_solve: for the scalar sigma exactly
@@ -174,11 +175,25 @@ int esdc_set_stimulus(esdc_handle* h, int nbox, const int* box, const double* am
  * (-v_{i-2} + 16 v_{i-1} - 30 v_i + 16 v_{i+1} - v_{i+2}) / (12 h^2), ghost cells
  * mirrored about the boundary faces (zero flux; the operator stays symmetric
  * and is diagonalised by DCT-II).  Order 4 needs the scalar sigma and the FP64
- * path; its solves use the one-node-per-thread CG with Jacobi weights from the
- * operator's diagonal.  Synchronises the device.
+ * path; its solves are the ones options.solver selects (DCT-II and Chebyshev
+ * on the exact fourth-order spectrum; the CG with Jacobi weights from the
+ * operator's diagonal).  Synchronises the device.
  * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
  */
 int esdc_set_stencil_order(esdc_handle* h, int order);
+
+/*
+ * The diffusion solver the handle's solves take now (options.solver resolved
+ * against the mesh, the conductivity and the stencil order): *solver = 2 for
+ * the DCT-II direct solve, 3 for the Chebyshev semi-iteration (with its CG
+ * fallback when g is too small for the interval, and the precision form's
+ * refinement), 1 for the CG.  The automatic choice (0) takes the DCT-II with
+ * precision 0 and the scalar sigma while its transforms are cheap: every
+ * transformed axis (x and y; z too for the fourth order) has power-of-two
+ * length, except dense axes of total length at most 32.  Host only.
+ * Errors: INVALID_ARG (null h or solver).
+ */
+int esdc_get_solver(const esdc_handle* h, int* solver);
 
 /*
  * Heterogeneous isotropic conductivity: sigma[p] (host array of N values,

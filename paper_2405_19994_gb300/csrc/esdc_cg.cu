@@ -596,7 +596,7 @@ cudaError_t esdc_cg_launch(const MeshDev& mesh, const CgWork& w, double g, const
 {
     // the DCT-II solve: requested (2), or automatic (0) on the scalar sigma
     // where the handle holds its tables
-    if (solver == 2 || (solver == 0 && w.dct && !mesh.lay && !mesh.sig)) {
+    if (solver == 2 || (solver == 0 && w.dct && w.dct->cheap && !mesh.lay && !mesh.sig)) {
         if (!w.dct) return cudaErrorInvalidValue;
         return esdc_dct_launch(mesh, w, g, b, x, iter_log, flags, s);
     }

@@ -82,12 +82,14 @@ struct StimDev {
 // The gate functions tabulated in V (esdc_vtab.cpp; SYN19 and HH1952): ESDC_VTAB_N
 // intervals of ESDC_VTAB_W mV from ESDC_VTAB_VLO, a polynomial of degree
 // ESDC_VTAB_NC - 1 in t = V - V_mid per function and interval; a row holds
-// V_mid, then per gate the coefficients of w_inf and of Lambda.
+// V_mid and a pad (16-byte alignment), then per gate the coefficient pairs
+// (w_inf, Lambda) of t^0, t^1, ..., so that one 16-byte load feeds both
+// Horner recurrences.
 #define ESDC_VTAB_VLO (-140.0)
 #define ESDC_VTAB_W 1.0
 #define ESDC_VTAB_N 240
 #define ESDC_VTAB_NC 9
-#define ESDC_VTAB_ROW (1 + 2 * ESDC_NGMAX * ESDC_VTAB_NC)
+#define ESDC_VTAB_ROW (2 + 2 * ESDC_NGMAX * ESDC_VTAB_NC)
 #define ESDC_VTAB_TOL 4e-15        // refuse a table whose FP64 evaluation misses by more
 struct ModelDev {
     double p[ESDC_NPMAX];
@@ -137,6 +139,7 @@ struct DctDev {
     int nslot = 0, next_slot = 0;
     double gkey[ESDC_DCT_SLOTS] = {};
     bool used[ESDC_DCT_SLOTS] = {};
+    bool cheap = false;             // esdc_dct_cheap for the current stencil order (the automatic choice)
 };
 
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).
@@ -151,6 +154,13 @@ struct CgWork {
     DctDev* dct = nullptr;          // set when options.solver = 2
 };
 
+// Whether the DCT solve costs less than an iterative one on this mesh for the
+// given stencil order: every transformed axis (x and y; z for the fourth
+// order) is of power-of-two length (FFT, about 13 FP64 operations per value
+// and pass) or dense, and the dense axes together cost at most 32 FMAs per
+// value and pass (a dense axis of length n costs n).  The automatic solver
+// choice takes the DCT only then.
+bool esdc_dct_cheap(const MeshDev& m, int order);
 // Whether the DCT solve takes this mesh (every axis length does, up to the
 // shared-memory size of a dense tile).
 bool esdc_dct_supported(const MeshDev& m);

@@ -14,14 +14,20 @@
 
 namespace esdc {
 
-// A polynomial of the gate table (esdc_vtab.cpp) at t = V - V_mid: Horner's
-// rule, ESDC_VTAB_NC - 1 FMAs.
-__device__ __forceinline__ double vt_poly(const double* __restrict__ c, double t)
+// The two polynomials of one gate in the gate table (esdc_vtab.cpp) at
+// t = V - V_mid: Horner's rule, ESDC_VTAB_NC - 1 FMAs each, on the interleaved
+// coefficient pairs c[k] = (w_inf, Lambda) of t^k.
+__device__ __forceinline__ void vt_poly2(const double2* __restrict__ c, double t, double& w, double& l)
 {
-    double r = __ldg(c + ESDC_VTAB_NC - 1);
+    const double2 top = __ldg(c + ESDC_VTAB_NC - 1);
+    w = top.x;
+    l = top.y;
 #pragma unroll
-    for (int k = ESDC_VTAB_NC - 2; k >= 0; --k) r = fma(r, t, __ldg(c + k));
-    return r;
+    for (int k = ESDC_VTAB_NC - 2; k >= 0; --k) {
+        const double2 ck = __ldg(c + k);
+        w = fma(w, t, ck.x);
+        l = fma(l, t, ck.y);
+    }
 }
 
 // x/(e^x - 1), removable singularity at x = 0.  |x| < 1/2: its Taylor series
@@ -115,9 +121,7 @@ struct HH1952 {
                                 double& yinf)
     {
         if (c.row) {
-            const double* cw = c.row + 1 + q * (2 * ESDC_VTAB_NC);
-            yinf = vt_poly(cw, c.t);
-            lam = vt_poly(cw + ESDC_VTAB_NC, c.t);
+            vt_poly2(reinterpret_cast<const double2*>(c.row + 2) + q * ESDC_VTAB_NC, c.t, yinf, lam);
             return;
         }
         gate(mp, q, V, lam, yinf);
@@ -299,9 +303,7 @@ struct SYN19 {
                                 double& yinf)
     {
         if (c.row) {
-            const double* cw = c.row + 1 + q * (2 * ESDC_VTAB_NC);
-            yinf = vt_poly(cw, c.t);
-            lam = vt_poly(cw + ESDC_VTAB_NC, c.t);
+            vt_poly2(reinterpret_cast<const double2*>(c.row + 2) + q * ESDC_VTAB_NC, c.t, yinf, lam);
             return;
         }
         gate(mp, q, V, lam, yinf);

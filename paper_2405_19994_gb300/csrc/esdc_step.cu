@@ -357,8 +357,10 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     cudaMemset(h->flags, 0, sizeof(int));
     cudaMemset(h->cg_log, 0, sizeof(int) * h->cg_log_len);
     // the DCT-II tables: for the DCT solve itself (2) and for the automatic
-    // choice on the FP64 path (0), which takes it while sigma is scalar
-    const bool dct_auto = o.solver == 0 && o.precision == 0 && esdc_dct_supported(h->mesh);
+    // choice on the FP64 path (0), which takes it while sigma is scalar and the
+    // transforms are cheap (x and y; the fourth order, set later, adds z)
+    const bool dct_auto = o.solver == 0 && o.precision == 0 && esdc_dct_supported(h->mesh) &&
+                          esdc_dct_cheap(h->mesh, 2);
     if (o.solver == 2 || dct_auto) {
         if (!esdc_dct_supported(h->mesh)) return fail(ESDC_ERR_UNSUPPORTED);
         const cudaError_t e = esdc_dct_create(h->mesh, o.M_max, &h->dct);
@@ -485,6 +487,15 @@ int esdc_set_stencil_order(esdc_handle* h, int order)
     CUDA_TRY(h, cudaGetLastError());
     if (h->cg.dct) CUDA_TRY(h, esdc_dct_set_order(h->mesh, &h->dct));
     CUDA_TRY(h, cudaDeviceSynchronize());
+    return ESDC_OK;
+}
+
+int esdc_get_solver(const esdc_handle* h, int* solver)
+{
+    if (!h || !solver) return ESDC_ERR_INVALID_ARG;
+    const int o = h->opt.solver;
+    if (o != 0) *solver = o;
+    else *solver = (h->cg.dct && h->dct.cheap && !h->mesh.lay && !h->mesh.sig) ? 2 : 3;
     return ESDC_OK;
 }
 

@@ -20,8 +20,8 @@
 // Horner evaluation misses them by more than ESDC_VTAB_TOL.  The oracle keeps
 // the direct formulas; the table is a way of computing the same functions.
 //
-// Row i of the table (ESDC_VTAB_ROW doubles): V_mid,i, then for each gate q
-// the 9 coefficients of w_inf,q and the 9 of Lambda_q, lowest power first.
+// Row i of the table (ESDC_VTAB_ROW doubles): V_mid,i, a zero pad, then for
+// each gate q the 9 coefficient pairs (w_inf,q, Lambda_q) of t^0, ..., t^8.
 #include <cmath>
 #include <vector>
 
@@ -80,10 +80,12 @@ void cheb_monomial(F f, LD m, LD h, int d, LD* out)
     }
 }
 
-double horner(const double* c, int n, double t)
+// Horner's rule on every second entry of c (the interleaved pairs), as the
+// kernels evaluate it.
+double horner2(const double* c, int n, double t)
 {
-    double r = c[n - 1];
-    for (int k = n - 2; k >= 0; --k) r = std::fma(r, t, c[k]);
+    double r = c[2 * (n - 1)];
+    for (int k = n - 2; k >= 0; --k) r = std::fma(r, t, c[2 * k]);
     return r;
 }
 
@@ -118,18 +120,18 @@ int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, 
                 hh_rates(q, V - Vrest, al, be);
                 return -(al + be);
             };
-            double* cw = row + 1 + q * 2 * NC;
-            double* cl = cw + NC;
+            double* cw = row + 2 + q * 2 * NC;             // w_inf at even, Lambda at odd offsets
+            double* cl = cw + 1;
             cheb_monomial(winf, mid, h, d, coef);
-            for (int c = 0; c < NC; ++c) cw[c] = (double)coef[c];
+            for (int c = 0; c < NC; ++c) cw[2 * c] = (double)coef[c];
             cheb_monomial(lam, mid, h, d, coef);
-            for (int c = 0; c < NC; ++c) cl[c] = (double)coef[c];
+            for (int c = 0; c < NC; ++c) cl[2 * c] = (double)coef[c];
             for (int s = 0; s <= 16; ++s) {           // the FP64 evaluation against the direct values
                 const double V = (double)(lo + (LD)ESDC_VTAB_W * s / 16.0L);
                 const double t = V - row[0];
                 const LD w0 = winf((LD)V), l0 = lam((LD)V);
-                ew = std::fmax(ew, (double)fabsl((LD)horner(cw, NC, t) - w0));
-                el = std::fmax(el, (double)(fabsl((LD)horner(cl, NC, t) - l0) / fabsl(l0)));
+                ew = std::fmax(ew, (double)fabsl((LD)horner2(cw, NC, t) - w0));
+                el = std::fmax(el, (double)(fabsl((LD)horner2(cl, NC, t) - l0) / fabsl(l0)));
             }
         }
     }

@@ -62,6 +62,7 @@ def lib() -> C.CDLL:
                                                        C.POINTER(_D)]),
             "esdc_set_conductivity_field": (C.c_int, [_VP, C.POINTER(_D)]),
             "esdc_set_stencil_order": (C.c_int, [_VP, C.c_int]),
+            "esdc_get_solver": (C.c_int, [_VP, C.POINTER(C.c_int)]),
             "esdc_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
             "esdc_sweep": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
             "esdc_sweep_host": (C.c_int, [_VP, _VP, _I64, _D, _D, C.c_int, C.c_int, _VP]),
@@ -234,6 +235,12 @@ class Solver:
     def set_stencil_order(self, order: int):
         """2: the 3/5/7-point Laplacian; 4: the fourth-order five-point differences per axis."""
         self._check(lib().esdc_set_stencil_order(self._h, int(order)))
+
+    def solver_in_use(self) -> str:
+        """The diffusion solver the solves take now: "dct", "cheb" or "cg"."""
+        v = C.c_int(0)
+        self._check(lib().esdc_get_solver(self._h, C.byref(v)))
+        return {1: "cg", 2: "dct", 3: "cheb"}[v.value]
 
     def set_conductivity_field(self, sigma):
         """Per-node conductivity [N] (mS/mm), or None for the scalar sigma."""

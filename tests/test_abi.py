@@ -135,6 +135,7 @@ def test_later_entry_points_reject_invalid_arguments_without_gpu(L):
     D = C.POINTER(C.c_double)
     # null handles
     assert L.esdc_set_stencil_order(None, 4) == -1
+    assert L.esdc_get_solver(None, None) == -1
     assert L.esdc_set_conductivity_field(None, None) == -1
     assert L.esdc_set_conductivity_layers(None, None, None, None, None) == -1
     assert L.esdc_set_params(None, None, 7) == -1

@@ -418,6 +418,51 @@ def test_dct_errors_reported():
     assert s.residual()[0] == -4                              # NONFINITE
 
 
+
+def _solve_matches_oracle(s, wl, seed=3):
+    m = O.Monodomain(wl)
+    b = np.random.default_rng(seed).normal(size=wl.n_nodes)
+    g = 0.3 * 0.17
+    xd = torch.zeros(wl.n_nodes, dtype=torch.float64, device="cuda")
+    s.diffusion_solve(g, torch.from_numpy(b).cuda(), xd)
+    return rel(xd.cpu().numpy(), m.solve_shifted(g, b))
+
+
+def test_auto_solver_takes_the_dct_only_where_it_is_cheap():
+    # "auto" on the FP64 path with the scalar sigma: the DCT-II where every
+    # transformed axis is of power-of-two length or the dense ones add up to
+    # at most 32; the Chebyshev semi-iteration otherwise (a dense axis costs
+    # n FMAs per value and pass)
+    base = I.hh_sheet_32()
+    for shape, want in [((32, 32, 1), "dct"), ((32, 24, 1), "dct"), ((13, 11, 1), "dct"),
+                        ((48, 40, 1), "cheb"), ((64, 33, 1), "cheb"), ((16, 16, 40), "dct")]:
+        wl = base.with_mesh(*shape)
+        s = P.Solver.from_workload(wl)
+        assert s.solver_in_use() == want, shape
+        assert _solve_matches_oracle(s, wl) < 1e-12, shape
+    # the fourth order transforms z as well: nz = 40 is a dense axis of 40
+    wl = base.with_mesh(16, 16, 40)
+    s = P.Solver.from_workload(wl)
+    s.set_stencil_order(4)
+    assert s.solver_in_use() == "cheb"
+    wl4 = base.with_mesh(16, 16, 40)
+    wl4.order = 4
+    assert _solve_matches_oracle(s, wl4) < 1e-12
+    s.set_stencil_order(2)
+    assert s.solver_in_use() == "dct"
+    # a conductivity field is not diagonalised by the DCT
+    sig = np.random.default_rng(4).uniform(0.05, 0.2, size=wl.n_nodes)
+    s.set_conductivity_field(sig)
+    assert s.solver_in_use() == "cheb"
+    s.set_conductivity_field(None)
+    assert s.solver_in_use() == "dct"
+    # explicit choices and the precision form
+    assert P.Solver.from_workload(wl, solver="cg").solver_in_use() == "cg"
+    assert P.Solver.from_workload(wl, solver="cheb").solver_in_use() == "cheb"
+    assert P.Solver.from_workload(wl, solver="dct").solver_in_use() == "dct"
+    assert P.Solver.from_workload(wl, precision="mixed").solver_in_use() == "cheb"
+
+
 # ---------------------------------------------------------------- precision form (FP32 ionic model)
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5), (16, 12, 3)])
