@@ -39,16 +39,24 @@ UNIT = "node-updates/s"
 #  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu
 #  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep, with the gate
 #  functions evaluated from their V table:
-#  191.0 + 3 x 723.7 + 511.7 = 2873.8 flops per node per sweep
-#  (profiles/k_node_syn19_slab_128x128x16.md).
+#  191.0 + 3 x 722.7 + 510.7 = 2869.8 flops per node per sweep
+#  (profiles/classes_syn19_slab_128x128x16.md).
 #  Algorithmic bytes per node: node 1 reads 158 / writes 20 doubles, nodes 2..M
-#  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep, 1493 B per launch
-#  on average; DRAM traffic measured by ncu: 7048 B per sweep (1410 B per launch).
+#  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep.  DRAM traffic
+#  per node and launch measured by ncu, keyed by (M, node 1 fused), in
+#  NODE_DRAM_BYTES_PER_LAUNCH_MEASURED (profiles/classes_syn19_slab_128x128x16.md).
 #  cg (per mesh node and iteration): [A] z (stencil), p, q -> p, q;
 #  [B] q, r, x, p -> x, r, z: 12 doubles = 96 B, plus 8 doubles per solve.
-NODE_FLOPS_PER_SWEEP = {4: 2873.8}
-NODE_BYTES_PER_LAUNCH = {4: 1493}
-NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {4: 1410}
+#  Node 1 of each sweep (quadrature only: 96.0 FP64 instructions, 191.0 flops,
+#  158 + 20 doubles) runs inside the launch before it (the set-up, or the
+#  previous sweep's final evaluation): a step has K M node launches, and the
+#  set-up class carries the first sweep's node 1.
+NODE_FLOPS_PER_SWEEP = {4: 2869.8}
+NODE_BYTES_PER_SWEEP = {4: 7464}
+NODE1 = {"fp64_ops": 96.0, "flops": 191.0, "bytes": 1424}
+#  ncu, 262,144 nodes, node 1 fused: 18 x 1800.6 + 5 x 1728.3 + 425.6 B per step
+#  over 24 launches.
+NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {(4, True): 1728.2}
 CG_BYTES_PER_NODE_ITER = 96
 CG_BYTES_PER_NODE_SETUP = 64
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.
@@ -63,21 +71,23 @@ FP64_ISSUE_PEAK = 152 * 2 * 2.07e9
 # step; node: per sweep (M + 1 launches); DCT solve: four transform passes
 # and the tridiagonal z solve; Chebyshev and CG: per iteration; residual: per
 # step.
-CLASS_FP64_OPS = {"setup": 2949.1, "node_sweep": 1642.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
+CLASS_FP64_OPS = {"setup": 2949.1, "node_sweep": 1638.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
                   "residual": 703.0}
 CLASS_BYTES = {"setup": 3256.0, "node_sweep": 7464.0, "dct_solve": 120.0, "cheb_iter": 48.0, "cg_iter": 96.0,
                "residual": 2904.0}
 
 
-def class_work(solver_kind: str, K: int, it_mean: float, M: int = 4) -> dict:
-    """(FP64 instructions, bytes) per node and step of each kernel class."""
+def class_work(solver_kind: str, K: int, it_mean: float, M: int = 4, fused: bool = True) -> dict:
+    """(FP64 instructions, bytes) per node and step of each kernel class; with
+    `fused`, the first sweep's node 1 belongs to the set-up launch."""
     solves = M * K
     if solver_kind == "dct":
         sv = (CLASS_FP64_OPS["dct_solve"] * solves, CLASS_BYTES["dct_solve"] * solves)
     else:
         sv = (CLASS_FP64_OPS["cheb_iter"] * it_mean * solves, CLASS_BYTES["cheb_iter"] * it_mean * solves)
-    return {"setup": (CLASS_FP64_OPS["setup"], CLASS_BYTES["setup"]),
-            "node": (CLASS_FP64_OPS["node_sweep"] * K, CLASS_BYTES["node_sweep"] * K),
+    n1 = (NODE1["fp64_ops"], NODE1["bytes"]) if fused else (0.0, 0.0)
+    return {"setup": (CLASS_FP64_OPS["setup"] + n1[0], CLASS_BYTES["setup"] + n1[1]),
+            "node": (CLASS_FP64_OPS["node_sweep"] * K - n1[0], CLASS_BYTES["node_sweep"] * K - n1[1]),
             "cg": sv,
             "residual": (CLASS_FP64_OPS["residual"], CLASS_BYTES["residual"])}
 
@@ -337,30 +347,36 @@ def run_ours(args):
     it_mean = sum(cg_iters) / max(len(cg_iters), 1)
     solver_kind = "dct" if solver.solver_in_use() == "dct" else "iter"
     roof = {"kernel": dom}
+    node_launches_step = prof["node"][1] / args.steps if prof["node"][1] else 0
+    fused = abs(node_launches_step - K * M) < 0.5                # node 1 inside the launch before it
     if dom == "node" and M in NODE_FLOPS_PER_SWEEP and args.precision == "fp64":
-        flops = NODE_FLOPS_PER_SWEEP[M] * N / (M + 1)           # per launch, average over a sweep
+        # per launch: the node class's work per step over its launches per step
+        flops = (NODE_FLOPS_PER_SWEEP[M] * K - (NODE1["flops"] if fused else 0.0)) * N / node_launches_step
+        byts = (NODE_BYTES_PER_SWEEP[M] * K - (NODE1["bytes"] if fused else 0)) * N / node_launches_step
         ach = flops / (per_launch_ms["node"] * 1e-3) / 1e12
+        dram = NODE_DRAM_BYTES_PER_LAUNCH_MEASURED.get((M, fused))
         roof.update({"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                      "frac": ach / FP64_PEAK_TFLOPS,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; the "
                                     "library's FMA probe (bench.py --form peaks) measures 1.256 TFLOP/s",
-                     "traffic": NODE_DRAM_BYTES_PER_LAUNCH_MEASURED[M] * N,
-                     "algorithmic_bytes": NODE_BYTES_PER_LAUNCH[M] * N,
-                     "hbm_gbs": NODE_BYTES_PER_LAUNCH[M] * N / (per_launch_ms["node"] * 1e-3) / 1e9,
+                     "launches_per_step": node_launches_step, "node1_fused": fused,
+                     "traffic": dram * N if dram else None,
+                     "algorithmic_bytes": byts,
+                     "hbm_gbs": byts / (per_launch_ms["node"] * 1e-3) / 1e9,
                      "hbm_peak_gbs": peaks["hbm_gbs"]})
     else:
         bytes_launch = None
         if dom == "cg":
             bytes_launch = (CG_BYTES_PER_NODE_ITER * it_mean + CG_BYTES_PER_NODE_SETUP) * N
         elif dom == "node":
-            bytes_launch = NODE_BYTES_PER_LAUNCH.get(M, 1493) * N
+            bytes_launch = NODE_BYTES_PER_SWEEP.get(M, 7464) * K * N / max(node_launches_step, 1)
         ach = bytes_launch / (per_launch_ms[dom] * 1e-3) / 1e9 if bytes_launch else None
         roof.update({"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
                      "frac": ach / peaks["hbm_gbs"] if ach else None, "peak_source": peaks["source"],
                      "traffic": None})
     if args.precision == "fp64" and M == 4:
         classes = {}
-        for cls, (ops, byts) in class_work(solver_kind, K, it_mean).items():
+        for cls, (ops, byts) in class_work(solver_kind, K, it_mean, fused=fused).items():
             sec = prof[cls][0] * 1e-3 / args.steps
             if sec <= 0:
                 continue
@@ -752,12 +768,13 @@ def run_batch_form(args):
     graph = b.graph_active()
     iters = b.stats(K, M)
 
-    # ---- one tissue at a time, as batches of one (same kernels)
+    # ---- one tissue at a time, as batches of one (same kernels).  They run the
+    # launch sequence with the tuned sequence shape whatever mode the tuner chose
+    # for the whole batch: a persistent grid over all SMs for one small tissue
+    # only adds grid barriers (measured: twice the time).
     singles = [P.Batch.from_workloads([w], M_max=M, solver=args.solver) for w in wls]
     for s1 in singles:
         s1.set_shape(*shape[:2], 1)
-        if pers[0]:
-            s1.set_persistent(True, pers[1], pers[2])
     ys = [s1.new_state() for s1 in singles]
     for s1, y1 in zip(singles, ys):
         s1.init_state(y1, w0.V0)

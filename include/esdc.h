@@ -121,10 +121,16 @@ typedef struct {
                           Batches take 0, 1 or 3 (0 and 3 alike: Chebyshev).
                           1 and 3 stop at the same ||r|| <= tol_cg ||b||.  The
                           paper solves these systems with the DCT-II.            */
+    int    fuse_node1; /* 1: node 1 of each sweep (its explicit rows need no
+                          stencil) runs inside the launch (batches' persistent
+                          step: the phase) before it, the set-up or the
+                          previous sweep's final evaluation, for M >= 2 and not
+                          while the adjoint records a step; 0: its own launch.
+                          The results are the same bit for bit.                  */
 } esdc_options;
 
 /* Fills *opt with the defaults: M_max 8, tol_cg 1e-14, cg_maxit 200, precond 1,
- * precision 0, solver 0. */
+ * precision 0, solver 0, fuse_node1 1. */
 void esdc_default_options(esdc_options* opt);
 
 /*

@@ -76,6 +76,10 @@ __global__ void __launch_bounds__(128) k_setup_iter(StepArgs a)
         BatchNode n;
         if (!batch_node(a, p, n)) continue;
         setup_iter_body<Model, M>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+        // node 1 of the first sweep (it writes y_1's explicit rows, never the
+        // V row the stencils of this launch read)
+        if (M >= 2 && a.fuse1)
+            node_body<Model, M, false, true>(a, next_node1(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
     }
 }
 
@@ -703,6 +707,7 @@ __global__ void __launch_bounds__(512, 1) k_chebb(BCgArgs a)
 struct BStepArgs {
     int K;
     int from_iter;
+    int fuse1;                      // node 1 of each sweep inside the phase before it (M >= 2)
     int tile;                       // node tile: consecutive nodes a warp takes in a node phase (a multiple of 32)
     double gfac[ESDC_MMAX + 1];     // dt d_i, the solves' shifts
     double rho0[ESDC_MMAX + 1];     // warm-start weights c_i / c_{i-1} of sweep 0 from y^0
@@ -742,6 +747,9 @@ __global__ void __launch_bounds__(512, 1) k_bstep(StepArgs a, BCgArgs c, BStepAr
         if (!batch_node(a, p, nd)) return;
         if (s.from_iter) setup_iter_body<Model, M>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
         else setup_body<Model, M, false>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
+        if (M >= 2 && s.fuse1)
+            node_body<Model, M, false, true>(a, PhaseArgs{1, 0.0, s.G0, s.G0, nullptr}, nd.m, nd.T->st, nd.on,
+                                             nd.T->D, p, nd.ix, nd.iy, nd.iz);
     });
     if (!grid_barrier(c.bar, target, c.flags)) return;
     double* Gold = s.G0;
@@ -752,12 +760,19 @@ __global__ void __launch_bounds__(512, 1) k_bstep(StepArgs a, BCgArgs c, BStepAr
             ph.Gold = Gold;
             ph.Gnew = Gnew;
             ph.rho = (i >= 2 && i <= M) ? (k == 0 && !s.from_iter ? s.rho0[i] : 1.0) : 0.0;
-            node_phase(n, s.tile, [&](int p) {
-                BatchNode nd;
-                if (!batch_node(a, p, nd)) return;
-                node_body<Model, M, false, true>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
-            });
-            if (!grid_barrier(c.bar, target, c.flags)) return;
+            const bool fused1 = M >= 2 && s.fuse1;
+            const bool next1 = fused1 && i == M + 1 && k + 1 < s.K;      // node 1 of sweep k + 1 as well
+            if (!(fused1 && i == 1)) {                                     // node 1 ran in the phase before
+                node_phase(n, s.tile, [&](int p) {
+                    BatchNode nd;
+                    if (!batch_node(a, p, nd)) return;
+                    node_body<Model, M, false, true>(a, ph, nd.m, nd.T->st, nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
+                    if (next1)
+                        node_body<Model, M, false, true>(a, PhaseArgs{1, 0.0, Gnew, Gnew, nullptr}, nd.m, nd.T->st,
+                                                         nd.on, nd.T->D, p, nd.ix, nd.iy, nd.iz);
+                });
+                if (!grid_barrier(c.bar, target, c.flags)) return;
+            }
             if (i <= M) {
                 BCgArgs ci = c;
                 ci.gfac = s.gfac[i];
@@ -1005,6 +1020,9 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
         return e;
     a.Gnew = b->G0;
     a.Gold = b->G0;
+    // node 1 of each sweep inside the launch before it (as esdc_sweep does)
+    const bool fuse = b->opt.fuse_node1 && M >= 2 && K >= 1;
+    a.fuse1 = fuse;
     if (from_iter) k_setup_iter<Model, M><<<grid_nodes(b, b->occ_iter[M], b->node_waves), T, 0, s>>>(a);
     else k_setup<Model, M, false, true><<<grid_nodes(b, b->occ_setup[M], b->node_waves), T, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1018,8 +1036,11 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
             a.i = i;
             a.k = k;
             a.rho = (i >= 2 && i <= M) ? (k == 0 && !from_iter ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
-            k_node<Model, M, false, true><<<nb_node, T, 0, s>>>(a);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            a.fuse1 = fuse && i == M + 1 && k + 1 < K;
+            if (!(fuse && i == 1)) {
+                k_node<Model, M, false, true><<<nb_node, T, 0, s>>>(a);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
             if (i <= M) {
                 double* Vi = b->Y + (int64_t)(i - 1) * b->NS * b->ld;
                 const int slot = k * M + (i - 1);
@@ -1049,6 +1070,7 @@ cudaError_t batch_step_persist(esdc_batch* b, const double* yin, double* yout, b
     BStepArgs st{};
     st.K = K;
     st.from_iter = from_iter ? 1 : 0;
+    st.fuse1 = b->opt.fuse_node1 && M >= 2 && K >= 1;
     st.tile = b->p_tile;
     for (int i = 0; i <= M; ++i) {
         st.gfac[i] = dt * C->d[i];

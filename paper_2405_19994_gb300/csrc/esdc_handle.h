@@ -15,6 +15,7 @@ struct StepArgs {
     ModelDevF mpf;         // FP32 parameters (precision form)
     int i;                 // collocation node 1..M (k_node), M+1: evaluate G at node M only
     int k;                 // sweep index (0-based)
+    int fuse1;             // k_setup, and k_node at i = M+1 (M >= 2): also node 1 of the next sweep
     double rho;            // warm-start extrapolation weight for node i
     double* Vprev;         // [ld] V_{i-1}^k, saved before node i-1 was solved
     double dt, t_n, D, inv_Cm;

@@ -324,22 +324,6 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const PhaseArgs& p
 #ifndef ESDC_SETUP_MINBLOCKS
 #define ESDC_SETUP_MINBLOCKS 1     // blocks of 128 threads per SM the register budget must allow
 #endif
-template <class Model, int M, bool MIXED, bool BATCH>
-__global__ void __launch_bounds__(128, ESDC_SETUP_MINBLOCKS) k_setup(StepArgs a)
-{
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
-        if (!BATCH) {
-            int ix, iy, iz;
-            node_xyz(a.m, p, ix, iy, iz);
-            setup_body<Model, M, MIXED>(a, phase_of(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
-        } else {
-            BatchNode n;
-            if (!batch_node(a, p, n)) continue;
-            setup_body<Model, M, MIXED>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
-        }
-    }
-}
-
 // ------------------------------------------------------------------ sweep node i
 // i in 1..M: ionic evaluation at y_{i-1}^{k+1} (i >= 2), G_{i-1}^{k+1}, FI_{i-1}^{k+1},
 // explicit rows (auxiliaries, gates) of y_i^{k+1} and the right-hand side of the
@@ -458,6 +442,13 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const PhaseArgs& ph
     }
 }
 
+// Node 1 of the next sweep fused into a launch (a.fuse1, M >= 2): the explicit
+// rows of y_1 from the G this thread has just written, at the same node.  It
+// reads only this node's values (no stencil), and for M >= 2 it writes rows
+// (y_1's) that no stencil of the launch reads, so the fused launch computes
+// exactly what the two launches compute.
+__device__ __forceinline__ PhaseArgs next_node1(const StepArgs& a) { return PhaseArgs{1, 0.0, a.Gnew, a.Gnew, nullptr}; }
+
 template <class Model, int M, bool MIXED, bool BATCH>
 __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
 {
@@ -466,13 +457,36 @@ __global__ void __launch_bounds__(128, ESDC_NODE_MINBLOCKS) k_node(StepArgs a)
             int ix, iy, iz;
             node_xyz(a.m, p, ix, iy, iz);
             node_body<Model, M, MIXED>(a, phase_of(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+            if (M >= 2 && a.fuse1) node_body<Model, M, MIXED>(a, next_node1(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
         } else {
             BatchNode n;
             if (!batch_node(a, p, n)) continue;
             node_body<Model, M, MIXED, true>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+            if (M >= 2 && a.fuse1)
+                node_body<Model, M, MIXED, true>(a, next_node1(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
         }
     }
 }
+
+template <class Model, int M, bool MIXED, bool BATCH>
+__global__ void __launch_bounds__(128, ESDC_SETUP_MINBLOCKS) k_setup(StepArgs a)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.m.N; p += gridDim.x * blockDim.x) {
+        if (!BATCH) {
+            int ix, iy, iz;
+            node_xyz(a.m, p, ix, iy, iz);
+            setup_body<Model, M, MIXED>(a, phase_of(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+            if (M >= 2 && a.fuse1) node_body<Model, M, MIXED>(a, next_node1(a), a.m, a.st, a.stim_on, a.D, p, ix, iy, iz);
+        } else {
+            BatchNode n;
+            if (!batch_node(a, p, n)) continue;
+            setup_body<Model, M, MIXED>(a, phase_of(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+            if (M >= 2 && a.fuse1)
+                node_body<Model, M, MIXED, true>(a, next_node1(a), n.m, n.T->st, n.on, n.T->D, p, n.ix, n.iy, n.iz);
+        }
+    }
+}
+
 
 // ------------------------------------------------------------------ residual + output
 // r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C), accumulated over i from the row
@@ -619,6 +633,11 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     }
     a.Gnew = h->G0;
     a.Gold = h->G0;
+    // Node 1 of each sweep runs inside the launch before it (the set-up, or the
+    // previous sweep's final evaluation), except while the adjoint records the
+    // iterate after every sweep (node 1 would already have overwritten y_1).
+    const bool fuse = h->opt.fuse_node1 && M >= 2 && K >= 1 && !h->tapeY;
+    a.fuse1 = fuse;
     prof_begin(h, 0, s);
     k_setup<Model, M, MIXED, false><<<nb_setup, T, 0, s>>>(a);
     prof_end(h, s);
@@ -642,10 +661,13 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
             a.k = k;
             // first sweep: y^0 = y_n, so the change grows with the node time c_i
             a.rho = (i >= 2 && i <= M) ? (k == 0 ? C->c[i] / C->c[i - 1] : 1.0) : 0.0;
-            prof_begin(h, 1, s);
-            k_node<Model, M, MIXED, false><<<nb_node, T, 0, s>>>(a);
-            prof_end(h, s);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            a.fuse1 = fuse && i == M + 1 && k + 1 < K;
+            if (!(fuse && i == 1)) {
+                prof_begin(h, 1, s);
+                k_node<Model, M, MIXED, false><<<nb_node, T, 0, s>>>(a);
+                prof_end(h, s);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
             if (i <= M) {
                 double* Vi = h->Y + (int64_t)(i - 1) * h->NS * h->mesh.ld;
                 const double g = a.dt * C->d[i] * g0;

@@ -260,6 +260,7 @@ void esdc_default_options(esdc_options* opt)
     opt->precond = 1;
     opt->precision = 0;
     opt->solver = 0;
+    opt->fuse_node1 = 1;
 }
 
 int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int model,
@@ -293,6 +294,7 @@ int esdc_create(const esdc_mesh* mesh, double sigma, double chi, double Cm, int 
     if (o.M_max < 1 || o.M_max > ESDC_MMAX || !(o.tol_cg >= 0.0) || o.cg_maxit < 1) return ESDC_ERR_INVALID_ARG;
     if (o.precision != 0 && o.precision != 1) return ESDC_ERR_INVALID_ARG;
     if (o.solver < 0 || o.solver > 3) return ESDC_ERR_INVALID_ARG;
+    if (o.fuse_node1 != 0 && o.fuse_node1 != 1) return ESDC_ERR_INVALID_ARG;
     if (o.solver == 2 && o.precision != 0) return ESDC_ERR_UNSUPPORTED;     // the DCT solve is FP64
 
     esdc_handle* h = new (std::nothrow) esdc_handle();

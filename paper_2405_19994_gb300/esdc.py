@@ -34,7 +34,7 @@ class esdc_mesh(C.Structure):
 
 class esdc_options(C.Structure):
     _fields_ = [("M_max", C.c_int), ("tol_cg", C.c_double), ("cg_maxit", C.c_int), ("precond", C.c_int),
-                ("precision", C.c_int), ("solver", C.c_int)]
+                ("precision", C.c_int), ("solver", C.c_int), ("fuse_node1", C.c_int)]
 
 
 _lib = None
@@ -161,7 +161,8 @@ class Solver:
 
     def __init__(self, dim: int, nx: int, ny: int, nz: int, h: float, sigma: float, chi: float,
                  Cm: float, model: int, params, M_max: int = 8, tol_cg: float = 1e-14,
-                 cg_maxit: int = 200, precond: bool = True, precision: str = "fp64", solver: str = "auto"):
+                 cg_maxit: int = 200, precond: bool = True, precision: str = "fp64", solver: str = "auto",
+                 fuse_node1: bool = True):
         self._h = None
         L = lib()
         mesh = esdc_mesh(dim, nx, ny, nz, h)
@@ -174,6 +175,7 @@ class Solver:
         if solver not in ("auto", "cg", "dct", "cheb"):
             raise ValueError("solver must be 'auto', 'cg', 'dct' or 'cheb'")
         opt.solver = {"auto": 0, "cg": 1, "dct": 2, "cheb": 3}[solver]
+        opt.fuse_node1 = int(bool(fuse_node1))
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_create(C.byref(mesh), sigma, chi, Cm, model, p.ctypes.data_as(C.POINTER(_D)), len(p),
@@ -367,7 +369,8 @@ class Batch:
     offsets[b] .. offsets[b] + n_nodes[b]."""
 
     def __init__(self, meshes, sigmas, chi: float, Cm: float, model: int, params, M_max: int = 8,
-                 tol_cg: float = 1e-14, cg_maxit: int = 200, precond: bool = True, solver: str = "auto"):
+                 tol_cg: float = 1e-14, cg_maxit: int = 200, precond: bool = True, solver: str = "auto",
+                 fuse_node1: bool = True):
         self._b = None
         L = lib()
         n = len(meshes)
@@ -379,6 +382,7 @@ class Batch:
         if solver not in ("auto", "cg", "cheb"):
             raise ValueError("solver must be 'auto', 'cg' or 'cheb'")
         opt.solver = 1 if solver == "cg" else 0
+        opt.fuse_node1 = int(bool(fuse_node1))
         p = np.ascontiguousarray(params, np.float64)
         out = _VP()
         rc = L.esdc_batch_create(n, arr, sig.ctypes.data_as(C.POINTER(_D)), chi, Cm, model,

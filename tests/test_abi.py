@@ -63,7 +63,8 @@ def test_invalid_arguments_rejected_without_gpu(L):
     bad = p.copy(); bad[2] = np.inf
     assert create(ok, params=bad.ctypes.data_as(C.POINTER(C.c_double))) == -1
     opt = E.esdc_options(); L.esdc_default_options(C.byref(opt))
-    assert (opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond, opt.precision, opt.solver) == (8, 1e-14, 200, 1, 0, 0)
+    assert (opt.M_max, opt.tol_cg, opt.cg_maxit, opt.precond, opt.precision, opt.solver, opt.fuse_node1) == \
+        (8, 1e-14, 200, 1, 0, 0, 1)
     opt.precision = 2
     assert create(ok, optp=C.byref(opt)) == -1
     opt.precision = 0
@@ -75,6 +76,8 @@ def test_invalid_arguments_rejected_without_gpu(L):
     opt.M_max = 9
     assert create(ok, optp=C.byref(opt)) == -1
     opt.M_max = 4; opt.cg_maxit = 0
+    assert create(ok, optp=C.byref(opt)) == -1
+    opt.cg_maxit = 200; opt.fuse_node1 = 2
     assert create(ok, optp=C.byref(opt)) == -1
     # null handles
     assert L.esdc_sweep(None, None, 0.0, 0.1, 3, 4, None) == -1

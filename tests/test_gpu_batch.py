@@ -30,8 +30,9 @@ def small_batch():
     return wls
 
 
-def run_batch(wls, steps, shape=None, graph=True, t0=0.0, solver="auto", persistent=None, want_iters=False):
-    b = P.Batch.from_workloads(wls, M_max=3, solver=solver)
+def run_batch(wls, steps, shape=None, graph=True, t0=0.0, solver="auto", persistent=None, want_iters=False,
+              fuse_node1=True):
+    b = P.Batch.from_workloads(wls, M_max=3, solver=solver, fuse_node1=fuse_node1)
     if shape:
         b.set_shape(*shape)
     if persistent:
@@ -71,6 +72,19 @@ def test_batch_matches_oracle_per_tissue(solver):
         err = np.abs(got[k][0] - y[0]).max() / np.abs(y[0]).max()
         assert err < 1e-12, (k, w.name, err)
         assert np.abs(got[k][1:] - y[1:]).max() < 1e-12, (k, w.name)
+
+
+@pytest.mark.parametrize("persistent", [None, (512, 128)])
+def test_batch_fused_node1_equals_separate_launches(persistent):
+    # node 1 of each sweep inside the set-up / final-evaluation launch (or, in
+    # the persistent step, phase) against its own: the same bits
+    wls = small_batch()
+    a, ra, _, ia = run_batch(wls, 5, persistent=persistent, want_iters=True)
+    b, rb, _, ib = run_batch(wls, 5, persistent=persistent, want_iters=True, fuse_node1=False)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(ra, rb)
+    np.testing.assert_array_equal(ia, ib)
 
 
 @pytest.mark.parametrize("solver", ["auto", "cg"])

@@ -362,6 +362,50 @@ def test_one_step_matches_oracle(model, mesh, M, K, t0):
     assert y_inf == max(np.abs(y0).max(), np.abs(col).max())
 
 
+
+@pytest.mark.parametrize("model,mesh,M,K,precision,solver", [
+    (I.MODEL_HH1952, (32, 32, 1), 3, 4, "fp64", "auto"),
+    (I.MODEL_HH1952, (21, 9, 3), 2, 1, "fp64", "cheb"),
+    (I.MODEL_HH1952, (16, 16, 4), 4, 2, "mixed", "auto"),
+    (I.MODEL_HH1952, (12, 8, 1), 1, 3, "fp64", "auto"),       # M = 1: never fused
+    (I.MODEL_HH1952, (12, 8, 1), 3, 0, "fp64", "auto"),       # K = 0: no sweep
+    (I.MODEL_SYN19, (16, 16, 8), 4, 6, "fp64", "auto"),
+    (I.MODEL_SYN19, (11, 6, 4), 5, 3, "fp64", "cg"),
+])
+def test_fused_node1_equals_separate_launches(model, mesh, M, K, precision, solver):
+    # Node 1 of each sweep inside the set-up / previous final-evaluation launch
+    # (the default) against its own launch: the same state, iterate, residual
+    # vectors and residual norms, bit for bit, over three steps.
+    base = I.hh_sheet_32() if model == I.MODEL_HH1952 else I.syn19_slab()
+    wl = base.with_mesh(*mesh)
+    wl.boxes = np.array([[0, 3, 0, 3, 0, 2]], np.int32)
+    y0 = I.random_state(wl, seed=7)
+    out = []
+    for fuse in (True, False):
+        s = P.Solver.from_workload(wl, M_max=M, precision=precision, solver=solver, fuse_node1=fuse)
+        s.keep_residual(True)
+        if M >= 2:
+            yd = to_dev(s, y0)
+        else:                     # M = 1 diverges from a random state (the oracle too): start at rest
+            yd = s.new_state()
+            s.init_state(yd, wl.V0)
+        t = 0.2
+        for _ in range(3):
+            s.sweep(yd, t, wl.dt, M, K)
+            t += wl.dt
+        rc, res_inf, y_inf, res_state = s.residual()
+        col, res = s.collocation(M, with_residual=True)
+        n = wl.n_nodes
+        out.append((from_dev(s, yd), col[:, :, :n].cpu().numpy(), res[:, :, :n].cpu().numpy(), rc, res_inf, y_inf,
+                    s.stats(max(M * K, 1))))
+    (ya, ca, ra, rca, ria, yia, ita), (yb, cb, rb, rcb, rib, yib, itb) = out
+    assert rca == rcb == 0
+    np.testing.assert_array_equal(ya, yb)
+    np.testing.assert_array_equal(ca, cb)
+    np.testing.assert_array_equal(ra, rb)
+    assert (ria, yia) == (rib, yib)
+    np.testing.assert_array_equal(ita, itb)
+
 def test_sweep_host_matches_device():
     wl = I.hh_sheet_32().with_mesh(20, 9, 1)
     s = P.Solver.from_workload(wl)
