@@ -927,7 +927,10 @@ StepArgs step_args(esdc_batch* b, const double* yin, const double* tau, bool kee
     a.dt = dt;
     a.inv_Cm = 1.0 / b->Cm;
     for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j) a.dS0[i][j] = dt * C->S0[i][j];
+        for (int j = 0; j < M; ++j) {
+            a.dS0[i][j] = dt * C->S0[i][j];
+            for (int q = 0; q < M; ++q) a.dtB[i][j][q] = dt * C->B[i][j][q];
+        }
     for (int i = 0; i <= M; ++i) a.dtd[i] = dt * C->d[i];
     a.yn = yin;
     a.Y = b->Y; a.FI = b->FI; a.S = b->S; a.PHI = b->PHI; a.LAMN = b->LAMN; a.rhs = b->rhs;

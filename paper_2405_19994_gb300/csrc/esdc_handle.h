@@ -20,6 +20,7 @@ struct StepArgs {
     double* Vprev;         // [ld] V_{i-1}^k, saved before node i-1 was solved
     double dt, t_n, D, inv_Cm;
     double dS0[ESDC_MMAX][ESDC_MMAX];   // dt * (a_ij(0) - a_{i-1,j}(0))
+    double dtB[ESDC_MMAX][ESDC_MMAX][ESDC_MMAX];   // dt * B_ijk (set-up: dt a_ij = sum_k dt B_ijk phi_k)
     double dtd[ESDC_MMAX + 1];          // dt * d_i
     unsigned stim_on[ESDC_MMAX + 1];    // boxes active at t_{n,j}, j = 0..M (bit b = box b)
     const double* yn;
@@ -52,7 +53,7 @@ struct esdc_handle {
     ModelDevF mpf{};
     double sigma = 0, chi = 0, Cm = 0, D = 0;
     double* vtab = nullptr;                    // the gate table of the model (SYN19), see ModelDev
-    double vtab_err[2] = {0, 0};               // its build-time errors (w_inf absolute, Lambda relative)
+    double vtab_err[2] = {0, 0};               // its build-time errors (b / |Lambda| absolute, Lambda relative)
     double *lay = nullptr, *wdiag = nullptr;   // layered conductivity (see MeshDev)
     double* sigf = nullptr;                    // conductivity field (see MeshDev)
     float* layf = nullptr;

@@ -83,12 +83,16 @@ struct StimDev {
 // intervals of ESDC_VTAB_W mV from ESDC_VTAB_VLO, a polynomial of degree
 // ESDC_VTAB_NC - 1 in t = V - V_mid per function and interval; a row holds
 // V_mid and a pad (16-byte alignment), then per gate the coefficient pairs
-// (w_inf, Lambda) of t^0, t^1, ..., so that one 16-byte load feeds both
+// (b, Lambda) of t^0, t^1, ..., b = -Lambda w_inf, so that one 16-byte load feeds both
 // Horner recurrences.
 #define ESDC_VTAB_VLO (-140.0)
-#define ESDC_VTAB_W 1.0
-#define ESDC_VTAB_N 240
-#define ESDC_VTAB_NC 9
+#ifndef ESDC_VTAB_W
+#define ESDC_VTAB_W 0.125          // interval width (mV), a power of two
+#endif
+#ifndef ESDC_VTAB_NC
+#define ESDC_VTAB_NC 6             // coefficients per function (degree 5)
+#endif
+#define ESDC_VTAB_N ((int)(240.0 / ESDC_VTAB_W))
 #define ESDC_VTAB_ROW (2 + 2 * ESDC_NGMAX * ESDC_VTAB_NC)
 #define ESDC_VTAB_TOL 4e-15        // refuse a table whose FP64 evaluation misses by more
 struct ModelDev {

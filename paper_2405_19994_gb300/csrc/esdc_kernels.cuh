@@ -210,10 +210,9 @@ __device__ __forceinline__ void gate_tables(const StepArgs& a, int g, int NG, do
         a.PHI[((int64_t)i * NG + g) * ld + p] = a.dtd[i + 1] * p1;      // dt d_i phi_1
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            double aij = 0.0;
+            double aij = 0.0;                                            // dt a_ij
 #pragma unroll
-            for (int k = 0; k < M; ++k) aij = fma(C.B[i][j][k], ph[k], aij);
-            aij *= a.dt;                                                 // dt a_ij
+            for (int k = 0; k < M; ++k) aij = fma(a.dtB[i][j][k], ph[k], aij);
             a.S[(((int64_t)i * M + j) * NG + g) * ld + p] = aij - aprev[j];
             aprev[j] = aij;
         }
@@ -235,8 +234,8 @@ __device__ __forceinline__ void setup_iter_body(const StepArgs& a, const PhaseAr
     const typename Model::VCtx vcn = Model::vctx(a.mp, vn);
 #pragma unroll 1
     for (int g = 0; g < NG; ++g) {
-        double lam, yinf;
-        Model::gate(a.mp.p, vcn, g, vn, lam, yinf);
+        double lam, b;
+        Model::gate_lb(a.mp.p, vcn, g, vn, lam, b);
         gate_tables<M>(a, g, NG, lam, p);
     }
 #pragma unroll 1
@@ -257,9 +256,9 @@ __device__ __forceinline__ void setup_iter_body(const StepArgs& a, const PhaseAr
 #pragma unroll 1
         for (int g = 0; g < NG; ++g) {
             const int s = 1 + NA + g;
-            double lam, yinf;
-            Model::gate(a.mp.p, vc, g, u[0], lam, yinf);
-            Gj[s * ld + p] = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
+            double lam, b;
+            Model::gate_lb(a.mp.p, vc, g, u[0], lam, b);
+            Gj[s * ld + p] = fma(a.LAMN[(int64_t)g * ld + p], a.yn[s * ld + p] - u[s], fma(lam, u[s], b));
         }
     }
 }
@@ -302,16 +301,18 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const PhaseArgs& p
 #pragma unroll 1
     for (int g = 0; g < NG; ++g) {
         const int s = 1 + NA + g;
-        double lam, yinf;
+        const double us = a.yn[s * ld + p];
+        double lam, g0;                          // g0 = Lambda (u - w_inf) = Lambda u + b
         if (MIXED) {
             float lf, yf;
             Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
-            lam = lf; yinf = yf;
+            lam = lf;
+            g0 = lam * (us - (double)yf);
         } else {
-            Model::gate(a.mp.p, vc, g, u[0], lam, yinf);
+            double b;
+            Model::gate_lb(a.mp.p, vc, g, u[0], lam, b);
+            g0 = fma(lam, us, b);
         }
-        const double us = a.yn[s * ld + p];
-        const double g0 = lam * (us - yinf);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             ph.Gnew[((int64_t)j * NS + s) * ld + p] = g0;
@@ -417,15 +418,18 @@ __device__ __forceinline__ void node_body(const StepArgs& a, const PhaseArgs& ph
         const int s = 1 + NA + g;
         double dl = 0.0;
         if (eval) {
-            double lam, yinf;
+            // g_n = Lambda(V) u + b(V) + Lambda_n (u_n - u), b = -Lambda w_inf
+            const double ln = a.LAMN[(int64_t)g * ld + p], du = a.yn[s * ld + p] - u[s];
+            double gn;
             if (MIXED) {
                 float lf, yf;
                 Model::gate_f(a.mpf.p, g, uf[0], lf, yf);
-                lam = lf; yinf = yf;
+                gn = (double)lf * (u[s] - (double)yf) + ln * du;
             } else {
-                Model::gate(a.mp.p, vc, g, u[0], lam, yinf);
+                double lam, b;
+                Model::gate_lb(a.mp.p, vc, g, u[0], lam, b);
+                gn = fma(ln, du, fma(lam, u[s], b));
             }
-            const double gn = lam * (u[s] - yinf) + a.LAMN[(int64_t)g * ld + p] * (a.yn[s * ld + p] - u[s]);
             Gq[s * ld + p] = gn;
             dl = gn - Gp[s * ld + p];
         }
@@ -622,7 +626,10 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     const ColloData* C = &h->col[M - 1];
 
     for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j) a.dS0[i][j] = a.dt * C->S0[i][j];
+        for (int j = 0; j < M; ++j) {
+            a.dS0[i][j] = a.dt * C->S0[i][j];
+            for (int q = 0; q < M; ++q) a.dtB[i][j][q] = a.dt * C->B[i][j][q];
+        }
     for (int i = 0; i <= M; ++i) {
         a.dtd[i] = a.dt * C->d[i];
         const double tj = a.t_n + C->c[i] * a.dt;

@@ -16,7 +16,7 @@ namespace esdc {
 
 // The two polynomials of one gate in the gate table (esdc_vtab.cpp) at
 // t = V - V_mid: Horner's rule, ESDC_VTAB_NC - 1 FMAs each, on the interleaved
-// coefficient pairs c[k] = (w_inf, Lambda) of t^k.
+// coefficient pairs c[k] = (b, Lambda) of t^k, b = -Lambda w_inf.
 __device__ __forceinline__ void vt_poly2(const double2* __restrict__ c, double t, double& w, double& l)
 {
     const double2 top = __ldg(c + ESDC_VTAB_NC - 1);
@@ -117,11 +117,27 @@ struct HH1952 {
         }
         return c;
     }
+    // Lambda_q and b_q = -Lambda_q w_inf,q (here alpha_q): the table, else the
+    // direct rates.  The gate's rate is then Lambda u + b.
+    __device__ static void gate_lb(const double* __restrict__ mp, const VCtx& c, int q, double V, double& lam,
+                                   double& b)
+    {
+        if (c.row) {
+            vt_poly2(reinterpret_cast<const double2*>(c.row + 2) + q * ESDC_VTAB_NC, c.t, b, lam);
+            return;
+        }
+        double yinf;
+        gate(mp, q, V, lam, yinf);
+        b = -lam * yinf;
+    }
+    // Lambda_q and w_inf,q (diagnostics): w_inf = -b / Lambda on the table.
     __device__ static void gate(const double* __restrict__ mp, const VCtx& c, int q, double V, double& lam,
                                 double& yinf)
     {
         if (c.row) {
-            vt_poly2(reinterpret_cast<const double2*>(c.row + 2) + q * ESDC_VTAB_NC, c.t, yinf, lam);
+            double b;
+            gate_lb(mp, c, q, V, lam, b);
+            yinf = -b / lam;
             return;
         }
         gate(mp, q, V, lam, yinf);
@@ -297,13 +313,28 @@ struct SYN19 {
         }
         return c;
     }
-    // w_inf and Lambda of gate q: two degree-8 polynomials (16 FMAs) on the
-    // table, else the direct formulas (about 35 FP64 operations).
+    // Lambda_q and b_q = -Lambda_q w_inf,q of gate q: two polynomials
+    // (2 (ESDC_VTAB_NC - 1) FMAs) on the table, else the direct formulas (about
+    // 35 FP64 operations).  The gate's rate is then Lambda u + b.
+    __device__ static void gate_lb(const double* __restrict__ mp, const VCtx& c, int q, double V, double& lam,
+                                   double& b)
+    {
+        if (c.row) {
+            vt_poly2(reinterpret_cast<const double2*>(c.row + 2) + q * ESDC_VTAB_NC, c.t, b, lam);
+            return;
+        }
+        double yinf;
+        gate(mp, q, V, lam, yinf);
+        b = -lam * yinf;
+    }
+    // Lambda_q and w_inf,q (diagnostics): w_inf = -b / Lambda on the table.
     __device__ static void gate(const double* __restrict__ mp, const VCtx& c, int q, double V, double& lam,
                                 double& yinf)
     {
         if (c.row) {
-            vt_poly2(reinterpret_cast<const double2*>(c.row + 2) + q * ESDC_VTAB_NC, c.t, yinf, lam);
+            double b;
+            gate_lb(mp, c, q, V, lam, b);
+            yinf = -b / lam;
             return;
         }
         gate(mp, q, V, lam, yinf);

@@ -10,19 +10,32 @@
 // reciprocals (about 35 FP64 operations), an HH gate about as much; on a GPU
 // with two FP64 lane operations per SM and clock that is most of the node
 // kernel.  Here each function is replaced, on each interval
-// [V_lo + i w, V_lo + (i+1) w) of width w = 1 mV, by its Chebyshev interpolant
-// of degree 8 (9 Chebyshev points, values in long double), written as a
-// polynomial in t = V - V_mid,i: 8 FMAs per function.  On the model's
-// parameter ranges (slopes k, sr of 4 mV and more) the interpolation error of
-// degree 8 over 1 mV is below 1e-15 of the function's magnitude; the table is
-// checked at build time against the direct long-double values at 17 points
-// per interval and refused (the kernels then evaluate directly) if the FP64
-// Horner evaluation misses them by more than ESDC_VTAB_TOL.  The oracle keeps
-// the direct formulas; the table is a way of computing the same functions.
+// [V_lo + i w, V_lo + (i+1) w) of width w = ESDC_VTAB_W (1/8 mV), by its
+// Chebyshev interpolant of degree ESDC_VTAB_NC - 1 (5: 6 Chebyshev points,
+// values in long double), written as a polynomial in t = V - V_mid,i:
+// ESDC_VTAB_NC - 1 FMAs per function.  The functions are analytic in a strip
+// about the real axis of half-width about pi k (k, sr >= 4 mV on the models'
+// parameter ranges), so the interpolation error falls like (w / (4 pi k))^NC:
+// narrow intervals allow a low degree.  Measured (FP64 Horner against long
+// double, 17 points per interval, SYN19): degree 8 on 1 mV, 7 on 1/2, 6 on
+// 1/4 and 5 on 1/8 mV all stay at the rounding floor (at most 4.0e-16 absolute
+// for w_inf, 2.2e-16 relative for Lambda); 4 on 1/16 mV reaches 2.9e-15.  Fewer FMAs per
+// evaluation paid for more than the larger table cost: the headline node
+// class went from 9.53 to 9.06, 8.59 and 8.16 ms per step along that series.
+// A table whose FP64 evaluation misses by more than ESDC_VTAB_TOL is refused
+// (the kernels then evaluate directly).  The oracle keeps the direct
+// formulas; the table is a way of computing the same functions.
 //
 // Row i of the table (ESDC_VTAB_ROW doubles): V_mid,i, a zero pad, then for
-// each gate q the 9 coefficient pairs (w_inf,q, Lambda_q) of t^0, ..., t^8.
+// each gate q the ESDC_VTAB_NC coefficient pairs (b_q, Lambda_q) of t^0, t^1,
+// ..., with b_q = -Lambda_q w_inf,q (for HH, alpha_q).  The kernels need the
+// gate's rate Lambda (u - w_inf) = Lambda u + b, one FMA from (Lambda, b);
+// w_inf itself (diagnostics) is -b / Lambda.  The error check scales b's error
+// by |Lambda|, which makes it the error in w_inf.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "esdc_internal.h"
@@ -89,21 +102,19 @@ double horner2(const double* c, int n, double t)
     return r;
 }
 
-}  // namespace
-
-int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, double* err_winf, double* err_lam)
+// Rows [i0, i1) of the table; returns the largest errors of their FP64
+// evaluation against the direct long-double values.
+void build_rows(int model, const double* params, int i0, int i1, double* out, double& ew, double& el)
 {
-    rows.clear();
-    if (model != ESDC_MODEL_SYN19 && model != ESDC_MODEL_HH1952) return -1;
     const int NC = ESDC_VTAB_NC, d = NC - 1, NG = model == ESDC_MODEL_SYN19 ? 12 : 3;
-    rows.assign((size_t)ESDC_VTAB_N * ESDC_VTAB_ROW, 0.0);
-    double ew = 0.0, el = 0.0;
+    ew = 0.0;
+    el = 0.0;
     LD coef[ESDC_VTAB_NC];
-    for (int i = 0; i < ESDC_VTAB_N; ++i) {
+    for (int i = i0; i < i1; ++i) {
         const LD lo = (LD)ESDC_VTAB_VLO + (LD)i * ESDC_VTAB_W;
         const LD h = 0.5L * ESDC_VTAB_W, mid = lo + h;
-        double* row = rows.data() + (size_t)i * ESDC_VTAB_ROW;
-        row[0] = (double)mid;                         // exact: multiples of 1/2 mV
+        double* row = out + (size_t)i * ESDC_VTAB_ROW;
+        row[0] = (double)mid;                         // exact: multiples of ESDC_VTAB_W / 2
         for (int q = 0; q < NG; ++q) {
             const bool syn = model == ESDC_MODEL_SYN19;
             const double* p = params + (syn ? 6 * q : 0);     // SYN19: Vh, k, r, ln rho, Vr, sr
@@ -120,20 +131,83 @@ int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, 
                 hh_rates(q, V - Vrest, al, be);
                 return -(al + be);
             };
-            double* cw = row + 2 + q * 2 * NC;             // w_inf at even, Lambda at odd offsets
-            double* cl = cw + 1;
-            cheb_monomial(winf, mid, h, d, coef);
-            for (int c = 0; c < NC; ++c) cw[2 * c] = (double)coef[c];
+            auto bfun = [&](LD V) { return -lam(V) * winf(V); };
+            double* cb = row + 2 + q * 2 * NC;             // b at even, Lambda at odd offsets
+            double* cl = cb + 1;
+            cheb_monomial(bfun, mid, h, d, coef);
+            for (int c = 0; c < NC; ++c) cb[2 * c] = (double)coef[c];
             cheb_monomial(lam, mid, h, d, coef);
             for (int c = 0; c < NC; ++c) cl[2 * c] = (double)coef[c];
             for (int s = 0; s <= 16; ++s) {           // the FP64 evaluation against the direct values
                 const double V = (double)(lo + (LD)ESDC_VTAB_W * s / 16.0L);
                 const double t = V - row[0];
-                const LD w0 = winf((LD)V), l0 = lam((LD)V);
-                ew = std::fmax(ew, (double)fabsl((LD)horner2(cw, NC, t) - w0));
+                const LD l0 = lam((LD)V), b0 = -l0 * winf((LD)V);
+                // b's error relative to |Lambda|: the error it makes in w_inf
+                ew = std::fmax(ew, (double)(fabsl((LD)horner2(cb, NC, t) - b0) / fabsl(l0)));
                 el = std::fmax(el, (double)(fabsl((LD)horner2(cl, NC, t) - l0) / fabsl(l0)));
             }
         }
+    }
+}
+
+// Tables already built in this process, keyed by the model and the parameters
+// the gate functions depend on (SYN19: the six of each gate; HH: V_rest), so
+// that handles of the same model and a change of conductances reuse them.
+struct Cached {
+    int model;
+    std::vector<double> key, rows;
+    double ew, el;
+};
+std::mutex g_cache_mu;
+std::vector<Cached> g_cache;            // most recent last, at most kCacheSize
+constexpr size_t kCacheSize = 8;
+
+}  // namespace
+
+int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, double* err_winf, double* err_lam)
+{
+    rows.clear();
+    if (model != ESDC_MODEL_SYN19 && model != ESDC_MODEL_HH1952) return -1;
+    const std::vector<double> key = model == ESDC_MODEL_SYN19 ? std::vector<double>(params, params + 72)
+                                                               : std::vector<double>{params[6]};
+    double ew = 0.0, el = 0.0;
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (size_t k = 0; k < g_cache.size(); ++k)
+            if (g_cache[k].model == model && g_cache[k].key == key) {
+                Cached c = g_cache[k];
+                g_cache.erase(g_cache.begin() + (long)k);
+                g_cache.push_back(c);
+                rows = c.rows;
+                ew = c.ew;
+                el = c.el;
+                hit = true;
+                break;
+            }
+    }
+    if (!hit) {
+        rows.assign((size_t)ESDC_VTAB_N * ESDC_VTAB_ROW, 0.0);
+        // rows are independent: split them over the host's cores; the maxima
+        // do not depend on the split
+        unsigned nt = std::thread::hardware_concurrency();
+        nt = std::max(1u, std::min(nt, 16u));
+        std::vector<double> tw(nt, 0.0), tl(nt, 0.0);
+        std::vector<std::thread> th;
+        const int per = (ESDC_VTAB_N + (int)nt - 1) / (int)nt;
+        for (unsigned t = 0; t < nt; ++t) {
+            const int i0 = (int)t * per, i1 = std::min(ESDC_VTAB_N, i0 + per);
+            if (i0 >= i1) break;
+            th.emplace_back(build_rows, model, params, i0, i1, rows.data(), std::ref(tw[t]), std::ref(tl[t]));
+        }
+        for (auto& x : th) x.join();
+        for (unsigned t = 0; t < nt; ++t) {
+            ew = std::fmax(ew, tw[t]);
+            el = std::fmax(el, tl[t]);
+        }
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (g_cache.size() >= kCacheSize) g_cache.erase(g_cache.begin());
+        g_cache.push_back(Cached{model, key, rows, ew, el});
     }
     if (err_winf) *err_winf = ew;
     if (err_lam) *err_lam = el;
