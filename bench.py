@@ -38,9 +38,9 @@ UNIT = "node-updates/s"
 #  sweep are node 1 (quadrature only), nodes 2..M (ionic evaluation + quadrature)
 #  and the final evaluation at node M.  FP64 flops (FMA = 2) counted by ncu
 #  (thread-level DFMA/DADD/DMUL) over the 5 launches of one sweep, with the gate
-#  functions evaluated from their V table (degree 5 on 1/8 mV intervals, the
+#  functions evaluated from their V table (degree 3 on 1/128 mV intervals, the
 #  pairs (Lambda, -Lambda w_inf)):
-#  191.0 + 3 x 579.7 + 367.7 = 2297.8 flops per node per sweep
+#  191.0 + 3 x 483.7 + 271.7 = 1913.8 flops per node per sweep
 #  (profiles/classes_syn19_slab_128x128x16.md).
 #  Algorithmic bytes per node: node 1 reads 158 / writes 20 doubles, nodes 2..M
 #  204 / 20, the final evaluation 63 / 20 -> 7464 B per sweep.  DRAM traffic
@@ -52,12 +52,12 @@ UNIT = "node-updates/s"
 #  158 + 20 doubles) runs inside the launch before it (the set-up, or the
 #  previous sweep's final evaluation): a step has K M node launches, and the
 #  set-up class carries the first sweep's node 1.
-NODE_FLOPS_PER_SWEEP = {4: 2297.8}
+NODE_FLOPS_PER_SWEEP = {4: 1913.8}
 NODE_BYTES_PER_SWEEP = {4: 7464}
 NODE1 = {"fp64_ops": 96.0, "flops": 191.0, "bytes": 1424}
-#  ncu, 262,144 nodes, node 1 fused: 18 x 1806.6 + 5 x 1718.7 + 423.9 B per step
+#  ncu, 262,144 nodes, node 1 fused: 18 x 1796.2 + 5 x 1702.4 + 425.1 B per step
 #  over 24 launches.
-NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {(4, True): 1730.7}
+NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {(4, True): 1719.5}
 CG_BYTES_PER_NODE_ITER = 96
 CG_BYTES_PER_NODE_SETUP = 64
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.
@@ -72,7 +72,7 @@ FP64_ISSUE_PEAK = 152 * 2 * 2.07e9
 # step; node: per sweep (M + 1 launches); DCT solve: four transform passes
 # and the tridiagonal z solve; Chebyshev and CG: per iteration; residual: per
 # step.
-CLASS_FP64_OPS = {"setup": 2770.9, "node_sweep": 1306.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
+CLASS_FP64_OPS = {"setup": 2722.9, "node_sweep": 1114.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
                   "residual": 703.0}
 CLASS_BYTES = {"setup": 3256.0, "node_sweep": 7464.0, "dct_solve": 120.0, "cheb_iter": 48.0, "cg_iter": 96.0,
                "residual": 2904.0}

@@ -87,10 +87,10 @@ struct StimDev {
 // Horner recurrences.
 #define ESDC_VTAB_VLO (-140.0)
 #ifndef ESDC_VTAB_W
-#define ESDC_VTAB_W 0.125          // interval width (mV), a power of two
+#define ESDC_VTAB_W 0.0078125      // interval width (mV): 1/128, a power of two
 #endif
 #ifndef ESDC_VTAB_NC
-#define ESDC_VTAB_NC 6             // coefficients per function (degree 5)
+#define ESDC_VTAB_NC 4             // coefficients per function (degree 3)
 #endif
 #define ESDC_VTAB_N ((int)(240.0 / ESDC_VTAB_W))
 #define ESDC_VTAB_ROW (2 + 2 * ESDC_NGMAX * ESDC_VTAB_NC)

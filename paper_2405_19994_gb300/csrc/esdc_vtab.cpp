@@ -10,18 +10,21 @@
 // reciprocals (about 35 FP64 operations), an HH gate about as much; on a GPU
 // with two FP64 lane operations per SM and clock that is most of the node
 // kernel.  Here each function is replaced, on each interval
-// [V_lo + i w, V_lo + (i+1) w) of width w = ESDC_VTAB_W (1/8 mV), by its
-// Chebyshev interpolant of degree ESDC_VTAB_NC - 1 (5: 6 Chebyshev points,
+// [V_lo + i w, V_lo + (i+1) w) of width w = ESDC_VTAB_W (1/128 mV), by its
+// Chebyshev interpolant of degree ESDC_VTAB_NC - 1 (3: 4 Chebyshev points,
 // values in long double), written as a polynomial in t = V - V_mid,i:
 // ESDC_VTAB_NC - 1 FMAs per function.  The functions are analytic in a strip
 // about the real axis of half-width about pi k (k, sr >= 4 mV on the models'
 // parameter ranges), so the interpolation error falls like (w / (4 pi k))^NC:
 // narrow intervals allow a low degree.  Measured (FP64 Horner against long
 // double, 17 points per interval, SYN19): degree 8 on 1 mV, 7 on 1/2, 6 on
-// 1/4 and 5 on 1/8 mV all stay at the rounding floor (at most 4.0e-16 absolute
-// for w_inf, 2.2e-16 relative for Lambda); 4 on 1/16 mV reaches 2.9e-15.  Fewer FMAs per
-// evaluation paid for more than the larger table cost: the headline node
-// class went from 9.53 to 9.06, 8.59 and 8.16 ms per step along that series.
+// 1/4, 5 on 1/8 and 4 on 1/32 mV all stay at the rounding floor (at most
+// 4.0e-16 absolute for w_inf, 2.2e-16 relative for Lambda); 4 on 1/16 mV
+// reaches 2.9e-15, 3 on 1/64 mV 7.6e-15 and 3 on 1/128 mV 5.4e-16.  Fewer
+// FMAs per evaluation paid for more than the larger table (24 MB at degree 3,
+// held in L2) cost: the headline node class went from 9.53 to 9.06, 8.59,
+// 8.16, 7.28 and 6.93 ms per step along that series.  The table in use is
+// checked at 9 points per interval.
 // A table whose FP64 evaluation misses by more than ESDC_VTAB_TOL is refused
 // (the kernels then evaluate directly).  The oracle keeps the direct
 // formulas; the table is a way of computing the same functions.
@@ -138,8 +141,8 @@ void build_rows(int model, const double* params, int i0, int i1, double* out, do
             for (int c = 0; c < NC; ++c) cb[2 * c] = (double)coef[c];
             cheb_monomial(lam, mid, h, d, coef);
             for (int c = 0; c < NC; ++c) cl[2 * c] = (double)coef[c];
-            for (int s = 0; s <= 16; ++s) {           // the FP64 evaluation against the direct values
-                const double V = (double)(lo + (LD)ESDC_VTAB_W * s / 16.0L);
+            for (int s = 0; s <= 8; ++s) {            // the FP64 evaluation against the direct values
+                const double V = (double)(lo + (LD)ESDC_VTAB_W * s / 8.0L);
                 const double t = V - row[0];
                 const LD l0 = lam((LD)V), b0 = -l0 * winf((LD)V);
                 // b's error relative to |Lambda|: the error it makes in w_inf
