@@ -68,11 +68,11 @@ FP64_ISSUE_PEAK = 152 * 2 * 2.07e9
 # Work per mesh node of each kernel class of one step (M = 4, SYN19): FP64
 # instructions (thread-level DFMA + DADD + DMUL, counted by ncu on the
 # 128x128x16 slab, profiles/classes_syn19_slab_128x128x16.md) and the bytes the
-# method streams.  Set-up: the coefficient tables and one ionic evaluation per
-# step; node: per sweep (M + 1 launches); DCT solve: four transform passes
+# method streams.  Set-up: the coefficient tables (from their table in z) and
+# one ionic evaluation per step; node: per sweep (M + 1 launches); DCT solve: four transform passes
 # and the tridiagonal z solve; Chebyshev and CG: per iteration; residual: per
 # step.
-CLASS_FP64_OPS = {"setup": 2722.9, "node_sweep": 1114.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
+CLASS_FP64_OPS = {"setup": 1143.1, "node_sweep": 1114.8, "dct_solve": 54.3, "cheb_iter": 12.2, "cg_iter": 15.0,
                   "residual": 703.0}
 CLASS_BYTES = {"setup": 3256.0, "node_sweep": 7464.0, "dct_solve": 120.0, "cheb_iter": 48.0, "cg_iter": 96.0,
                "residual": 2904.0}

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libesdc.so")
 SOURCES = ["esdc_step.cu", "esdc_step_mixed.cu", "esdc_cg.cu", "esdc_cg4.cu", "esdc_batch.cu", "esdc_adjoint.cu",
-           "esdc_static.cu", "esdc_dct.cu", "esdc_colloc.cpp", "esdc_vtab.cpp"]
+           "esdc_static.cu", "esdc_dct.cu", "esdc_colloc.cpp", "esdc_vtab.cpp", "esdc_ztab.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 

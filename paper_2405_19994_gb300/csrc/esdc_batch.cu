@@ -812,6 +812,7 @@ struct esdc_batch {
     ModelDev mp{};
     ModelDevF mpf{};
     double* vtab = nullptr;                // the gate table of the model (see ModelDev)
+    ZtabSlots zt;                          // set-up coefficient tables per (M, dt)
     std::vector<TissueDev> tis_h;
     std::vector<unsigned> on_h;            // [ntis][ESDC_MMAX + 1]
     TissueDev* tis = nullptr;
@@ -844,6 +845,7 @@ struct esdc_batch {
         bool keepR = false;
         int M = 0, K = 0;
         double dt = 0.0;
+        unsigned ztgen = 0;                // the set-up tables the recording points to
     } graphs[2];
     bool last_graph = false;
     char graph_err[128] = {0};
@@ -865,6 +867,7 @@ void free_batch(esdc_batch* b)
 {
     for (auto& g : b->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    esdc_ztab_free(b->zt);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     void* ptrs[] = {b->vtab, b->R, b->tis, b->tile_tissue, b->tis_on, b->Y, b->G0, b->G1, b->FI, b->S, b->PHI, b->LAMN,
                     b->rhs, b->Vprev, b->r, b->p, b->q, b->z, b->part, b->bar, b->done_at, b->status,
@@ -1016,6 +1019,7 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
     batch_prime<Model, M>(b);
     const ColloData* C = &b->col[M - 1];
     StepArgs a = step_args(b, yin, tau, keepR, dt, M);
+    a.ztab = esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(b->flags, 0, sizeof(int), s)) != cudaSuccess) return e;
@@ -1069,6 +1073,7 @@ cudaError_t batch_step_persist(esdc_batch* b, const double* yin, double* yout, b
     const int nb = bstep_grid(b, M);
     if (nb < 1) return cudaErrorInvalidConfiguration;
     StepArgs a = step_args(b, yin, tau, keepR, dt, M);
+    a.ztab = esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);
     BCgArgs c = cg_args(b, 0.0, b->rhs, nullptr, nullptr);
     BStepArgs st{};
     st.K = K;
@@ -1177,6 +1182,7 @@ bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, const doub
     G = esdc_batch::Graph{};
     if (b->model == ESDC_MODEL_HH1952) batch_prime_M<esdc::HH1952>(b, M);
     else batch_prime_M<esdc::SYN19>(b, M);
+    esdc_ztab_device(b->zt, M, dt, b->col[M - 1], nullptr);   // before the recording: a graph cannot build it
     auto fail = [&](const char* what, cudaError_t e) {
         std::snprintf(b->graph_err, sizeof b->graph_err, "%s: %s", what, cudaGetErrorString(e));
         cudaGetLastError();
@@ -1201,6 +1207,7 @@ bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, const doub
         return fail("instantiate", e);
     }
     G.yin = yin; G.yout = yout; G.tau = tau; G.keepR = keepR; G.M = M; G.K = K; G.dt = dt;
+    G.ztgen = b->zt.gen;
     return true;
 }
 
@@ -1227,9 +1234,10 @@ int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const do
     b->last_M = M; b->last_K = K; b->last_stream = s;
     b->last_graph = false;
     if (b->use_graph && !b->graph_failed) {
+        esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);          // (re)filling a slot moves zt.gen on
         const esdc_batch::Graph& G = b->graphs[fi ? 1 : 0];
         if (!(G.exec && G.yin == yin && G.yout == yout && G.tau == tau && G.keepR == keepR && G.M == M && G.K == K &&
-              G.dt == dt)) {
+              G.dt == dt && G.ztgen == b->zt.gen)) {
             if (!capture(b, yin, yout, fi, tau, keepR, dt, M, K)) b->graph_failed = true;
         }
         if (b->graphs[fi ? 1 : 0].exec && !b->graph_failed) {

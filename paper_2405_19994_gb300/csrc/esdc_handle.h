@@ -21,6 +21,7 @@ struct StepArgs {
     double dt, t_n, D, inv_Cm;
     double dS0[ESDC_MMAX][ESDC_MMAX];   // dt * (a_ij(0) - a_{i-1,j}(0))
     double dtB[ESDC_MMAX][ESDC_MMAX][ESDC_MMAX];   // dt * B_ijk (set-up: dt a_ij = sum_k dt B_ijk phi_k)
+    const double* ztab;                 // set-up coefficient table for (M, dt) (esdc_ztab.cpp), or nullptr
     double dtd[ESDC_MMAX + 1];          // dt * d_i
     unsigned stim_on[ESDC_MMAX + 1];    // boxes active at t_{n,j}, j = 0..M (bit b = box b)
     const double* yn;
@@ -53,6 +54,7 @@ struct esdc_handle {
     ModelDevF mpf{};
     double sigma = 0, chi = 0, Cm = 0, D = 0;
     double* vtab = nullptr;                    // the gate table of the model (SYN19), see ModelDev
+    ZtabSlots zt;                              // set-up coefficient tables per (M, dt)
     double vtab_err[2] = {0, 0};               // its build-time errors (b / |Lambda| absolute, Lambda relative)
     double *lay = nullptr, *wdiag = nullptr;   // layered conductivity (see MeshDev)
     double* sigf = nullptr;                    // conductivity field (see MeshDev)

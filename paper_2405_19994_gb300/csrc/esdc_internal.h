@@ -183,6 +183,41 @@ cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const d
 // model; -2: an error above ESDC_VTAB_TOL (rows cleared).
 int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, double* err_winf, double* err_lam);
 
+// The set-up's exponential coefficients tabulated in y = 1 - z, z = dt Lambda
+// (esdc_ztab.cpp): ESDC_ZTAB_OCT octaves of y, 2^ESDC_ZTAB_SUB intervals each,
+// a polynomial of degree ESDC_ZTAB_NC - 1 per function and interval; a row
+// holds y_mid, a pad, then for i = 0..M-1 the coefficients of dt d_{i+1}
+// phi_1(d_{i+1} z) and of dt S_{i+1,j}(z), j = 0..M-1.
+#define ESDC_ZTAB_OCT 12
+#ifndef ESDC_ZTAB_SUB
+#define ESDC_ZTAB_SUB 8            // 256 intervals per octave of y
+#endif
+#ifndef ESDC_ZTAB_NC
+#define ESDC_ZTAB_NC 5             // coefficients per function (degree 4)
+#endif
+#define ESDC_ZTAB_ROW(M) (2 + (M) * ((M) + 1) * ESDC_ZTAB_NC)
+#define ESDC_ZTAB_TOL 4e-15         // refuse a table whose FP64 evaluation misses by more (units of dt)
+// Builds (or takes from this process's cache) the table for (M, dt, C);
+// returns 0, -1 (bad arguments) or -2 (error above ESDC_ZTAB_TOL, rows
+// cleared); *err: the largest error, in units of dt.
+int esdc_ztab_build(int M, double dt, const ColloData& C, std::vector<double>& rows, double* err);
+// Device copies of the set-up tables of a handle or batch for a few (M, dt).
+#define ESDC_ZTAB_SLOTS 4
+struct ZtabSlots {
+    int M[ESDC_ZTAB_SLOTS] = {};
+    double dt[ESDC_ZTAB_SLOTS] = {};
+    double* dev[ESDC_ZTAB_SLOTS] = {};
+    size_t n[ESDC_ZTAB_SLOTS] = {};      // doubles allocated
+    int next = 0;
+    unsigned gen = 0;                    // counts slot fills (recorded graphs check it)
+};
+// The device table for (M, dt): built and uploaded on first use (which
+// synchronises the device), or nullptr for the direct evaluation (no table
+// within ESDC_ZTAB_TOL, a CUDA error, or the stream is being captured and the
+// table is not there yet).
+const double* esdc_ztab_device(ZtabSlots& z, int M, double dt, const ColloData& C, cudaStream_t s);
+void esdc_ztab_free(ZtabSlots& z);
+
 // Validates ionic-model parameters and fills the device parameter blocks;
 // returns ESDC_OK or ESDC_ERR_INVALID_ARG.
 int esdc_model_setup(int model, const double* params, int n_params, ModelDev* mp, ModelDevF* mpf, int* NS, int* NG);

@@ -190,8 +190,20 @@ struct PhaseArgs {
 };
 __device__ __forceinline__ PhaseArgs phase_of(const StepArgs& a) { return PhaseArgs{a.i, a.rho, a.Gold, a.Gnew, a.yout}; }
 
+// One function of the set-up table (esdc_ztab.cpp) at t: Horner's rule on its
+// ESDC_ZTAB_NC coefficients.
+__device__ __forceinline__ double ztab_poly(const double* __restrict__ c, double t)
+{
+    double r = __ldg(c + ESDC_ZTAB_NC - 1);
+#pragma unroll
+    for (int k = ESDC_ZTAB_NC - 2; k >= 0; --k) r = fma(r, t, __ldg(c + k));
+    return r;
+}
+
 // Per-step tables of gate g at node p: Lambda_n, dt d_i phi_1(d_i dt Lambda_n)
-// and dt S_ij(dt Lambda_n) (App. A).
+// and dt S_ij(dt Lambda_n) (App. A).  From the set-up table when there is one
+// and z = dt Lambda_n lies in its range (1 <= y = 1 - z < 2^ESDC_ZTAB_OCT: the
+// interval is y's exponent and leading mantissa bits), else directly.
 template <int M>
 __device__ __forceinline__ void gate_tables(const StepArgs& a, int g, int NG, double lam, int p)
 {
@@ -199,6 +211,26 @@ __device__ __forceinline__ void gate_tables(const StepArgs& a, int g, int NG, do
     const int64_t ld = a.m.ld;
     const double z = a.dt * lam;
     a.LAMN[(int64_t)g * ld + p] = lam;
+    if (a.ztab) {
+        const double y = 1.0 - z;
+        const long long bits = __double_as_longlong(y);
+        const int e = (int)(bits >> 52) - 1023;             // NaN, Inf and y < 1 fall outside
+        if (e >= 0 && e < ESDC_ZTAB_OCT) {
+            const int r = (e << ESDC_ZTAB_SUB) + (int)((bits >> (52 - ESDC_ZTAB_SUB)) & ((1 << ESDC_ZTAB_SUB) - 1));
+            const double* row = a.ztab + (size_t)r * ESDC_ZTAB_ROW(M);
+            const double t = y - __ldg(row);
+            const double* c = row + 2;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                a.PHI[((int64_t)i * NG + g) * ld + p] = ztab_poly(c + (i * (M + 1)) * ESDC_ZTAB_NC, t);
+#pragma unroll
+                for (int j = 0; j < M; ++j)
+                    a.S[(((int64_t)i * M + j) * NG + g) * ld + p] =
+                        ztab_poly(c + (i * (M + 1) + 1 + j) * ESDC_ZTAB_NC, t);
+            }
+            return;
+        }
+    }
     double aprev[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) aprev[j] = 0.0;
@@ -323,7 +355,7 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const PhaseArgs& p
 }
 
 #ifndef ESDC_SETUP_MINBLOCKS
-#define ESDC_SETUP_MINBLOCKS 1     // blocks of 128 threads per SM the register budget must allow
+#define ESDC_SETUP_MINBLOCKS 5     // blocks of 128 threads per SM the register budget must allow (96 registers)
 #endif
 // ------------------------------------------------------------------ sweep node i
 // i in 1..M: ionic evaluation at y_{i-1}^{k+1} (i >= 2), G_{i-1}^{k+1}, FI_{i-1}^{k+1},
@@ -645,6 +677,7 @@ cudaError_t launch_step_kernels(esdc_handle* h, StepArgs& a, double* y, int K, c
     // iterate after every sweep (node 1 would already have overwritten y_1).
     const bool fuse = h->opt.fuse_node1 && M >= 2 && K >= 1 && !h->tapeY;
     a.fuse1 = fuse;
+    a.ztab = esdc_ztab_device(h->zt, M, a.dt, *C, s);
     prof_begin(h, 0, s);
     k_setup<Model, M, MIXED, false><<<nb_setup, T, 0, s>>>(a);
     prof_end(h, s);

@@ -188,6 +188,7 @@ void free_all(esdc_handle* h)
     if (h->wdiag) cudaFree(h->wdiag);
     if (h->sigf) cudaFree(h->sigf);
     if (h->vtab) cudaFree(h->vtab);
+    esdc_ztab_free(h->zt);
     void* ptrs[] = {h->Y, h->G0, h->G1, h->FI, h->S, h->PHI, h->LAMN, h->rhs, h->R, h->ydev, h->Vprev,
                     h->cg.r, h->cg.p, h->cg.q, h->cg.z, h->cg.r32, h->cg.p32, h->cg.q32, h->cg.z32,
                     h->cg.e32, h->cg.part, h->cg.bar, h->cg.status,
@@ -197,6 +198,45 @@ void free_all(esdc_handle* h)
 }
 
 }  // namespace
+
+const double* esdc_ztab_device(ZtabSlots& z, int M, double dt, const ColloData& C, cudaStream_t s)
+{
+    for (int k = 0; k < ESDC_ZTAB_SLOTS; ++k)
+        if (z.dev[k] && z.M[k] == M && z.dt[k] == dt) return z.dev[k];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    std::vector<double> rows;
+    double err = 0.0;
+    if (esdc_ztab_build(M, dt, C, rows, &err) != 0) return nullptr;
+    const int k = z.next;
+    z.next = (z.next + 1) % ESDC_ZTAB_SLOTS;
+    // the slot may hold a table that kernels in flight read
+    if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+    if (z.n[k] < rows.size()) {
+        if (z.dev[k]) cudaFree(z.dev[k]);
+        z.dev[k] = nullptr;
+        z.n[k] = 0;
+        if (cudaMalloc((void**)&z.dev[k], sizeof(double) * rows.size()) != cudaSuccess) {
+            z.dev[k] = nullptr;
+            return nullptr;
+        }
+        z.n[k] = rows.size();
+    }
+    z.M[k] = 0;
+    if (cudaMemcpy(z.dev[k], rows.data(), sizeof(double) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return nullptr;
+    z.M[k] = M;
+    z.dt[k] = dt;
+    ++z.gen;
+    return z.dev[k];
+}
+
+void esdc_ztab_free(ZtabSlots& z)
+{
+    for (int k = 0; k < ESDC_ZTAB_SLOTS; ++k)
+        if (z.dev[k]) cudaFree(z.dev[k]);
+    z = ZtabSlots{};
+}
 
 // The gate table of the handle's model for the parameters in h->mp (built on
 // the host, copied into h->vtab, allocated on first use); h->mp.vtab points

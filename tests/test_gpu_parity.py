@@ -406,6 +406,25 @@ def test_fused_node1_equals_separate_launches(model, mesh, M, K, precision, solv
     assert (ria, yia) == (rib, yib)
     np.testing.assert_array_equal(ita, itb)
 
+
+@pytest.mark.parametrize("dt", [1.0, 0.05])
+def test_setup_table_and_direct_coefficients_match_oracle(dt):
+    # The set-up takes dt S_ij and dt d_i phi_1 from a table in z = dt Lambda
+    # for |z| < 4095 and evaluates them directly beyond.  With dt = 1 ms the
+    # synthetic model's fastest gates (Lambda down to -5189/ms) fall beyond, so
+    # one node mixes both; one step against the oracle.
+    wl = I.syn19_slab().with_mesh(9, 7, 3)
+    y0 = I.random_state(wl, seed=11)
+    s = P.Solver.from_workload(wl, M_max=3)
+    yd = to_dev(s, y0)
+    s.sweep(yd, 0.0, dt, 3, 2)
+    assert s.residual()[0] == 0
+    got = from_dev(s, yd)
+    want = O.Monodomain(wl, solver=O.SOLVE_DCT).step(y0, 0.0, dt, 3, 2)[0]
+    for srow in range(wl.n_state):
+        scale = max(np.abs(want[srow]).max(), 1e-3)
+        assert np.abs(got[srow] - want[srow]).max() / scale < 1e-11, (srow, np.abs(got[srow] - want[srow]).max())
+
 def test_sweep_host_matches_device():
     wl = I.hh_sheet_32().with_mesh(20, 9, 1)
     s = P.Solver.from_workload(wl)
