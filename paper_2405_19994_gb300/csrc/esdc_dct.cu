@@ -204,8 +204,9 @@ __global__ void __launch_bounds__(256) k_dct_fft(AxisArgs a)
     const size_t bstride = (size_t)P * pitch;           // buffer c starts at sm + c * bstride
     __shared__ int base[32];
     tile_bases(a, blockIdx.x * a.lpt, base);
-    for (int m = threadIdx.x; m < n; m += blockDim.x) stw[m] = __ldg(a.tw + m);
     __syncthreads();
+    // the twiddles (first used by the FFT stages) load together with the tile
+    for (int m = threadIdx.x; m < n; m += blockDim.x) stw[m] = __ldg(a.tw + m);
     const int tile_elems = a.lpt * n;
 
     // load: line l of the tile into the real (l even) or imaginary (l odd)

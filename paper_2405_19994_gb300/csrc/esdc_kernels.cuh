@@ -528,8 +528,8 @@ __global__ void __launch_bounds__(128, ESDC_SETUP_MINBLOCKS) k_setup(StepArgs a)
 // r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C), accumulated over i from the row
 // differences dt S_ij = dt (a_ij - a_{i-1,j});
 // per-state max |r| and max |y|; y_{n+1} = y_M.
-// One state s of one node: the residual recursion over the M nodes, the
-// largest |r_i| and |y| (y_n included), and y_{n+1} = y_{n,M} (c_M = 1).
+// One state s of one node: the residuals of the M nodes, the largest |r_i|
+// and |y| (y_n included), and y_{n+1} = y_{n,M} (c_M = 1).
 // Returns false if a residual or iterate is not finite.
 // The maxima are taken on the bit patterns of |r| and |y| with integer
 // operations: for non-negative doubles the patterns order like the values, and
@@ -549,21 +549,20 @@ __device__ __forceinline__ bool residual_state(const StepArgs& a, const PhaseArg
     const int g = s - 1 - NA;
     const double yns = a.yn[s * ld + p];
     unsigned long long rb = 0ULL, yb = abs_bits(yns);
-    // r_i = r_{i-1} + sum_j dt S_ij G_j - (y_i - y_{i-1}), r_0 = 0 (y_0 = y_n)
-    double r = 0.0, yprev = yns;
+    // r_i = y_n + dt sum_j a_ij G_j - y_i (eq. def_C; the batches' FAS form adds
+    // tau_i): the row sums of dt S are dt a_ij, so A_i = y_n + sum_{l <= i}
+    // sum_j dt S_lj G_j is carried through the FMAs and r_i = A_i - y_i.
+    double A = yns;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        double q = 0.0;
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             const double sij = (g >= 0) ? a.S[(((int64_t)i * M + j) * NG + g) * ld + p] : a.dS0[i][j];
-            q = fma(sij, ph.Gold[((int64_t)j * NS + s) * ld + p], q);
+            A = fma(sij, ph.Gold[((int64_t)j * NS + s) * ld + p], A);
         }
         const double yi = a.Y[((int64_t)i * NS + s) * ld + p];
-        r += q - (yi - yprev);
-        if (TAU && a.tau)
-            r += a.tau[((int64_t)i * NS + s) * ld + p] - (i > 0 ? a.tau[((int64_t)(i - 1) * NS + s) * ld + p] : 0.0);
-        yprev = yi;
+        double r = A - yi;
+        if (TAU && a.tau) r += a.tau[((int64_t)i * NS + s) * ld + p];
         if (a.R) a.R[((int64_t)i * NS + s) * ld + p] = r;
         rb = max(rb, abs_bits(r));
         yb = max(yb, abs_bits(yi));
