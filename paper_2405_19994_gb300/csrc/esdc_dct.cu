@@ -326,8 +326,10 @@ __global__ void k_dct_dense(AxisArgs a)
 // diagonal d_k = a + (g/h^2) (number of z-neighbours of layer k);
 // inv_k = 1/(d_k - e C_{k-1}), A_k = w inv_k, C_k = e inv_k, with w the
 // spectral weight of the transformed axes.
+// Layout: [z][ky][kx] (the z kernel), or [kx][z][ky] (yzy: the fused kernel's
+// blocks read their kx contiguously).
 __global__ void k_dct_ztab(DctDev d, int nx, int ny, int nz, double ih2, double g, double w,
-                           double* A, double* C)
+                           double* A, double* C, bool yzy)
 {
     const int sxy = nx * ny;
     const double e = -g * ih2;
@@ -338,9 +340,10 @@ __global__ void k_dct_ztab(DctDev d, int nx, int ny, int nz, double ih2, double 
         for (int k = 0; k < nz; ++k) {
             const int nb = (k > 0) + (k < nz - 1);
             const double inv = 1.0 / ((a + g * ih2 * nb) - e * cprev);
-            A[k * sxy + m] = w * inv;
+            const size_t q = yzy ? ((size_t)kx * nz + k) * ny + ky : (size_t)k * sxy + m;
+            A[q] = w * inv;
             cprev = e * inv;
-            C[k * sxy + m] = cprev;
+            C[q] = cprev;
         }
     }
 }
@@ -408,6 +411,139 @@ __global__ void __launch_bounds__(ESDC_DCT_ZTHREADS) k_dct_z(const double* __res
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         status[0] = 1;
         if (iter_log) *iter_log = 1;
+    }
+}
+
+// The y forward transform, the z solves and the y inverse transform of the
+// second-order solve in one kernel: block kx holds the y-z slab of x-mode kx
+// (nz lines of n = ny values, paired into (nz + 1)/2 complex lines) in shared
+// memory, transforms it along y (as k_dct_fft), solves the tridiagonal z
+// system of every y-mode ky in place (as k_dct_z, factors in the [kx][z][ky]
+// layout, loaded into shared memory with the data), transforms back and
+// stores it.  One pass over the data instead of three, and the z recurrences
+// read shared memory.
+struct YzyArgs {
+    const double* src;
+    double* dst;
+    int nx, n, logn, nz, pairs, G;
+    const double2* tw;                  // y axis: [n] e^{-2 pi i k/n}
+    const double2* csh;                 // [n/2 + 1] (cos, sin)(pi k/(2n)) / 2
+    const double2* cs;                  // [n/2 + 1] (cos, sin)(pi k/(2n))
+    const double* A;                    // [nx][nz][n]
+    const double* C;
+    int* status;
+    int* iter_log;
+    int* flags;
+};
+
+__global__ void __launch_bounds__(1024) k_dct_yzy(YzyArgs a)
+{
+    extern __shared__ double2 smem_all[];
+    const int n = a.n, pitch = n + 1, P = a.pairs, nz = a.nz, nx = a.nx, h = n >> 1;
+    const int kx = blockIdx.x;
+    double2* stw = smem_all;
+    double2* sm = smem_all + n;
+    const size_t bstride = (size_t)P * pitch;
+    double* zA = reinterpret_cast<double*>(sm + 2 * bstride);   // this kx's z factors, [z][ky]
+    double* zC = zA + (size_t)nz * n;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) stw[m] = __ldg(a.tw + m);
+    // the factors load with the data (contiguous per kx), used after the forward transform
+    for (int e = threadIdx.x; e < nz * n; e += blockDim.x) {
+        zA[e] = __ldg(a.A + (size_t)kx * nz * n + e);
+        zC[e] = __ldg(a.C + (size_t)kx * nz * n + e);
+    }
+    // line z (its n values along y) into the real (z even) or imaginary part of
+    // pair row z/2 of buffer 0, at its reordered position; a missing last line is 0
+    for (int e = threadIdx.x; e < 2 * P * n; e += blockDim.x) {
+        const int z = e >> a.logn, y = e & (n - 1);
+        const double v = z < nz ? a.src[((size_t)z * n + y) * nx + kx] : 0.0;
+        double* row = reinterpret_cast<double*>(sm + (size_t)(z >> 1) * pitch);
+        row[2 * makhoul_pos(y, n) + (z & 1)] = v;
+    }
+    __syncthreads();
+    const int p0 = threadIdx.x / a.G, g = threadIdx.x - p0 * a.G;
+    const bool active = p0 < P;
+    const int p = active ? p0 : 0;
+    const int stages = (a.logn >> 1) + (a.logn & 1);
+    // forward along y: buffer 0 -> buffer c1; real rows of X into buffer c1 ^ 1
+    const double2* zf = fft_pow2(sm + (size_t)p * pitch, sm + bstride + (size_t)p * pitch, n, a.logn, g, a.G, active,
+                                 stw);
+    const int c1 = stages & 1;
+    double* rows = reinterpret_cast<double*>(sm + (size_t)(c1 ^ 1) * bstride);   // row z at pitch n + 1 doubles
+    if (active) {
+        double* ra = rows + (size_t)(2 * p) * pitch;
+        double* rb = ra + pitch;
+        for (int k = g; k <= h; k += a.G) {
+            if (k == 0) { ra[0] = zf[0].x; rb[0] = zf[0].y; continue; }
+            const double2 Zk = zf[k], Zm = zf[n - k];
+            const double Pr = Zk.x + Zm.x, Pi = Zk.y - Zm.y;
+            const double Qr = Zk.x - Zm.x, Qi = Zk.y + Zm.y;
+            const double2 t = __ldg(a.csh + k);
+            ra[k] = fma(t.x, Pr, t.y * Pi);
+            rb[k] = fma(t.x, Qi, -t.y * Qr);
+            if (k < h) {
+                ra[n - k] = fma(t.y, Pr, -t.x * Pi);
+                rb[n - k] = fma(t.y, Qi, t.x * Qr);
+            }
+        }
+    }
+    __syncthreads();
+    // z: the tridiagonal system of y-mode ky, in place in the real rows
+    bool bad = false;
+    for (int ky = threadIdx.x; ky < n; ky += blockDim.x) {
+        double rp = 0.0;
+        for (int z = 0; z < nz; ++z) {
+            rp = fma(rows[(size_t)z * pitch + ky], zA[(size_t)z * n + ky], -rp * zC[(size_t)z * n + ky]);
+            rows[(size_t)z * pitch + ky] = rp;
+        }
+        double xn = rp;
+        bad |= !isfinite(xn);
+        for (int z = nz - 2; z >= 0; --z) {
+            xn = fma(-zC[(size_t)z * n + ky], xn, rows[(size_t)z * pitch + ky]);
+            rows[(size_t)z * pitch + ky] = xn;
+            bad |= !isfinite(xn);
+        }
+    }
+    if (bad) atomicOr(a.flags, ESDC_FLAG_NONFINITE);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = 1;
+        if (a.iter_log) *a.iter_log = 1;
+    }
+    __syncthreads();
+    // inverse along y: the real rows (buffer c1 ^ 1) packed into buffer c1 as in
+    // k_dct_fft, then the FFT; a pair writes only its own two rows' storage
+    double2* xi = sm + (size_t)c1 * bstride + (size_t)p * pitch;
+    if (active) {
+        const double* ra = rows + (size_t)(2 * p) * pitch;
+        const double* rb = ra + pitch;
+        for (int k = g; k <= h; k += a.G) {
+            if (k == 0) { xi[0] = make_double2(ra[0], -rb[0]); continue; }
+            const double Akx = ra[k], Aky = rb[k], Amx = ra[n - k], Amy = rb[n - k];
+            const double2 t = __ldg(a.cs + k);
+            const double ar = fma(t.x, Akx, t.y * Amx), ai = fma(t.y, Akx, -t.x * Amx);
+            const double br = fma(t.x, Aky, t.y * Amy), bi = fma(t.y, Aky, -t.x * Amy);
+            xi[k] = make_double2(ar - bi, -(ai + br));
+            if (k < h) xi[n - k] = make_double2(ar + bi, ai - br);
+        }
+    }
+    pair_sync(a.G);
+    const double2* zi = fft_pow2(xi, sm + (size_t)(c1 ^ 1) * bstride + (size_t)p * pitch, n, a.logn, g, a.G, active,
+                                 stw);
+    const int c2 = (c1 + stages) & 1;
+    double* out = reinterpret_cast<double*>(sm + (size_t)(c2 ^ 1) * bstride);
+    if (active) {
+        double* ra = out + (size_t)(2 * p) * pitch;
+        double* rb = ra + pitch;
+        for (int i = g; i < n; i += a.G) {
+            const double2 v = zi[makhoul_pos(i, n)];
+            ra[i] = v.x;
+            rb[i] = -v.y;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nz * n; e += blockDim.x) {
+        const int z = e >> a.logn, y = e & (n - 1);
+        a.dst[((size_t)z * n + y) * nx + kx] = out[(size_t)z * pitch + y];
     }
 }
 
@@ -594,6 +730,8 @@ cudaError_t prepare_kernels()
         return e;
     if ((e = cudaFuncSetAttribute(k_dct_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_dct_yzy, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
     done = true;
     return cudaSuccess;
 }
@@ -649,6 +787,20 @@ cudaError_t esdc_dct_set_order(const MeshDev& m, DctDev* d)
     }
     for (int k = 0; k < ESDC_DCT_SLOTS; ++k) d->used[k] = false;   // the z tables follow the eigenvalues
     d->cheap = esdc_dct_cheap(m, m.order);
+    // the fused y-z kernel: second order, y of power-of-two length >= 16, and a
+    // y-z slab that fits a block (threads and shared memory)
+    d->yzy = false;
+    if (m.order == 2 && m.nz >= 2 && m.ny >= 16 && log2_exact(m.ny) >= 0) {
+        const int n = m.ny, G = n / 4 < 256 ? n / 4 : 256, P = (m.nz + 1) / 2;
+        const int threads = (P * G + 31) / 32 * 32;
+        const size_t smem = (size_t)(n + 2 * (size_t)P * (n + 1)) * sizeof(double2) +
+                            2 * (size_t)m.nz * n * sizeof(double);          // + the z factors
+        if (threads <= 1024 && smem <= (size_t)kDctSmemLimit) {
+            d->yzy = true;
+            d->yzy_threads = threads;
+            d->yzy_smem = smem;
+        }
+    }
     return cudaSuccess;
 }
 
@@ -682,10 +834,13 @@ cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const d
         src = o;
         wgt /= nx;
     }
+    const bool yzy = m.order == 2 && d.yzy;        // y forward, z, y inverse in k_dct_yzy
     if (ny > 1) {
-        double* o = next();
-        if ((e = axis_pass(d.ay, true, src, o, N / ny, nx, s)) != cudaSuccess) return e;
-        src = o;
+        if (!yzy) {
+            double* o = next();
+            if ((e = axis_pass(d.ay, true, src, o, N / ny, nx, s)) != cudaSuccess) return e;
+            src = o;
+        }
         wgt /= ny;
     }
     if (m.order == 2) {
@@ -701,19 +856,43 @@ cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const d
             A = d.ztab + (size_t)2 * N * slot;
             C = A + N;
             const int nblk = (sxy + 127) / 128;
-            k_dct_ztab<<<(unsigned)(nblk < 4096 ? nblk : 4096), 128, 0, s>>>(d, nx, ny, nz, m.ih2, g, wgt, A, C);
+            k_dct_ztab<<<(unsigned)(nblk < 4096 ? nblk : 4096), 128, 0, s>>>(d, nx, ny, nz, m.ih2, g, wgt, A, C, yzy);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             d.used[slot] = true;
             d.gkey[slot] = g;
         }
         A = d.ztab + (size_t)2 * N * slot;
         C = A + N;
-        double* o = next();
-        const int nblk = (sxy + ESDC_DCT_ZTHREADS - 1) / ESDC_DCT_ZTHREADS;
-        k_dct_z<<<(unsigned)(nblk < 65535 ? nblk : 65535), ESDC_DCT_ZTHREADS, 0, s>>>(src, o, A, C, nx, ny, nz,
-                                                                                   w.status, iter_log, flags);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        src = o;
+        if (yzy) {
+            double* o = nx > 1 ? next() : x;
+            YzyArgs ya{};
+            ya.src = src;
+            ya.dst = o;
+            ya.nx = nx;
+            ya.n = ny;
+            ya.logn = d.ay.logn;
+            ya.nz = nz;
+            ya.pairs = (nz + 1) / 2;
+            ya.G = ny / 4 < 256 ? ny / 4 : 256;
+            ya.tw = d.ay.tw;
+            ya.csh = d.ay.csh;
+            ya.cs = d.ay.cs;
+            ya.A = A;
+            ya.C = C;
+            ya.status = w.status;
+            ya.iter_log = iter_log;
+            ya.flags = flags;
+            k_dct_yzy<<<(unsigned)nx, (unsigned)d.yzy_threads, d.yzy_smem, s>>>(ya);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            src = o;
+        } else {
+            double* o = next();
+            const int nblk = (sxy + ESDC_DCT_ZTHREADS - 1) / ESDC_DCT_ZTHREADS;
+            k_dct_z<<<(unsigned)(nblk < 65535 ? nblk : 65535), ESDC_DCT_ZTHREADS, 0, s>>>(src, o, A, C, nx, ny, nz,
+                                                                                       w.status, iter_log, flags);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            src = o;
+        }
     } else {
         if (nz > 1) {
             double* o = next();
@@ -738,7 +917,7 @@ cudaError_t esdc_dct_launch(const MeshDev& m, const CgWork& w, double g, const d
         }
     }
     // inverse: y, then x; the last stage writes x
-    if (ny > 1) {
+    if (ny > 1 && !yzy) {
         double* o = nx > 1 ? next() : x;
         if ((e = axis_pass(d.ay, false, src, o, N / ny, nx, s)) != cudaSuccess) return e;
         src = o;

@@ -144,6 +144,9 @@ struct DctDev {
     double gkey[ESDC_DCT_SLOTS] = {};
     bool used[ESDC_DCT_SLOTS] = {};
     bool cheap = false;             // esdc_dct_cheap for the current stencil order (the automatic choice)
+    bool yzy = false;               // second order: y transforms and z solves in one kernel (k_dct_yzy)
+    int yzy_threads = 0;
+    size_t yzy_smem = 0;
 };
 
 // CG solve on the handle's mesh: (I - g L) x = b (Jacobi-preconditioned).

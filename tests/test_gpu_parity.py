@@ -235,7 +235,10 @@ def test_one_step_either_solver_matches_oracle(solver):
 # ---------------------------------------------------------------- DCT-II direct solve (options.solver = 2)
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1, 1), (33, 17, 1), (19, 13, 7), (64, 48, 5), (2, 3, 2),
-                                   (128, 8, 4), (8, 128, 3), (16, 16, 16), (256, 3, 2), (2, 2, 64), (32, 1, 1)])
+                                   (128, 8, 4), (8, 128, 3), (16, 16, 16), (256, 3, 2), (2, 2, 64), (32, 1, 1),
+                                   # the fused y-z kernel (second order, ny a power of two >= 16, nz >= 2):
+                                   # odd nz, nx = 1, and more than a warp per line pair (ny 256, 512)
+                                   (4, 32, 7), (1, 16, 4), (1, 64, 9), (3, 256, 3), (5, 512, 2)])
 @pytest.mark.parametrize("order", [2, 4])
 @pytest.mark.parametrize("g", [1e-3, 0.05, 2.0])
 def test_dct_solve_matches_oracle(shape, order, g):
