@@ -193,10 +193,10 @@ int esdc_vtab_build(int model, const double* params, std::vector<double>& rows, 
 // phi_1(d_{i+1} z) and of dt S_{i+1,j}(z), j = 0..M-1.
 #define ESDC_ZTAB_OCT 12
 #ifndef ESDC_ZTAB_SUB
-#define ESDC_ZTAB_SUB 8            // 256 intervals per octave of y
+#define ESDC_ZTAB_SUB 10           // 1024 intervals per octave of y
 #endif
 #ifndef ESDC_ZTAB_NC
-#define ESDC_ZTAB_NC 5             // coefficients per function (degree 4)
+#define ESDC_ZTAB_NC 4             // coefficients per function (degree 3)
 #endif
 #define ESDC_ZTAB_ROW(M) (2 + (M) * ((M) + 1) * ESDC_ZTAB_NC)
 #define ESDC_ZTAB_TOL 4e-15         // refuse a table whose FP64 evaluation misses by more (units of dt)

@@ -27,11 +27,12 @@
 // the long-double functions at 9 points per interval, the error measured in
 // units of dt (a_ij and phi_1 are of order one).  A table that misses by more
 // than ESDC_ZTAB_TOL is refused and the kernels evaluate directly.  Measured
-// with degree 4 on 256 intervals per octave (12 octaves, 3072 rows): at most
-// 1.2e-16 for M = 4 and 4.1e-16 for M <= 7, 2.0e-15 for M = 8 (larger B),
-// for every dt from 1e-3 to 10 ms (the error does not depend on dt); degree 3
-// needs 1024 intervals per octave for 6.6e-16.  On the synthetic slab the
-// set-up went from 2.90 to 1.16 ms per step.
+// (the error does not depend on dt; checked from 1e-3 to 10 ms): degree 4 on
+// 256 intervals per octave, at most 1.2e-16 for M = 4 and 2.0e-15 for M = 8;
+// degree 3 on 512 intervals per octave misses the tolerance; degree 3 on 1024
+// (12 octaves, 12288 rows, the table in use), at most 6.6e-16 for M = 4 and
+// 2.0e-15 over M = 1..8.  On the synthetic slab the set-up went from 2.90 ms
+// per step (direct) to 1.16 (degree 4) and 0.94 ms (degree 3).
 //
 // Row r of the table (ESDC_ZTAB_ROW(M) doubles): y_mid, a zero pad, then for
 // i = 0..M-1 the function dt d_{i+1} phi_1 and the M functions dt S_{i+1,j},
