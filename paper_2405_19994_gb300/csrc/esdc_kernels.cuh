@@ -363,7 +363,9 @@ __device__ __forceinline__ void setup_body(const StepArgs& a, const PhaseArgs& p
 // V row.  i == M+1: only the evaluation at y_M^{k+1}.  Each gate's rate is used
 // as soon as it is computed (its G, Delta and update), which keeps few values live.
 #ifndef ESDC_NODE_MINBLOCKS
-#define ESDC_NODE_MINBLOCKS 5      // 5 x 128 threads per SM: at most 102 registers
+#define ESDC_NODE_MINBLOCKS 6      // 6 x 128 threads per SM: at most 85 registers (SYN19: 80, a
+                                   // 76-byte spill; the kernel waits on memory more than on FP64,
+                                   // and 6 blocks beat 5, 7 and 8 on the headline slab)
 #endif
 // TAU: batched kernels may add the FAS correction tau (a.tau, rows 1..M; the
 // recursive form adds tau_i - tau_{i-1}, tau_0 = 0, to every row of node i).
