@@ -232,12 +232,19 @@ int esdc_init_state(esdc_handle* h, double* y, double V0, void* stream);
  *   Lambda_n = Lambda(y_n) is frozen for the step (eq. (def_ode_esdc));
  *   the gate coefficients a_ij(dt Lambda_n) follow App. A eq.
  *   (def_aij_computable); y^0 = 1 (x) y_n; each sweep visits the nodes
- *   i = 1..M in order and solves (I - dt d_i (chi C_m)^{-1} A) V_i = rhs with
- *   preconditioned CG (the implicit f_I row of P); K >= 0 sweeps are taken.
+ *   i = 1..M in order and solves (I - dt d_i (chi C_m)^{-1} A) V_i = rhs (the
+ *   implicit f_I row of P) with the solver options.solver selects
+ *   (esdc_get_solver); K >= 0 sweeps are taken.
  * After the sweeps the residual r_i = y_n + dt sum_j a_ij G_j - y_i of
  * eq. (def_C) is formed on the device (see esdc_residual).
  * 1 <= M <= M_max, dt > 0.  Work is enqueued on `stream`; the call does not
- * synchronise.  Errors: INVALID_ARG, CUDA.  Convergence failures of the
+ * synchronise, except the first step with a new (M, dt): it builds the table
+ * of the set-up's coefficients dt S_ij(z), dt d_i phi_1(d_i z) for them on the
+ * host (cached per process) and synchronises the device once to upload it (a
+ * handle keeps four such tables; a fifth (M, dt) replaces the oldest).  While
+ * `stream` is being captured into a CUDA graph and the table is not there, the
+ * step evaluates the coefficients directly (the same values within a few
+ * units of 1e-16 dt).  Errors: INVALID_ARG, CUDA.  Convergence failures of the
  * solves are recorded on the device and reported by esdc_residual/esdc_stats.
  */
 int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, void* stream);
@@ -476,10 +483,13 @@ int esdc_batch_init_state(esdc_batch* b, double* y, double V0, void* stream);
 
 /* One HSDC step of every tissue, in place on y (device, [n_state][ld]).
  * t (host, [n]) holds each tissue's t_n; dt, M (<= M_max) and K are shared.
- * Stream-ordered, no synchronisation.  The first call for a given (y, M, K,
- * dt) records the step's launches in a CUDA graph on a stream of the batch's
- * own and later calls launch that graph on `stream` (falling back to direct
- * launches if the CUDA runtime cannot record them).  Errors: INVALID_ARG, CUDA. */
+ * Stream-ordered, no synchronisation, except the first step with a new
+ * (M, dt), which builds and uploads the set-up's coefficient table as
+ * esdc_sweep does (before any recording).  The first call for a given
+ * (y, M, K, dt) records the step's launches in a CUDA graph on a stream of
+ * the batch's own and later calls launch that graph on `stream` (falling back
+ * to direct launches if the CUDA runtime cannot record them); a refilled
+ * table slot makes the next call record again.  Errors: INVALID_ARG, CUDA. */
 int esdc_batch_sweep(esdc_batch* b, double* y, const double* t, double dt, int M, int K, void* stream);
 
 /* As esdc_batch_sweep with a separate output: y_n from y_in, y_{n+1} of every
