@@ -517,3 +517,39 @@ def test_full_batch_in_bench_configuration_matches_oracle():
         got = b.tissue(y, k).cpu().numpy()
         assert np.abs(got - yo).max() < 1e-12 * max(1.0, np.abs(yo).max()), (k, w.name)
     b.close()
+
+
+def test_batch_graph_rerecorded_after_setup_table_refill():
+    # A recorded step points at the set-up coefficient table of its (M, dt).
+    # Record a step from the stored iterate at dt0 (the batch's second graph),
+    # then let plain steps at five other step sizes refill all four table
+    # slots, then repeat the first call unchanged: its graph must be recorded
+    # again against the rebuilt table.  The same sequence without graphs gives
+    # the reference bits.
+    wls = small_batch()
+    dt0 = wls[0].dt
+    others = [0.011, 0.013, 0.017, 0.019, 0.023]
+
+    def run(graph):
+        b = P.Batch.from_workloads(wls, M_max=3)
+        b.set_graph(graph)
+        y = b.new_state()
+        y2 = b.new_state()
+        b.init_state(y, -75.0)
+        b.sweep(y, 0.0, dt0, 3, 2)
+        b.sweep_from(y, y2, 0.0, dt0, 3, 1, True)
+        for dt in others:
+            b.sweep(y, 0.0, dt, 3, 1)
+        b.sweep_from(y, y2, 0.0, dt0, 3, 1, True)
+        assert b.residual()[0] == 0
+        used = b.graph_active()
+        torch.cuda.synchronize()
+        out = [b.tissue(y2, k).cpu().numpy().copy() for k in range(len(wls))]
+        b.close()
+        return out, used
+
+    got, used = run(True)
+    want, _ = run(False)
+    assert used
+    for x, w in zip(got, want):
+        np.testing.assert_array_equal(x, w)

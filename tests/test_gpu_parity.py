@@ -428,6 +428,29 @@ def test_setup_table_and_direct_coefficients_match_oracle(dt):
         scale = max(np.abs(want[srow]).max(), 1e-3)
         assert np.abs(got[srow] - want[srow]).max() / scale < 1e-11, (srow, np.abs(got[srow] - want[srow]).max())
 
+
+def test_setup_tables_for_many_step_sizes():
+    # A handle keeps four set-up coefficient tables (one per (M, dt)); a fifth
+    # step size replaces the oldest.  Every step still matches the oracle, and a
+    # step size whose table was replaced gives the bits it gave before.
+    wl = I.hh_sheet_32().with_mesh(12, 9, 2)
+    y0 = I.random_state(wl, seed=5)
+    s = P.Solver.from_workload(wl, M_max=3)
+    m = O.Monodomain(wl, solver=O.SOLVE_DCT)
+    first = None
+    for dt in [0.025, 0.01, 0.02, 0.03, 0.04, 0.05, 0.025]:
+        yd = to_dev(s, y0)
+        s.sweep(yd, 0.2, dt, 3, 2)
+        assert s.residual()[0] == 0
+        got = from_dev(s, yd)
+        want = m.step(y0, 0.2, dt, 3, 2)[0]
+        for srow in range(wl.n_state):
+            scale = max(np.abs(want[srow]).max(), 1e-3)
+            assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (dt, srow)
+        if first is None:
+            first = got
+    np.testing.assert_array_equal(got, first)
+
 def test_sweep_host_matches_device():
     wl = I.hh_sheet_32().with_mesh(20, 9, 1)
     s = P.Solver.from_workload(wl)
