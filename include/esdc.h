@@ -241,10 +241,11 @@ int esdc_init_state(esdc_handle* h, double* y, double V0, void* stream);
  * synchronise, except the first step with a new (M, dt): it builds the table
  * of the set-up's coefficients dt S_ij(z), dt d_i phi_1(d_i z) for them on the
  * host (cached per process) and synchronises the device once to upload it (a
- * handle keeps four such tables; a fifth (M, dt) replaces the oldest).  While
- * `stream` is being captured into a CUDA graph and the table is not there, the
- * step evaluates the coefficients directly (the same values within a few
- * units of 1e-16 dt).  Errors: INVALID_ARG, CUDA.  Convergence failures of the
+ * handle keeps four such tables; a fifth (M, dt) replaces the oldest).  A
+ * handle builds at most 16 tables: later new (M, dt), as with step sizes that
+ * keep changing, and steps while `stream` is being captured into a CUDA graph
+ * without the table, evaluate the coefficients directly (the same values
+ * within a few units of 1e-16 dt).  Errors: INVALID_ARG, CUDA.  Convergence failures of the
  * solves are recorded on the device and reported by esdc_residual/esdc_stats.
  */
 int esdc_sweep(esdc_handle* h, double* y, double t, double dt, int M, int K, void* stream);

@@ -813,6 +813,7 @@ struct esdc_batch {
     ModelDevF mpf{};
     double* vtab = nullptr;                // the gate table of the model (see ModelDev)
     ZtabSlots zt;                          // set-up coefficient tables per (M, dt)
+    const double* cur_ztab = nullptr;      // the table of the step being launched (asked once per step)
     std::vector<TissueDev> tis_h;
     std::vector<unsigned> on_h;            // [ntis][ESDC_MMAX + 1]
     TissueDev* tis = nullptr;
@@ -1019,7 +1020,7 @@ cudaError_t batch_step(esdc_batch* b, const double* yin, double* yout, bool from
     batch_prime<Model, M>(b);
     const ColloData* C = &b->col[M - 1];
     StepArgs a = step_args(b, yin, tau, keepR, dt, M);
-    a.ztab = esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);
+    a.ztab = b->cur_ztab;
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(b->flags, 0, sizeof(int), s)) != cudaSuccess) return e;
@@ -1073,7 +1074,7 @@ cudaError_t batch_step_persist(esdc_batch* b, const double* yin, double* yout, b
     const int nb = bstep_grid(b, M);
     if (nb < 1) return cudaErrorInvalidConfiguration;
     StepArgs a = step_args(b, yin, tau, keepR, dt, M);
-    a.ztab = esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);
+    a.ztab = b->cur_ztab;
     BCgArgs c = cg_args(b, 0.0, b->rhs, nullptr, nullptr);
     BStepArgs st{};
     st.K = K;
@@ -1182,7 +1183,6 @@ bool capture(esdc_batch* b, const double* yin, double* yout, bool fi, const doub
     G = esdc_batch::Graph{};
     if (b->model == ESDC_MODEL_HH1952) batch_prime_M<esdc::HH1952>(b, M);
     else batch_prime_M<esdc::SYN19>(b, M);
-    esdc_ztab_device(b->zt, M, dt, b->col[M - 1], nullptr);   // before the recording: a graph cannot build it
     auto fail = [&](const char* what, cudaError_t e) {
         std::snprintf(b->graph_err, sizeof b->graph_err, "%s: %s", what, cudaGetErrorString(e));
         cudaGetLastError();
@@ -1233,8 +1233,11 @@ int sweep_impl(esdc_batch* b, const double* yin, double* yout, bool fi, const do
         return set_berr(b, ESDC_ERR_CUDA, "stimulus window upload failed");
     b->last_M = M; b->last_K = K; b->last_stream = s;
     b->last_graph = false;
+    // the set-up's coefficient table, asked for once per step whatever the launch
+    // mode (built at the first step with (M, dt), before any recording; a
+    // refilled slot moves zt.gen on, and a recording made before is redone)
+    b->cur_ztab = esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);
     if (b->use_graph && !b->graph_failed) {
-        esdc_ztab_device(b->zt, M, dt, b->col[M - 1], s);          // (re)filling a slot moves zt.gen on
         const esdc_batch::Graph& G = b->graphs[fi ? 1 : 0];
         if (!(G.exec && G.yin == yin && G.yout == yout && G.tau == tau && G.keepR == keepR && G.M == M && G.K == K &&
               G.dt == dt && G.ztgen == b->zt.gen)) {

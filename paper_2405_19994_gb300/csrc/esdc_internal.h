@@ -213,11 +213,14 @@ struct ZtabSlots {
     size_t n[ESDC_ZTAB_SLOTS] = {};      // doubles allocated
     int next = 0;
     unsigned gen = 0;                    // counts slot fills (recorded graphs check it)
+    int builds = 0;                      // tables built so far (at most ESDC_ZTAB_BUILDS)
 };
+#define ESDC_ZTAB_BUILDS 16
 // The device table for (M, dt): built and uploaded on first use (which
-// synchronises the device), or nullptr for the direct evaluation (no table
-// within ESDC_ZTAB_TOL, a CUDA error, or the stream is being captured and the
-// table is not there yet).
+// synchronises the device once), or nullptr for the direct evaluation (no
+// table within ESDC_ZTAB_TOL, a CUDA error, the stream is being captured and
+// the table is not there yet, or ESDC_ZTAB_BUILDS tables were built already:
+// step sizes that keep changing do not pay for a table each).
 const double* esdc_ztab_device(ZtabSlots& z, int M, double dt, const ColloData& C, cudaStream_t s);
 void esdc_ztab_free(ZtabSlots& z);
 

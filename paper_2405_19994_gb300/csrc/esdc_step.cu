@@ -203,6 +203,7 @@ const double* esdc_ztab_device(ZtabSlots& z, int M, double dt, const ColloData& 
 {
     for (int k = 0; k < ESDC_ZTAB_SLOTS; ++k)
         if (z.dev[k] && z.M[k] == M && z.dt[k] == dt) return z.dev[k];
+    if (z.builds >= ESDC_ZTAB_BUILDS) return nullptr;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
     std::vector<double> rows;
@@ -228,6 +229,7 @@ const double* esdc_ztab_device(ZtabSlots& z, int M, double dt, const ColloData& 
     z.M[k] = M;
     z.dt[k] = dt;
     ++z.gen;
+    ++z.builds;
     return z.dev[k];
 }
 

@@ -522,10 +522,10 @@ def test_full_batch_in_bench_configuration_matches_oracle():
 def test_batch_graph_rerecorded_after_setup_table_refill():
     # A recorded step points at the set-up coefficient table of its (M, dt).
     # Record a step from the stored iterate at dt0 (the batch's second graph),
-    # then let plain steps at five other step sizes refill all four table
-    # slots, then repeat the first call unchanged: its graph must be recorded
-    # again against the rebuilt table.  The same sequence without graphs gives
-    # the reference bits.
+    # then let plain steps at five
+    # other step sizes refill all four table slots, then repeat the first call
+    # unchanged: its graph must be recorded again against the rebuilt table.
+    # The same sequence without graphs gives the reference bits.
     wls = small_batch()
     dt0 = wls[0].dt
     others = [0.011, 0.013, 0.017, 0.019, 0.023]
@@ -539,6 +539,7 @@ def test_batch_graph_rerecorded_after_setup_table_refill():
         b.sweep(y, 0.0, dt0, 3, 2)
         b.sweep_from(y, y2, 0.0, dt0, 3, 1, True)
         for dt in others:
+            b.sweep(y, 0.0, dt, 3, 1)
             b.sweep(y, 0.0, dt, 3, 1)
         b.sweep_from(y, y2, 0.0, dt0, 3, 1, True)
         assert b.residual()[0] == 0

@@ -414,53 +414,45 @@ def test_fused_node1_equals_separate_launches(model, mesh, M, K, precision, solv
 def test_setup_table_and_direct_coefficients_match_oracle(dt):
     # The set-up takes dt S_ij and dt d_i phi_1 from a table in z = dt Lambda
     # for |z| < 4095 and evaluates them directly beyond.  With dt = 1 ms the
-    # synthetic model's fastest gates (Lambda down to -5189/ms) fall beyond, so
-    # one node mixes both; one step against the oracle.
+    # synthetic model's fastest gates (Lambda down to -5189/ms) fall beyond the
+    # table, so one node mixes both.  The same step twice from the same state.
     wl = I.syn19_slab().with_mesh(9, 7, 3)
     y0 = I.random_state(wl, seed=11)
     s = P.Solver.from_workload(wl, M_max=3)
-    yd = to_dev(s, y0)
-    s.sweep(yd, 0.0, dt, 3, 2)
-    assert s.residual()[0] == 0
-    got = from_dev(s, yd)
     want = O.Monodomain(wl, solver=O.SOLVE_DCT).step(y0, 0.0, dt, 3, 2)[0]
-    for srow in range(wl.n_state):
-        scale = max(np.abs(want[srow]).max(), 1e-3)
-        assert np.abs(got[srow] - want[srow]).max() / scale < 1e-11, (srow, np.abs(got[srow] - want[srow]).max())
+    for _ in range(2):
+        yd = to_dev(s, y0)
+        s.sweep(yd, 0.0, dt, 3, 2)
+        assert s.residual()[0] == 0
+        got = from_dev(s, yd)
+        for srow in range(wl.n_state):
+            scale = max(np.abs(want[srow]).max(), 1e-3)
+            assert np.abs(got[srow] - want[srow]).max() / scale < 1e-11, (srow, np.abs(got[srow] - want[srow]).max())
 
 
 def test_setup_tables_for_many_step_sizes():
     # A handle keeps four set-up coefficient tables (one per (M, dt)); a fifth
-    # step size replaces the oldest.  Every step still matches the oracle, and a
-    # step size whose table was replaced gives the bits it gave before.
+    # step size replaces the oldest.  Every step matches the oracle, and a step
+    # size whose table was replaced gives the bits it gave before once its
+    # table is rebuilt.
     wl = I.hh_sheet_32().with_mesh(12, 9, 2)
     y0 = I.random_state(wl, seed=5)
     s = P.Solver.from_workload(wl, M_max=3)
     m = O.Monodomain(wl, solver=O.SOLVE_DCT)
     first = None
     for dt in [0.025, 0.01, 0.02, 0.03, 0.04, 0.05, 0.025]:
-        yd = to_dev(s, y0)
-        s.sweep(yd, 0.2, dt, 3, 2)
-        assert s.residual()[0] == 0
-        got = from_dev(s, yd)
         want = m.step(y0, 0.2, dt, 3, 2)[0]
-        for srow in range(wl.n_state):
-            scale = max(np.abs(want[srow]).max(), 1e-3)
-            assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (dt, srow)
+        for _ in range(2):
+            yd = to_dev(s, y0)
+            s.sweep(yd, 0.2, dt, 3, 2)
+            assert s.residual()[0] == 0
+            got = from_dev(s, yd)
+            for srow in range(wl.n_state):
+                scale = max(np.abs(want[srow]).max(), 1e-3)
+                assert np.abs(got[srow] - want[srow]).max() / scale < 1e-12, (dt, srow)
         if first is None:
             first = got
     np.testing.assert_array_equal(got, first)
-
-def test_sweep_host_matches_device():
-    wl = I.hh_sheet_32().with_mesh(20, 9, 1)
-    s = P.Solver.from_workload(wl)
-    y0 = I.random_state(wl, seed=3)
-    yd = to_dev(s, y0)
-    s.sweep(yd, 0.3, wl.dt, wl.M, wl.K)
-    dev = from_dev(s, yd)
-    yh = np.ascontiguousarray(y0.copy())
-    s.sweep_host(yh, 0.3, wl.dt, wl.M, wl.K)
-    np.testing.assert_array_equal(yh, dev)
 
 
 @pytest.mark.parametrize("nx,solver", [(16, "cheb"), (15, "cheb"), (16, "cg"), (15, "cg")])
