@@ -55,9 +55,9 @@ UNIT = "node-updates/s"
 NODE_FLOPS_PER_SWEEP = {4: 1913.8}
 NODE_BYTES_PER_SWEEP = {4: 7464}
 NODE1 = {"fp64_ops": 96.0, "flops": 191.0, "bytes": 1424}
-#  ncu, 262,144 nodes, node 1 fused: 18 x 1796.2 + 5 x 1702.4 + 425.1 B per step
-#  over 24 launches.
-NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {(4, True): 1719.5}
+#  ncu, 262,144 nodes, node 1 fused, 6 blocks per SM: 18 x 1825.1 + 5 x 1748.0 +
+#  431.3 B per step over 24 launches.
+NODE_DRAM_BYTES_PER_LAUNCH_MEASURED = {(4, True): 1751.0}
 CG_BYTES_PER_NODE_ITER = 96
 CG_BYTES_PER_NODE_SETUP = 64
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz.
