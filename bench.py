@@ -95,9 +95,15 @@ def class_work(solver_kind: str, K: int, it_mean: float, M: int = 4, fused: bool
 
 def DCT_KERNELS_PER_SOLVE(wl) -> int:
     """Kernel launches of one DCT-II solve of the second-order stencil: the
-    forward and inverse transform of every axis of x, y longer than one cell,
-    and the z solve."""
-    return 2 * ((wl.nx > 1) + (wl.ny > 1)) + 1
+    forward and inverse x transforms (nx > 1), then either the fused y-z kernel
+    (the library's rule: ny a power of two >= 16, nz >= 2, and the y-z slab,
+    its z factors and the twiddles within one block's 200 KB of shared memory
+    and 1024 threads) or the y transforms (ny > 1) and the z solve."""
+    ny, nz = wl.ny, wl.nz
+    pairs, g = (nz + 1) // 2, min(ny // 4, 256)
+    fused = (ny >= 16 and ny & (ny - 1) == 0 and nz >= 2 and (pairs * g + 31) // 32 * 32 <= 1024
+             and (ny + 2 * pairs * (ny + 1)) * 16 + 2 * nz * ny * 8 <= 200 * 1024)
+    return 2 * (wl.nx > 1) + (1 if fused else 2 * (ny > 1) + 1)
 
 
 def _peaks():
