@@ -349,6 +349,21 @@ int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* st
 int esdc_fma_probe(int fp32, int64_t n, double* ms, double* flops, void* stream);
 
 /*
+ * The build-time errors of the two tables the kernels evaluate in place of
+ * transcendental functions (host only: no device work, no handle).  For the
+ * ionic model `model` with its parameters (as for esdc_create) the gate table
+ * in V: err[0] = the largest error of the FP64 evaluation of b = -Lambda w_inf
+ * over |Lambda| (i.e. of w_inf), err[1] = the largest relative error of
+ * Lambda.  For M (1..8) and dt > 0 the set-up's coefficient table in z:
+ * err[2] = the largest error of dt S_ij and dt d_i phi_1 in units of dt.  All
+ * against long-double evaluations of the same functions, as checked when a
+ * handle builds them (a table above 4e-15 is refused and the kernels evaluate
+ * directly).  Not part of the method.  Errors: INVALID_ARG (unknown model,
+ * wrong parameter count, M or dt out of range, null err).
+ */
+int esdc_table_errors(int model, const double* params, int n_params, int M, double dt, double* err);
+
+/*
  * Allocation-free diffusion solve (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, e.g. code that
  * runs inside a memory-pool or allocator callback, in a process whose device

@@ -789,6 +789,21 @@ int esdc_ionic(esdc_handle* h, const double* y, double* fE, double* lam, double*
     return ESDC_OK;
 }
 
+int esdc_table_errors(int model, const double* params, int n_params, int M, double dt, double* err)
+{
+    if (!err || !params || M < 1 || M > ESDC_MMAX || !(dt > 0.0) || !std::isfinite(dt)) return ESDC_ERR_INVALID_ARG;
+    const int need = model == ESDC_MODEL_HH1952 ? 7 : model == ESDC_MODEL_SYN19 ? 88 : -1;
+    if (need < 0 || n_params != need) return ESDC_ERR_INVALID_ARG;
+    for (int k = 0; k < n_params; ++k)
+        if (!std::isfinite(params[k])) return ESDC_ERR_INVALID_ARG;
+    std::vector<double> rows;
+    if (esdc_vtab_build(model, params, rows, &err[0], &err[1]) == -1) return ESDC_ERR_INVALID_ARG;
+    ColloData C;
+    if (esdc_colloc_build(M, &C) != 0) return ESDC_ERR_INVALID_ARG;
+    if (esdc_ztab_build(M, dt, C, rows, &err[2]) == -1) return ESDC_ERR_INVALID_ARG;
+    return ESDC_OK;
+}
+
 int esdc_math_check(const double* x, int64_t n, double* ex, double* rc, void* stream)
 {
     if (!x || !ex || !rc || n < 0) return ESDC_ERR_INVALID_ARG;

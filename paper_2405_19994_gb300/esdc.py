@@ -63,6 +63,7 @@ def lib() -> C.CDLL:
             "esdc_set_conductivity_field": (C.c_int, [_VP, C.POINTER(_D)]),
             "esdc_set_stencil_order": (C.c_int, [_VP, C.c_int]),
             "esdc_get_solver": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+            "esdc_table_errors": (C.c_int, [C.c_int, C.POINTER(_D), C.c_int, C.c_int, _D, C.POINTER(_D)]),
             "esdc_init_state": (C.c_int, [_VP, _VP, _D, _VP]),
             "esdc_sweep": (C.c_int, [_VP, _VP, _D, _D, C.c_int, C.c_int, _VP]),
             "esdc_sweep_host": (C.c_int, [_VP, _VP, _I64, _D, _D, C.c_int, C.c_int, _VP]),
