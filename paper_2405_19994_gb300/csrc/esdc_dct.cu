@@ -20,18 +20,22 @@
 //    real part, line b in the imaginary part), after Makhoul's reordering
 //    (J. Makhoul, IEEE Trans. ASSP 28 (1980), "A fast cosine transform in one
 //    and two dimensions"): v[m] = x[2m], v[n-1-m] = x[2m+1] gives
-//    X[k] = Re(e^{-i pi k/(2n)} V[k]), V = DFT(v).  The FFT is a radix-2
-//    Stockham decimation-in-time (Cooley-Tukey) in shared memory: the
-//    butterfly c = a + w b, d = 2a - c costs six FMAs.  The inverse packs
-//    V[k] = e^{i pi k/(2n)} (Y[k] - i Y[n-k]) and runs the same FFT on the
-//    conjugate.  Axes whose length is not a power of two use a plain dense
-//    product with a cosine table instead.
+//    X[k] = Re(e^{-i pi k/(2n)} V[k]), V = DFT(v).  The FFT is a Stockham
+//    decimation-in-time (Cooley-Tukey) in shared memory with radix-4 stages
+//    (24 FP64 operations per four points) and one radix-2 stage when log2 n
+//    is odd (see fft_pow2).  The inverse packs V[k] = e^{i pi k/(2n)}
+//    (Y[k] - i Y[n-k]) and runs the same FFT on the conjugate.  Axes whose
+//    length is not a power of two use a plain dense product with a cosine
+//    table instead.
 //  * z (second-order stencil): after the x and y transforms the operator is,
 //    per mode (kx, ky), the tridiagonal a I - g L_z with a = 1 - g(mu_x + mu_y).
 //    It is solved directly (Thomas' elimination) with its factors tabulated
 //    once per value of g: r'_k = r_k A_k - r'_{k-1} C_k, x_k = r'_k - C_k x_{k+1},
 //    three FP64 operations per node.  A 2D or 1D mesh has nz = 1, where this
-//    reduces to the division by a.
+//    reduces to the division by a.  When the y-z slab of one x-mode fits a
+//    block (ny a power of two >= 16, nz >= 2), k_dct_yzy does the y forward
+//    transform, these z solves and the y inverse transform of that x-mode in
+//    shared memory: three kernels per solve (x forward, yzy, x inverse).
 //  * Scaling: the inverse of this pair packing computes U^T diag(1, 1/2, ...,
 //    1/2), so with the forward transform unnormalised, every transformed axis
 //    contributes the same factor 1/n to the spectral weight.
